@@ -1,0 +1,392 @@
+"""Benchmark of the consensus deblurring hot path (Algorithm 1 on the GPU).
+
+One step = one dv_consensus_solve of the 2048x2048 star-field workload
+(8x8 grid of 31x31 Moffat PSFs, 4x4 tiles overlapping by 64 px, 100 consensus
+iterations x 10 projected-gradient steps): start, all local solves, consensus
+and dual updates, assembly of x_hat.  Inputs are resident in HBM when the timed
+region starts; L2 is flushed (256 MB write) before every timed step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
+independent image (replicas: the method's only exchange is inside one image),
+timings are max-reduced and rank 0 prints.  --impl reference times the FP64
+oracle on the host cores on a bounded sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "stars2048"
+METRIC = "Mpixel/s to converged objective (plain FP32 form, 100 x 10 iterations)"
+UNIT = "Mpixel/s"
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                rows.append(parts)
+        os.unlink(self.f.name)
+        mine = [r for r in rows if self.bus_id and self.bus_id.endswith(r[1].lower()[-12:])]
+        rows = mine or rows
+        try:
+            sm = [float(r[2]) for r in rows]
+            smax = max(float(r[3]) for r in rows)
+        except ValueError:
+            return None
+        load = [s for s in sm if s > 0.5 * smax] or sm
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[6:10]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- inputs
+
+
+def make_inputs(torch, dv, w, psfs, rank):
+    from paper_1705_06603_gb300.synth import gaussian_noise, star_field
+    x_true = star_field(w.nx, w.scene_seed + 1000 * rank)
+    plan0 = dv.Plan(w.hy, w.wy, psfs, n_outer=0, n_inner=0)
+    y = plan0.apply_H(torch.from_numpy(x_true).cuda())
+    y += torch.from_numpy(gaussian_noise((w.hy, w.wy), w.noise_sigma,
+                                         w.noise_seed + 1000 * rank, np.float32)).cuda()
+    torch.cuda.synchronize()
+    plan0.close()
+    return y
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f).get(kernel)
+    if not t:
+        return None
+    src = os.path.join(ROOT, t["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] if os.path.exists(src) else ""
+    if sha != t.get("source_sha"):
+        return None
+    return t["bytes_per_launch"]
+
+
+# --------------------------------------------------------------------------- oracle arm
+
+
+def oracle_sample(w, psfs64, seed=0):
+    """Inputs of the bounded CPU sample: interior tile (1, 1) of the workload,
+    its observation made with the oracle's own operator."""
+    from oracle import dv_oracle as O
+    from paper_1705_06603_gb300.synth import gaussian_noise, star_field
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap)
+    tr, tc = 1, 1
+    rs, cs = lay.xslice(tr, tc)
+    x_true = star_field(w.nx, w.scene_seed + seed, dtype=np.float64)
+    wr = O.bilinear_weights(lay.nx[0], w.grid[0])[:, rs]
+    wc = O.bilinear_weights(lay.nx[1], w.grid[1])[:, cs]
+    yi = O.apply_H(x_true[rs, cs], psfs64, wr, wc)
+    yi = yi + gaussian_noise(yi.shape, w.noise_sigma, w.noise_seed)
+    w0 = O.start_image(yi, w.K)
+    tau = O.tile_step(lay, tr, tc, psfs64, None, w.lam, w.gamma)
+    alpha = w.gamma * lay.omega(tr, tc)
+    return lay, (w0, yi, wr, wc, alpha, tau)
+
+
+def oracle_step_seconds(O, w, psfs64, sample):
+    w0, yi, wr, wc, alpha, tau = sample
+    t = time.perf_counter()
+    O.local_solve(w0, w0, yi, None, psfs64, wr, wc, alpha, w.lam, w.delta, tau, 1)
+    return time.perf_counter() - t
+
+
+def oracle_rate(w, lay, t_step, t_cons):
+    """Mpixel/s of the oracle's full solve extrapolated from one tile step."""
+    T = len(lay.tiles)
+    t_solve = w.n_outer * (w.n_inner * T * t_step + t_cons)
+    return w.hy * w.wy / t_solve / 1e6, t_solve
+
+
+def oracle_consensus_seconds(O, lay):
+    g = np.random.default_rng(0)
+    xs = [g.uniform(0, 1, (r.stop - r.start, c.stop - c.start))
+          for r, c in (lay.xslice(*t) for t in lay.tiles)]
+    al = [0.4 * lay.omega(*t) for t in lay.tiles]
+    t = time.perf_counter()
+    z = O.consensus_average(lay, [2 * x - x for x in xs], al)
+    _ = [x + (z[lay.xslice(*tt)] - x) for x, tt in zip(xs, lay.tiles)]
+    return time.perf_counter() - t
+
+
+SAMPLE_DESC = ("one Local-Solver step (H, H^T, Huber prior, projected update) of the FP64 "
+               "oracle on interior tile (1,1) (590x590 x-pixels) plus one consensus step over "
+               "the 2078x2078 x grid, extrapolated to 100 outer x 10 inner steps on 16 tiles")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import dv_oracle as O
+    from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
+    w = WORKLOADS[WORKLOAD]
+    psfs64 = psf_grid_for(w)
+    lay, sample = oracle_sample(w, psfs64)
+    t_cons = oracle_consensus_seconds(O, lay)
+    for _ in range(args.warmup):
+        oracle_step_seconds(O, w, psfs64, sample)
+    ts = [oracle_step_seconds(O, w, psfs64, sample) for _ in range(args.steps)]
+    t_step = sum(ts) / len(ts)
+    value, t_solve = oracle_rate(w, lay, t_step, t_cons)
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "stars2048: 2048x2048 star field, 8x8 "
+                                        "Moffat 31x31 PSFs, 4x4 tiles / 64 px, 100 x 10 "
+                                        "iterations", "sample": "bounded (see cpu_baseline)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_06603_gb300 import build as dvbuild
+    dvbuild.build()
+    from paper_1705_06603_gb300 import dv
+    from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
+
+    w = WORKLOADS[WORKLOAD]
+    psfs = psf_grid_for(w).astype(np.float32)
+    y = make_inputs(torch, dv, w, psfs, rank)
+    stream = torch.cuda.current_stream()
+    plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_tiles=w.n_tiles, overlap=w.overlap,
+                   lam=w.lam, delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=w.n_outer,
+                   n_inner=w.n_inner)
+    x_out = torch.empty(plan.nx, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, device="cuda")   # 256 MB > 129 MB L2
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    for i in range(args.warmup):
+        dv.dv_consensus_solve(plan.handle, y, None, x_out, None, stream)
+    barrier()
+    dv.dv_plan_set_timing(plan.handle, 1)
+    launches0 = dv.dv_plan_get_info(plan.handle).kernel_launches
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+        bus = f"{bus:02x}:00.0" if isinstance(bus, int) else None
+    except Exception:
+        bus = None
+    clocks = ClockSampler(bus)
+    clocks.start()
+    total_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dv.dv_consensus_solve(plan.handle, y, None, x_out, None, stream)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    barrier()
+    clk = clocks.stop()
+    launches = dv.dv_plan_get_info(plan.handle).kernel_launches - launches0
+    ktime = {k: dv.dv_plan_kernel_time(plan.handle, k) for k in (0, 1, 2)}
+    dv.dv_plan_set_timing(plan.handle, 0)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = w.hy * w.wy * world / (ms_step * 1e-3) / 1e6
+
+    # objective reached by this (plain) form, for the record
+    st = dv.dv_stats()
+    dv.dv_consensus_solve(plan.handle, y, None, x_out, st, stream)
+    objective = st.objective
+
+    # end to end: host buffers through dv_consensus_solve_host (H2D + solve + D2H)
+    yh = torch.empty((w.hy, w.wy), dtype=torch.float32, pin_memory=True)
+    yh.copy_(y)
+    xh = torch.empty(plan.nx, dtype=torch.float32, pin_memory=True)
+    yn, xn = yh.numpy(), xh.numpy()
+    dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream)
+    t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([t_e2e], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": w.hy * w.wy * world / t_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1]}
+
+    # roofline of the dominant kernel (FP32 FMA issue bound)
+    info = dv.dv_plan_get_info(plan.handle)
+    rows, cols, _ = dv.dv_layout_query(plan.problem)
+    lay_tiles = [(r, c) for r in rows for c in cols]
+    y_px = sum((r1 - r0) * (c1 - c0) for (r0, r1), (c0, c1) in lay_tiles)
+    x_px = sum((r1 - r0 + w.K - 1) * (c1 - c0 + w.K - 1) for (r0, r1), (c0, c1) in lay_tiles)
+    names = {0: "direct_H_kernel<31> (H_i with residual)", 1: "direct_Ht_kernel<31> (H_i^T + "
+             "fused prox step)", 2: "consensus_kernel"}
+    dom = max((0, 1), key=lambda k: ktime[k][0])
+    ms_launch = ktime[dom][0] / max(ktime[dom][1], 1)
+    flops = 8.0 * w.K * w.K * (y_px if dom == 0 else x_px)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+    achieved = flops / (ms_launch * 1e-3) / 1e12
+    kern = ["direct_H_kernel", "direct_Ht_kernel"][dom]
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_for(kern),
+            "kernel": names[dom],
+            "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x "
+                           f"{sm_max:.0f} MHz (unit counts and max SM clock)",
+            "algorithmic": f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch "
+                           f"(4 active PSFs), {(y_px if dom == 0 else x_px)} pixels"}
+    kernels = {names[k]: {"launches": ktime[k][1], "ms_per_launch": ktime[k][0] / max(ktime[k][1], 1),
+                          "share": ktime[k][0] / max(total_ms, 1e-9)} for k in (0, 1, 2)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import dv_oracle as O
+        psfs64 = psfs.astype(np.float64)
+        lay, sample = oracle_sample(w, psfs64)
+        t_cons = oracle_consensus_seconds(O, lay)
+        t_step = min(oracle_step_seconds(O, w, psfs64, sample) for _ in range(2))
+        cval, _ = oracle_rate(w, lay, t_step, t_cons)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "stars2048: 2048x2048 star field (Poisson stars, power-law "
+                                   "fluxes, elliptical blobs), 8x8 Moffat 31x31 PSFs, 4x4 tiles "
+                                   "overlapping by 64 px, 100 outer x 10 inner iterations, "
+                                   "sigma 0.005",
+                       "form": "plain FP32, direct operator, CUDA graph per local solve",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}", "objective": objective},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "device_bytes": info.device_bytes,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * dv.h -- C ABI of libdv, a GB300 (sm_103a) implementation of distributed
+ * shift-variant deblurring by Douglas-Rachford consensus ("Distributed
+ * Deblurring of Large Images of Wide Field-Of-View").
+ *
+ * Model (Eq. (2), Eq. (3), Sec. II-B):
+ *   y = H x + noise,  H x = R sum_p h_p * (w_p . x)
+ * where the PSFs h_p sit on a G_r x G_c field grid, w_p are first-order
+ * interpolation weights (sum_p w_p = 1) and R keeps the "valid" part: the
+ * observed image y is hy x wy, the unknown x is (hy + K - 1) x (wy + K - 1).
+ * Convolution is centred at (K/2, K/2):
+ *   (H x)(i, j) = sum_p sum_{ka,kb} h_p(ka, kb) w_p(i + K-1 - ka, j + K-1 - kb)
+ *                                            x(i + K-1 - ka, j + K-1 - kb).
+ *
+ * Distributed formulation (Sec. III-A, Eq. (4)): the observed image is split
+ * into overlapping y-blocks; tile i estimates the x-tile P_i = its y-block
+ * dilated by K - 1 (so the local operator H_i is exact), with local cost
+ *   f_i(x_i) = 1/2 ||y_i - H_i x_i||^2_W + lambda phi(D x_i) + indicator(x_i >= 0)
+ * and phi the Huber function of the forward-difference gradient (Sec. IV-A).
+ * Algorithm 1 (Sec. III-B) alternates, n_outer times:
+ *   x_i  <- Local-Solver(u_i)         n_inner projected-gradient steps on
+ *                                     f_i + 1/2 ||. - u_i||^2_alpha_i
+ *   zbar <- sum_i alpha_i (2 x_i - u_i) / sum_i alpha_i     (Lemma 1)
+ *   u_i  <- u_i + rho (zbar - x_i)
+ * with alpha_i = gamma omega_i and omega_i the consensus weights of the tiles
+ * (sum_i omega_i = 1).  The result is x_hat = sum_i omega_i x_i / sum_i omega_i.
+ *
+ * Conventions for every entry point:
+ *   - Images are row-major float32, densely packed (row pitch = width).
+ *   - "_dev" pointers are CUDA device pointers, borrowed for the call only;
+ *     "_host" pointers are host memory (pageable or pinned), borrowed likewise.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All work is ordered on it; calls return when the work is enqueued unless
+ *     stated otherwise.
+ *   - Return codes only: nothing throws or aborts across the ABI.  After
+ *     DV_ERR_INVALID_ARG or DV_ERR_UNSUPPORTED the plan is unchanged and usable.
+ *     After DV_ERR_CUDA, DV_ERR_OOM (during a call) or DV_ERR_TIMEOUT only
+ *     dv_destroy is valid on that plan.  dv_last_error() describes the last
+ *     failure of the calling thread.
+ *   - A plan is not thread-safe: calls on one plan must be serialised.
+ */
+#ifndef DV_H
+#define DV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DV_ABI_VERSION 1
+
+typedef enum dv_status {
+  DV_OK = 0,
+  DV_ERR_INVALID_ARG = 1,  /* bad argument; message in dv_last_error()       */
+  DV_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  DV_ERR_OOM = 3,          /* device or pinned-host allocation failed         */
+  DV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up              */
+  DV_ERR_UNSUPPORTED = 5   /* valid request this build does not implement     */
+} dv_status;
+
+/* Arithmetic of the blur operator H and its adjoint (Sec. II-B).  Every other
+ * step runs in FP32 with FP64 reductions. */
+typedef enum dv_precision {
+  DV_PREC_FP32 = 0,        /* FP32 operands, FP32 accumulation                 */
+  DV_PREC_TF32 = 1,        /* TF32 operands on tensor cores, FP32 accumulation */
+  DV_PREC_BF16 = 2         /* BF16 operands on tensor cores, FP32 accumulation */
+} dv_precision;
+
+/* Interpolation weights w_p (Sec. II-B, Fig. 1). */
+typedef enum dv_weight_kind {
+  /* Tents on G equidistant grid points per axis, corners included: grid
+   * point a sits at c_a = a (n - 1)/(G - 1) (x-pixel coordinates) and
+   * w_a(t) = max(0, 1 - |t - c_a| / ((n - 1)/(G - 1))).  w_p = w_a(row) w_b(col). */
+  DV_WEIGHTS_BILINEAR = 0,
+  /* Caller-given separable profiles weights_r [G_r][hy+K-1] and
+   * weights_c [G_c][wy+K-1]; at most two neighbouring grid points may be
+   * nonzero at any coordinate (first-order interpolation). */
+  DV_WEIGHTS_SEPARABLE = 1
+} dv_weight_kind;
+
+/* How H and H^T are computed; all give the same operator. */
+typedef enum dv_operator_path {
+  DV_PATH_AUTO = 0,        /* plan-time autotuner picks the fastest          */
+  DV_PATH_DIRECT = 1,      /* spatial-domain correlation                     */
+  DV_PATH_FFT = 2          /* block FFT (overlap-save)                       */
+} dv_operator_path;
+
+typedef struct dv_problem {
+  /* observed image size (Eq. (2)); x is (hy + K - 1) x (wy + K - 1) */
+  int32_t hy, wy;
+  /* PSF grid and odd PSF side (Sec. II-B) */
+  int32_t grid_r, grid_c, K;
+  /* host [grid_r][grid_c][K][K]; nonnegative with unit sum is expected by the
+   * step-size bound but not enforced.  Deep-copied by dv_plan_create. */
+  const float* psfs;
+  /* dv_weight_kind; for DV_WEIGHTS_SEPARABLE the two host profiles below
+   * (deep-copied), otherwise they must be NULL */
+  int32_t weight_kind;
+  const float* weights_r;
+  const float* weights_c;
+  /* tile grid (Sec. III-A, III-C): n_tr x n_tc y-blocks.  If the four bound
+   * arrays are NULL the blocks are uniform: B = ceil((n + (count-1) overlap) / count)
+   * and block i starts at round(i (n - B)/(count - 1)).  Otherwise host arrays
+   * of n_tr (rows) / n_tc (cols) half-open y-block bounds, sorted, covering
+   * [0, hy) x [0, wy) with no gaps, and with each x-tile overlapping only its
+   * immediate neighbours along each axis. */
+  int32_t n_tr, n_tc;
+  const int32_t* tile_r0;
+  const int32_t* tile_r1;
+  const int32_t* tile_c0;
+  const int32_t* tile_c1;
+  int32_t overlap;
+  /* host [hy][wy] noise weights W (Eq. (3); 0 = unmeasured pixel), or NULL
+   * for W = 1.  Deep-copied. */
+  const float* noise_w;
+  /* prior weight, Huber threshold (Sec. IV-A), alpha_i = gamma omega_i and the
+   * relaxation rho in (0, 2) (Sec. III-B) */
+  double lambda, delta, gamma, rho;
+  /* Algorithm 1: n_outer D-R iterations; the local solve at outer iteration k
+   * runs n_inner + k * inner_increment projected-gradient steps (Sec. IV-B) */
+  int32_t n_outer, n_inner, inner_increment;
+  int32_t precision;       /* dv_precision */
+  int32_t path;            /* dv_operator_path */
+  int32_t use_warmstart;   /* 0: blurred-image start; 1: learned warm start */
+  /* if > 0, evaluate the objective every check_every outer iterations and
+   * stop as soon as it is <= target_objective (when target_objective > 0) */
+  int32_t check_every;
+  double target_objective;
+  int32_t use_graphs;      /* 1: replay each outer iteration as a CUDA graph */
+  int32_t reserved[7];
+} dv_problem;
+
+typedef struct dv_stats {
+  double objective;        /* F(x_hat) = sum_i f_i(C_i x_hat) without indicator */
+  double data_term;        /* sum_i 1/2 ||y_i - H_i C_i x_hat||^2_W */
+  double prior_term;       /* sum_i phi(D C_i x_hat) (times lambda in F) */
+  double primal_res;       /* sqrt(sum_i ||x_i - C_i zbar||^2), last iteration */
+  double dual_res;         /* ||zbar^k - zbar^{k-1}|| over x pixels, last iteration */
+  int32_t outer_done;      /* outer iterations performed */
+  int32_t inner_done;      /* projected-gradient steps per tile performed */
+  double ms_total;         /* wall time of the solve on the stream (events) */
+  int64_t kernel_launches; /* libdv kernels launched by the call */
+} dv_stats;
+
+typedef struct dv_plan dv_plan;
+
+/* Fills *p with defaults: the paper's rho = 1 and outer/inner schedule shape,
+ * lambda = 1e-3, delta = 1/60, gamma = 0.4, 30 x 10 iterations, one tile,
+ * one PSF, FP32, automatic path, graphs on.  Pointers are set to NULL. */
+void dv_problem_init(dv_problem* p);
+
+/* Host-only: validates *prob and writes the y-block bounds the plan would use
+ * (tile_r0/r1: n_tr entries, tile_c0/c1: n_tc entries) and the local step
+ * sizes tau (n_tr * n_tc entries, row-major over tiles).  Any output may be NULL. */
+dv_status dv_layout_query(const dv_problem* prob, int32_t* tile_r0, int32_t* tile_r1,
+                          int32_t* tile_c0, int32_t* tile_c1, double* tau);
+
+/* Builds a plan (Sec. III-A "distribute blocks, PSFs and weights"): validates
+ * the problem, lays out the tile-stacked iterates x_i, u_i and residuals in
+ * HBM, uploads PSFs, weight tables, consensus weights and noise weights, and
+ * (DV_PATH_AUTO) times the operator paths.  Allocates all device workspace;
+ * uses stream for uploads and synchronises it before returning.
+ * Errors: DV_ERR_INVALID_ARG, DV_ERR_UNSUPPORTED, DV_ERR_OOM, DV_ERR_CUDA. */
+dv_status dv_plan_create(const dv_problem* prob, void* stream, dv_plan** out);
+
+/* y_dev [hy][wy] = H x_dev [(hy+K-1)][(wy+K-1)]: the global shift-variant
+ * operator of Sec. II-B.  x_dev and y_dev must not alias. */
+dv_status dv_apply_H(dv_plan* plan, const float* x_dev, float* y_dev, void* stream);
+
+/* g_dev [(hy+K-1)][(wy+K-1)] = H^T r_dev [hy][wy], the adjoint of dv_apply_H
+ * (<H x, r> = <x, H^T r>).  r_dev and g_dev must not alias. */
+dv_status dv_apply_Ht(dv_plan* plan, const float* r_dev, float* g_dev, void* stream);
+
+/* Algorithm 1 on the observed image y_dev [hy][wy]: starts from
+ * x_i = u_i = C_i x0 with x0 = x0_dev [(hy+K-1)][(wy+K-1)] if given, else y
+ * edge-replicated by K/2 (or the learned warm start when enabled), runs the
+ * outer/inner schedule of the problem and writes x_hat to x_out_dev
+ * [(hy+K-1)][(wy+K-1)].  If stats is not NULL the call synchronises the stream
+ * and fills it (one extra operator pass for the objective).  The plan keeps
+ * the final x_i, u_i (see dv_state_export). */
+dv_status dv_consensus_solve(dv_plan* plan, const float* y_dev, const float* x0_dev,
+                             float* x_out_dev, dv_stats* stats, void* stream);
+
+/* dv_consensus_solve from host buffers: copies y_host (and x0_host if not
+ * NULL) to plan-owned device memory, solves, copies x_hat back to x_out_host,
+ * and synchronises the stream before returning. */
+dv_status dv_consensus_solve_host(dv_plan* plan, const float* y_host, const float* x0_host,
+                                  float* x_out_host, dv_stats* stats, void* stream);
+
+/* Continues Algorithm 1 for n_outer more outer iterations from the plan's
+ * current x_i, u_i (after a solve or dv_state_import), with y_dev as data,
+ * then writes x_hat.  Outer-iteration numbering (for inner_increment)
+ * continues from the state's count. */
+dv_status dv_consensus_continue(dv_plan* plan, const float* y_dev, int32_t n_outer,
+                                float* x_out_dev, dv_stats* stats, void* stream);
+
+/* Checkpoint / resume of the D-R state (x_i, u_i, k): copies the tile-stacked
+ * iterates to / from caller device buffers of dv_plan_info().stack_elems
+ * floats each (tile after tile, row pitch stack_pitch of each tile), plus the
+ * number of outer iterations done. */
+dv_status dv_state_export(dv_plan* plan, float* x_stack_dev, float* u_stack_dev,
+                          int32_t* outer_done, void* stream);
+dv_status dv_state_import(dv_plan* plan, const float* x_stack_dev, const float* u_stack_dev,
+                          int32_t outer_done, void* stream);
+
+typedef struct dv_plan_info {
+  int32_t nx_r, nx_c;      /* x size */
+  int32_t n_tiles;
+  int32_t path;            /* dv_operator_path chosen (never AUTO) */
+  int64_t stack_elems;     /* floats in one x-shaped tile stack */
+  int64_t device_bytes;    /* device memory owned by the plan */
+  double tau_min, tau_max; /* local step sizes */
+  int64_t kernel_launches; /* total libdv kernel launches on this plan */
+} dv_plan_info;
+
+dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);
+
+/* Per-kernel CUDA-event timing of the solve's launches (off by default).
+ * kind: 0 = operator H with residual, 1 = operator H^T with fused prox step,
+ * 2 = consensus + dual update.  Reports the summed duration (ms) and launch
+ * count since the last reset; dv_consensus_solve must have returned (stats or
+ * a synchronised stream) before reading. */
+dv_status dv_plan_set_timing(dv_plan* plan, int32_t enable);
+dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int64_t* launches);
+
+/* Releases everything the plan owns.  NULL is accepted. */
+dv_status dv_destroy(dv_plan* plan);
+
+/* Message of the calling thread's last failure ("" if none).  Valid until the
+ * thread's next libdv call. */
+const char* dv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DV_H */

@@ -1,0 +1,240 @@
+// Internal declarations of libdv: device-side descriptors, the plan object and
+// the kernel launchers shared by the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dv.h"
+
+namespace dv {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message behind dv_last_error)
+// ---------------------------------------------------------------------------
+dv_status fail(dv_status code, const char* fmt, ...);
+void clear_error();
+dv_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define DV_TRY_CUDA(call)                                                     \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::dv::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define DV_TRY(call)                         \
+  do {                                       \
+    dv_status s_ = (call);                   \
+    if (s_ != DV_OK) return s_;              \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device descriptors
+// ---------------------------------------------------------------------------
+
+// One tile: its y-block (global y coordinates) equals the origin of its x-tile
+// in global x coordinates; the x-tile is the y-block grown by K - 1.
+struct TileDesc {
+  int32_t xr0, xc0;      // x-tile origin (global x) == y-block origin (global y)
+  int32_t nyr, nyc;      // y-block extent
+  int32_t nxr, nxc;      // x-tile extent (nyr + K - 1, nyc + K - 1)
+  int32_t xpitch, ypitch;  // row pitch (floats) in x-shaped / y-shaped stacks
+  int64_t xoff, yoff;    // element offset of (0,0) in x-shaped / y-shaped stacks
+  int32_t omr_off, omc_off;  // offsets of this tile's consensus profiles
+  int32_t tr, tc;
+  float tau;             // local projected-gradient step
+  int32_t pad[3];
+};
+static_assert(sizeof(TileDesc) == 80, "TileDesc layout");
+
+// One CTA's output block of the direct operator kernels.
+struct WorkItem {
+  int32_t tile;          // tile index
+  int32_t r0, c0;        // output block origin (tile-local: y coords for H, x for H^T)
+  int32_t pad;
+  int32_t a_lo, a_hi;    // active PSF grid rows  (inclusive)
+  int32_t b_lo, b_hi;    // active PSF grid cols  (inclusive)
+};
+static_assert(sizeof(WorkItem) == 32, "WorkItem layout");
+
+// Interpolation weights at one global x coordinate: grid index a0 has weight
+// w0 and a0 + 1 has weight w1; every other grid index has weight 0.
+struct WTab {
+  int32_t a0;
+  float w0, w1;
+  int32_t pad;
+};
+
+__host__ __device__ inline float wsel(const WTab& t, int a) {
+  return a == t.a0 ? t.w0 : (a == t.a0 + 1 ? t.w1 : 0.0f);
+}
+
+// Operator kernel modes
+enum OpMode : int32_t {
+  OP_PLAIN = 0,   // write H x (or H^T r) to a global image
+  OP_RESID = 1,   // H: write r = W (H x - y) into the residual stack
+  OP_OBJ = 2,     // H: FP64 partial of sum W (H x - y)^2, no write
+  OP_STEP = 3     // H^T: fused projected-gradient step into w_next
+};
+
+struct OpArgs {
+  const TileDesc* tiles;
+  const WorkItem* work;
+  int32_t n_work;
+  int32_t mode;
+  const WTab* wrow;
+  const WTab* wcol;
+  const float* psf;       // [Gr*Gc][K][KP]: flipped (H) or as given (H^T)
+  int32_t Gc, K, KP;
+  int32_t pad0;
+  const float* in;        // x-shaped (H) or y-shaped (H^T) input base
+  float* out;             // output base
+  // H, OP_RESID / OP_OBJ: global observed image and noise weights (pitch wy)
+  const float* y;
+  const float* W;         // nullable
+  int32_t wy;
+  int32_t pad1;
+  double* partials;       // OP_OBJ: one double per work item
+  // H^T, OP_STEP: current iterate, dual variable, consensus profiles, prior
+  const float* w;
+  const float* u;
+  const float* omr;
+  const float* omc;
+  float lambda, delta, gamma;
+  int32_t pad2;
+};
+
+// Streaming kernels' shared view of the tile grid
+struct GridArgs {
+  const TileDesc* tiles;
+  const int2* rowcov;     // per global x row: covering tile rows (second = -1 if none)
+  const int2* colcov;
+  const float* omr;
+  const float* omc;
+  int32_t n_tc;
+  int32_t nxr, nxc;
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (stream-ordered; return cudaGetLastError of the launch)
+// ---------------------------------------------------------------------------
+cudaError_t launch_direct_H(const OpArgs& a, cudaStream_t s);
+cudaError_t launch_direct_Ht(const OpArgs& a, cudaStream_t s);
+int direct_tile_m();   // output block rows of the direct kernels
+int direct_tile_n();   // output block cols
+
+// start / gather: tile stacks from a global x image (x0 = NULL: y edge-padded);
+// zg (nullable) also receives the global start image
+cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_nxc,
+                           const float* x0, const float* y, int hy, int wy, int rad,
+                           float* w, float* u, cudaStream_t s, float* zg);
+// consensus + dual update (Lemma 1, Sec. III-B); zbuf (nullable) holds the
+// previous zbar and receives the new one; partials (nullable): 2 x n_blocks
+cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma,
+                             float rho, float* zbuf, double* partials, cudaStream_t s,
+                             int* n_blocks_out);
+int consensus_blocks(int nxr, int nxc);
+// x_hat = sum omega_i x_i / sum omega_i
+cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s);
+// FP64 block partials of the Huber prior over the tile stacks
+int huber_blocks(int n_tiles, int max_nxr, int max_nxc);
+cudaError_t launch_huber_value(const TileDesc* tiles, int n_tiles, int max_nxr, int max_nxc,
+                               const float* x, double delta, double* partials, cudaStream_t s);
+// out[k] = sum_{i < counts[k]} parts[k][i] in a fixed order (one block), nk <= 8
+cudaError_t launch_reduce(const double* const* parts, const int* counts, int nk, double* out,
+                          cudaStream_t s);
+size_t direct_smem_bytes(int K);
+cudaError_t direct_prepare(int K);   // shared-memory limits of the direct kernels
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+// One captured local solve (n_inner projected-gradient steps on all tiles),
+// replayed once per outer iteration.  With timing on, every kernel node is
+// bracketed by event-record nodes whose events are swapped before each launch.
+struct GraphEntry {
+  int n_inner = 0;
+  int parity = 0;          // w buffer holding x_i when the local solve starts
+  bool timed = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaGraphNode_t> ev_start, ev_end;  // per kernel node (timed only)
+  std::vector<int> kinds;
+};
+
+struct Pending {
+  int kind;
+  int ev0, ev1;            // indices into the event pool
+};
+
+struct KernelTimer {
+  std::vector<cudaEvent_t> pool;
+  std::vector<cudaEvent_t> placeholders;
+  std::vector<Pending> pending;
+  size_t next = 0;
+  double total_ms[3] = {0, 0, 0};
+  int64_t count[3] = {0, 0, 0};
+};
+
+}  // namespace dv
+
+struct dv_plan {
+  dv_problem prob;        // copy with host pointers cleared
+  int hy, wy, K, rad, Gr, Gc, nxr, nxc, n_tr, n_tc, T;
+  int path;
+  std::vector<int> yr0, yr1, yc0, yc1;
+  std::vector<double> tau;
+  std::vector<dv::TileDesc> h_tiles;
+  int max_nxr, max_nxc;
+  int64_t xstack, ystack;
+  // device data
+  float* d_psf_flip = nullptr;
+  float* d_psf = nullptr;
+  dv::WTab* d_wrow = nullptr;
+  dv::WTab* d_wcol = nullptr;
+  float* d_omr = nullptr;
+  float* d_omc = nullptr;
+  dv::TileDesc* d_tiles = nullptr;
+  dv::TileDesc* d_gtile = nullptr;
+  dv::WorkItem* d_workH = nullptr;
+  dv::WorkItem* d_workHt = nullptr;
+  dv::WorkItem* d_workHg = nullptr;
+  dv::WorkItem* d_workHtg = nullptr;
+  int nH = 0, nHt = 0, nHg = 0, nHtg = 0;
+  int2* d_rowcov = nullptr;
+  int2* d_colcov = nullptr;
+  float* d_w[2] = {nullptr, nullptr};
+  float* d_u = nullptr;
+  float* d_r = nullptr;
+  float* d_y = nullptr;
+  float* d_W = nullptr;
+  float* d_z = nullptr;        // previous zbar (global x image)
+  float* d_xg = nullptr;       // x_hat (global x image)
+  double* d_part = nullptr;
+  int64_t n_part = 0;
+  double* d_scal = nullptr;
+  double* h_scal = nullptr;    // pinned
+  float* d_hx = nullptr;       // host-solve staging (x-sized), lazily allocated
+  float* d_hy = nullptr;       // host-solve staging (y-sized)
+  float* d_hx0 = nullptr;
+  int64_t device_bytes = 0;
+  int cur = 0;                 // w buffer holding x_i
+  int outer_done = 0;
+  int64_t launches = 0;
+  bool timing = false;
+  dv::KernelTimer timer;
+  std::vector<dv::GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace dv {
+dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global);
+dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
+                      const float* w, const float* u);
+dv::GridArgs grid_args(const dv_plan* p);
+}  // namespace dv

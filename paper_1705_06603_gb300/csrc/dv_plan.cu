@@ -1,0 +1,636 @@
+// Plan construction for libdv: validation of the problem, tile layout
+// (Sec. III-A, III-C), first-order interpolation weight tables (Sec. II-B),
+// consensus weights omega_i and metric alpha_i = gamma omega_i (Sec. III-B),
+// local step sizes, operator work tables and the HBM layout of the tile
+// stacks.  Host code; every device buffer the plan uses is allocated here.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+
+static thread_local std::string g_err;
+
+dv_status fail(dv_status code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+dv_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  const dv_status code = (e == cudaErrorMemoryAllocation) ? DV_ERR_OOM : DV_ERR_CUDA;
+  return fail(code, "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+
+constexpr int kMaxK = 127;
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Equal blocks of B = ceil((n + (count-1) overlap) / count) pixels, block i
+// starting at round(i (n - B) / (count - 1)).
+void uniform_blocks(int n, int count, int overlap, std::vector<int>& s, std::vector<int>& e) {
+  s.assign(count, 0);
+  e.assign(count, n);
+  if (count == 1) return;
+  int64_t B = ((int64_t)n + (int64_t)(count - 1) * overlap + count - 1) / count;
+  if (B > n) B = n;
+  for (int i = 0; i < count; ++i) {
+    const int64_t st = ((int64_t)i * (n - B) + (count - 1) / 2) / (count - 1);
+    s[i] = (int)st;
+    e[i] = (int)(st + B);
+  }
+}
+
+dv_status check_blocks(const char* axis, int n, int K, const std::vector<int>& s,
+                       const std::vector<int>& e) {
+  const int cnt = (int)s.size();
+  if (s[0] != 0 || e[cnt - 1] != n)
+    return fail(DV_ERR_INVALID_ARG, "%s y-blocks must start at 0 and end at %d", axis, n);
+  for (int i = 0; i < cnt; ++i) {
+    if (s[i] < 0 || e[i] > n || s[i] >= e[i])
+      return fail(DV_ERR_INVALID_ARG, "%s y-block %d = [%d, %d) is empty or out of range", axis,
+                  i, s[i], e[i]);
+    if (i + 1 < cnt) {
+      if (s[i + 1] <= s[i] || e[i + 1] <= e[i])
+        return fail(DV_ERR_INVALID_ARG, "%s y-blocks must be sorted", axis);
+      if (s[i + 1] > e[i])
+        return fail(DV_ERR_INVALID_ARG, "%s y-blocks %d and %d leave a gap", axis, i, i + 1);
+    }
+    // x-tile i = [s_i, e_i + K - 1); tile i + 2 must not reach into tile i
+    if (i + 2 < cnt && s[i + 2] < e[i] + K - 1)
+      return fail(DV_ERR_INVALID_ARG,
+                  "%s x-tiles %d and %d overlap: each x-tile may only overlap its neighbours",
+                  axis, i, i + 2);
+  }
+  return DV_OK;
+}
+
+// Per-tile 1-D consensus profiles on x-ranges [xs_i, xe_i): 1 where no other
+// tile reaches, ramps (j + 1/2)/B across each band of width B shared with a
+// neighbour, normalised so that the profiles sum to 1 at every coordinate.
+std::vector<std::vector<double>> consensus_profiles(const std::vector<int>& xs,
+                                                    const std::vector<int>& xe) {
+  const int cnt = (int)xs.size();
+  std::vector<std::vector<double>> t(cnt);
+  for (int i = 0; i < cnt; ++i) t[i].assign(xe[i] - xs[i], 1.0);
+  for (int i = 0; i + 1 < cnt; ++i) {
+    const int B = xe[i] - xs[i + 1];
+    for (int j = 0; j < B; ++j) {
+      const double up = (j + 0.5) / B;
+      t[i + 1][j] *= up;
+      t[i][xs[i + 1] - xs[i] + j] *= 1.0 - up;
+    }
+  }
+  std::vector<double> tot(xe[cnt - 1], 0.0);
+  for (int i = 0; i < cnt; ++i)
+    for (int j = 0; j < xe[i] - xs[i]; ++j) tot[xs[i] + j] += t[i][j];
+  for (int i = 0; i < cnt; ++i)
+    for (int j = 0; j < xe[i] - xs[i]; ++j) t[i][j] /= tot[xs[i] + j];
+  return t;
+}
+
+// Interpolation weight table of one axis (n coordinates, G grid points).
+dv_status weight_table(const char* axis, int n, int G, const float* prof, std::vector<WTab>& tab) {
+  tab.assign(n, WTab{0, 0.f, 0.f, 0});
+  if (!prof) {
+    if (G == 1) {
+      for (int t = 0; t < n; ++t) tab[t] = WTab{0, 1.f, 0.f, 0};
+      return DV_OK;
+    }
+    const double D = (n - 1.0) / (G - 1.0);
+    for (int t = 0; t < n; ++t) {
+      int a0 = (int)std::floor(t / D);
+      a0 = std::min(std::max(a0, 0), G - 2);
+      const double w0 = std::max(0.0, 1.0 - std::fabs(t - a0 * D) / D);
+      const double w1 = std::max(0.0, 1.0 - std::fabs(t - (a0 + 1) * D) / D);
+      tab[t] = WTab{a0, (float)w0, (float)w1, 0};
+    }
+    return DV_OK;
+  }
+  for (int t = 0; t < n; ++t) {
+    int first = -1, last = -1, cnt = 0;
+    for (int a = 0; a < G; ++a) {
+      const float v = prof[(size_t)a * n + t];
+      if (!(v >= 0.f) || !std::isfinite(v))
+        return fail(DV_ERR_INVALID_ARG, "%s weights must be finite and >= 0 (grid %d, t=%d)",
+                    axis, a, t);
+      if (v != 0.f) {
+        if (first < 0) first = a;
+        last = a;
+        ++cnt;
+      }
+    }
+    if (cnt > 2 || (cnt == 2 && last != first + 1))
+      return fail(DV_ERR_INVALID_ARG,
+                  "%s weights at coordinate %d: at most two neighbouring grid points may be "
+                  "nonzero (first-order interpolation)", axis, t);
+    if (cnt == 0) continue;
+    int a0 = first;
+    if (G == 1) a0 = 0;
+    else if (a0 > G - 2) a0 = G - 2;
+    tab[t] = WTab{a0, prof[(size_t)a0 * n + t], G > 1 ? prof[(size_t)(a0 + 1) * n + t] : 0.f, 0};
+  }
+  return DV_OK;
+}
+
+// Grid indices with a nonzero weight somewhere in [lo, hi).
+void active_range(const std::vector<WTab>& tab, int lo, int hi, int& amin, int& amax) {
+  amin = INT_MAX;
+  amax = -1;
+  for (int t = lo; t < hi; ++t) {
+    if (tab[t].w0 != 0.f) {
+      amin = std::min(amin, tab[t].a0);
+      amax = std::max(amax, tab[t].a0);
+    }
+    if (tab[t].w1 != 0.f) {
+      amin = std::min(amin, tab[t].a0 + 1);
+      amax = std::max(amax, tab[t].a0 + 1);
+    }
+  }
+  if (amax < 0) {
+    amin = 0;
+    amax = -1;
+  }
+}
+
+struct Layout {
+  std::vector<int> yr0, yr1, yc0, yc1;
+  std::vector<std::vector<double>> omr, omc;
+  std::vector<WTab> wrow, wcol;
+  std::vector<double> tau;
+};
+
+dv_status validate_and_layout(const dv_problem* p, Layout& L) {
+  if (!p) return fail(DV_ERR_INVALID_ARG, "problem is NULL");
+  if (p->hy < 1 || p->wy < 1) return fail(DV_ERR_INVALID_ARG, "image size must be >= 1");
+  if (p->K < 1 || p->K % 2 == 0 || p->K > kMaxK)
+    return fail(DV_ERR_INVALID_ARG, "K must be odd and in [1, %d]", kMaxK);
+  if (p->grid_r < 1 || p->grid_c < 1) return fail(DV_ERR_INVALID_ARG, "PSF grid must be >= 1x1");
+  if (!p->psfs) return fail(DV_ERR_INVALID_ARG, "psfs is NULL");
+  if (p->n_tr < 1 || p->n_tc < 1) return fail(DV_ERR_INVALID_ARG, "tile grid must be >= 1x1");
+  if (!(p->lambda >= 0.0) || !(p->delta > 0.0) || !(p->gamma > 0.0))
+    return fail(DV_ERR_INVALID_ARG, "need lambda >= 0, delta > 0, gamma > 0");
+  if (!(p->rho > 0.0 && p->rho < 2.0)) return fail(DV_ERR_INVALID_ARG, "rho must be in (0, 2)");
+  if (p->n_outer < 0 || p->n_inner < 0 || p->inner_increment < 0)
+    return fail(DV_ERR_INVALID_ARG, "iteration counts must be >= 0");
+  if (p->weight_kind != DV_WEIGHTS_BILINEAR && p->weight_kind != DV_WEIGHTS_SEPARABLE)
+    return fail(DV_ERR_INVALID_ARG, "unknown weight_kind %d", p->weight_kind);
+  if (p->weight_kind == DV_WEIGHTS_SEPARABLE && (!p->weights_r || !p->weights_c))
+    return fail(DV_ERR_INVALID_ARG, "separable weights need weights_r and weights_c");
+  if (p->weight_kind == DV_WEIGHTS_BILINEAR && (p->weights_r || p->weights_c))
+    return fail(DV_ERR_INVALID_ARG, "bilinear weights take no weight arrays");
+  if (p->precision != DV_PREC_FP32 && p->precision != DV_PREC_TF32 &&
+      p->precision != DV_PREC_BF16)
+    return fail(DV_ERR_INVALID_ARG, "unknown precision %d", p->precision);
+  if (p->path < DV_PATH_AUTO || p->path > DV_PATH_FFT)
+    return fail(DV_ERR_INVALID_ARG, "unknown operator path %d", p->path);
+  if (p->overlap < 0) return fail(DV_ERR_INVALID_ARG, "overlap must be >= 0");
+  if (p->check_every < 0) return fail(DV_ERR_INVALID_ARG, "check_every must be >= 0");
+
+  const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
+  if ((int64_t)nxr * nxc > (int64_t)1 << 40) return fail(DV_ERR_INVALID_ARG, "image too large");
+  const bool given = p->tile_r0 || p->tile_r1 || p->tile_c0 || p->tile_c1;
+  if (given) {
+    if (!(p->tile_r0 && p->tile_r1 && p->tile_c0 && p->tile_c1))
+      return fail(DV_ERR_INVALID_ARG, "give all four tile bound arrays or none");
+    L.yr0.assign(p->tile_r0, p->tile_r0 + p->n_tr);
+    L.yr1.assign(p->tile_r1, p->tile_r1 + p->n_tr);
+    L.yc0.assign(p->tile_c0, p->tile_c0 + p->n_tc);
+    L.yc1.assign(p->tile_c1, p->tile_c1 + p->n_tc);
+  } else {
+    if (p->n_tr > p->hy || p->n_tc > p->wy)
+      return fail(DV_ERR_INVALID_ARG, "more tiles than pixels");
+    uniform_blocks(p->hy, p->n_tr, p->overlap, L.yr0, L.yr1);
+    uniform_blocks(p->wy, p->n_tc, p->overlap, L.yc0, L.yc1);
+  }
+  DV_TRY(check_blocks("row", p->hy, K, L.yr0, L.yr1));
+  DV_TRY(check_blocks("column", p->wy, K, L.yc0, L.yc1));
+
+  std::vector<int> xe(p->n_tr), xce(p->n_tc);
+  for (int i = 0; i < p->n_tr; ++i) xe[i] = L.yr1[i] + K - 1;
+  for (int i = 0; i < p->n_tc; ++i) xce[i] = L.yc1[i] + K - 1;
+  L.omr = consensus_profiles(L.yr0, xe);
+  L.omc = consensus_profiles(L.yc0, xce);
+
+  DV_TRY(weight_table("row", nxr, p->grid_r,
+                      p->weight_kind == DV_WEIGHTS_SEPARABLE ? p->weights_r : nullptr, L.wrow));
+  DV_TRY(weight_table("column", nxc, p->grid_c,
+                      p->weight_kind == DV_WEIGHTS_SEPARABLE ? p->weights_c : nullptr, L.wcol));
+
+  // Lipschitz bound of the data gradient: ||H||^2 <= (max_p sum|h_p|)(sum_k max_p |h_p(k)|)
+  const int G = p->grid_r * p->grid_c, KK = K * K;
+  double colmax = 0.0, rowsum = 0.0;
+  std::vector<double> kmax(KK, 0.0);
+  for (int g = 0; g < G; ++g) {
+    double s = 0.0;
+    for (int k = 0; k < KK; ++k) {
+      const double v = std::fabs((double)p->psfs[(size_t)g * KK + k]);
+      if (!std::isfinite(v)) return fail(DV_ERR_INVALID_ARG, "PSF %d has a non-finite tap", g);
+      s += v;
+      kmax[k] = std::max(kmax[k], v);
+    }
+    colmax = std::max(colmax, s);
+  }
+  for (int k = 0; k < KK; ++k) rowsum += kmax[k];
+  const double LH = colmax * rowsum;
+  L.tau.assign((size_t)p->n_tr * p->n_tc, 0.0);
+  for (int tr = 0; tr < p->n_tr; ++tr) {
+    for (int tc = 0; tc < p->n_tc; ++tc) {
+      double wmax = 1.0;
+      if (p->noise_w) {
+        wmax = 0.0;
+        for (int i = L.yr0[tr]; i < L.yr1[tr]; ++i)
+          for (int j = L.yc0[tc]; j < L.yc1[tc]; ++j) {
+            const double v = p->noise_w[(size_t)i * p->wy + j];
+            if (!(v >= 0.0) || !std::isfinite(v))
+              return fail(DV_ERR_INVALID_ARG, "noise weights must be finite and >= 0");
+            wmax = std::max(wmax, v);
+          }
+      }
+      const double omax = *std::max_element(L.omr[tr].begin(), L.omr[tr].end()) *
+                          *std::max_element(L.omc[tc].begin(), L.omc[tc].end());
+      L.tau[(size_t)tr * p->n_tc + tc] = 1.0 / (wmax * LH + 8.0 * p->lambda + p->gamma * omax);
+    }
+  }
+  return DV_OK;
+}
+
+template <class T>
+dv_status upload(dv_plan* P, T** dst, const T* src, size_t n, cudaStream_t s) {
+  if (n == 0) n = 1;
+  DV_TRY_CUDA(cudaMalloc((void**)dst, n * sizeof(T)));
+  P->device_bytes += (int64_t)(n * sizeof(T));
+  if (src) DV_TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+  return DV_OK;
+}
+
+template <class T>
+dv_status alloc(dv_plan* P, T** dst, size_t n) {
+  if (n == 0) n = 1;
+  DV_TRY_CUDA(cudaMalloc((void**)dst, n * sizeof(T)));
+  P->device_bytes += (int64_t)(n * sizeof(T));
+  return DV_OK;
+}
+
+// Work items of one operator over the given tiles: output blocks of
+// TM x TN, with the PSF grid range active on the block's input (H) or
+// output (H^T) region.
+void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const Layout& L,
+               std::vector<WorkItem>& out) {
+  const int TM = direct_tile_m(), TN = direct_tile_n();
+  out.clear();
+  for (int t = 0; t < (int)tiles.size(); ++t) {
+    const TileDesc& td = tiles[t];
+    const int nr = adjoint ? td.nxr : td.nyr, nc = adjoint ? td.nxc : td.nyc;
+    for (int r0 = 0; r0 < nr; r0 += TM) {
+      for (int c0 = 0; c0 < nc; c0 += TN) {
+        WorkItem w{};
+        w.tile = t;
+        w.r0 = r0;
+        w.c0 = c0;
+        // global x coordinate range whose weights matter
+        int rlo = td.xr0 + r0, clo = td.xc0 + c0;
+        int rhi = td.xr0 + std::min(r0 + TM, nr) + (adjoint ? 0 : K - 1);
+        int chi = td.xc0 + std::min(c0 + TN, nc) + (adjoint ? 0 : K - 1);
+        active_range(L.wrow, rlo, rhi, w.a_lo, w.a_hi);
+        active_range(L.wcol, clo, chi, w.b_lo, w.b_hi);
+        out.push_back(w);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global) {
+  OpArgs a{};
+  a.tiles = global ? p->d_gtile : p->d_tiles;
+  a.work = global ? p->d_workHg : p->d_workH;
+  a.n_work = global ? p->nHg : p->nH;
+  a.mode = mode;
+  a.wrow = p->d_wrow;
+  a.wcol = p->d_wcol;
+  a.psf = p->d_psf_flip;
+  a.Gc = p->Gc;
+  a.K = p->K;
+  a.KP = (p->K + 3) & ~3;
+  a.in = in;
+  a.out = out;
+  a.y = p->d_y;
+  a.W = p->d_W;
+  a.wy = p->wy;
+  a.partials = p->d_part;
+  a.lambda = (float)p->prob.lambda;
+  a.delta = (float)p->prob.delta;
+  a.gamma = (float)p->prob.gamma;
+  return a;
+}
+
+dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
+                      const float* w, const float* u) {
+  OpArgs a = op_args_H(p, mode, in, out, global);
+  a.tiles = global ? p->d_gtile : p->d_tiles;
+  a.work = global ? p->d_workHtg : p->d_workHt;
+  a.n_work = global ? p->nHtg : p->nHt;
+  a.psf = p->d_psf;
+  a.w = w;
+  a.u = u;
+  a.omr = p->d_omr;
+  a.omc = p->d_omc;
+  return a;
+}
+
+dv::GridArgs grid_args(const dv_plan* p) {
+  GridArgs g{};
+  g.tiles = p->d_tiles;
+  g.rowcov = p->d_rowcov;
+  g.colcov = p->d_colcov;
+  g.omr = p->d_omr;
+  g.omc = p->d_omc;
+  g.n_tc = p->n_tc;
+  g.nxr = p->nxr;
+  g.nxc = p->nxc;
+  return g;
+}
+
+dv_status release(dv_plan* P);
+
+}  // namespace dv
+
+using namespace dv;
+
+extern "C" const char* dv_last_error(void) { return g_err.c_str(); }
+
+extern "C" void dv_problem_init(dv_problem* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->hy = p->wy = 1;
+  p->grid_r = p->grid_c = 1;
+  p->K = 1;
+  p->weight_kind = DV_WEIGHTS_BILINEAR;
+  p->n_tr = p->n_tc = 1;
+  p->overlap = 16;
+  p->lambda = 1e-3;
+  p->delta = 1.0 / 60.0;
+  p->gamma = 0.4;
+  p->rho = 1.0;
+  p->n_outer = 30;
+  p->n_inner = 10;
+  p->precision = DV_PREC_FP32;
+  p->path = DV_PATH_AUTO;
+  p->use_graphs = 1;
+}
+
+extern "C" dv_status dv_layout_query(const dv_problem* prob, int32_t* tile_r0, int32_t* tile_r1,
+                                     int32_t* tile_c0, int32_t* tile_c1, double* tau) {
+  clear_error();
+  Layout L;
+  DV_TRY(validate_and_layout(prob, L));
+  for (int i = 0; i < prob->n_tr; ++i) {
+    if (tile_r0) tile_r0[i] = L.yr0[i];
+    if (tile_r1) tile_r1[i] = L.yr1[i];
+  }
+  for (int i = 0; i < prob->n_tc; ++i) {
+    if (tile_c0) tile_c0[i] = L.yc0[i];
+    if (tile_c1) tile_c1[i] = L.yc1[i];
+  }
+  if (tau) std::copy(L.tau.begin(), L.tau.end(), tau);
+  return DV_OK;
+}
+
+namespace dv {
+static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) {
+  Layout L;
+  DV_TRY(validate_and_layout(prob, L));
+  if (prob->precision != DV_PREC_FP32)
+    return fail(DV_ERR_UNSUPPORTED, "precision %d is not available in this build",
+                prob->precision);
+  if (prob->use_warmstart)
+    return fail(DV_ERR_UNSUPPORTED, "the learned warm start is not available in this build");
+  if (prob->path == DV_PATH_FFT)
+    return fail(DV_ERR_UNSUPPORTED, "the FFT operator path is not available in this build");
+
+  P->prob = *prob;
+  P->prob.psfs = nullptr;
+  P->prob.weights_r = P->prob.weights_c = nullptr;
+  P->prob.tile_r0 = P->prob.tile_r1 = P->prob.tile_c0 = P->prob.tile_c1 = nullptr;
+  P->prob.noise_w = nullptr;
+  P->hy = prob->hy;
+  P->wy = prob->wy;
+  P->K = prob->K;
+  P->rad = prob->K / 2;
+  P->Gr = prob->grid_r;
+  P->Gc = prob->grid_c;
+  P->nxr = prob->hy + prob->K - 1;
+  P->nxc = prob->wy + prob->K - 1;
+  P->n_tr = prob->n_tr;
+  P->n_tc = prob->n_tc;
+  P->T = P->n_tr * P->n_tc;
+  P->path = DV_PATH_DIRECT;
+  P->yr0 = L.yr0;
+  P->yr1 = L.yr1;
+  P->yc0 = L.yc0;
+  P->yc1 = L.yc1;
+  P->tau = L.tau;
+  const int K = P->K, KP = (K + 3) & ~3;
+
+  // PSFs as given and flipped, rows padded to KP
+  const int G = P->Gr * P->Gc;
+  std::vector<float> psf((size_t)G * K * KP, 0.f), flip((size_t)G * K * KP, 0.f);
+  for (int g = 0; g < G; ++g)
+    for (int a = 0; a < K; ++a)
+      for (int b = 0; b < K; ++b) {
+        const float v = prob->psfs[((size_t)g * K + a) * K + b];
+        psf[((size_t)g * K + a) * KP + b] = v;
+        flip[((size_t)g * K + (K - 1 - a)) * KP + (K - 1 - b)] = v;
+      }
+  DV_TRY(upload(P, &P->d_psf, psf.data(), psf.size(), s));
+  DV_TRY(upload(P, &P->d_psf_flip, flip.data(), flip.size(), s));
+  DV_TRY(upload(P, &P->d_wrow, L.wrow.data(), L.wrow.size(), s));
+  DV_TRY(upload(P, &P->d_wcol, L.wcol.data(), L.wcol.size(), s));
+
+  // consensus profiles, concatenated per tile row / column
+  std::vector<float> omr, omc;
+  std::vector<int> omr_off(P->n_tr), omc_off(P->n_tc);
+  for (int i = 0; i < P->n_tr; ++i) {
+    omr_off[i] = (int)omr.size();
+    for (double v : L.omr[i]) omr.push_back((float)v);
+  }
+  for (int i = 0; i < P->n_tc; ++i) {
+    omc_off[i] = (int)omc.size();
+    for (double v : L.omc[i]) omc.push_back((float)v);
+  }
+  DV_TRY(upload(P, &P->d_omr, omr.data(), omr.size(), s));
+  DV_TRY(upload(P, &P->d_omc, omc.data(), omc.size(), s));
+
+  // tile descriptors and stack layout (rows padded to 32 floats)
+  P->h_tiles.clear();
+  int64_t xo = 0, yo = 0;
+  P->max_nxr = P->max_nxc = 0;
+  for (int tr = 0; tr < P->n_tr; ++tr) {
+    for (int tc = 0; tc < P->n_tc; ++tc) {
+      TileDesc d{};
+      d.xr0 = L.yr0[tr];
+      d.xc0 = L.yc0[tc];
+      d.nyr = L.yr1[tr] - L.yr0[tr];
+      d.nyc = L.yc1[tc] - L.yc0[tc];
+      d.nxr = d.nyr + K - 1;
+      d.nxc = d.nyc + K - 1;
+      d.xpitch = (int)round_up(d.nxc, 32);
+      d.ypitch = (int)round_up(d.nyc, 32);
+      d.xoff = xo;
+      d.yoff = yo;
+      xo += round_up((int64_t)d.nxr * d.xpitch, 32);
+      yo += round_up((int64_t)d.nyr * d.ypitch, 32);
+      d.omr_off = omr_off[tr];
+      d.omc_off = omc_off[tc];
+      d.tr = tr;
+      d.tc = tc;
+      d.tau = (float)L.tau[(size_t)tr * P->n_tc + tc];
+      P->max_nxr = std::max(P->max_nxr, d.nxr);
+      P->max_nxc = std::max(P->max_nxc, d.nxc);
+      P->h_tiles.push_back(d);
+    }
+  }
+  P->xstack = xo;
+  P->ystack = yo;
+  DV_TRY(upload(P, &P->d_tiles, P->h_tiles.data(), P->h_tiles.size(), s));
+  TileDesc gt{};
+  gt.nyr = P->hy;
+  gt.nyc = P->wy;
+  gt.nxr = P->nxr;
+  gt.nxc = P->nxc;
+  gt.xpitch = P->nxc;
+  gt.ypitch = P->wy;
+  gt.omr_off = gt.omc_off = 0;
+  gt.tau = 0.f;
+  DV_TRY(upload(P, &P->d_gtile, &gt, 1, s));
+  // host copy of the global tile for work-table construction
+  std::vector<TileDesc> gtiles{gt};
+
+  std::vector<WorkItem> w;
+  make_work(P->h_tiles, false, K, L, w);
+  P->nH = (int)w.size();
+  DV_TRY(upload(P, &P->d_workH, w.data(), w.size(), s));
+  make_work(P->h_tiles, true, K, L, w);
+  P->nHt = (int)w.size();
+  DV_TRY(upload(P, &P->d_workHt, w.data(), w.size(), s));
+  make_work(gtiles, false, K, L, w);
+  P->nHg = (int)w.size();
+  DV_TRY(upload(P, &P->d_workHg, w.data(), w.size(), s));
+  make_work(gtiles, true, K, L, w);
+  P->nHtg = (int)w.size();
+  DV_TRY(upload(P, &P->d_workHtg, w.data(), w.size(), s));
+
+  // tiles covering each global x row / column (at most two)
+  std::vector<int2> rc(P->nxr, make_int2(-1, -1)), cc(P->nxc, make_int2(-1, -1));
+  for (int tr = 0; tr < P->n_tr; ++tr)
+    for (int R = L.yr0[tr]; R < L.yr1[tr] + K - 1; ++R) (rc[R].x < 0 ? rc[R].x : rc[R].y) = tr;
+  for (int tc = 0; tc < P->n_tc; ++tc)
+    for (int C = L.yc0[tc]; C < L.yc1[tc] + K - 1; ++C) (cc[C].x < 0 ? cc[C].x : cc[C].y) = tc;
+  DV_TRY(upload(P, &P->d_rowcov, rc.data(), rc.size(), s));
+  DV_TRY(upload(P, &P->d_colcov, cc.data(), cc.size(), s));
+
+  // iterates, dual variable, residuals, data, scratch
+  DV_TRY(alloc(P, &P->d_w[0], P->xstack));
+  DV_TRY(alloc(P, &P->d_w[1], P->xstack));
+  DV_TRY(alloc(P, &P->d_u, P->xstack));
+  DV_TRY(alloc(P, &P->d_r, P->ystack));
+  DV_TRY(cudaMemsetAsync(P->d_w[0], 0, P->xstack * sizeof(float), s) == cudaSuccess
+             ? DV_OK : fail(DV_ERR_CUDA, "memset"));
+  DV_TRY(cudaMemsetAsync(P->d_w[1], 0, P->xstack * sizeof(float), s) == cudaSuccess
+             ? DV_OK : fail(DV_ERR_CUDA, "memset"));
+  DV_TRY(cudaMemsetAsync(P->d_u, 0, P->xstack * sizeof(float), s) == cudaSuccess
+             ? DV_OK : fail(DV_ERR_CUDA, "memset"));
+  DV_TRY(alloc(P, &P->d_y, (size_t)P->hy * P->wy));
+  if (prob->noise_w) DV_TRY(upload(P, &P->d_W, prob->noise_w, (size_t)P->hy * P->wy, s));
+  DV_TRY(alloc(P, &P->d_z, (size_t)P->nxr * P->nxc));
+  DV_TRY(alloc(P, &P->d_xg, (size_t)P->nxr * P->nxc));
+  const int64_t ncons = consensus_blocks(P->nxr, P->nxc);
+  const int64_t nhub = huber_blocks(P->T, P->max_nxr, P->max_nxc);
+  P->n_part = P->nH + nhub + 2 * ncons;
+  DV_TRY(alloc(P, &P->d_part, (size_t)P->n_part));
+  DV_TRY(alloc(P, &P->d_scal, 8));
+  DV_TRY_CUDA(cudaMallocHost((void**)&P->h_scal, 8 * sizeof(double)));
+  DV_TRY_CUDA(direct_prepare(K));
+  DV_TRY_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  DV_TRY_CUDA(cudaEventCreate(&P->ev0));
+  DV_TRY_CUDA(cudaEventCreate(&P->ev1));
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  return DV_OK;
+}
+}  // namespace dv
+
+extern "C" dv_status dv_plan_create(const dv_problem* prob, void* stream, dv_plan** out) {
+  clear_error();
+  if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  dv_plan* P = new (std::nothrow) dv_plan();
+  if (!P) return fail(DV_ERR_OOM, "host allocation of the plan failed");
+  const dv_status st = build_plan(prob, (cudaStream_t)stream, P);
+  if (st != DV_OK) {
+    const std::string msg = g_err;
+    release(P);
+    g_err = msg;
+    return st;
+  }
+  *out = P;
+  return DV_OK;
+}
+
+namespace dv {
+dv_status release(dv_plan* P) {
+  if (!P) return DV_OK;
+  for (auto& g : P->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  for (cudaEvent_t e : P->timer.pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : P->timer.placeholders) cudaEventDestroy(e);
+  void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
+                  P->d_tiles, P->d_gtile, P->d_workH, P->d_workHt, P->d_workHg, P->d_workHtg,
+                  P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
+                  P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (P->h_scal) cudaFreeHost(P->h_scal);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  delete P;
+  return DV_OK;
+}
+}  // namespace dv
+
+extern "C" dv_status dv_destroy(dv_plan* plan) {
+  clear_error();
+  return release(plan);
+}
+
+extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
+  clear_error();
+  if (!P || !info) return fail(DV_ERR_INVALID_ARG, "plan or info is NULL");
+  info->nx_r = P->nxr;
+  info->nx_c = P->nxc;
+  info->n_tiles = P->T;
+  info->path = P->path;
+  info->stack_elems = P->xstack;
+  info->device_bytes = P->device_bytes;
+  info->tau_min = *std::min_element(P->tau.begin(), P->tau.end());
+  info->tau_max = *std::max_element(P->tau.begin(), P->tau.end());
+  info->kernel_launches = P->launches;
+  return DV_OK;
+}

@@ -1,0 +1,416 @@
+// Entry points of libdv that run work: the global operator and its adjoint
+// (Sec. II-B), Algorithm 1 (Sec. III-B) with the local solves replayed as CUDA
+// graphs, the FP64 objective / residual reductions, host-buffer solves,
+// checkpoint / resume of the D-R state, and per-kernel event timing.
+#include <algorithm>
+#include <cmath>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+namespace {
+
+enum Kind { KIND_H = 0, KIND_HT = 1, KIND_CONS = 2 };
+
+int nhub(const dv_plan* P) { return huber_blocks(P->T, P->max_nxr, P->max_nxc); }
+int ncons(const dv_plan* P) { return consensus_blocks(P->nxr, P->nxc); }
+double* part_data(dv_plan* P) { return P->d_part; }
+double* part_hub(dv_plan* P) { return P->d_part + P->nH; }
+double* part_cons(dv_plan* P) { return P->d_part + P->nH + nhub(P); }
+
+dv_status pool_event(dv_plan* P, int* idx) {
+  KernelTimer& T = P->timer;
+  if (T.next == T.pool.size()) {
+    cudaEvent_t e;
+    DV_TRY_CUDA(cudaEventCreate(&e));
+    T.pool.push_back(e);
+  }
+  *idx = (int)T.next++;
+  return DV_OK;
+}
+
+// Collects the durations of every pending timed launch (synchronising on them).
+dv_status harvest(dv_plan* P) {
+  KernelTimer& T = P->timer;
+  for (const Pending& q : T.pending) {
+    DV_TRY_CUDA(cudaEventSynchronize(T.pool[q.ev1]));
+    float ms = 0.f;
+    DV_TRY_CUDA(cudaEventElapsedTime(&ms, T.pool[q.ev0], T.pool[q.ev1]));
+    T.total_ms[q.kind] += ms;
+    T.count[q.kind] += 1;
+  }
+  T.pending.clear();
+  T.next = 0;
+  return DV_OK;
+}
+
+// Launches one kernel through fn, bracketed by pool events when timing is on.
+template <class F>
+dv_status timed_launch(dv_plan* P, int kind, cudaStream_t s, F fn) {
+  int e0 = -1, e1 = -1;
+  if (P->timing) {
+    DV_TRY(pool_event(P, &e0));
+    DV_TRY(pool_event(P, &e1));
+    DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e0], s));
+  }
+  DV_TRY_CUDA(fn(s));
+  P->launches += 1;
+  if (P->timing) {
+    DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e1], s));
+    P->timer.pending.push_back(Pending{kind, e0, e1});
+  }
+  return DV_OK;
+}
+
+cudaError_t launch_inner_H(dv_plan* P, int par, cudaStream_t s) {
+  return launch_direct_H(op_args_H(P, OP_RESID, P->d_w[par], P->d_r, false), s);
+}
+
+cudaError_t launch_inner_Ht(dv_plan* P, int par, cudaStream_t s) {
+  return launch_direct_Ht(
+      op_args_Ht(P, OP_STEP, P->d_r, P->d_w[par ^ 1], false, P->d_w[par], P->d_u), s);
+}
+
+dv_status capture_node(cudaStream_t cs, cudaGraphNode_t* node) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  DV_TRY_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive || nd != 1 || !deps)
+    return fail(DV_ERR_CUDA, "unexpected capture state while recording a timing node");
+  *node = deps[0];
+  return DV_OK;
+}
+
+dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
+  cudaStream_t cs = P->cap_stream;
+  if (g.timed && P->timer.placeholders.empty()) {
+    cudaEvent_t a, b;
+    DV_TRY_CUDA(cudaEventCreate(&a));
+    DV_TRY_CUDA(cudaEventCreate(&b));
+    P->timer.placeholders = {a, b};
+  }
+  DV_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  dv_status st = DV_OK;
+  int par = g.parity;
+  for (int i = 0; i < g.n_inner && st == DV_OK; ++i) {
+    for (int k = 0; k < 2 && st == DV_OK; ++k) {
+      cudaGraphNode_t n0 = nullptr, n1 = nullptr;
+      if (g.timed) {
+        cudaError_t e = cudaEventRecord(P->timer.placeholders[0], cs);
+        st = e == cudaSuccess ? capture_node(cs, &n0) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+        if (st != DV_OK) break;
+      }
+      cudaError_t e = k == 0 ? launch_inner_H(P, par, cs) : launch_inner_Ht(P, par, cs);
+      if (e != cudaSuccess) {
+        st = cuda_fail(e, "kernel launch during capture", __FILE__, __LINE__);
+        break;
+      }
+      if (g.timed) {
+        e = cudaEventRecord(P->timer.placeholders[1], cs);
+        st = e == cudaSuccess ? capture_node(cs, &n1) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+        g.ev_start.push_back(n0);
+        g.ev_end.push_back(n1);
+        g.kinds.push_back(k == 0 ? KIND_H : KIND_HT);
+      }
+    }
+    par ^= 1;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+  if (st != DV_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture", __FILE__, __LINE__);
+  g.graph = graph;
+  DV_TRY_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+  return DV_OK;
+}
+
+dv_status get_graph(dv_plan* P, int n_inner, int par, GraphEntry** out) {
+  for (GraphEntry& g : P->graphs)
+    if (g.n_inner == n_inner && g.parity == par && g.timed == P->timing) {
+      *out = &g;
+      return DV_OK;
+    }
+  GraphEntry g;
+  g.n_inner = n_inner;
+  g.parity = par;
+  g.timed = P->timing;
+  DV_TRY(capture_local_solve(P, g));
+  P->graphs.push_back(g);
+  *out = &P->graphs.back();
+  return DV_OK;
+}
+
+// The Local-Solver of Algorithm 1 on every tile: n_inner x {r = W (H_i w - y_i);
+// w <- max(0, w - tau (H_i^T r + lambda D^T psi(D w) + alpha (w - u)))}.
+dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
+  if (n_inner <= 0) return DV_OK;
+  if (P->prob.use_graphs) {
+    GraphEntry* g = nullptr;
+    DV_TRY(get_graph(P, n_inner, P->cur, &g));
+    if (g->timed) {
+      for (size_t j = 0; j < g->kinds.size(); ++j) {
+        int e0, e1;
+        DV_TRY(pool_event(P, &e0));
+        DV_TRY(pool_event(P, &e1));
+        DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_start[j], P->timer.pool[e0]));
+        DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_end[j], P->timer.pool[e1]));
+        P->timer.pending.push_back(Pending{g->kinds[j], e0, e1});
+      }
+    }
+    DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
+    P->launches += 2 * n_inner;
+  } else {
+    int par = P->cur;
+    for (int i = 0; i < n_inner; ++i) {
+      DV_TRY(timed_launch(P, KIND_H, s, [&](cudaStream_t st) { return launch_inner_H(P, par, st); }));
+      DV_TRY(timed_launch(P, KIND_HT, s, [&](cudaStream_t st) { return launch_inner_Ht(P, par, st); }));
+      par ^= 1;
+    }
+  }
+  P->cur ^= (n_inner & 1);
+  return DV_OK;
+}
+
+dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t s) {
+  const GridArgs g = grid_args(P);
+  return timed_launch(P, KIND_CONS, s, [&](cudaStream_t st) {
+    return launch_consensus(g, P->d_w[P->cur], P->d_u, (float)P->prob.gamma, (float)P->prob.rho,
+                            track_z ? P->d_z : nullptr, residuals ? part_cons(P) : nullptr, st,
+                            nullptr);
+  });
+}
+
+// F(x_hat) = sum_i [1/2 ||y_i - H_i C_i x_hat||^2_W + lambda phi(D C_i x_hat)]
+// plus (when the last consensus step wrote them) the primal / dual residual
+// sums, reduced in FP64 into h_scal[0..3].  Synchronises the stream.
+dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
+  const GridArgs g = grid_args(P);
+  float* tmp = P->d_w[P->cur ^ 1];
+  DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
+  DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, P->d_xg, nullptr, P->hy, P->wy,
+                             P->rad, tmp, nullptr, s, nullptr));
+  DV_TRY_CUDA(launch_direct_H(op_args_H(P, OP_OBJ, tmp, nullptr, false), s));
+  DV_TRY_CUDA(launch_huber_value(P->d_tiles, P->T, P->max_nxr, P->max_nxc, tmp, P->prob.delta,
+                                 part_hub(P), s));
+  const double* parts[4] = {part_data(P), part_hub(P), part_cons(P), part_cons(P) + ncons(P)};
+  const int counts[4] = {P->nH, nhub(P), ncons(P), ncons(P)};
+  DV_TRY_CUDA(launch_reduce(parts, counts, residuals ? 4 : 2, P->d_scal, s));
+  P->launches += 5;
+  DV_TRY_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  if (!residuals) P->h_scal[2] = P->h_scal[3] = NAN;
+  return DV_OK;
+}
+
+struct RunResult {
+  int inner_done = 0;
+  bool have_resid = false;
+  bool have_obj = false;
+};
+
+// n outer iterations of Algorithm 1 from the plan's current state.
+dv_status run_outer(dv_plan* P, int n, bool want_stats, cudaStream_t s, RunResult& rr) {
+  const dv_problem& pr = P->prob;
+  const bool track_z = want_stats || pr.check_every > 0;
+  for (int k = 0; k < n; ++k) {
+    const int ni = pr.n_inner + P->outer_done * pr.inner_increment;
+    DV_TRY(local_solve(P, ni, s));
+    rr.inner_done += ni;
+    const bool check = pr.check_every > 0 && (k + 1) % pr.check_every == 0;
+    const bool last = k + 1 == n;
+    const bool resid = track_z && (check || last);
+    DV_TRY(consensus_step(P, track_z, resid, s));
+    P->outer_done += 1;
+    rr.have_resid = resid;
+    rr.have_obj = false;
+    if (check) {
+      DV_TRY(eval_objective(P, true, s));
+      rr.have_obj = true;
+      const double F = P->h_scal[0] + pr.lambda * P->h_scal[1];
+      if (pr.target_objective > 0.0 && F <= pr.target_objective) break;
+    }
+  }
+  return DV_OK;
+}
+
+dv_status finish(dv_plan* P, float* x_out, dv_stats* st, const RunResult& rr, int64_t l0,
+                 cudaStream_t s) {
+  DV_TRY_CUDA(launch_assemble(grid_args(P), P->d_w[P->cur], P->d_xg, s));
+  P->launches += 1;
+  if (x_out && x_out != P->d_xg)
+    DV_TRY_CUDA(cudaMemcpyAsync(x_out, P->d_xg, (size_t)P->nxr * P->nxc * sizeof(float),
+                                cudaMemcpyDeviceToDevice, s));
+  DV_TRY_CUDA(cudaEventRecord(P->ev1, s));
+  if (st) {
+    if (!rr.have_obj) DV_TRY(eval_objective(P, rr.have_resid, s));
+    st->data_term = P->h_scal[0];
+    st->prior_term = P->h_scal[1];
+    st->objective = P->h_scal[0] + P->prob.lambda * P->h_scal[1];
+    st->primal_res = std::sqrt(P->h_scal[2]);
+    st->dual_res = std::sqrt(P->h_scal[3]);
+    st->outer_done = P->outer_done;
+    st->inner_done = rr.inner_done;
+    float ms = 0.f;
+    DV_TRY_CUDA(cudaEventSynchronize(P->ev1));
+    DV_TRY_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+    st->ms_total = ms;
+    st->kernel_launches = P->launches - l0;
+  }
+  return DV_OK;
+}
+
+dv_status check_plan(const dv_plan* P) {
+  if (!P) return fail(DV_ERR_INVALID_ARG, "plan is NULL");
+  return DV_OK;
+}
+
+// Algorithm 1 from the start image; y is already in P->d_y.
+dv_status solve_internal(dv_plan* P, const float* x0, float* x_out, dv_stats* st, cudaStream_t s,
+                         int64_t l0) {
+  const GridArgs g = grid_args(P);
+  const bool track_z = st || P->prob.check_every > 0;
+  DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, x0, P->d_y, P->hy, P->wy, P->rad,
+                             P->d_w[0], P->d_u, s, track_z ? P->d_z : nullptr));
+  P->launches += 1;
+  P->cur = 0;
+  P->outer_done = 0;
+  RunResult rr;
+  DV_TRY(run_outer(P, P->prob.n_outer, st != nullptr, s, rr));
+  return finish(P, x_out, st, rr, l0, s);
+}
+
+}  // namespace
+}  // namespace dv
+
+using namespace dv;
+
+extern "C" dv_status dv_apply_H(dv_plan* P, const float* x_dev, float* y_dev, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!x_dev || !y_dev) return fail(DV_ERR_INVALID_ARG, "x_dev and y_dev must not be NULL");
+  DV_TRY_CUDA(launch_direct_H(op_args_H(P, OP_PLAIN, x_dev, y_dev, true), (cudaStream_t)stream));
+  P->launches += 1;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_apply_Ht(dv_plan* P, const float* r_dev, float* g_dev, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!r_dev || !g_dev) return fail(DV_ERR_INVALID_ARG, "r_dev and g_dev must not be NULL");
+  DV_TRY_CUDA(launch_direct_Ht(op_args_Ht(P, OP_PLAIN, r_dev, g_dev, true, nullptr, nullptr),
+                               (cudaStream_t)stream));
+  P->launches += 1;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_consensus_solve(dv_plan* P, const float* y_dev, const float* x0_dev,
+                                        float* x_out_dev, dv_stats* stats, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!y_dev || !x_out_dev) return fail(DV_ERR_INVALID_ARG, "y_dev and x_out_dev must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t l0 = P->launches;
+  DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(P->d_y, y_dev, (size_t)P->hy * P->wy * sizeof(float),
+                              cudaMemcpyDeviceToDevice, s));
+  return solve_internal(P, x0_dev, x_out_dev, stats, s, l0);
+}
+
+extern "C" dv_status dv_consensus_solve_host(dv_plan* P, const float* y_host, const float* x0_host,
+                                             float* x_out_host, dv_stats* stats, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!y_host || !x_out_host)
+    return fail(DV_ERR_INVALID_ARG, "y_host and x_out_host must not be NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nx = (size_t)P->nxr * P->nxc;
+  if (x0_host && !P->d_hx0) {
+    DV_TRY_CUDA(cudaMalloc((void**)&P->d_hx0, nx * sizeof(float)));
+    P->device_bytes += nx * sizeof(float);
+  }
+  const int64_t l0 = P->launches;
+  DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(P->d_y, y_host, (size_t)P->hy * P->wy * sizeof(float),
+                              cudaMemcpyHostToDevice, s));
+  if (x0_host)
+    DV_TRY_CUDA(cudaMemcpyAsync(P->d_hx0, x0_host, nx * sizeof(float), cudaMemcpyHostToDevice, s));
+  DV_TRY(solve_internal(P, x0_host ? P->d_hx0 : nullptr, P->d_xg, stats, s, l0));
+  DV_TRY_CUDA(cudaMemcpyAsync(x_out_host, P->d_xg, nx * sizeof(float), cudaMemcpyDeviceToHost, s));
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  return DV_OK;
+}
+
+extern "C" dv_status dv_consensus_continue(dv_plan* P, const float* y_dev, int32_t n_outer,
+                                           float* x_out_dev, dv_stats* stats, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!y_dev || !x_out_dev || n_outer < 0)
+    return fail(DV_ERR_INVALID_ARG, "need y_dev, x_out_dev and n_outer >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t l0 = P->launches;
+  DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(P->d_y, y_dev, (size_t)P->hy * P->wy * sizeof(float),
+                              cudaMemcpyDeviceToDevice, s));
+  RunResult rr;
+  if ((stats || P->prob.check_every > 0) && n_outer > 0) {
+    // the dual residual needs the previous zbar: rebuild it from the current state
+    DV_TRY_CUDA(launch_assemble(grid_args(P), P->d_w[P->cur], P->d_z, s));
+    P->launches += 1;
+  }
+  DV_TRY(run_outer(P, n_outer, stats != nullptr, s, rr));
+  return finish(P, x_out_dev, stats, rr, l0, s);
+}
+
+extern "C" dv_status dv_state_export(dv_plan* P, float* x_stack_dev, float* u_stack_dev,
+                                     int32_t* outer_done, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b = (size_t)P->xstack * sizeof(float);
+  if (x_stack_dev) DV_TRY_CUDA(cudaMemcpyAsync(x_stack_dev, P->d_w[P->cur], b, cudaMemcpyDeviceToDevice, s));
+  if (u_stack_dev) DV_TRY_CUDA(cudaMemcpyAsync(u_stack_dev, P->d_u, b, cudaMemcpyDeviceToDevice, s));
+  if (outer_done) *outer_done = P->outer_done;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_state_import(dv_plan* P, const float* x_stack_dev, const float* u_stack_dev,
+                                     int32_t outer_done, void* stream) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!x_stack_dev || !u_stack_dev || outer_done < 0)
+    return fail(DV_ERR_INVALID_ARG, "need both stacks and outer_done >= 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t b = (size_t)P->xstack * sizeof(float);
+  DV_TRY_CUDA(cudaMemcpyAsync(P->d_w[0], x_stack_dev, b, cudaMemcpyDeviceToDevice, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(P->d_u, u_stack_dev, b, cudaMemcpyDeviceToDevice, s));
+  P->cur = 0;
+  P->outer_done = outer_done;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_plan_set_timing(dv_plan* P, int32_t enable) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  DV_TRY(harvest(P));
+  P->timing = enable != 0;
+  for (int k = 0; k < 3; ++k) {
+    P->timer.total_ms[k] = 0.0;
+    P->timer.count[k] = 0;
+  }
+  return DV_OK;
+}
+
+extern "C" dv_status dv_plan_kernel_time(dv_plan* P, int32_t kind, double* total_ms,
+                                         int64_t* launches) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (kind < 0 || kind > 2) return fail(DV_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
+  DV_TRY(harvest(P));
+  if (total_ms) *total_ms = P->timer.total_ms[kind];
+  if (launches) *launches = P->timer.count[kind];
+  return DV_OK;
+}

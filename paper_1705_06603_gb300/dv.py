@@ -1,0 +1,320 @@
+"""Thin Python binding of libdv (the C ABI declared in include/dv.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Device buffers are torch CUDA tensors (float32, contiguous); streams are torch
+CUDA streams.  Importing this module loads libdv.so and raises ImportError if
+the library has not been built (python -m paper_1705_06603_gb300.build) or
+cannot be loaded: there is no fallback implementation.
+
+Names follow the C ABI: dv_plan_create, dv_apply_H, dv_apply_Ht,
+dv_consensus_solve, dv_destroy, ...  `Plan` is a small convenience wrapper.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdv.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libdv.so is not built ({_LIB_PATH}); run python -m "
+                      "paper_1705_06603_gb300.build (needs nvcc)")
+try:
+    _lib = C.CDLL(_LIB_PATH)
+except OSError as e:  # pragma: no cover - depends on the machine
+    raise ImportError(f"cannot load {_LIB_PATH}: {e}") from e
+
+DV_OK, DV_ERR_INVALID_ARG, DV_ERR_CUDA, DV_ERR_OOM, DV_ERR_TIMEOUT, DV_ERR_UNSUPPORTED = range(6)
+DV_PREC_FP32, DV_PREC_TF32, DV_PREC_BF16 = 0, 1, 2
+DV_WEIGHTS_BILINEAR, DV_WEIGHTS_SEPARABLE = 0, 1
+DV_PATH_AUTO, DV_PATH_DIRECT, DV_PATH_FFT = 0, 1, 2
+KERNEL_H, KERNEL_HT_STEP, KERNEL_CONSENSUS = 0, 1, 2
+
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+
+
+class dv_problem(C.Structure):
+    _fields_ = [("hy", C.c_int32), ("wy", C.c_int32),
+                ("grid_r", C.c_int32), ("grid_c", C.c_int32), ("K", C.c_int32),
+                ("psfs", _fp),
+                ("weight_kind", C.c_int32), ("weights_r", _fp), ("weights_c", _fp),
+                ("n_tr", C.c_int32), ("n_tc", C.c_int32),
+                ("tile_r0", _ip), ("tile_r1", _ip), ("tile_c0", _ip), ("tile_c1", _ip),
+                ("overlap", C.c_int32),
+                ("noise_w", _fp),
+                ("lambda_", C.c_double), ("delta", C.c_double), ("gamma", C.c_double),
+                ("rho", C.c_double),
+                ("n_outer", C.c_int32), ("n_inner", C.c_int32), ("inner_increment", C.c_int32),
+                ("precision", C.c_int32), ("path", C.c_int32), ("use_warmstart", C.c_int32),
+                ("check_every", C.c_int32), ("target_objective", C.c_double),
+                ("use_graphs", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class dv_stats(C.Structure):
+    _fields_ = [("objective", C.c_double), ("data_term", C.c_double),
+                ("prior_term", C.c_double), ("primal_res", C.c_double),
+                ("dual_res", C.c_double), ("outer_done", C.c_int32), ("inner_done", C.c_int32),
+                ("ms_total", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+class dv_plan_info(C.Structure):
+    _fields_ = [("nx_r", C.c_int32), ("nx_c", C.c_int32), ("n_tiles", C.c_int32),
+                ("path", C.c_int32), ("stack_elems", C.c_int64), ("device_bytes", C.c_int64),
+                ("tau_min", C.c_double), ("tau_max", C.c_double),
+                ("kernel_launches", C.c_int64)]
+
+
+_vp = C.c_void_p
+_sigs = {
+    "dv_problem_init": (None, [C.POINTER(dv_problem)]),
+    "dv_layout_query": (C.c_int, [C.POINTER(dv_problem), _ip, _ip, _ip, _ip,
+                                  C.POINTER(C.c_double)]),
+    "dv_plan_create": (C.c_int, [C.POINTER(dv_problem), _vp, C.POINTER(_vp)]),
+    "dv_apply_H": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "dv_apply_Ht": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "dv_consensus_solve": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(dv_stats), _vp]),
+    "dv_consensus_solve_host": (C.c_int, [_vp, _vp, _vp, _vp, C.POINTER(dv_stats), _vp]),
+    "dv_consensus_continue": (C.c_int, [_vp, _vp, C.c_int32, _vp, C.POINTER(dv_stats), _vp]),
+    "dv_state_export": (C.c_int, [_vp, _vp, _vp, _ip, _vp]),
+    "dv_state_import": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),
+    "dv_plan_get_info": (C.c_int, [_vp, C.POINTER(dv_plan_info)]),
+    "dv_plan_set_timing": (C.c_int, [_vp, C.c_int32]),
+    "dv_plan_kernel_time": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int64)]),
+    "dv_destroy": (C.c_int, [_vp]),
+    "dv_last_error": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+class DVError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdv error {code}: {msg}")
+        self.code = code
+
+
+def _check(code):
+    if code != DV_OK:
+        raise DVError(code, (_lib.dv_last_error() or b"").decode())
+
+
+def dv_last_error() -> str:
+    return (_lib.dv_last_error() or b"").decode()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, name, shape=None, writable=False):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a, name, shape=None):
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+        raise TypeError(f"{name} must be a C-contiguous float32 numpy array")
+    if shape is not None and tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {a.shape}, expected {tuple(shape)}")
+    return C.c_void_p(a.ctypes.data)
+
+
+def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, weights=None,
+                 noise_w=None, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, rho=1.0, n_outer=30,
+                 n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
+                 use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1):
+    """Builds a dv_problem.  Returns (problem, keepalive) where keepalive holds
+    the host arrays the struct points to until dv_plan_create has copied them."""
+    p = dv_problem()
+    _lib.dv_problem_init(C.byref(p))
+    psfs = np.ascontiguousarray(psfs, dtype=np.float32)
+    Gr, Gc, K, K2 = psfs.shape
+    if K != K2:
+        raise ValueError("PSFs must be square")
+    keep = [psfs]
+    p.hy, p.wy, p.grid_r, p.grid_c, p.K = hy, wy, Gr, Gc, K
+    p.psfs = psfs.ctypes.data_as(_fp)
+    if weights is not None:
+        wr = np.ascontiguousarray(weights[0], dtype=np.float32)
+        wc = np.ascontiguousarray(weights[1], dtype=np.float32)
+        keep += [wr, wc]
+        p.weight_kind = DV_WEIGHTS_SEPARABLE
+        p.weights_r, p.weights_c = wr.ctypes.data_as(_fp), wc.ctypes.data_as(_fp)
+    p.n_tr, p.n_tc = n_tiles
+    p.overlap = overlap
+    if tile_bounds is not None:
+        arrs = [np.ascontiguousarray(np.asarray(v, dtype=np.int32)) for v in
+                ([b[0] for b in tile_bounds[0]], [b[1] for b in tile_bounds[0]],
+                 [b[0] for b in tile_bounds[1]], [b[1] for b in tile_bounds[1]])]
+        keep += arrs
+        p.tile_r0, p.tile_r1, p.tile_c0, p.tile_c1 = (a.ctypes.data_as(_ip) for a in arrs)
+    if noise_w is not None:
+        nw = np.ascontiguousarray(noise_w, dtype=np.float32)
+        keep.append(nw)
+        p.noise_w = nw.ctypes.data_as(_fp)
+    p.lambda_, p.delta, p.gamma, p.rho = lam, delta, gamma, rho
+    p.n_outer, p.n_inner, p.inner_increment = n_outer, n_inner, inner_increment
+    p.precision, p.path, p.use_warmstart = precision, path, use_warmstart
+    p.check_every, p.target_objective, p.use_graphs = check_every, target_objective, use_graphs
+    return p, keep
+
+
+def dv_layout_query(problem):
+    """Host-only: (row blocks, col blocks, tau[n_tr, n_tc]) the plan would use."""
+    ntr, ntc = problem.n_tr, problem.n_tc
+    r0, r1 = (C.c_int32 * ntr)(), (C.c_int32 * ntr)()
+    c0, c1 = (C.c_int32 * ntc)(), (C.c_int32 * ntc)()
+    tau = (C.c_double * (ntr * ntc))()
+    _check(_lib.dv_layout_query(C.byref(problem), r0, r1, c0, c1, tau))
+    return (list(zip(r0, r1)), list(zip(c0, c1)), np.array(tau[:]).reshape(ntr, ntc))
+
+
+def dv_plan_create(problem, stream=None):
+    h = C.c_void_p()
+    _check(_lib.dv_plan_create(C.byref(problem), _stream_handle(stream), C.byref(h)))
+    return h
+
+
+def dv_apply_H(plan, x, y, stream=None):
+    _check(_lib.dv_apply_H(plan, _dptr(x, "x"), _dptr(y, "y"), _stream_handle(stream)))
+
+
+def dv_apply_Ht(plan, r, g, stream=None):
+    _check(_lib.dv_apply_Ht(plan, _dptr(r, "r"), _dptr(g, "g"), _stream_handle(stream)))
+
+
+def dv_consensus_solve(plan, y, x0, x_out, stats=None, stream=None):
+    _check(_lib.dv_consensus_solve(plan, _dptr(y, "y"), _dptr(x0, "x0"), _dptr(x_out, "x_out"),
+                                   C.byref(stats) if stats is not None else None,
+                                   _stream_handle(stream)))
+
+
+def dv_consensus_solve_host(plan, y, x0, x_out, stats=None, stream=None):
+    _check(_lib.dv_consensus_solve_host(plan, _hptr(y, "y"), _hptr(x0, "x0"),
+                                        _hptr(x_out, "x_out"),
+                                        C.byref(stats) if stats is not None else None,
+                                        _stream_handle(stream)))
+
+
+def dv_consensus_continue(plan, y, n_outer, x_out, stats=None, stream=None):
+    _check(_lib.dv_consensus_continue(plan, _dptr(y, "y"), int(n_outer), _dptr(x_out, "x_out"),
+                                      C.byref(stats) if stats is not None else None,
+                                      _stream_handle(stream)))
+
+
+def dv_state_export(plan, x_stack, u_stack, stream=None):
+    k = C.c_int32()
+    _check(_lib.dv_state_export(plan, _dptr(x_stack, "x_stack"), _dptr(u_stack, "u_stack"),
+                                C.byref(k), _stream_handle(stream)))
+    return k.value
+
+
+def dv_state_import(plan, x_stack, u_stack, outer_done, stream=None):
+    _check(_lib.dv_state_import(plan, _dptr(x_stack, "x_stack"), _dptr(u_stack, "u_stack"),
+                                int(outer_done), _stream_handle(stream)))
+
+
+def dv_plan_get_info(plan):
+    i = dv_plan_info()
+    _check(_lib.dv_plan_get_info(plan, C.byref(i)))
+    return i
+
+
+def dv_plan_set_timing(plan, enable):
+    _check(_lib.dv_plan_set_timing(plan, int(bool(enable))))
+
+
+def dv_plan_kernel_time(plan, kind):
+    ms, n = C.c_double(), C.c_int64()
+    _check(_lib.dv_plan_kernel_time(plan, int(kind), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def dv_destroy(plan):
+    _check(_lib.dv_destroy(plan))
+
+
+def stats_dict(s: dv_stats) -> dict:
+    return {f: getattr(s, f) for f, _ in dv_stats._fields_}
+
+
+class Plan:
+    """Owns one dv_plan; the methods are the C-ABI calls on torch tensors."""
+
+    def __init__(self, hy, wy, psfs, stream=None, **kw):
+        import torch
+        self.problem, keep = make_problem(hy, wy, psfs, **kw)
+        self.hy, self.wy, self.K = hy, wy, self.problem.K
+        self.nx = (hy + self.K - 1, wy + self.K - 1)
+        self.stream = stream
+        self._h = dv_plan_create(self.problem, stream)
+        del keep
+        self.info = dv_plan_get_info(self._h)
+        self._torch = torch
+
+    @property
+    def handle(self):
+        return self._h
+
+    def apply_H(self, x, y=None):
+        y = y if y is not None else self._torch.empty((self.hy, self.wy), device=x.device)
+        _dptr(x, "x", self.nx)
+        _dptr(y, "y", (self.hy, self.wy))
+        dv_apply_H(self._h, x, y, self.stream)
+        return y
+
+    def apply_Ht(self, r, g=None):
+        g = g if g is not None else self._torch.empty(self.nx, device=r.device)
+        _dptr(r, "r", (self.hy, self.wy))
+        _dptr(g, "g", self.nx)
+        dv_apply_Ht(self._h, r, g, self.stream)
+        return g
+
+    def solve(self, y, x0=None, x_out=None, stats=True):
+        x_out = x_out if x_out is not None else self._torch.empty(self.nx, device=y.device)
+        _dptr(y, "y", (self.hy, self.wy))
+        _dptr(x0, "x0", self.nx)
+        _dptr(x_out, "x_out", self.nx)
+        st = dv_stats() if stats else None
+        dv_consensus_solve(self._h, y, x0, x_out, st, self.stream)
+        return x_out, (stats_dict(st) if stats else None)
+
+    def solve_host(self, y, x0=None, stats=True):
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        out = np.empty(self.nx, dtype=np.float32)
+        st = dv_stats() if stats else None
+        dv_consensus_solve_host(self._h, y, x0, out, st, self.stream)
+        return out, (stats_dict(st) if stats else None)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            dv_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

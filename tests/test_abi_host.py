@@ -1,0 +1,123 @@
+"""Host-only checks of the C ABI (no GPU needed): libdv.so loads, exports every
+function include/dv.h declares, and its host-side layout logic (tiling,
+consensus weights, local step sizes) agrees with the oracle; invalid problems
+are rejected with DV_ERR_INVALID_ARG."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dv_oracle as O
+from paper_1705_06603_gb300 import build as dvbuild
+from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dv():
+    dvbuild.build()
+    from paper_1705_06603_gb300 import dv as mod
+    return mod
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "dv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dv_[a-z_0-9A-Z]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("dv_plan_create", "dv_apply_H", "dv_apply_Ht", "dv_consensus_solve", "dv_destroy",
+              "dv_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(dv):
+    lib = C.CDLL(dv._LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) == set(dv.EXPORTED)
+
+
+@pytest.mark.parametrize("name", ["disks128", "stars2048", "wide8192", "giga32768"])
+def test_layout_and_steps_match_oracle(dv, name):
+    w = WORKLOADS[name]
+    psfs = psf_grid_for(w) if name != "giga32768" else np.full((2, 2, w.K, w.K), 1.0 / w.K**2)
+    bounds = (w.yrows, w.ycols) if w.yrows is not None else None
+    p, keep = dv.make_problem(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap,
+                              tile_bounds=bounds, lam=w.lam, delta=w.delta, gamma=w.gamma)
+    rows, cols, tau = dv.dv_layout_query(p)
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap, w.yrows, w.ycols)
+    assert rows == [tuple(r) for r in lay.yrows]
+    assert cols == [tuple(c) for c in lay.ycols]
+    ps = psfs.astype(np.float32).astype(np.float64)
+    for tr, tc in lay.tiles:
+        ref = O.tile_step(lay, tr, tc, ps, None, w.lam, w.gamma)
+        assert abs(tau[tr, tc] - ref) <= 1e-12 * ref
+
+
+def test_layout_with_noise_weights(dv):
+    g = np.random.default_rng(0)
+    K = 5
+    psfs = g.uniform(0, 1, (2, 2, K, K))
+    psfs /= psfs.sum(axis=(2, 3), keepdims=True)
+    W = g.uniform(0.1, 1.0, (40, 30)).astype(np.float32)
+    p, keep = dv.make_problem(40, 30, psfs, n_tiles=(3, 2), overlap=6, noise_w=W, lam=0.01,
+                              gamma=0.7)
+    _, _, tau = dv.dv_layout_query(p)
+    lay = O.make_layout(40, 30, K, 3, 2, 6)
+    for tr, tc in lay.tiles:
+        ref = O.tile_step(lay, tr, tc, psfs.astype(np.float32).astype(np.float64),
+                          W.astype(np.float64), 0.01, 0.7)
+        assert abs(tau[tr, tc] - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("change,needle", [
+    (dict(K=4), "K must be odd"),
+    (dict(rho=2.0), "rho"),
+    (dict(gamma=0.0), "gamma"),
+    (dict(delta=-1.0), "delta"),
+    (dict(n_outer=-1), "iteration"),
+])
+def test_invalid_problems_rejected(dv, change, needle):
+    psfs = np.full((1, 1, 3, 3), 1 / 9.0)
+    p, keep = dv.make_problem(20, 20, psfs)
+    for k, v in change.items():
+        setattr(p, k, v)
+    with pytest.raises(dv.DVError) as e:
+        dv.dv_layout_query(p)
+    assert e.value.code == dv.DV_ERR_INVALID_ARG
+    assert needle in str(e.value)
+
+
+def test_bad_tilings_rejected(dv):
+    psfs = np.full((1, 1, 3, 3), 1 / 9.0)
+    # a gap between y-blocks
+    p, keep = dv.make_problem(20, 20, psfs, n_tiles=(2, 1),
+                              tile_bounds=([(0, 9), (10, 20)], [(0, 20)]))
+    with pytest.raises(dv.DVError, match="gap"):
+        dv.dv_layout_query(p)
+    # x-tiles 0 and 2 overlap (each x-tile may only overlap its neighbours)
+    p, keep = dv.make_problem(20, 20, psfs, n_tiles=(3, 1),
+                              tile_bounds=([(0, 10), (5, 15), (10, 20)], [(0, 20)]))
+    with pytest.raises(dv.DVError, match="overlap"):
+        dv.dv_layout_query(p)
+
+
+def test_separable_weights_validated(dv):
+    K, hy, wy = 3, 10, 12
+    psfs = np.full((3, 2, K, K), 1 / 9.0)
+    wr = O.bilinear_weights(hy + K - 1, 3).astype(np.float32)
+    wc = O.bilinear_weights(wy + K - 1, 2).astype(np.float32)
+    p, keep = dv.make_problem(hy, wy, psfs, weights=(wr, wc))
+    dv.dv_layout_query(p)
+    bad = wr.copy()
+    bad[:, 4] = 0.3        # three grid points nonzero at one coordinate
+    p, keep = dv.make_problem(hy, wy, psfs, weights=(bad, wc))
+    with pytest.raises(dv.DVError, match="at most two"):
+        dv.dv_layout_query(p)

@@ -1,0 +1,248 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (FP32 arithmetic against FP64): operator relative L2 <= 1e-5;
+short solves relative L2 <= 1e-4; the full 30 x 10 solve relative RMSE <= 1e-3
+and objective within 1e-4 relative (the precision targets of the method's
+FP32 form)."""
+
+import numpy as np
+import pytest
+
+from oracle import dv_oracle as O
+from tests.gpu_common import (need_gpu, oracle_solve, random_psfs, rel_l2, workload_case)
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    return need_gpu()
+
+
+def _apply_both(env, hy, wy, K, G, seed, negative=False, weights=None):
+    torch, dv = env
+    g = np.random.default_rng(seed)
+    psfs = random_psfs(g, G, K, negative)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
+    r = g.standard_normal((hy, wy)).astype(np.float32)
+    plan = dv.Plan(hy, wy, psfs, weights=weights)
+    yd = plan.apply_H(torch.from_numpy(x).cuda())
+    gd = plan.apply_Ht(torch.from_numpy(r).cuda())
+    torch.cuda.synchronize()
+    wr, wc = weights if weights is not None else (O.bilinear_weights(nxr, G[0]),
+                                                  O.bilinear_weights(nxc, G[1]))
+    wr, wc = np.asarray(wr, np.float64), np.asarray(wc, np.float64)
+    ps = psfs.astype(np.float64)
+    y_ref = O.apply_H(x.astype(np.float64), ps, wr, wc)
+    g_ref = O.apply_Ht(r.astype(np.float64), ps, wr, wc)
+    plan.close()
+    return yd.cpu().numpy(), y_ref, gd.cpu().numpy(), g_ref, x, r
+
+
+@pytest.mark.parametrize("hy,wy,K,G", [
+    (150, 133, 3, (3, 4)),     # several 64x64 blocks, ragged tails
+    (130, 70, 9, (3, 3)),
+    (97, 140, 11, (2, 5)),     # run-time K kernel
+    (200, 180, 31, (4, 3)),
+    (70, 75, 63, (2, 2)),
+    (40, 33, 1, (2, 2)),       # 1x1 PSFs: H is pointwise, x and y share a size
+    (66, 64, 5, (1, 1)),       # a single PSF: plain convolution
+])
+def test_operator_matches_oracle(env, hy, wy, K, G):
+    yd, y_ref, gd, g_ref, x, r = _apply_both(env, hy, wy, K, G, seed=K * 7 + hy)
+    assert rel_l2(yd, y_ref) <= OP_TOL
+    assert rel_l2(gd, g_ref) <= OP_TOL
+
+
+def test_operator_signed_psfs_and_separable_weights(env):
+    hy, wy, K, G = 90, 101, 7, (3, 3)
+    g = np.random.default_rng(5)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    # a non-tent first-order profile (still two neighbouring points at most)
+    t = np.linspace(0, 1, nxr)
+    wr = np.stack([np.clip(1 - 2 * t, 0, 1), 1 - np.abs(2 * t - 1), np.clip(2 * t - 1, 0, 1)])
+    wc = O.bilinear_weights(nxc, 3) * 0.8
+    yd, y_ref, gd, g_ref, *_ = _apply_both(env, hy, wy, K, G, 5, negative=True,
+                                           weights=(wr.astype(np.float32), wc.astype(np.float32)))
+    assert rel_l2(yd, y_ref) <= OP_TOL
+    assert rel_l2(gd, g_ref) <= OP_TOL
+
+
+def test_adjoint_identity_on_gpu(env):
+    yd, _, gd, _, x, r = _apply_both(env, 123, 77, 9, (3, 2), seed=99)
+    lhs = np.vdot(yd.astype(np.float64), r.astype(np.float64))
+    rhs = np.vdot(x.astype(np.float64), gd.astype(np.float64))
+    assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(yd) * np.linalg.norm(r)
+
+
+def _gpu_solve(env, w, psfs, y, n_outer, n_inner, use_graphs=1, x0=None, **kw):
+    torch, dv = env
+    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap,
+                   tile_bounds=(w.yrows, w.ycols) if w.yrows is not None else None,
+                   lam=w.lam, delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=n_outer,
+                   n_inner=n_inner, use_graphs=use_graphs, **kw)
+    xd, st = plan.solve(torch.from_numpy(y).cuda(),
+                        None if x0 is None else torch.from_numpy(x0).cuda())
+    torch.cuda.synchronize()
+    return plan, xd.cpu().numpy(), st
+
+
+def test_short_solve_matches_oracle(env):
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 2)
+    lay, xr, info = oracle_solve(w, psfs, y, 3, 2)
+    assert rel_l2(xd, xr) <= 1e-5
+    F, data, prior = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam,
+                                 w.delta)
+    assert abs(st["objective"] - F) <= 1e-5 * F
+    assert abs(st["data_term"] - data) <= 1e-5 * data
+    assert abs(st["prior_term"] - prior) <= 1e-5 * prior
+    assert abs(st["primal_res"] - info.primal[-1]) <= 1e-3 * info.primal[-1]
+    assert abs(st["dual_res"] - info.dual[-1]) <= 1e-3 * info.dual[-1]
+    assert st["outer_done"] == 3 and st["inner_done"] == 6
+    plan.close()
+
+
+def test_full_small_workload_matches_oracle(env):
+    """The 128x128 workload, 30 consensus iterations x 10 inner steps."""
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner)
+    lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
+    assert rel_l2(xd, xr) <= 1e-3
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
+    assert abs(st["objective"] - F) <= 1e-4 * F
+    assert xd.min() >= 0.0
+    plan.close()
+
+
+def test_graph_eager_host_and_repeat_are_bit_identical(env):
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    p1, x1, s1 = _gpu_solve(env, w, psfs, y, 4, 3, use_graphs=1)
+    p2, x2, s2 = _gpu_solve(env, w, psfs, y, 4, 3, use_graphs=0)
+    xh, sh = p1.solve_host(y)
+    x3 = p1.solve(torch.from_numpy(y).cuda())[0].cpu().numpy()
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(x1, xh)
+    np.testing.assert_array_equal(x1, x3)
+    assert s1["objective"] == s2["objective"] == sh["objective"]
+    p1.close()
+    p2.close()
+
+
+def test_checkpoint_resume_equals_uninterrupted(env):
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    plan, x_full, _ = _gpu_solve(env, w, psfs, y, 6, 4, inner_increment=2)
+    p2, _, _ = _gpu_solve(env, w, psfs, y, 3, 4, inner_increment=2)
+    n = p2.info.stack_elems
+    xs = torch.empty(n, device="cuda")
+    us = torch.empty(n, device="cuda")
+    k = dv.dv_state_export(p2.handle, xs, us)
+    assert k == 3
+    p3 = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
+                 delta=w.delta, gamma=w.gamma, n_outer=6, n_inner=4, inner_increment=2)
+    dv.dv_state_import(p3.handle, xs, us, k)
+    out = torch.empty(p3.nx, device="cuda")
+    st = dv.dv_stats()
+    dv.dv_consensus_continue(p3.handle, torch.from_numpy(y).cuda(), 3, out, st)
+    np.testing.assert_array_equal(out.cpu().numpy(), x_full)
+    assert st.outer_done == 6
+    for p in (plan, p2, p3):
+        p.close()
+
+
+@pytest.mark.parametrize("case", ["one_tile", "no_inner", "no_outer", "uneven_tiles",
+                                  "noise_weights", "no_prior", "paper_schedule"])
+def test_edge_cases_match_oracle(env, case):
+    torch, dv = env
+    g = np.random.default_rng(17)
+    K, G = 5, (2, 3)
+    hy, wy = 70, 83
+    psfs = random_psfs(g, G, K)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    x = g.uniform(0, 1, (nxr, nxc))
+    wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
+    y = (O.apply_H(x, psfs.astype(np.float64), wr, wc) +
+         0.01 * g.standard_normal((hy, wy))).astype(np.float32)
+    kw = dict(n_tiles=(2, 3), overlap=8, lam=0.01, delta=0.05, gamma=0.4, n_outer=4, n_inner=3)
+    okw = {}
+    W = None
+    bounds = None
+    if case == "one_tile":
+        kw["n_tiles"] = (1, 1)
+    elif case == "no_inner":
+        kw["n_inner"] = 0
+    elif case == "no_outer":
+        kw["n_outer"] = 0
+    elif case == "uneven_tiles":
+        bounds = ([(0, 30), (22, 70)], [(0, 20), (12, 60), (50, 83)])
+        kw["tile_bounds"] = bounds
+    elif case == "noise_weights":
+        W = g.uniform(0.2, 1.0, (hy, wy)).astype(np.float32)
+        W[10:14, 20:30] = 0.0      # unmeasured pixels
+        kw["noise_w"] = W
+    elif case == "no_prior":
+        kw["lam"] = 0.0
+    elif case == "paper_schedule":
+        kw["inner_increment"] = 2
+        okw["inner_increment"] = 2
+    plan = dv.Plan(hy, wy, psfs, **kw)
+    xd, st = plan.solve(torch.from_numpy(y).cuda())
+    xd = xd.cpu().numpy()
+    lay = O.make_layout(hy, wy, K, *kw["n_tiles"], kw["overlap"],
+                        bounds[0] if bounds else None, bounds[1] if bounds else None)
+    xr, info = O.solve(y.astype(np.float64), psfs.astype(np.float64), lay, kw["lam"], kw["delta"],
+                       kw["gamma"], 1.0, kw["n_outer"], kw["n_inner"],
+                       W=None if W is None else W.astype(np.float64), **okw)
+    assert rel_l2(xd, xr) <= 1e-5
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, kw["lam"],
+                    kw["delta"], None if W is None else W.astype(np.float64))[0]
+    assert abs(st["objective"] - F) <= 1e-5 * F
+    plan.close()
+
+
+def test_full_size_tile_step_matches_oracle(env):
+    """The 2048x2048 star-field workload in the benchmark's launch configuration:
+    one inner step and one consensus step on all 16 tiles; an interior tile's
+    x_i is compared element by element with the oracle's Local-Solver step."""
+    torch, dv = env
+    from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for, scene_for, gaussian_noise
+    w = WORKLOADS["stars2048"]
+    psfs = psf_grid_for(w).astype(np.float32)
+    rng = np.random.default_rng(3)
+    y = (scene_for(w)[15:-15, 15:-15] * 0.9 +
+         gaussian_noise((w.hy, w.wy), w.noise_sigma, w.noise_seed)).astype(np.float32)
+    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
+                   delta=w.delta, gamma=w.gamma, n_outer=1, n_inner=1)
+    plan.solve(torch.from_numpy(y).cuda(), stats=False)
+    xs = torch.empty(plan.info.stack_elems, device="cuda")
+    us = torch.empty_like(xs)
+    dv.dv_state_export(plan.handle, xs, us)
+    xs = xs.cpu().numpy()
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap)
+    tr, tc = 1, 2
+    n = tr * w.n_tiles[1] + tc
+    # stack layout: tiles in row-major order, rows padded to 32 floats
+    off = 0
+    for t, (a, b) in enumerate(lay.tiles):
+        rs, cs = lay.xslice(a, b)
+        nr, nc = rs.stop - rs.start, cs.stop - cs.start
+        pitch = -(-nc // 32) * 32
+        if t == n:
+            x_gpu = xs[off:off + nr * pitch].reshape(nr, pitch)[:, :nc]
+            break
+        off += -(-(nr * pitch) // 32) * 32
+    x0 = O.start_image(y.astype(np.float64), w.K)
+    rs, cs = lay.xslice(tr, tc)
+    wr = O.bilinear_weights(lay.nx[0], w.grid[0])[:, rs]
+    wc = O.bilinear_weights(lay.nx[1], w.grid[1])[:, cs]
+    tau = O.tile_step(lay, tr, tc, psfs.astype(np.float64), None, w.lam, w.gamma)
+    xi = O.local_solve(x0[rs, cs], x0[rs, cs], y.astype(np.float64)[lay.yslice(tr, tc)], None,
+                       psfs.astype(np.float64), wr, wc, w.gamma * lay.omega(tr, tc), w.lam,
+                       w.delta, tau, 1)
+    assert rel_l2(x_gpu, xi) <= 1e-5
+    plan.close()
