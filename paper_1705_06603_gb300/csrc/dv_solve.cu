@@ -97,7 +97,7 @@ dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
     for (int k = 0; k < 2 && st == DV_OK; ++k) {
       cudaGraphNode_t n0 = nullptr, n1 = nullptr;
       if (g.timed) {
-        cudaError_t e = cudaEventRecord(P->timer.placeholders[0], cs);
+        cudaError_t e = cudaEventRecordWithFlags(P->timer.placeholders[0], cs, cudaEventRecordExternal);
         st = e == cudaSuccess ? capture_node(cs, &n0) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
         if (st != DV_OK) break;
       }
@@ -107,7 +107,7 @@ dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
         break;
       }
       if (g.timed) {
-        e = cudaEventRecord(P->timer.placeholders[1], cs);
+        e = cudaEventRecordWithFlags(P->timer.placeholders[1], cs, cudaEventRecordExternal);
         st = e == cudaSuccess ? capture_node(cs, &n1) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
         g.ev_start.push_back(n0);
         g.ev_end.push_back(n1);
@@ -184,9 +184,10 @@ dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t 
   });
 }
 
-// F(x_hat) = sum_i [1/2 ||y_i - H_i C_i x_hat||^2_W + lambda phi(D C_i x_hat)]
-// plus (when the last consensus step wrote them) the primal / dual residual
-// sums, reduced in FP64 into h_scal[0..3].  Synchronises the stream.
+// Terms of F(x_hat) = sum_i [1/2 ||y_i - H_i C_i x_hat||^2_W + lambda phi(D C_i x_hat)]
+// reduced in FP64: h_scal[0] = sum_i ||y_i - H_i C_i x_hat||^2_W (without the 1/2),
+// h_scal[1] = sum_i phi(D C_i x_hat), and (when the last consensus step wrote
+// them) h_scal[2..3] = the squared primal / dual residuals.  Synchronises the stream.
 dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
   const GridArgs g = grid_args(P);
   float* tmp = P->d_w[P->cur ^ 1];
@@ -230,7 +231,7 @@ dv_status run_outer(dv_plan* P, int n, bool want_stats, cudaStream_t s, RunResul
     if (check) {
       DV_TRY(eval_objective(P, true, s));
       rr.have_obj = true;
-      const double F = P->h_scal[0] + pr.lambda * P->h_scal[1];
+      const double F = 0.5 * P->h_scal[0] + pr.lambda * P->h_scal[1];
       if (pr.target_objective > 0.0 && F <= pr.target_objective) break;
     }
   }
@@ -247,9 +248,9 @@ dv_status finish(dv_plan* P, float* x_out, dv_stats* st, const RunResult& rr, in
   DV_TRY_CUDA(cudaEventRecord(P->ev1, s));
   if (st) {
     if (!rr.have_obj) DV_TRY(eval_objective(P, rr.have_resid, s));
-    st->data_term = P->h_scal[0];
+    st->data_term = 0.5 * P->h_scal[0];
     st->prior_term = P->h_scal[1];
-    st->objective = P->h_scal[0] + P->prob.lambda * P->h_scal[1];
+    st->objective = 0.5 * P->h_scal[0] + P->prob.lambda * P->h_scal[1];
     st->primal_res = std::sqrt(P->h_scal[2]);
     st->dual_res = std::sqrt(P->h_scal[3]);
     st->outer_done = P->outer_done;

@@ -246,3 +246,21 @@ def test_full_size_tile_step_matches_oracle(env):
                        w.delta, tau, 1)
     assert rel_l2(x_gpu, xi) <= 1e-5
     plan.close()
+
+
+@pytest.mark.parametrize("use_graphs", [1, 0])
+def test_kernel_timing_counts(env, use_graphs):
+    """Per-kernel event timing sees every launch of the solve, in graphs and eagerly,
+    and does not change the result."""
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    plan, x_ref, _ = _gpu_solve(env, w, psfs, y, 3, 4, use_graphs=use_graphs)
+    dv.dv_plan_set_timing(plan.handle, 1)
+    xd, _ = plan.solve(torch.from_numpy(y).cuda(), stats=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(xd.cpu().numpy(), x_ref)
+    for kind, n in ((0, 12), (1, 12), (2, 3)):
+        ms, cnt = dv.dv_plan_kernel_time(plan.handle, kind)
+        assert cnt == n and ms > 0.0
+    dv.dv_plan_set_timing(plan.handle, 0)
+    plan.close()
