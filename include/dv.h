@@ -224,6 +224,28 @@ dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);
 dv_status dv_plan_set_timing(dv_plan* plan, int32_t enable);
 dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int64_t* launches);
 
+/* Allocation-free Huber prior value (the paper has no counterpart; this is a
+ * service for callers that may not allocate device memory, such as plug-ins
+ * running inside a host framework that owns all device memory, or real-time
+ * loops where a cudaMalloc could stall the device).  Writes to value_dev[0]
+ * (device, one double) the FP64 sum over the rows x cols image x_dev of
+ * hub_delta(|grad x|) with forward differences set to zero on the last row and
+ * column -- the prior term phi(D x) of dv_stats for a one-tile plan.  Needs no
+ * plan and allocates nothing: its per-block partial sums live in a static
+ * device array of DV_NOALLOC_MAX_BLOCKS doubles (512 KiB) that every GPU
+ * loading libdv keeps until the process exits.  One partial is used per row
+ * and 256 columns, so rows * ceil(cols / 256) must not exceed
+ * DV_NOALLOC_MAX_BLOCKS and rows must not exceed 65535; larger images are
+ * rejected with DV_ERR_INVALID_ARG.  The first call on each device looks up
+ * the array's device address (no allocation); make that first call before any
+ * stream capture.  All calls share the array, so calls whose work overlaps on
+ * the GPU (different streams, no ordering) race and give wrong sums; calls
+ * ordered on one stream are safe.  Enqueued on stream; returns without
+ * synchronising. */
+#define DV_NOALLOC_MAX_BLOCKS 65536
+dv_status dv_prior_value_noalloc(const float* x_dev, int32_t rows, int32_t cols, double delta,
+                                 double* value_dev, void* stream);
+
 /* Releases everything the plan owns.  NULL is accepted. */
 dv_status dv_destroy(dv_plan* plan);
 

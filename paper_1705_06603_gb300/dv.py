@@ -84,6 +84,7 @@ _sigs = {
     "dv_plan_set_timing": (C.c_int, [_vp, C.c_int32]),
     "dv_plan_kernel_time": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]),
+    "dv_prior_value_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, _vp, _vp]),
     "dv_destroy": (C.c_int, [_vp]),
     "dv_last_error": (C.c_char_p, []),
 }
@@ -250,6 +251,20 @@ def dv_plan_kernel_time(plan, kind):
     ms, n = C.c_double(), C.c_int64()
     _check(_lib.dv_plan_kernel_time(plan, int(kind), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def dv_prior_value_noalloc(x, delta, value, stream=None):
+    """Huber prior value of the 2-D image x written to value (a 1-element float64
+    CUDA tensor), with no device allocation (see include/dv.h)."""
+    import torch
+    if not (isinstance(value, torch.Tensor) and value.is_cuda and value.dtype == torch.float64
+            and value.numel() >= 1):
+        raise TypeError("value must be a float64 CUDA tensor with at least one element")
+    if x.dim() != 2:
+        raise ValueError("x must be a 2-D image")
+    _check(_lib.dv_prior_value_noalloc(_dptr(x, "x"), int(x.shape[0]), int(x.shape[1]),
+                                       float(delta), C.c_void_p(value.data_ptr()),
+                                       _stream_handle(stream)))
 
 
 def dv_destroy(plan):
