@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
+                         "short, fixed launch sequence for ncu captures); prints nothing")
     return ap.parse_args()
 
 
@@ -380,8 +383,30 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_case():
+    """Launch sequence for ncu: inputs, plan, then scatter, H, H^T (+ step),
+    consensus and assembly of one 1 x 1 solve, eagerly (no graphs)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1705_06603_gb300 import build as dvbuild
+    dvbuild.build()
+    from paper_1705_06603_gb300 import dv
+    from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
+    w = WORKLOADS[WORKLOAD]
+    psfs = psf_grid_for(w).astype(np.float32)
+    y = make_inputs(torch, dv, w, psfs, 0)
+    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
+                   delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=1, n_inner=1, use_graphs=0)
+    plan.solve(y, stats=False)
+    torch.cuda.synchronize()
+    plan.close()
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
