@@ -212,6 +212,8 @@ typedef struct dv_plan_info {
   int64_t device_bytes;    /* device memory owned by the plan */
   double tau_min, tau_max; /* local step sizes */
   int64_t kernel_launches; /* total libdv kernel launches on this plan */
+  double tune_ms_direct;   /* autotuner: one H + one H^T apply, direct path (0 if not timed) */
+  double tune_ms_fft;      /* same for the block-FFT path (0 if not timed / not available) */
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

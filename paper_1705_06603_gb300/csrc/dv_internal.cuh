@@ -105,6 +105,8 @@ struct OpArgs {
   const float* omc;
   float lambda, delta, gamma;
   int32_t pad2;
+  const float2* spec;     // FFT path: [Gr*Gc][S][S] PSF spectra / S^2
+  int* counter;           // FFT path: work counter, zeroed before each launch
 };
 
 // Streaming kernels' shared view of the tile grid
@@ -150,6 +152,15 @@ cudaError_t launch_reduce(const double* const* parts, const int* counts, int nk,
 size_t direct_smem_bytes(int K);
 cudaError_t direct_prepare(int K);   // shared-memory limits of the direct kernels
 
+// Block-FFT path (overlap-save, S = 128)
+int fft_size();
+int fft_block(int K);                 // valid outputs per block side, S - K + 1
+bool fft_supported(int K);
+cudaError_t fft_prepare();            // twiddles + shared-memory limits (plan time)
+void fft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
+cudaError_t launch_fft_H(const OpArgs& a, cudaStream_t s, int grid);
+cudaError_t launch_fft_Ht(const OpArgs& a, cudaStream_t s, int grid);
+
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
@@ -182,10 +193,28 @@ struct KernelTimer {
 
 }  // namespace dv
 
+namespace dv {
+// Work tables of one operator path: tile mode (H over y-blocks, H^T over
+// x-tiles) and the single global pseudo-tile of dv_apply_H / dv_apply_Ht.
+struct OpTables {
+  WorkItem* H = nullptr;
+  WorkItem* Ht = nullptr;
+  WorkItem* Hg = nullptr;
+  WorkItem* Htg = nullptr;
+  int nH = 0, nHt = 0, nHg = 0, nHtg = 0;
+};
+}  // namespace dv
+
 struct dv_plan {
   dv_problem prob;        // copy with host pointers cleared
   int hy, wy, K, rad, Gr, Gc, nxr, nxc, n_tr, n_tc, T;
-  int path;
+  int path;               // operator path in use: DV_PATH_DIRECT or DV_PATH_FFT
+  dv::OpTables tab[2];    // [0] direct 64x64 blocks, [1] FFT b x b blocks (if supported)
+  bool fft_ok = false;
+  float2* d_spec = nullptr;
+  int* d_counter = nullptr;        // [0] H launches, [1] H^T launches (FFT path)
+  int n_sm = 0;
+  double tune_ms[2] = {0.0, 0.0};   // autotuner: one H + one H^T apply per path
   std::vector<int> yr0, yr1, yc0, yc1;
   std::vector<double> tau;
   std::vector<dv::TileDesc> h_tiles;
@@ -200,11 +229,6 @@ struct dv_plan {
   float* d_omc = nullptr;
   dv::TileDesc* d_tiles = nullptr;
   dv::TileDesc* d_gtile = nullptr;
-  dv::WorkItem* d_workH = nullptr;
-  dv::WorkItem* d_workHt = nullptr;
-  dv::WorkItem* d_workHg = nullptr;
-  dv::WorkItem* d_workHtg = nullptr;
-  int nH = 0, nHt = 0, nHg = 0, nHtg = 0;
   int2* d_rowcov = nullptr;
   int2* d_colcov = nullptr;
   float* d_w[2] = {nullptr, nullptr};
@@ -233,6 +257,11 @@ struct dv_plan {
 };
 
 namespace dv {
+// Operator launches on the plan's path; the H launch in OP_OBJ mode writes
+// obj_parts(P) FP64 partials.
+cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s);
+cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s);
+int obj_parts(const dv_plan* P);
 dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global);
 dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
                       const float* w, const float* u);

@@ -285,26 +285,25 @@ dv_status alloc(dv_plan* P, T** dst, size_t n) {
   return DV_OK;
 }
 
-// Work items of one operator over the given tiles: output blocks of
-// TM x TN, with the PSF grid range active on the block's input (H) or
-// output (H^T) region.
-void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const Layout& L,
-               std::vector<WorkItem>& out) {
-  const int TM = direct_tile_m(), TN = direct_tile_n();
+// Work items of one operator over the given tiles: output blocks of bm x bn,
+// with the PSF grid range active on the block's input (H) or output (H^T)
+// region.
+void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const Layout& L, int bm,
+               int bn, std::vector<WorkItem>& out) {
   out.clear();
   for (int t = 0; t < (int)tiles.size(); ++t) {
     const TileDesc& td = tiles[t];
     const int nr = adjoint ? td.nxr : td.nyr, nc = adjoint ? td.nxc : td.nyc;
-    for (int r0 = 0; r0 < nr; r0 += TM) {
-      for (int c0 = 0; c0 < nc; c0 += TN) {
+    for (int r0 = 0; r0 < nr; r0 += bm) {
+      for (int c0 = 0; c0 < nc; c0 += bn) {
         WorkItem w{};
         w.tile = t;
         w.r0 = r0;
         w.c0 = c0;
         // global x coordinate range whose weights matter
-        int rlo = td.xr0 + r0, clo = td.xc0 + c0;
-        int rhi = td.xr0 + std::min(r0 + TM, nr) + (adjoint ? 0 : K - 1);
-        int chi = td.xc0 + std::min(c0 + TN, nc) + (adjoint ? 0 : K - 1);
+        const int rlo = td.xr0 + r0, clo = td.xc0 + c0;
+        const int rhi = td.xr0 + std::min(r0 + bm, nr) + (adjoint ? 0 : K - 1);
+        const int chi = td.xc0 + std::min(c0 + bn, nc) + (adjoint ? 0 : K - 1);
         active_range(L.wrow, rlo, rhi, w.a_lo, w.a_hi);
         active_range(L.wcol, clo, chi, w.b_lo, w.b_hi);
         out.push_back(w);
@@ -317,9 +316,10 @@ void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const La
 
 dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global) {
   OpArgs a{};
+  const OpTables& tb = p->tab[p->path == DV_PATH_FFT ? 1 : 0];
   a.tiles = global ? p->d_gtile : p->d_tiles;
-  a.work = global ? p->d_workHg : p->d_workH;
-  a.n_work = global ? p->nHg : p->nH;
+  a.work = global ? tb.Hg : tb.H;
+  a.n_work = global ? tb.nHg : tb.nH;
   a.mode = mode;
   a.wrow = p->d_wrow;
   a.wcol = p->d_wcol;
@@ -333,6 +333,8 @@ dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bo
   a.W = p->d_W;
   a.wy = p->wy;
   a.partials = p->d_part;
+  a.spec = p->d_spec;
+  a.counter = p->d_counter;
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
@@ -342,15 +344,29 @@ dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bo
 dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
                       const float* w, const float* u) {
   OpArgs a = op_args_H(p, mode, in, out, global);
+  const OpTables& tb = p->tab[p->path == DV_PATH_FFT ? 1 : 0];
   a.tiles = global ? p->d_gtile : p->d_tiles;
-  a.work = global ? p->d_workHtg : p->d_workHt;
-  a.n_work = global ? p->nHtg : p->nHt;
+  a.work = global ? tb.Htg : tb.Ht;
+  a.n_work = global ? tb.nHtg : tb.nHt;
   a.psf = p->d_psf;
+  a.counter = p->d_counter ? p->d_counter + 1 : nullptr;
   a.w = w;
   a.u = u;
   a.omr = p->d_omr;
   a.omc = p->d_omc;
   return a;
+}
+
+cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s) {
+  return P->path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
+}
+
+cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s) {
+  return P->path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
+}
+
+int obj_parts(const dv_plan* P) {
+  return P->path == DV_PATH_FFT ? P->tab[1].nH : P->tab[0].nH;
 }
 
 dv::GridArgs grid_args(const dv_plan* p) {
@@ -412,6 +428,38 @@ extern "C" dv_status dv_layout_query(const dv_problem* prob, int32_t* tile_r0, i
 }
 
 namespace dv {
+// Autotuner: times one H (with residual) and one H^T (with the fused step) on
+// the plan's tile stacks for each available path and keeps the faster one.
+static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
+  if (requested == DV_PATH_DIRECT || !P->fft_ok) {
+    P->path = DV_PATH_DIRECT;
+    return DV_OK;
+  }
+  if (requested == DV_PATH_FFT) {
+    P->path = DV_PATH_FFT;
+    return DV_OK;
+  }
+  const int paths[2] = {DV_PATH_DIRECT, DV_PATH_FFT};
+  for (int k = 0; k < 2; ++k) {
+    P->path = paths[k];
+    double best = 1e30;
+    for (int rep = 0; rep < 4; ++rep) {
+      DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
+      DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_RESID, P->d_w[0], P->d_r, false), s));
+      DV_TRY_CUDA(launch_op_Ht(P, op_args_Ht(P, OP_STEP, P->d_r, P->d_w[1], false, P->d_w[0],
+                                            P->d_u), s));
+      DV_TRY_CUDA(cudaEventRecord(P->ev1, s));
+      DV_TRY_CUDA(cudaEventSynchronize(P->ev1));
+      float ms = 0.f;
+      DV_TRY_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+      if (rep > 0) best = std::min(best, (double)ms);   // first repetition warms up
+    }
+    P->tune_ms[k] = best;
+  }
+  P->path = P->tune_ms[1] < P->tune_ms[0] ? DV_PATH_FFT : DV_PATH_DIRECT;
+  return DV_OK;
+}
+
 static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) {
   Layout L;
   DV_TRY(validate_and_layout(prob, L));
@@ -420,8 +468,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
                 prob->precision);
   if (prob->use_warmstart)
     return fail(DV_ERR_UNSUPPORTED, "the learned warm start is not available in this build");
-  if (prob->path == DV_PATH_FFT)
-    return fail(DV_ERR_UNSUPPORTED, "the FFT operator path is not available in this build");
+  if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
+    return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
 
   P->prob = *prob;
   P->prob.psfs = nullptr;
@@ -440,6 +488,12 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   P->n_tc = prob->n_tc;
   P->T = P->n_tr * P->n_tc;
   P->path = DV_PATH_DIRECT;
+  P->fft_ok = prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
+  {
+    int dev = 0;
+    DV_TRY_CUDA(cudaGetDevice(&dev));
+    DV_TRY_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, dev));
+  }
   P->yr0 = L.yr0;
   P->yr1 = L.yr1;
   P->yc0 = L.yc0;
@@ -521,19 +575,44 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   // host copy of the global tile for work-table construction
   std::vector<TileDesc> gtiles{gt};
 
+  // work tables: direct path always, FFT path when K allows it
   std::vector<WorkItem> w;
-  make_work(P->h_tiles, false, K, L, w);
-  P->nH = (int)w.size();
-  DV_TRY(upload(P, &P->d_workH, w.data(), w.size(), s));
-  make_work(P->h_tiles, true, K, L, w);
-  P->nHt = (int)w.size();
-  DV_TRY(upload(P, &P->d_workHt, w.data(), w.size(), s));
-  make_work(gtiles, false, K, L, w);
-  P->nHg = (int)w.size();
-  DV_TRY(upload(P, &P->d_workHg, w.data(), w.size(), s));
-  make_work(gtiles, true, K, L, w);
-  P->nHtg = (int)w.size();
-  DV_TRY(upload(P, &P->d_workHtg, w.data(), w.size(), s));
+  for (int k = 0; k < (P->fft_ok ? 2 : 1); ++k) {
+    const int bm = k == 0 ? direct_tile_m() : fft_block(K);
+    const int bn = k == 0 ? direct_tile_n() : fft_block(K);
+    OpTables& tb = P->tab[k];
+    // FFT items are handed out dynamically: heaviest (most PSF pairs) first
+    auto order = [&](std::vector<WorkItem>& v) {
+      if (k == 1)
+        std::stable_sort(v.begin(), v.end(), [](const WorkItem& x, const WorkItem& y) {
+          return (x.a_hi - x.a_lo + 1) * (x.b_hi - x.b_lo + 1) + 1 >
+                 (y.a_hi - y.a_lo + 1) * (y.b_hi - y.b_lo + 1) + 1;
+        });
+    };
+    make_work(P->h_tiles, false, K, L, bm, bn, w);
+    order(w);
+    tb.nH = (int)w.size();
+    DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
+    make_work(P->h_tiles, true, K, L, bm, bn, w);
+    order(w);
+    tb.nHt = (int)w.size();
+    DV_TRY(upload(P, &tb.Ht, w.data(), w.size(), s));
+    make_work(gtiles, false, K, L, bm, bn, w);
+    order(w);
+    tb.nHg = (int)w.size();
+    DV_TRY(upload(P, &tb.Hg, w.data(), w.size(), s));
+    make_work(gtiles, true, K, L, bm, bn, w);
+    order(w);
+    tb.nHtg = (int)w.size();
+    DV_TRY(upload(P, &tb.Htg, w.data(), w.size(), s));
+  }
+  if (P->fft_ok) {
+    DV_TRY(alloc(P, &P->d_counter, 2));
+    std::vector<float2> spec;
+    fft_spectra(prob->psfs, G, K, spec);
+    DV_TRY(upload(P, &P->d_spec, spec.data(), spec.size(), s));
+    DV_TRY_CUDA(fft_prepare());
+  }
 
   // tiles covering each global x row / column (at most two)
   std::vector<int2> rc(P->nxr, make_int2(-1, -1)), cc(P->nxc, make_int2(-1, -1));
@@ -561,7 +640,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   DV_TRY(alloc(P, &P->d_xg, (size_t)P->nxr * P->nxc));
   const int64_t ncons = consensus_blocks(P->nxr, P->nxc);
   const int64_t nhub = huber_blocks(P->T, P->max_nxr, P->max_nxc);
-  P->n_part = P->nH + nhub + 2 * ncons;
+  P->n_part = std::max(P->tab[0].nH, P->tab[1].nH) + nhub + 2 * ncons;
   DV_TRY(alloc(P, &P->d_part, (size_t)P->n_part));
   DV_TRY(alloc(P, &P->d_scal, 8));
   DV_TRY_CUDA(cudaMallocHost((void**)&P->h_scal, 8 * sizeof(double)));
@@ -569,6 +648,9 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   DV_TRY_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   DV_TRY_CUDA(cudaEventCreate(&P->ev0));
   DV_TRY_CUDA(cudaEventCreate(&P->ev1));
+  DV_TRY_CUDA(cudaMemsetAsync(P->d_y, 0, (size_t)P->hy * P->wy * sizeof(float), s));
+  DV_TRY_CUDA(cudaMemsetAsync(P->d_r, 0, (size_t)P->ystack * sizeof(float), s));
+  DV_TRY(choose_path(P, prob->path, s));
   DV_TRY_CUDA(cudaStreamSynchronize(s));
   return DV_OK;
 }
@@ -601,7 +683,9 @@ dv_status release(dv_plan* P) {
   for (cudaEvent_t e : P->timer.pool) cudaEventDestroy(e);
   for (cudaEvent_t e : P->timer.placeholders) cudaEventDestroy(e);
   void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
-                  P->d_tiles, P->d_gtile, P->d_workH, P->d_workHt, P->d_workHg, P->d_workHtg,
+                  P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
+                  P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
+                  P->d_spec, P->d_counter,
                   P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
@@ -632,5 +716,7 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->tau_min = *std::min_element(P->tau.begin(), P->tau.end());
   info->tau_max = *std::max_element(P->tau.begin(), P->tau.end());
   info->kernel_launches = P->launches;
+  info->tune_ms_direct = P->tune_ms[0];
+  info->tune_ms_fft = P->tune_ms[1];
   return DV_OK;
 }

@@ -64,7 +64,8 @@ class dv_plan_info(C.Structure):
     _fields_ = [("nx_r", C.c_int32), ("nx_c", C.c_int32), ("n_tiles", C.c_int32),
                 ("path", C.c_int32), ("stack_elems", C.c_int64), ("device_bytes", C.c_int64),
                 ("tau_min", C.c_double), ("tau_max", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("tune_ms_direct", C.c_double),
+                ("tune_ms_fft", C.c_double)]
 
 
 _vp = C.c_void_p

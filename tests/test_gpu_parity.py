@@ -21,14 +21,15 @@ def env():
     return need_gpu()
 
 
-def _apply_both(env, hy, wy, K, G, seed, negative=False, weights=None):
+def _apply_both(env, hy, wy, K, G, seed, negative=False, weights=None, path=1):
     torch, dv = env
     g = np.random.default_rng(seed)
     psfs = random_psfs(g, G, K, negative)
     nxr, nxc = hy + K - 1, wy + K - 1
     x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
     r = g.standard_normal((hy, wy)).astype(np.float32)
-    plan = dv.Plan(hy, wy, psfs, weights=weights)
+    plan = dv.Plan(hy, wy, psfs, weights=weights, path=path)
+    assert plan.info.path == path
     yd = plan.apply_H(torch.from_numpy(x).cuda())
     gd = plan.apply_Ht(torch.from_numpy(r).cuda())
     torch.cuda.synchronize()
@@ -42,22 +43,28 @@ def _apply_both(env, hy, wy, K, G, seed, negative=False, weights=None):
     return yd.cpu().numpy(), y_ref, gd.cpu().numpy(), g_ref, x, r
 
 
+DIRECT, FFT = 1, 2
+
+
+@pytest.mark.parametrize("path", [DIRECT, FFT])
 @pytest.mark.parametrize("hy,wy,K,G", [
-    (150, 133, 3, (3, 4)),     # several 64x64 blocks, ragged tails
+    (150, 133, 3, (3, 4)),     # several blocks, ragged tails
     (130, 70, 9, (3, 3)),
-    (97, 140, 11, (2, 5)),     # run-time K kernel
+    (97, 140, 11, (2, 5)),     # run-time K kernel (direct)
     (200, 180, 31, (4, 3)),
+    (250, 301, 31, (5, 6)),    # several 98x98 FFT blocks, straddling PSF cells
     (70, 75, 63, (2, 2)),
     (40, 33, 1, (2, 2)),       # 1x1 PSFs: H is pointwise, x and y share a size
     (66, 64, 5, (1, 1)),       # a single PSF: plain convolution
 ])
-def test_operator_matches_oracle(env, hy, wy, K, G):
-    yd, y_ref, gd, g_ref, x, r = _apply_both(env, hy, wy, K, G, seed=K * 7 + hy)
+def test_operator_matches_oracle(env, hy, wy, K, G, path):
+    yd, y_ref, gd, g_ref, x, r = _apply_both(env, hy, wy, K, G, seed=K * 7 + hy, path=path)
     assert rel_l2(yd, y_ref) <= OP_TOL
     assert rel_l2(gd, g_ref) <= OP_TOL
 
 
-def test_operator_signed_psfs_and_separable_weights(env):
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_operator_signed_psfs_and_separable_weights(env, path):
     hy, wy, K, G = 90, 101, 7, (3, 3)
     g = np.random.default_rng(5)
     nxr, nxc = hy + K - 1, wy + K - 1
@@ -66,13 +73,15 @@ def test_operator_signed_psfs_and_separable_weights(env):
     wr = np.stack([np.clip(1 - 2 * t, 0, 1), 1 - np.abs(2 * t - 1), np.clip(2 * t - 1, 0, 1)])
     wc = O.bilinear_weights(nxc, 3) * 0.8
     yd, y_ref, gd, g_ref, *_ = _apply_both(env, hy, wy, K, G, 5, negative=True,
-                                           weights=(wr.astype(np.float32), wc.astype(np.float32)))
+                                           weights=(wr.astype(np.float32), wc.astype(np.float32)),
+                                           path=path)
     assert rel_l2(yd, y_ref) <= OP_TOL
     assert rel_l2(gd, g_ref) <= OP_TOL
 
 
-def test_adjoint_identity_on_gpu(env):
-    yd, _, gd, _, x, r = _apply_both(env, 123, 77, 9, (3, 2), seed=99)
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_adjoint_identity_on_gpu(env, path):
+    yd, _, gd, _, x, r = _apply_both(env, 123, 77, 9, (3, 2), seed=99, path=path)
     lhs = np.vdot(yd.astype(np.float64), r.astype(np.float64))
     rhs = np.vdot(x.astype(np.float64), gd.astype(np.float64))
     assert abs(lhs - rhs) <= 1e-5 * np.linalg.norm(yd) * np.linalg.norm(r)
@@ -90,9 +99,10 @@ def _gpu_solve(env, w, psfs, y, n_outer, n_inner, use_graphs=1, x0=None, **kw):
     return plan, xd.cpu().numpy(), st
 
 
-def test_short_solve_matches_oracle(env):
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_short_solve_matches_oracle(env, path):
     w, psfs, y, _ = workload_case("disks128")
-    plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 2)
+    plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 2, path=path)
     lay, xr, info = oracle_solve(w, psfs, y, 3, 2)
     assert rel_l2(xd, xr) <= 1e-5
     F, data, prior = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam,
@@ -106,10 +116,11 @@ def test_short_solve_matches_oracle(env):
     plan.close()
 
 
-def test_full_small_workload_matches_oracle(env):
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_full_small_workload_matches_oracle(env, path):
     """The 128x128 workload, 30 consensus iterations x 10 inner steps."""
     w, psfs, y, _ = workload_case("disks128")
-    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner)
+    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, path=path)
     lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
     assert rel_l2(xd, xr) <= 1e-3
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
@@ -205,7 +216,8 @@ def test_edge_cases_match_oracle(env, case):
     plan.close()
 
 
-def test_full_size_tile_step_matches_oracle(env):
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_full_size_tile_step_matches_oracle(env, path):
     """The 2048x2048 star-field workload in the benchmark's launch configuration:
     one inner step and one consensus step on all 16 tiles; an interior tile's
     x_i is compared element by element with the oracle's Local-Solver step."""
@@ -217,7 +229,8 @@ def test_full_size_tile_step_matches_oracle(env):
     y = (scene_for(w)[15:-15, 15:-15] * 0.9 +
          gaussian_noise((w.hy, w.wy), w.noise_sigma, w.noise_seed)).astype(np.float32)
     plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
-                   delta=w.delta, gamma=w.gamma, n_outer=1, n_inner=1)
+                   delta=w.delta, gamma=w.gamma, n_outer=1, n_inner=1, path=path)
+    assert plan.info.path == path
     plan.solve(torch.from_numpy(y).cuda(), stats=False)
     xs = torch.empty(plan.info.stack_elems, device="cuda")
     us = torch.empty_like(xs)
@@ -263,4 +276,22 @@ def test_kernel_timing_counts(env, use_graphs):
         ms, cnt = dv.dv_plan_kernel_time(plan.handle, kind)
         assert cnt == n and ms > 0.0
     dv.dv_plan_set_timing(plan.handle, 0)
+    plan.close()
+
+
+def test_autotuner_times_both_paths_and_keeps_the_faster(env):
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, path=0)
+    i = plan.info
+    assert i.tune_ms_direct > 0 and i.tune_ms_fft > 0
+    assert i.path == (FFT if i.tune_ms_fft < i.tune_ms_direct else DIRECT)
+    plan.close()
+    # a PSF too large for 128-point blocks keeps the direct path
+    g = np.random.default_rng(0)
+    big = random_psfs(g, (1, 1), 101)
+    plan = dv.Plan(40, 40, big, path=0)
+    assert plan.info.path == DIRECT and plan.info.tune_ms_fft == 0
+    with pytest.raises(dv.DVError):
+        dv.Plan(40, 40, big, path=FFT)
     plan.close()
