@@ -171,18 +171,21 @@ __device__ __forceinline__ void row_inv(float2* A, const float2* sTw, int row_lo
 }
 
 // ---------------------------------------------------------------------------
-// Column pass with the spectral product fused in: forward 128-point
-// transforms of the 128 column positions, multiplication by F(kr, c), inverse
-// transforms; rows stay in natural order (n1 + 16 n2) throughout.
-// F(kr, c) = combination of the pair's permuted spectra h1[kr*S + c], h2[...].
+// Column pass: forward 128-point transforms of the 128 column positions,
+// spectral product, inverse transforms; rows stay in natural order (n1 + 16 n2).
+// Split in three steps so that spectra can be kept across PSF pairs in a
+// per-CTA scratch spectrum (scr, [kr][c] layout, written and read back by the
+// same thread only):
+//   col_fwd1: 8-point DFTs over n2 and twiddles (tasks (c, n1)).
+//   col_mid:  16-point DFT over n1 (or the stored spectrum), product with
+//             F(kr, c) built from the pair's permuted spectra h1, h2, optional
+//             accumulation through scr, inverse 16-point DFT (tasks (c, k2)).
+//   col_inv3: inverse 8-point DFTs over k2 back to natural rows.
 // ---------------------------------------------------------------------------
-template <bool ADJ>
-__device__ __forceinline__ void col_conv(float2* A, const float2* sTw, const float2* __restrict__ h1,
-                                         const float2* __restrict__ h2) {
+__device__ __forceinline__ void col_fwd1(float2* A, const float2* sTw) {
   const int c = threadIdx.x & (S - 1);
   const int p = (c & 15) + 17 * (c >> 4);
   const int t0 = threadIdx.x >> 7;   // 0..3, uniform in a warp
-  // step 1: tasks (c, n1 = t0 + 4 j): 8-point DFT over n2, twiddle
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     const int n1 = t0 + 4 * j;
@@ -194,14 +197,37 @@ __device__ __forceinline__ void col_conv(float2* A, const float2* sTw, const flo
     for (int k2 = 0; k2 < 8; ++k2) A[(n1 + 16 * k2) * P + p] = k2 ? cmul(v[k2], sTw[n1 * k2]) : v[k2];
   }
   __syncthreads();
-  // step 2: tasks (c, k2 = t0 + 4 j): DFT over n1, product, inverse DFT over k1
+}
+
+// load_spec:  take the column spectrum from scr instead of transforming A
+// store_spec: save the column spectrum to scr before the product
+// accum_in:   add the spectrum accumulated in scr to the product
+// final:      run the inverse transform into A; otherwise save the product
+//             (plus accumulation) to scr and stop
+template <bool ADJ>
+__device__ __forceinline__ void col_mid(float2* A, const float2* sTw, const float2* __restrict__ h1,
+                                        const float2* __restrict__ h2, float2* __restrict__ scr,
+                                        bool load_spec, bool store_spec, bool accum_in,
+                                        bool final) {
+  const int c = threadIdx.x & (S - 1);
+  const int p = (c & 15) + 17 * (c >> 4);
+  const int t0 = threadIdx.x >> 7;
 #pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     const int k2 = t0 + 4 * j;
     float2 u[16];
+    if (load_spec) {
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) u[n1] = A[(n1 + 16 * k2) * P + p];
-    dft<16, false>(u);
+      for (int k1 = 0; k1 < 16; ++k1) u[k1] = scr[(k2 + 8 * k1) * S + c];
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) u[n1] = A[(n1 + 16 * k2) * P + p];
+      dft<16, false>(u);
+      if (store_spec) {
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) scr[(k2 + 8 * k1) * S + c] = u[k1];
+      }
+    }
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) {
       const int kr = k2 + 8 * k1;
@@ -210,6 +236,12 @@ __device__ __forceinline__ void col_conv(float2* A, const float2* sTw, const flo
       // H:   F = Hh1 - i Hh2          H^T: F = conj(Hh1) + i conj(Hh2)
       const float2 f = ADJ ? make_float2(a.x + b.y, b.x - a.y) : make_float2(a.x + b.y, a.y - b.x);
       u[k1] = cmul(u[k1], f);
+      if (accum_in) u[k1] = cadd(u[k1], scr[kr * S + c]);
+    }
+    if (!final) {
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) scr[(k2 + 8 * k1) * S + c] = u[k1];
+      continue;
     }
     dft<16, true>(u);
 #pragma unroll
@@ -219,7 +251,12 @@ __device__ __forceinline__ void col_conv(float2* A, const float2* sTw, const flo
     }
   }
   __syncthreads();
-  // step 3: tasks (c, n1): inverse 8-point DFT over k2 -> natural rows
+}
+
+__device__ __forceinline__ void col_inv3(float2* A) {
+  const int c = threadIdx.x & (S - 1);
+  const int p = (c & 15) + 17 * (c >> 4);
+  const int t0 = threadIdx.x >> 7;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     const int n1 = t0 + 4 * j;
@@ -259,7 +296,7 @@ struct PairSched {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT, 1) fft_H_kernel(const OpArgs A) {
   extern __shared__ __align__(16) float2 buf[];
-  float* acc = reinterpret_cast<float*>(buf + S * P);   // b x b outputs, thread-owned slots
+  float2* scr = A.scratch + (size_t)blockIdx.x * S * S;  // this CTA's spectrum accumulator
   __shared__ float sw[4][S];
   __shared__ float2 sTw[S];
   __shared__ double red[NT / 32];
@@ -287,13 +324,16 @@ __global__ void __launch_bounds__(NT, 1) fft_H_kernel(const OpArgs A) {
     const int nb = wi.b_hi - wi.b_lo + 1;
     const int np = (wi.a_hi - wi.a_lo + 1) * nb;
     const PairSched ps{np, nb};
-    for (int e = threadIdx.x; e < b * b; e += NT) acc[e] = 0.f;
-    __syncthreads();
+    if (np == 0) {   // no PSF touches the block: the output is zero
+      for (int e = threadIdx.x; e < S * P; e += NT) buf[e] = make_float2(0.f, 0.f);
+      __syncthreads();
+    }
 
     for (int j = 0; j < np; j += 2) {
       int a1, b1, a2 = -1, b2 = -1;
       ps.psf(wi, j, a1, b1);
       const bool two = j + 1 < np;
+      const bool last = j + 2 >= np;
       if (two) ps.psf(wi, j + 1, a2, b2);
       __syncthreads();
       for (int e = threadIdx.x; e < S; e += NT) {
@@ -325,16 +365,14 @@ __global__ void __launch_bounds__(NT, 1) fft_H_kernel(const OpArgs A) {
       }
       __syncthreads();
       row_fwd(buf, sTw);
-      col_conv<false>(buf, sTw, spec + (size_t)(a1 * A.Gc + b1) * S * S,
-                      two ? spec + (size_t)(a2 * A.Gc + b2) * S * S : nullptr);
-      row_inv(buf, sTw, K - 1, b);
-      {
-        const int jj = threadIdx.x & (S - 1), i0 = threadIdx.x >> 7;
-        if (jj < b) {
-          const float2* srcp = buf + (i0 + K - 1) * P + pos(jj + K - 1);
-          float* a = acc + i0 * b + jj;
-          for (int i = i0; i < b; i += 4, srcp += 4 * P, a += 4 * b) *a += srcp->x;
-        }
+      col_fwd1(buf, sTw);
+      // sum over pairs of FFT(w1 x + i w2 x) (Hh1 - i Hh2) in scr; one inverse at the end
+      col_mid<false>(buf, sTw, spec + (size_t)(a1 * A.Gc + b1) * S * S,
+                     two ? spec + (size_t)(a2 * A.Gc + b2) * S * S : nullptr, scr, false, false,
+                     j > 0, last);
+      if (last) {
+        col_inv3(buf);
+        row_inv(buf, sTw, K - 1, b);
       }
     }
 
@@ -347,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1) fft_H_kernel(const OpArgs A) {
         for (int il = i0; il < b; il += 4) {
           const int i = wi.r0 + il;
           if (i >= td.nyr) break;
-          const float v = acc[il * b + jl];
+          const float v = buf[(il + K - 1) * P + pos(jl + K - 1)].x;
           if (A.mode == OP_PLAIN) {
             A.out[td.yoff + (int64_t)i * td.ypitch + jj] = v;
           } else {
@@ -392,6 +430,7 @@ __device__ __forceinline__ void huber_p(const float* sW, int SPW, int li, int lj
 __global__ void __launch_bounds__(NT, 1) fft_Ht_kernel(const OpArgs A) {
   extern __shared__ __align__(16) float2 buf[];
   float* g = reinterpret_cast<float*>(buf + S * P);     // b x b outputs, thread-owned slots
+  float2* scr = A.scratch + (size_t)blockIdx.x * S * S;  // this CTA's spectrum of r
   __shared__ float2 sTw[S];
   __shared__ float sw[4][S];
   const int K = A.K, b = S - K + 1;
@@ -438,7 +477,9 @@ __global__ void __launch_bounds__(NT, 1) fft_Ht_kernel(const OpArgs A) {
         sw[2][e] = (rin && two) ? wsel(tr, a2) : 0.f;
         sw[3][e] = (cin && two) ? wsel(tc, b2) : 0.f;
       }
-      {
+      const float2* h1 = spec + (size_t)(a1 * A.Gc + b1) * S * S;
+      const float2* h2 = two ? spec + (size_t)(a2 * A.Gc + b2) * S * S : nullptr;
+      if (j == 0) {
         // thread -> column n, rows m = m0 + 4 k of the residual region
         const int n = threadIdx.x & (S - 1), m0 = threadIdx.x >> 7;
         const int rx = wi.c0 - (K - 1) + n;
@@ -454,11 +495,15 @@ __global__ void __launch_bounds__(NT, 1) fft_Ht_kernel(const OpArgs A) {
           if (cin && ry >= 0 && ry < td.nyr) v = *src;
           *dst = make_float2(v, 0.f);
         }
+        __syncthreads();
+        row_fwd(buf, sTw);
+        col_fwd1(buf, sTw);
+        col_mid<true>(buf, sTw, h1, h2, scr, false, np > 2, false, true);
+      } else {
+        // FFT(r) of this block was kept in scr by the first pair
+        col_mid<true>(buf, sTw, h1, h2, scr, true, false, false, true);
       }
-      __syncthreads();
-      row_fwd(buf, sTw);
-      col_conv<true>(buf, sTw, spec + (size_t)(a1 * A.Gc + b1) * S * S,
-                     two ? spec + (size_t)(a2 * A.Gc + b2) * S * S : nullptr);
+      col_inv3(buf);
       row_inv(buf, sTw, 0, b);
       {
         const int jj = threadIdx.x & (S - 1), i0 = threadIdx.x >> 7;
@@ -514,6 +559,7 @@ __global__ void __launch_bounds__(NT, 1) fft_Ht_kernel(const OpArgs A) {
   }
 }
 
+constexpr size_t kSmemH = sizeof(float2) * (size_t)S * P;
 constexpr size_t kSmem = sizeof(float2) * (size_t)S * P + sizeof(float) * (size_t)BMAX * BMAX;
 
 }  // namespace
@@ -534,7 +580,7 @@ cudaError_t fft_prepare() {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_w128, w, sizeof w);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(fft_H_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  e = cudaFuncSetAttribute(fft_H_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemH);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(fft_Ht_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kSmem);
@@ -587,7 +633,7 @@ cudaError_t launch_fft_H(const OpArgs& a, cudaStream_t s, int grid) {
   if (a.n_work <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  fft_H_kernel<<<std::min(grid, a.n_work), NT, kSmem, s>>>(a);
+  fft_H_kernel<<<std::min(grid, a.n_work), NT, kSmemH, s>>>(a);
   return cudaGetLastError();
 }
 

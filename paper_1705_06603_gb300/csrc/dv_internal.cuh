@@ -107,6 +107,7 @@ struct OpArgs {
   int32_t pad2;
   const float2* spec;     // FFT path: [Gr*Gc][S][S] PSF spectra / S^2
   int* counter;           // FFT path: work counter, zeroed before each launch
+  float2* scratch;        // FFT path: one S x S spectrum per CTA of the launch grid
 };
 
 // Streaming kernels' shared view of the tile grid
@@ -213,6 +214,7 @@ struct dv_plan {
   bool fft_ok = false;
   float2* d_spec = nullptr;
   int* d_counter = nullptr;        // [0] H launches, [1] H^T launches (FFT path)
+  float2* d_fft_scr = nullptr;     // FFT path: n_sm spectra of S x S
   int n_sm = 0;
   double tune_ms[2] = {0.0, 0.0};   // autotuner: one H + one H^T apply per path
   std::vector<int> yr0, yr1, yc0, yc1;

@@ -335,6 +335,7 @@ dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bo
   a.partials = p->d_part;
   a.spec = p->d_spec;
   a.counter = p->d_counter;
+  a.scratch = p->d_fft_scr;
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
@@ -608,6 +609,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   }
   if (P->fft_ok) {
     DV_TRY(alloc(P, &P->d_counter, 2));
+    DV_TRY(alloc(P, &P->d_fft_scr, (size_t)P->n_sm * fft_size() * fft_size()));
     std::vector<float2> spec;
     fft_spectra(prob->psfs, G, K, spec);
     DV_TRY(upload(P, &P->d_spec, spec.data(), spec.size(), s));
@@ -685,7 +687,7 @@ dv_status release(dv_plan* P) {
   void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
-                  P->d_spec, P->d_counter,
+                  P->d_spec, P->d_counter, P->d_fft_scr,
                   P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
