@@ -128,7 +128,9 @@ typedef struct dv_problem {
   int32_t check_every;
   double target_objective;
   int32_t use_graphs;      /* 1: replay each outer iteration as a CUDA graph */
-  int32_t reserved[7];
+  /* noise standard deviation of y, an input of the learned warm start only */
+  double noise_sigma;
+  int32_t reserved[5];
 } dv_problem;
 
 typedef struct dv_stats {
@@ -144,6 +146,20 @@ typedef struct dv_stats {
 } dv_stats;
 
 typedef struct dv_plan dv_plan;
+
+/* Learned warm start (an addition to the paper's method, which starts from a
+ * given guess, Algorithm 1): a 6-layer 3x3 convolutional network with 32
+ * channels, bfloat16 weights and activations and FP32 accumulation, maps
+ * DV_CNN_IN_CH feature maps of the x grid -- the observed image edge-replicated
+ * by K/2; RMS radius / 8 px, 10 x peak and fraction of |h| beyond 3 px of the
+ * PSFs, interpolated with the weights w_p; 100 x noise_sigma -- to a
+ * correction d, and the solve starts from x0 = max(0, y_pad + d).  Network
+ * tensors are NHWC float32 at the interface: input [N][H][W][5], output
+ * [N][H][W].  Parameters (float32, the layout of dv_cnn_get_params) are, for
+ * each layer l in order, w_l[3][3][C_in][C_out] (correlation taps) then
+ * b_l[C_out], with C = 5, 32, 32, 32, 32, 32, 1. */
+#define DV_CNN_IN_CH 5
+typedef struct dv_cnn dv_cnn;
 
 /* Fills *p with defaults: the paper's rho = 1 and outer/inner schedule shape,
  * lambda = 1e-3, delta = 1/60, gamma = 0.4, 30 x 10 iterations, one tile,
@@ -173,8 +189,9 @@ dv_status dv_apply_H(dv_plan* plan, const float* x_dev, float* y_dev, void* stre
 dv_status dv_apply_Ht(dv_plan* plan, const float* r_dev, float* g_dev, void* stream);
 
 /* Algorithm 1 on the observed image y_dev [hy][wy]: starts from
- * x_i = u_i = C_i x0 with x0 = x0_dev [(hy+K-1)][(wy+K-1)] if given, else y
- * edge-replicated by K/2 (or the learned warm start when enabled), runs the
+ * x_i = u_i = C_i x0 with x0 = x0_dev [(hy+K-1)][(wy+K-1)] if given, else the
+ * learned warm start (use_warmstart = 1, network attached with
+ * dv_plan_set_warmstart), else y edge-replicated by K/2; runs the
  * outer/inner schedule of the problem and writes x_hat to x_out_dev
  * [(hy+K-1)][(wy+K-1)].  If stats is not NULL the call synchronises the stream
  * and fills it (one extra operator pass for the objective).  The plan keeps
@@ -247,6 +264,33 @@ dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int
 #define DV_NOALLOC_MAX_BLOCKS 65536
 dv_status dv_prior_value_noalloc(const float* x_dev, int32_t rows, int32_t cols, double delta,
                                  double* value_dev, void* stream);
+
+/* Creates the warm-start network (width 32, depth 6 are the only supported
+ * values) with He-normal weights drawn from seed; synchronises stream. */
+dv_status dv_cnn_create(int32_t width, int32_t depth, uint64_t seed, void* stream, dv_cnn** out);
+int64_t dv_cnn_param_count(const dv_cnn* cnn);
+/* float32 parameters to / from host memory (n = dv_cnn_param_count); set also
+ * resets the Adam state.  get also returns the number of training steps. */
+dv_status dv_cnn_get_params(const dv_cnn* cnn, float* host, int64_t n, int64_t* step);
+dv_status dv_cnn_set_params(dv_cnn* cnn, const float* host, int64_t n, void* stream);
+/* out_dev [N][H][W] = network(in_dev [N][H][W][5]) (zero padding at the borders). */
+dv_status dv_cnn_forward(dv_cnn* cnn, const float* in_dev, int32_t N, int32_t H, int32_t W,
+                         float* out_dev, void* stream);
+/* Loss 1/2 mean((out - target)^2) and its gradient (float32, parameter layout)
+ * for one batch, without updating; synchronises stream. */
+dv_status dv_cnn_gradients(dv_cnn* cnn, const float* in_dev, const float* target_dev, int32_t N,
+                           int32_t H, int32_t W, float* grad_host, double* loss_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on one
+ * batch; loss_host (optional) receives the loss before the step (synchronises). */
+dv_status dv_cnn_train_step(dv_cnn* cnn, const float* in_dev, const float* target_dev, int32_t N,
+                            int32_t H, int32_t W, float lr, double* loss_host, void* stream);
+dv_status dv_cnn_destroy(dv_cnn* cnn);
+/* Attaches a network to the plan (borrowed; keep it alive while the plan
+ * uses it).  With use_warmstart = 1 and no x0, dv_consensus_solve starts from
+ * the network's x0. */
+dv_status dv_plan_set_warmstart(dv_plan* plan, dv_cnn* cnn);
+/* feat_dev [(hy+K-1)][(wy+K-1)][5] = the warm-start features of y_dev. */
+dv_status dv_warmstart_features(dv_plan* plan, const float* y_dev, float* feat_dev, void* stream);
 
 /* Releases everything the plan owns.  NULL is accepted. */
 dv_status dv_destroy(dv_plan* plan);

@@ -1,0 +1,689 @@
+// Learned warm start of Algorithm 1: a small convolutional network that maps
+// the observed image and PSF descriptor maps to a correction of the start
+// image, x0 = max(0, y_pad + net(features)).  Hand-written training and
+// inference kernels:
+//   - 3x3 convolutions with zero padding, NHWC tensors, bfloat16 weights and
+//     activations, FP32 accumulation (CUDA cores);
+//   - backward data (the forward kernel on flipped, transposed weights, with
+//     the ReLU mask of the layer input fused in), backward weights (per-tile
+//     partial sums reduced in a fixed order), mean-squared-error loss, Adam.
+// Architecture: 5 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, ReLU between
+// layers, none after the last.  The first layer's 5 input channels are padded
+// to 8 with zeros.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "dv_internal.cuh"
+
+namespace dv {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int TS = 16;             // output tile side
+constexpr int HALO = TS + 2;
+constexpr int NTH = 128;           // threads per conv CTA: 16 columns x 8 row pairs
+constexpr int WID = 32;            // hidden width
+constexpr int CIN0 = 8;            // padded input channels
+constexpr int NLAYER = 6;
+constexpr int NB = 256;
+
+__host__ __device__ constexpr int layer_cin(int l) { return l == 0 ? CIN0 : WID; }
+__host__ __device__ constexpr int layer_cout(int l) { return l == NLAYER - 1 ? 1 : WID; }
+constexpr int layer_cin_logical(int l) { return l == 0 ? DV_CNN_IN_CH : WID; }
+
+__device__ __forceinline__ float tof(const bf16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float tof(const float v) { return v; }
+__device__ __forceinline__ void store(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store(float* p, float v) { *p = v; }
+
+size_t conv_smem(int cin, int cout) {
+  return sizeof(float) * ((size_t)cin * HALO * HALO + (size_t)9 * cin * cout + cout);
+}
+
+// out[n,y,x,o] = act(b[o] + sum_{dy,dx,i} w[dy*3+dx][i][o] in[n, y+dy-1, x+dx-1, i])
+// optionally multiplied by (mask[n,y,x,o] > 0).  Each thread computes the
+// COUT outputs of two vertically adjacent pixels of a 16x16 tile.
+template <int CIN, int COUT, typename TIN, typename TOUT, bool RELU, bool MASK>
+__global__ void __launch_bounds__(NTH) conv_kernel(const TIN* __restrict__ in,
+                                                   const float* __restrict__ w,
+                                                   const float* __restrict__ bias,
+                                                   const bf16* __restrict__ mask,
+                                                   TOUT* __restrict__ out, int H, int W) {
+  extern __shared__ __align__(16) float smem[];
+  float* sx = smem;                          // [CIN][HALO*HALO], channel-major
+  float* sw = sx + CIN * HALO * HALO;        // [9][CIN][COUT]
+  float* sb = sw + 9 * CIN * COUT;
+  const int n = blockIdx.z, y0 = blockIdx.y * TS, x0 = blockIdx.x * TS;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < 9 * CIN * COUT; e += NTH) sw[e] = w[e];
+  for (int e = tid; e < COUT; e += NTH) sb[e] = bias ? bias[e] : 0.f;
+  for (int e = tid; e < HALO * HALO * CIN; e += NTH) {
+    const int pix = e / CIN, ci = e - pix * CIN;
+    const int yy = y0 - 1 + pix / HALO, xx = x0 - 1 + pix % HALO;
+    float v = 0.f;
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = tof(in[(((int64_t)n * H + yy) * W + xx) * CIN + ci]);
+    sx[ci * HALO * HALO + pix] = v;
+  }
+  __syncthreads();
+  const int tx = tid & (TS - 1), ty = (tid >> 4) * 2;
+  float acc0[COUT], acc1[COUT];
+#pragma unroll
+  for (int o = 0; o < COUT; ++o) acc0[o] = acc1[o] = sb[o];
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap - dy * 3;
+    const float* xr = sx + (ty + dy) * HALO + tx + dx;
+#pragma unroll 4
+    for (int ci = 0; ci < CIN; ++ci) {
+      const float v0 = xr[ci * HALO * HALO], v1 = xr[ci * HALO * HALO + HALO];
+      const float* wr = sw + (tap * CIN + ci) * COUT;
+      if constexpr (COUT % 4 == 0) {
+#pragma unroll
+        for (int o = 0; o < COUT; o += 4) {
+          const float4 q = *reinterpret_cast<const float4*>(wr + o);
+          acc0[o] = fmaf(q.x, v0, acc0[o]);
+          acc0[o + 1] = fmaf(q.y, v0, acc0[o + 1]);
+          acc0[o + 2] = fmaf(q.z, v0, acc0[o + 2]);
+          acc0[o + 3] = fmaf(q.w, v0, acc0[o + 3]);
+          acc1[o] = fmaf(q.x, v1, acc1[o]);
+          acc1[o + 1] = fmaf(q.y, v1, acc1[o + 1]);
+          acc1[o + 2] = fmaf(q.z, v1, acc1[o + 2]);
+          acc1[o + 3] = fmaf(q.w, v1, acc1[o + 3]);
+        }
+      } else {
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) {
+          acc0[o] = fmaf(wr[o], v0, acc0[o]);
+          acc1[o] = fmaf(wr[o], v1, acc1[o]);
+        }
+      }
+    }
+  }
+  const int xx = x0 + tx;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int yy = y0 + ty + r;
+    if (yy >= H || xx >= W) continue;
+    const int64_t base = (((int64_t)n * H + yy) * W + xx) * COUT;
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) {
+      float v = r == 0 ? acc0[o] : acc1[o];
+      if (RELU) v = fmaxf(v, 0.f);
+      if (MASK && !(tof(mask[base + o]) > 0.f)) v = 0.f;
+      store(out + base + o, v);
+    }
+  }
+}
+
+// Per 16x16 tile: partial dW[tap][i][o] = sum_p in[p + off(tap)][i] dz[p][o]
+// and partial db[o] = sum_p dz[p][o].  Thread t < 9*CIN owns (tap, i).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NB) wgrad_kernel(const bf16* __restrict__ in,
+                                                   const float* __restrict__ dz,
+                                                   float* __restrict__ part, int H, int W) {
+  extern __shared__ __align__(16) float smem[];
+  float* sx = smem;                        // [CIN][HALO*HALO]
+  float* sd = sx + CIN * HALO * HALO;      // [TS*TS][COUT]
+  const int n = blockIdx.z, y0 = blockIdx.y * TS, x0 = blockIdx.x * TS;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < HALO * HALO * CIN; e += NB) {
+    const int pix = e / CIN, ci = e - pix * CIN;
+    const int yy = y0 - 1 + pix / HALO, xx = x0 - 1 + pix % HALO;
+    float v = 0.f;
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = tof(in[(((int64_t)n * H + yy) * W + xx) * CIN + ci]);
+    sx[ci * HALO * HALO + pix] = v;
+  }
+  for (int e = tid; e < TS * TS * COUT; e += NB) {
+    const int pix = e / COUT, o = e - pix * COUT;
+    const int yy = y0 + pix / TS, xx = x0 + pix % TS;
+    sd[e] = (yy < H && xx < W) ? dz[(((int64_t)n * H + yy) * W + xx) * COUT + o] : 0.f;
+  }
+  __syncthreads();
+  const int nblk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  float* out = part + (int64_t)nblk * (9 * CIN * COUT + COUT);
+  for (int t = tid; t < 9 * CIN; t += NB) {
+    const int tap = t / CIN, ci = t - tap * CIN;
+    const int dy = tap / 3, dx = tap - dy * 3;
+    float acc[COUT];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) acc[o] = 0.f;
+    const float* xr = sx + ci * HALO * HALO + dy * HALO + dx;
+#pragma unroll 2
+    for (int p = 0; p < TS * TS; ++p) {
+      const float v = xr[(p / TS) * HALO + (p % TS)];
+      const float* d = sd + p * COUT;
+#pragma unroll
+      for (int o = 0; o < COUT; ++o) acc[o] = fmaf(v, d[o], acc[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) out[(tap * CIN + ci) * COUT + o] = acc[o];
+  }
+  for (int o = tid; o < COUT; o += NB) {
+    float s = 0.f;
+    for (int p = 0; p < TS * TS; ++p) s += sd[p * COUT + o];
+    out[9 * CIN * COUT + o] = s;
+  }
+}
+
+// grad[k] = sum_{b < nblk} part[b][k] in a fixed order.
+__global__ void reduce_cols_kernel(const float* __restrict__ part, int nblk, int ncol,
+                                   float* __restrict__ grad) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ncol) return;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * ncol + k];
+  grad[k] = s;
+}
+
+// dz = (out - target) / npix; FP64 block partials of (out - target)^2.
+__global__ void __launch_bounds__(NB) mse_kernel(const float* __restrict__ out,
+                                                 const float* __restrict__ target, int64_t n,
+                                                 float* __restrict__ dz, double* __restrict__ part) {
+  __shared__ double red[NB / 32];
+  double acc = 0.0;
+  const float inv = 1.0f / (float)n;
+  for (int64_t i = blockIdx.x * (int64_t)NB + threadIdx.x; i < n; i += (int64_t)gridDim.x * NB) {
+    const float d = out[i] - target[i];
+    dz[i] = d * inv;
+    acc += (double)d * d;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < NB / 32; ++i) s += red[i];
+    part[blockIdx.x] = s;
+  }
+}
+
+__global__ void sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+// Adam on the FP32 master parameters (bias-corrected; t counts from 1).
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Compute copies of one layer's weights, rounded to bfloat16:
+//   wf[tap][i][o]  (forward, i padded to cin_p)
+//   wt[tap][o][i]  (backward data: taps flipped, channels transposed)
+__global__ void pack_kernel(const float* __restrict__ wl, int cin, int cin_p, int cout,
+                            float* __restrict__ wf, float* __restrict__ wt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 9 * cin_p * cout) return;
+  const int tap = e / (cin_p * cout), r = e - tap * cin_p * cout;
+  const int i = r / cout, o = r - i * cout;
+  const float v = i < cin ? __bfloat162float(__float2bfloat16_rn(wl[(tap * cin + i) * cout + o])) : 0.f;
+  wf[e] = v;
+  if (wt) wt[((8 - tap) * cout + o) * cin_p + i] = v;
+}
+
+// FP32 input (n, 5 channels) -> bfloat16 (n, 8 channels, zeros beyond 5).
+__global__ void input_kernel(const float* __restrict__ in, int64_t npix, bf16* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= npix * CIN0) return;
+  const int64_t p = i / CIN0;
+  const int c = (int)(i - p * CIN0);
+  out[i] = __float2bfloat16_rn(c < DV_CNN_IN_CH ? in[p * DV_CNN_IN_CH + c] : 0.f);
+}
+
+// Warm-start features of the global x grid (reading of the inputs in the
+// header): [y edge-replicated, 3 interpolated PSF descriptors, 100 sigma].
+__global__ void features_kernel(const float* __restrict__ y, int hy, int wy, int rad,
+                                const WTab* __restrict__ wrow, const WTab* __restrict__ wcol,
+                                const float* __restrict__ desc, int Gr, int Gc, float sig100,
+                                int nxr, int nxc, float* __restrict__ f) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x, R = blockIdx.y;
+  if (C >= nxc) return;
+  const int64_t o = ((int64_t)R * nxc + C) * DV_CNN_IN_CH;
+  const int ry = min(max(R - rad, 0), hy - 1), rx = min(max(C - rad, 0), wy - 1);
+  f[o] = y[(int64_t)ry * wy + rx];
+  const WTab tr = wrow[R], tc = wcol[C];
+  float m[3] = {0.f, 0.f, 0.f};
+  for (int da = 0; da < 2; ++da) {
+    const int a = tr.a0 + da;
+    if (a >= Gr) continue;
+    const float wa = da ? tr.w1 : tr.w0;
+    for (int db = 0; db < 2; ++db) {
+      const int b = tc.a0 + db;
+      if (b >= Gc) continue;
+      const float wgt = wa * (db ? tc.w1 : tc.w0);
+      for (int k = 0; k < 3; ++k) m[k] = fmaf(wgt, desc[(a * Gc + b) * 3 + k], m[k]);
+    }
+  }
+  f[o + 1] = m[0];
+  f[o + 2] = m[1];
+  f[o + 3] = m[2];
+  f[o + 4] = sig100;
+}
+
+// x0 = max(0, f[., 0] + d) on the global x grid
+__global__ void apply_warm_kernel(const float* __restrict__ f, const float* __restrict__ d,
+                                  int64_t n, float* __restrict__ x0) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x0[i] = fmaxf(0.f, f[i * DV_CNN_IN_CH] + d[i]);
+}
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+}  // namespace dv
+
+struct dv_cnn {
+  int64_t nparam = 0;
+  int64_t off_w[dv::NLAYER], off_b[dv::NLAYER];
+  float* d_p = nullptr;       // FP32 master parameters (logical layout)
+  float* d_g = nullptr;       // gradients
+  float* d_m = nullptr;       // Adam moments
+  float* d_v = nullptr;
+  float* d_wf[dv::NLAYER] = {};  // bfloat16-rounded compute weights
+  float* d_wt[dv::NLAYER] = {};
+  int64_t step = 0;
+  // activation buffers (grown on demand)
+  int64_t cap_pix = 0;
+  dv::bf16* d_act[dv::NLAYER] = {};  // layer inputs: [0] 8 channels, others 32
+  float* d_out = nullptr;
+  float* d_dz[2] = {nullptr, nullptr};
+  float* d_part = nullptr;
+  int64_t cap_part = 0;
+  double* d_lpart = nullptr;
+  double* d_loss = nullptr;
+  double* h_loss = nullptr;
+  bool packed = false;
+};
+
+namespace dv {
+namespace {
+
+template <int CIN, int COUT, typename TIN, typename TOUT, bool RELU, bool MASK>
+cudaError_t conv_launch(const TIN* in, const float* w, const float* b, const bf16* mask, TOUT* out,
+                        int N, int H, int W, cudaStream_t s) {
+  const size_t smem = conv_smem(CIN, COUT);
+  cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, TIN, TOUT, RELU, MASK>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(cdiv(W, TS), cdiv(H, TS), N);
+  conv_kernel<CIN, COUT, TIN, TOUT, RELU, MASK><<<grid, NTH, smem, s>>>(in, w, b, mask, out, H, W);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad_launch(const bf16* in, const float* dz, float* part, float* grad_w, float* grad_b,
+                         int N, int H, int W, cudaStream_t s) {
+  const size_t smem = sizeof(float) * ((size_t)CIN * HALO * HALO + (size_t)TS * TS * COUT);
+  cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN, COUT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(cdiv(W, TS), cdiv(H, TS), N);
+  wgrad_kernel<CIN, COUT><<<grid, NB, smem, s>>>(in, dz, part, H, W);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nblk = grid.x * grid.y * grid.z, ncol = 9 * CIN * COUT + COUT;
+  // columns of the padded layout map to the logical layout: only i < cin is kept
+  (void)grad_w;
+  (void)grad_b;
+  reduce_cols_kernel<<<cdiv(ncol, NB), NB, 0, s>>>(part, nblk, ncol, part + (int64_t)nblk * ncol);
+  return cudaGetLastError();
+}
+
+// Copies a reduced padded-layout gradient (9*cin_p*cout + cout) to the logical layout.
+__global__ void unpad_grad_kernel(const float* __restrict__ src, int cin, int cin_p, int cout,
+                                  float* __restrict__ gw, float* __restrict__ gb) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 9 * cin * cout) {
+    const int tap = e / (cin * cout), r = e - tap * cin * cout;
+    const int i = r / cout, o = r - i * cout;
+    gw[e] = src[(tap * cin_p + i) * cout + o];
+  } else if (e < 9 * cin * cout + cout) {
+    gb[e - 9 * cin * cout] = src[9 * cin_p * cout + (e - 9 * cin * cout)];
+  }
+}
+
+dv_status ensure_capacity(dv_cnn* c, int64_t npix, int64_t nblk) {
+  if (npix > c->cap_pix) {
+    for (int l = 0; l < NLAYER; ++l)
+      if (c->d_act[l]) cudaFree(c->d_act[l]);
+    for (float* p : {c->d_out, c->d_dz[0], c->d_dz[1]})
+      if (p) cudaFree(p);
+    for (int l = 0; l < NLAYER; ++l)
+      DV_TRY_CUDA(cudaMalloc(&c->d_act[l], (size_t)npix * layer_cin(l) * sizeof(bf16)));
+    DV_TRY_CUDA(cudaMalloc(&c->d_out, (size_t)npix * sizeof(float)));
+    DV_TRY_CUDA(cudaMalloc(&c->d_dz[0], (size_t)npix * WID * sizeof(float)));
+    DV_TRY_CUDA(cudaMalloc(&c->d_dz[1], (size_t)npix * WID * sizeof(float)));
+    c->cap_pix = npix;
+  }
+  const int64_t need = nblk * (9 * WID * WID + WID) + (9 * WID * WID + WID);
+  if (need > c->cap_part) {
+    if (c->d_part) cudaFree(c->d_part);
+    DV_TRY_CUDA(cudaMalloc(&c->d_part, (size_t)need * sizeof(float)));
+    c->cap_part = need;
+  }
+  return DV_OK;
+}
+
+dv_status pack(dv_cnn* c, cudaStream_t s) {
+  for (int l = 0; l < NLAYER; ++l) {
+    const int n = 9 * layer_cin(l) * layer_cout(l);
+    pack_kernel<<<cdiv(n, NB), NB, 0, s>>>(c->d_p + c->off_w[l], layer_cin_logical(l), layer_cin(l),
+                                           layer_cout(l), c->d_wf[l], c->d_wt[l]);
+    DV_TRY_CUDA(cudaGetLastError());
+  }
+  c->packed = true;
+  return DV_OK;
+}
+
+// Forward pass on N x H x W pixels; activations kept for the backward pass.
+dv_status forward(dv_cnn* c, const float* in, int N, int H, int W, float* out, cudaStream_t s) {
+  const int64_t npix = (int64_t)N * H * W;
+  DV_TRY(ensure_capacity(c, npix, (int64_t)N * cdiv(H, TS) * cdiv(W, TS)));
+  if (!c->packed) DV_TRY(pack(c, s));
+  input_kernel<<<cdiv(npix * CIN0, NB), NB, 0, s>>>(in, npix, c->d_act[0]);
+  DV_TRY_CUDA(cudaGetLastError());
+  DV_TRY_CUDA((conv_launch<CIN0, WID, bf16, bf16, true, false>(
+      c->d_act[0], c->d_wf[0], c->d_p + c->off_b[0], nullptr, c->d_act[1], N, H, W, s)));
+  for (int l = 1; l < NLAYER - 1; ++l)
+    DV_TRY_CUDA((conv_launch<WID, WID, bf16, bf16, true, false>(
+        c->d_act[l], c->d_wf[l], c->d_p + c->off_b[l], nullptr, c->d_act[l + 1], N, H, W, s)));
+  DV_TRY_CUDA((conv_launch<WID, 1, bf16, float, false, false>(
+      c->d_act[NLAYER - 1], c->d_wf[NLAYER - 1], c->d_p + c->off_b[NLAYER - 1], nullptr,
+      out ? out : c->d_out, N, H, W, s)));
+  return DV_OK;
+}
+
+// Loss and gradients (into d_g) for the last forward pass.
+dv_status backward(dv_cnn* c, const float* target, int N, int H, int W, cudaStream_t s) {
+  const int64_t npix = (int64_t)N * H * W;
+  const int grid = std::min(cdiv(npix, NB), 1024);
+  mse_kernel<<<grid, NB, 0, s>>>(c->d_out, target, npix, c->d_dz[0], c->d_lpart);
+  DV_TRY_CUDA(cudaGetLastError());
+  sum_kernel<<<1, 1, 0, s>>>(c->d_lpart, grid, c->d_loss);
+  DV_TRY_CUDA(cudaGetLastError());
+  const int nblk = N * cdiv(H, TS) * cdiv(W, TS);
+  int cur = 0;   // d_dz[cur] holds dL/dz of layer l
+  for (int l = NLAYER - 1; l >= 0; --l) {
+    const int cin = layer_cin(l), cout = layer_cout(l), ncol = 9 * cin * cout + cout;
+    if (l == NLAYER - 1)
+      DV_TRY_CUDA((wgrad_launch<WID, 1>(c->d_act[l], c->d_dz[cur], c->d_part, nullptr, nullptr, N, H, W, s)));
+    else if (l == 0)
+      DV_TRY_CUDA((wgrad_launch<CIN0, WID>(c->d_act[l], c->d_dz[cur], c->d_part, nullptr, nullptr, N, H, W, s)));
+    else
+      DV_TRY_CUDA((wgrad_launch<WID, WID>(c->d_act[l], c->d_dz[cur], c->d_part, nullptr, nullptr, N, H, W, s)));
+    unpad_grad_kernel<<<cdiv(ncol, NB), NB, 0, s>>>(c->d_part + (int64_t)nblk * ncol,
+                                                    layer_cin_logical(l), cin, cout,
+                                                    c->d_g + c->off_w[l], c->d_g + c->off_b[l]);
+    DV_TRY_CUDA(cudaGetLastError());
+    if (l == 0) break;
+    // dL/dz_{l-1} = (W_l^T dz_l) masked by relu'(z_{l-1}) = (act_l > 0)
+    if (l == NLAYER - 1)
+      DV_TRY_CUDA((conv_launch<1, WID, float, float, false, true>(
+          c->d_dz[cur], c->d_wt[l], nullptr, c->d_act[l], c->d_dz[cur ^ 1], N, H, W, s)));
+    else
+      DV_TRY_CUDA((conv_launch<WID, WID, float, float, false, true>(
+          c->d_dz[cur], c->d_wt[l], nullptr, c->d_act[l], c->d_dz[cur ^ 1], N, H, W, s)));
+    cur ^= 1;
+  }
+  return DV_OK;
+}
+
+dv_status check_shape(int N, int H, int W) {
+  if (N < 1 || H < 1 || W < 1 || H > 65535 * TS || N > 65535)
+    return fail(DV_ERR_INVALID_ARG, "bad network input shape %d x %d x %d", N, H, W);
+  return DV_OK;
+}
+
+}  // namespace
+
+// Forward pass of the whole global x grid in row strips (halo of NLAYER rows,
+// so every kept row is exact); writes x0 = max(0, y_pad + net(features)).
+dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0) {
+  dv_cnn* c = P->cnn;
+  const int nxr = P->nxr, nxc = P->nxc;
+  const int64_t n = (int64_t)nxr * nxc;
+  if (!P->d_feat) {
+    DV_TRY_CUDA(cudaMalloc(&P->d_feat, (size_t)n * DV_CNN_IN_CH * sizeof(float)));
+    DV_TRY_CUDA(cudaMalloc(&P->d_wsd, (size_t)n * sizeof(float)));
+    P->device_bytes += n * (DV_CNN_IN_CH + 1) * sizeof(float);
+  }
+  dim3 grid(cdiv(nxc, NB), nxr);
+  features_kernel<<<grid, NB, 0, s>>>(P->d_y, P->hy, P->wy, P->rad, P->d_wrow, P->d_wcol, P->d_desc,
+                                      P->Gr, P->Gc, (float)(100.0 * P->prob.noise_sigma), nxr, nxc,
+                                      P->d_feat);
+  DV_TRY_CUDA(cudaGetLastError());
+  const int strip = std::max(64, (int)std::min<int64_t>(nxr, (1 << 22) / std::max(nxc, 1)));
+  for (int r0 = 0; r0 < nxr; r0 += strip) {
+    const int r1 = std::min(nxr, r0 + strip);
+    const int a = std::max(0, r0 - NLAYER), b = std::min(nxr, r1 + NLAYER);
+    DV_TRY(forward(c, P->d_feat + (int64_t)a * nxc * DV_CNN_IN_CH, 1, b - a, nxc, nullptr, s));
+    DV_TRY_CUDA(cudaMemcpyAsync(P->d_wsd + (int64_t)r0 * nxc, c->d_out + (int64_t)(r0 - a) * nxc,
+                                (size_t)(r1 - r0) * nxc * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  apply_warm_kernel<<<cdiv(n, NB), NB, 0, s>>>(P->d_feat, P->d_wsd, n, x0);
+  DV_TRY_CUDA(cudaGetLastError());
+  P->launches += 2 + 7 * cdiv(nxr, strip);
+  return DV_OK;
+}
+
+// Per-PSF descriptors of the warm-start features: RMS radius / 8, 10 x peak,
+// fraction of |h| beyond radius 3 (|h| normalised to unit sum).
+void psf_descriptors(const float* psfs, int G, int K, std::vector<float>& out) {
+  out.assign((size_t)G * 3, 0.f);
+  const int c = K / 2;
+  for (int g = 0; g < G; ++g) {
+    const float* h = psfs + (size_t)g * K * K;
+    double s = 0.0;
+    for (int k = 0; k < K * K; ++k) s += std::fabs((double)h[k]);
+    if (!(s > 0.0)) continue;
+    double m2 = 0.0, pk = 0.0, wing = 0.0;
+    for (int i = 0; i < K; ++i)
+      for (int j = 0; j < K; ++j) {
+        const double v = std::fabs((double)h[i * K + j]) / s;
+        const int r2 = (i - c) * (i - c) + (j - c) * (j - c);
+        m2 += v * r2;
+        pk = std::max(pk, v);
+        if (r2 > 9) wing += v;
+      }
+    out[(size_t)g * 3 + 0] = (float)(std::sqrt(m2) / 8.0);
+    out[(size_t)g * 3 + 1] = (float)(10.0 * pk);
+    out[(size_t)g * 3 + 2] = (float)wing;
+  }
+}
+
+}  // namespace dv
+
+using namespace dv;
+
+namespace dv {
+namespace {
+void free_cnn(dv_cnn* c) {
+  if (!c) return;
+  for (float* p : {c->d_p, c->d_g, c->d_m, c->d_v, c->d_out, c->d_dz[0], c->d_dz[1], c->d_part})
+    if (p) cudaFree(p);
+  for (int l = 0; l < NLAYER; ++l) {
+    if (c->d_wf[l]) cudaFree(c->d_wf[l]);
+    if (c->d_wt[l]) cudaFree(c->d_wt[l]);
+    if (c->d_act[l]) cudaFree(c->d_act[l]);
+  }
+  if (c->d_lpart) cudaFree(c->d_lpart);
+  if (c->d_loss) cudaFree(c->d_loss);
+  if (c->h_loss) cudaFreeHost(c->h_loss);
+  delete c;
+}
+}  // namespace
+}  // namespace dv
+
+extern "C" dv_status dv_cnn_create(int32_t width, int32_t depth, uint64_t seed, void* stream,
+                                   dv_cnn** out) {
+  clear_error();
+  if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (width != WID || depth != NLAYER)
+    return fail(DV_ERR_UNSUPPORTED, "this build implements width %d and depth %d only", WID, NLAYER);
+  dv_cnn* c = new (std::nothrow) dv_cnn();
+  if (!c) return fail(DV_ERR_OOM, "host allocation failed");
+  int64_t off = 0;
+  for (int l = 0; l < NLAYER; ++l) {
+    c->off_w[l] = off;
+    off += 9LL * layer_cin_logical(l) * layer_cout(l);
+    c->off_b[l] = off;
+    off += layer_cout(l);
+  }
+  c->nparam = off;
+  // He-normal initialisation (seeded), biases zero
+  std::vector<float> p((size_t)off, 0.f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < NLAYER; ++l) {
+    const double sd = std::sqrt(2.0 / (9.0 * layer_cin_logical(l))) * (l == NLAYER - 1 ? 0.1 : 1.0);
+    std::normal_distribution<double> nd(0.0, sd);
+    for (int64_t k = 0; k < 9LL * layer_cin_logical(l) * layer_cout(l); ++k) p[c->off_w[l] + k] = (float)nd(rng);
+  }
+  auto cleanup = [&](dv_status st) {
+    free_cnn(c);
+    return st;
+  };
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  for (float** q : {&c->d_p, &c->d_g, &c->d_m, &c->d_v})
+    if ((e = cudaMalloc(q, (size_t)off * sizeof(float))) != cudaSuccess)
+      return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+  for (int l = 0; l < NLAYER; ++l) {
+    const size_t n = (size_t)9 * layer_cin(l) * layer_cout(l);
+    if ((e = cudaMalloc(&c->d_wf[l], n * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_wt[l], n * sizeof(float))) != cudaSuccess)
+      return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+  }
+  if ((e = cudaMalloc(&c->d_lpart, 1024 * sizeof(double))) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_loss, sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&c->h_loss, sizeof(double))) != cudaSuccess)
+    return cleanup(cuda_fail(e, "allocation", __FILE__, __LINE__));
+  if ((e = cudaMemcpyAsync(c->d_p, p.data(), (size_t)off * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_m, 0, (size_t)off * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_v, 0, (size_t)off * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_g, 0, (size_t)off * sizeof(float), s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cleanup(cuda_fail(e, "upload", __FILE__, __LINE__));
+  *out = c;
+  return DV_OK;
+}
+
+extern "C" int64_t dv_cnn_param_count(const dv_cnn* c) { return c ? c->nparam : 0; }
+
+extern "C" dv_status dv_cnn_get_params(const dv_cnn* c, float* host, int64_t n, int64_t* step) {
+  clear_error();
+  if (!c || !host || n != c->nparam) return fail(DV_ERR_INVALID_ARG, "need the cnn and %lld floats",
+                                                 (long long)(c ? c->nparam : 0));
+  DV_TRY_CUDA(cudaMemcpy(host, c->d_p, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost));
+  if (step) *step = c->step;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_cnn_set_params(dv_cnn* c, const float* host, int64_t n, void* stream) {
+  clear_error();
+  if (!c || !host || n != c->nparam) return fail(DV_ERR_INVALID_ARG, "need the cnn and %lld floats",
+                                                 (long long)(c ? c->nparam : 0));
+  cudaStream_t s = (cudaStream_t)stream;
+  DV_TRY_CUDA(cudaMemcpyAsync(c->d_p, host, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s));
+  DV_TRY_CUDA(cudaMemsetAsync(c->d_m, 0, (size_t)n * sizeof(float), s));
+  DV_TRY_CUDA(cudaMemsetAsync(c->d_v, 0, (size_t)n * sizeof(float), s));
+  c->step = 0;
+  DV_TRY(pack(c, s));
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  return DV_OK;
+}
+
+extern "C" dv_status dv_cnn_forward(dv_cnn* c, const float* in_dev, int32_t N, int32_t H, int32_t W,
+                                    float* out_dev, void* stream) {
+  clear_error();
+  if (!c || !in_dev || !out_dev) return fail(DV_ERR_INVALID_ARG, "NULL argument");
+  DV_TRY(check_shape(N, H, W));
+  return forward(c, in_dev, N, H, W, out_dev, (cudaStream_t)stream);
+}
+
+extern "C" dv_status dv_cnn_gradients(dv_cnn* c, const float* in_dev, const float* target_dev,
+                                      int32_t N, int32_t H, int32_t W, float* grad_host,
+                                      double* loss_host, void* stream) {
+  clear_error();
+  if (!c || !in_dev || !target_dev) return fail(DV_ERR_INVALID_ARG, "NULL argument");
+  DV_TRY(check_shape(N, H, W));
+  cudaStream_t s = (cudaStream_t)stream;
+  DV_TRY(forward(c, in_dev, N, H, W, nullptr, s));
+  DV_TRY(backward(c, target_dev, N, H, W, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(c->h_loss, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (grad_host)
+    DV_TRY_CUDA(cudaMemcpyAsync(grad_host, c->d_g, (size_t)c->nparam * sizeof(float),
+                                cudaMemcpyDeviceToHost, s));
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  if (loss_host) *loss_host = 0.5 * *c->h_loss / ((double)N * H * W);
+  return DV_OK;
+}
+
+extern "C" dv_status dv_cnn_train_step(dv_cnn* c, const float* in_dev, const float* target_dev,
+                                       int32_t N, int32_t H, int32_t W, float lr,
+                                       double* loss_host, void* stream) {
+  clear_error();
+  if (!c || !in_dev || !target_dev || !(lr > 0.f)) return fail(DV_ERR_INVALID_ARG, "bad argument");
+  DV_TRY(check_shape(N, H, W));
+  cudaStream_t s = (cudaStream_t)stream;
+  DV_TRY(forward(c, in_dev, N, H, W, nullptr, s));
+  DV_TRY(backward(c, target_dev, N, H, W, s));
+  c->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - (float)std::pow((double)b1, (double)c->step);
+  const float c2 = 1.f - (float)std::pow((double)b2, (double)c->step);
+  adam_kernel<<<cdiv(c->nparam, NB), NB, 0, s>>>(c->d_p, c->d_g, c->d_m, c->d_v, c->nparam, lr, b1, b2,
+                                                 1e-8f, c1, c2);
+  DV_TRY_CUDA(cudaGetLastError());
+  DV_TRY(pack(c, s));
+  if (loss_host) {
+    DV_TRY_CUDA(cudaMemcpyAsync(c->h_loss, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DV_TRY_CUDA(cudaStreamSynchronize(s));
+    *loss_host = 0.5 * *c->h_loss / ((double)N * H * W);
+  }
+  return DV_OK;
+}
+
+extern "C" dv_status dv_cnn_destroy(dv_cnn* c) {
+  clear_error();
+  free_cnn(c);
+  return DV_OK;
+}
+
+extern "C" dv_status dv_plan_set_warmstart(dv_plan* P, dv_cnn* c) {
+  clear_error();
+  if (!P) return fail(DV_ERR_INVALID_ARG, "plan is NULL");
+  P->cnn = c;
+  return DV_OK;
+}
+
+extern "C" dv_status dv_warmstart_features(dv_plan* P, const float* y_dev, float* feat_dev,
+                                           void* stream) {
+  clear_error();
+  if (!P || !y_dev || !feat_dev) return fail(DV_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  dim3 grid(cdiv(P->nxc, NB), P->nxr);
+  features_kernel<<<grid, NB, 0, s>>>(y_dev, P->hy, P->wy, P->rad, P->d_wrow, P->d_wcol, P->d_desc,
+                                      P->Gr, P->Gc, (float)(100.0 * P->prob.noise_sigma), P->nxr,
+                                      P->nxc, feat_dev);
+  DV_TRY_CUDA(cudaGetLastError());
+  P->launches += 1;
+  return DV_OK;
+}

@@ -217,6 +217,10 @@ struct dv_plan {
   float2* d_fft_scr = nullptr;     // FFT path: n_sm spectra of S x S
   int n_sm = 0;
   double tune_ms[2] = {0.0, 0.0};   // autotuner: one H + one H^T apply per path
+  dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
+  float* d_desc = nullptr;         // per-PSF descriptors [G][3]
+  float* d_feat = nullptr;         // warm-start features [nx][5] (lazy)
+  float* d_wsd = nullptr;          // network output on the x grid (lazy)
   std::vector<int> yr0, yr1, yc0, yc1;
   std::vector<double> tau;
   std::vector<dv::TileDesc> h_tiles;
@@ -259,6 +263,8 @@ struct dv_plan {
 };
 
 namespace dv {
+dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0);
+void psf_descriptors(const float* psfs, int G, int K, std::vector<float>& out);
 // Operator launches on the plan's path; the H launch in OP_OBJ mode writes
 // obj_parts(P) FP64 partials.
 cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s);

@@ -199,6 +199,7 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     return fail(DV_ERR_INVALID_ARG, "unknown operator path %d", p->path);
   if (p->overlap < 0) return fail(DV_ERR_INVALID_ARG, "overlap must be >= 0");
   if (p->check_every < 0) return fail(DV_ERR_INVALID_ARG, "check_every must be >= 0");
+  if (!(p->noise_sigma >= 0.0)) return fail(DV_ERR_INVALID_ARG, "noise_sigma must be >= 0");
 
   const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
   if ((int64_t)nxr * nxc > (int64_t)1 << 40) return fail(DV_ERR_INVALID_ARG, "image too large");
@@ -467,8 +468,6 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   if (prob->precision != DV_PREC_FP32)
     return fail(DV_ERR_UNSUPPORTED, "precision %d is not available in this build",
                 prob->precision);
-  if (prob->use_warmstart)
-    return fail(DV_ERR_UNSUPPORTED, "the learned warm start is not available in this build");
   if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
 
@@ -513,6 +512,11 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
         flip[((size_t)g * K + (K - 1 - a)) * KP + (K - 1 - b)] = v;
       }
   DV_TRY(upload(P, &P->d_psf, psf.data(), psf.size(), s));
+  {
+    std::vector<float> desc;
+    psf_descriptors(prob->psfs, G, K, desc);
+    DV_TRY(upload(P, &P->d_desc, desc.data(), desc.size(), s));
+  }
   DV_TRY(upload(P, &P->d_psf_flip, flip.data(), flip.size(), s));
   DV_TRY(upload(P, &P->d_wrow, L.wrow.data(), L.wrow.size(), s));
   DV_TRY(upload(P, &P->d_wcol, L.wcol.data(), L.wcol.size(), s));
@@ -687,7 +691,7 @@ dv_status release(dv_plan* P) {
   void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
-                  P->d_spec, P->d_counter, P->d_fft_scr,
+                  P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
                   P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)

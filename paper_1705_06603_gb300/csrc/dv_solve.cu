@@ -275,6 +275,11 @@ dv_status solve_internal(dv_plan* P, const float* x0, float* x_out, dv_stats* st
                          int64_t l0) {
   const GridArgs g = grid_args(P);
   const bool track_z = st || P->prob.check_every > 0;
+  if (!x0 && P->prob.use_warmstart) {
+    if (!P->cnn) return fail(DV_ERR_INVALID_ARG, "use_warmstart is set but no network is attached");
+    DV_TRY(warmstart_x0(P, s, P->d_xg));
+    x0 = P->d_xg;
+  }
   DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, x0, P->d_y, P->hy, P->wy, P->rad,
                              P->d_w[0], P->d_u, s, track_z ? P->d_z : nullptr));
   P->launches += 1;

@@ -50,7 +50,8 @@ class dv_problem(C.Structure):
                 ("n_outer", C.c_int32), ("n_inner", C.c_int32), ("inner_increment", C.c_int32),
                 ("precision", C.c_int32), ("path", C.c_int32), ("use_warmstart", C.c_int32),
                 ("check_every", C.c_int32), ("target_objective", C.c_double),
-                ("use_graphs", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("use_graphs", C.c_int32), ("noise_sigma", C.c_double),
+                ("reserved", C.c_int32 * 5)]
 
 
 class dv_stats(C.Structure):
@@ -86,6 +87,18 @@ _sigs = {
     "dv_plan_kernel_time": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]),
     "dv_prior_value_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, _vp, _vp]),
+    "dv_cnn_create": (C.c_int, [C.c_int32, C.c_int32, C.c_uint64, _vp, C.POINTER(_vp)]),
+    "dv_cnn_param_count": (C.c_int64, [_vp]),
+    "dv_cnn_get_params": (C.c_int, [_vp, _vp, C.c_int64, C.POINTER(C.c_int64)]),
+    "dv_cnn_set_params": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
+    "dv_cnn_forward": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_int32, _vp, _vp]),
+    "dv_cnn_gradients": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, _vp,
+                                   C.POINTER(C.c_double), _vp]),
+    "dv_cnn_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_float,
+                                    C.POINTER(C.c_double), _vp]),
+    "dv_cnn_destroy": (C.c_int, [_vp]),
+    "dv_plan_set_warmstart": (C.c_int, [_vp, _vp]),
+    "dv_warmstart_features": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dv_destroy": (C.c_int, [_vp]),
     "dv_last_error": (C.c_char_p, []),
 }
@@ -146,7 +159,8 @@ def _hptr(a, name, shape=None):
 def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, weights=None,
                  noise_w=None, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, rho=1.0, n_outer=30,
                  n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
-                 use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1):
+                 use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1,
+                 noise_sigma=0.0):
     """Builds a dv_problem.  Returns (problem, keepalive) where keepalive holds
     the host arrays the struct points to until dv_plan_create has copied them."""
     p = dv_problem()
@@ -180,6 +194,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
     p.n_outer, p.n_inner, p.inner_increment = n_outer, n_inner, inner_increment
     p.precision, p.path, p.use_warmstart = precision, path, use_warmstart
     p.check_every, p.target_objective, p.use_graphs = check_every, target_objective, use_graphs
+    p.noise_sigma = noise_sigma
     return p, keep
 
 
@@ -266,6 +281,81 @@ def dv_prior_value_noalloc(x, delta, value, stream=None):
     _check(_lib.dv_prior_value_noalloc(_dptr(x, "x"), int(x.shape[0]), int(x.shape[1]),
                                        float(delta), C.c_void_p(value.data_ptr()),
                                        _stream_handle(stream)))
+
+
+CNN_IN_CH = 5
+
+
+class Cnn:
+    """The learned warm-start network (dv_cnn_*): NHWC float32 CUDA tensors."""
+
+    def __init__(self, seed=0, stream=None):
+        self.stream = stream
+        h = C.c_void_p()
+        _check(_lib.dv_cnn_create(32, 6, seed, _stream_handle(stream), C.byref(h)))
+        self._h = h
+        self.nparam = int(_lib.dv_cnn_param_count(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        step = C.c_int64()
+        _check(_lib.dv_cnn_get_params(self._h, C.c_void_p(out.ctypes.data), self.nparam,
+                                      C.byref(step)))
+        return out, step.value
+
+    def set_params(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        _check(_lib.dv_cnn_set_params(self._h, C.c_void_p(params.ctypes.data), params.size,
+                                      _stream_handle(self.stream)))
+
+    def forward(self, x, out=None):
+        import torch
+        N, H, W, Cc = x.shape
+        assert Cc == CNN_IN_CH
+        out = out if out is not None else torch.empty((N, H, W), device=x.device)
+        _check(_lib.dv_cnn_forward(self._h, _dptr(x, "x"), N, H, W, _dptr(out, "out"),
+                                   _stream_handle(self.stream)))
+        return out
+
+    def gradients(self, x, target):
+        N, H, W, _ = x.shape
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = C.c_double()
+        _check(_lib.dv_cnn_gradients(self._h, _dptr(x, "x"), _dptr(target, "target"), N, H, W,
+                                     C.c_void_p(g.ctypes.data), C.byref(loss),
+                                     _stream_handle(self.stream)))
+        return g, loss.value
+
+    def train_step(self, x, target, lr):
+        N, H, W, _ = x.shape
+        loss = C.c_double()
+        _check(_lib.dv_cnn_train_step(self._h, _dptr(x, "x"), _dptr(target, "target"), N, H, W,
+                                      float(lr), C.byref(loss), _stream_handle(self.stream)))
+        return loss.value
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.dv_cnn_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dv_plan_set_warmstart(plan, cnn):
+    _check(_lib.dv_plan_set_warmstart(plan, cnn.handle if cnn is not None else None))
+
+
+def dv_warmstart_features(plan, y, feat, stream=None):
+    _check(_lib.dv_warmstart_features(plan, _dptr(y, "y"), _dptr(feat, "feat"),
+                                      _stream_handle(stream)))
 
 
 def dv_destroy(plan):
