@@ -231,6 +231,14 @@ typedef struct dv_plan_info {
   int64_t kernel_launches; /* total libdv kernel launches on this plan */
   double tune_ms_direct;   /* autotuner: one H + one H^T apply, direct path (0 if not timed) */
   double tune_ms_fft;      /* same for the block-FFT path (0 if not timed / not available) */
+  /* work scheduled by one tile-mode launch of the path in use: output blocks
+   * and (block, active PSF) pairs for H [0] and H^T [1]; the FFT path runs
+   * ceil(PSFs/2) packed transforms per block (psf_pairs) */
+  int64_t blocks[2];
+  int64_t block_psfs[2];
+  int64_t psf_pairs[2];
+  int32_t block_side;      /* output block side: 64 (direct) or 128 - K + 1 (FFT) */
+  int32_t pad;
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

@@ -198,6 +198,8 @@ namespace dv {
 // Work tables of one operator path: tile mode (H over y-blocks, H^T over
 // x-tiles) and the single global pseudo-tile of dv_apply_H / dv_apply_Ht.
 struct OpTables {
+  int64_t psfs[2] = {0, 0};    // sum over H / H^T items of active PSFs
+  int64_t pairs[2] = {0, 0};   // sum of ceil(active PSFs / 2)
   WorkItem* H = nullptr;
   WorkItem* Ht = nullptr;
   WorkItem* Hg = nullptr;

@@ -594,11 +594,20 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
                  (y.a_hi - y.a_lo + 1) * (y.b_hi - y.b_lo + 1) + 1;
         });
     };
+    auto count = [&](const std::vector<WorkItem>& v, int k2) {
+      for (const WorkItem& it : v) {
+        const int64_t np = (int64_t)(it.a_hi - it.a_lo + 1) * (it.b_hi - it.b_lo + 1);
+        tb.psfs[k2] += np;
+        tb.pairs[k2] += (np + 1) / 2;
+      }
+    };
     make_work(P->h_tiles, false, K, L, bm, bn, w);
+    count(w, 0);
     order(w);
     tb.nH = (int)w.size();
     DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
     make_work(P->h_tiles, true, K, L, bm, bn, w);
+    count(w, 1);
     order(w);
     tb.nHt = (int)w.size();
     DV_TRY(upload(P, &tb.Ht, w.data(), w.size(), s));
@@ -724,5 +733,14 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->kernel_launches = P->launches;
   info->tune_ms_direct = P->tune_ms[0];
   info->tune_ms_fft = P->tune_ms[1];
+  const int k = P->path == DV_PATH_FFT ? 1 : 0;
+  info->blocks[0] = P->tab[k].nH;
+  info->blocks[1] = P->tab[k].nHt;
+  info->block_psfs[0] = P->tab[k].psfs[0];
+  info->block_psfs[1] = P->tab[k].psfs[1];
+  info->psf_pairs[0] = P->tab[k].pairs[0];
+  info->psf_pairs[1] = P->tab[k].pairs[1];
+  info->block_side = k ? fft_block(P->K) : direct_tile_m();
+  info->pad = 0;
   return DV_OK;
 }

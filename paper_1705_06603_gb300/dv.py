@@ -66,7 +66,9 @@ class dv_plan_info(C.Structure):
                 ("path", C.c_int32), ("stack_elems", C.c_int64), ("device_bytes", C.c_int64),
                 ("tau_min", C.c_double), ("tau_max", C.c_double),
                 ("kernel_launches", C.c_int64), ("tune_ms_direct", C.c_double),
-                ("tune_ms_fft", C.c_double)]
+                ("tune_ms_fft", C.c_double), ("blocks", C.c_int64 * 2),
+                ("block_psfs", C.c_int64 * 2), ("psf_pairs", C.c_int64 * 2),
+                ("block_side", C.c_int32), ("pad", C.c_int32)]
 
 
 _vp = C.c_void_p

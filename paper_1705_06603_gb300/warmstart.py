@@ -31,10 +31,13 @@ def random_case(seed, size, K, grid):
 
 
 def make_pair(seed, size=96, K=15, grid=(3, 3), n_tiles=(2, 2), overlap=16, n_outer=40,
-              n_inner=10, lam=1e-3, delta=1.0 / 60.0, gamma=0.4):
-    """(features [nx, nx, 5], target [nx, nx]) of one seeded case, both CUDA tensors."""
+              n_inner=10, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, psfs=None, sigma=None):
+    """(features [nx, nx, 5], target [nx, nx], y, psfs, sigma) of one seeded case
+    (CUDA tensors); psfs / sigma, when given, replace the random draws."""
     import torch
-    x, psfs, sigma = random_case(seed, size, K, grid)
+    x, rpsfs, rsigma = random_case(seed, size, K, grid)
+    psfs = rpsfs if psfs is None else np.ascontiguousarray(psfs, dtype=np.float32)
+    sigma = rsigma if sigma is None else float(sigma)
     plan = dv.Plan(size, size, psfs, n_tiles=n_tiles, overlap=overlap, lam=lam, delta=delta,
                    gamma=gamma, n_outer=n_outer, n_inner=n_inner, noise_sigma=sigma)
     y = plan.apply_H(torch.from_numpy(x).cuda())
