@@ -108,6 +108,7 @@ struct OpArgs {
   const float2* spec;     // FFT path: [Gr*Gc][S][S] PSF spectra / S^2
   int* counter;           // FFT path: work counter, zeroed before each launch
   float2* scratch;        // FFT path: one S x S spectrum per CTA of the launch grid
+  const uint2* bfrag;     // BF16 tensor-core path: MMA B fragments [G][K][KS][32]
 };
 
 // Streaming kernels' shared view of the tile grid
@@ -161,6 +162,13 @@ cudaError_t fft_prepare();            // twiddles + shared-memory limits (plan t
 void fft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
 cudaError_t launch_fft_H(const OpArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_fft_Ht(const OpArgs& a, cudaStream_t s, int grid);
+
+// BF16 tensor-core path (direct work tables)
+bool tc_supported(int K);
+cudaError_t tc_prepare(int K);
+void tc_fragments(const float* psfs, int G, int K, bool flip, std::vector<uint2>& out);
+cudaError_t launch_tc_H(const OpArgs& a, cudaStream_t s);
+cudaError_t launch_tc_Ht(const OpArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Plan
@@ -218,6 +226,9 @@ struct dv_plan {
   int* d_counter = nullptr;        // [0] H launches, [1] H^T launches (FFT path)
   float2* d_fft_scr = nullptr;     // FFT path: n_sm spectra of S x S
   int n_sm = 0;
+  bool tc = false;                 // operator on BF16 tensor cores
+  uint2* d_bfragH = nullptr;       // MMA B fragments (flipped PSFs, for H)
+  uint2* d_bfragHt = nullptr;      // MMA B fragments (PSFs, for H^T)
   double tune_ms[2] = {0.0, 0.0};   // autotuner: one H + one H^T apply per path
   dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
   float* d_desc = nullptr;         // per-PSF descriptors [G][3]
@@ -269,7 +280,9 @@ dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0);
 void psf_descriptors(const float* psfs, int G, int K, std::vector<float>& out);
 // Operator launches on the plan's path; the H launch in OP_OBJ mode writes
 // obj_parts(P) FP64 partials.
-cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s);
+// fp32_only: use the plan's FP32 path even when the operator runs in BF16
+// (objective and stopping-test evaluation)
+cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s, bool fp32_only = false);
 cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s);
 int obj_parts(const dv_plan* P);
 dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global);

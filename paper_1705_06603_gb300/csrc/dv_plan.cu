@@ -337,6 +337,7 @@ dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bo
   a.spec = p->d_spec;
   a.counter = p->d_counter;
   a.scratch = p->d_fft_scr;
+  a.bfrag = p->d_bfragH;
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
@@ -352,6 +353,7 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, b
   a.n_work = global ? tb.nHtg : tb.nHt;
   a.psf = p->d_psf;
   a.counter = p->d_counter ? p->d_counter + 1 : nullptr;
+  a.bfrag = p->d_bfragHt;
   a.w = w;
   a.u = u;
   a.omr = p->d_omr;
@@ -359,11 +361,13 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, b
   return a;
 }
 
-cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s) {
+cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s, bool fp32_only) {
+  if (P->tc && !fp32_only) return launch_tc_H(a, s);
   return P->path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
 }
 
 cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s) {
+  if (P->tc) return launch_tc_Ht(a, s);
   return P->path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
 }
 
@@ -433,7 +437,7 @@ namespace dv {
 // Autotuner: times one H (with residual) and one H^T (with the fused step) on
 // the plan's tile stacks for each available path and keeps the faster one.
 static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
-  if (requested == DV_PATH_DIRECT || !P->fft_ok) {
+  if (P->tc || requested == DV_PATH_DIRECT || !P->fft_ok) {
     P->path = DV_PATH_DIRECT;
     return DV_OK;
   }
@@ -465,9 +469,10 @@ static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
 static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) {
   Layout L;
   DV_TRY(validate_and_layout(prob, L));
-  if (prob->precision != DV_PREC_FP32)
-    return fail(DV_ERR_UNSUPPORTED, "precision %d is not available in this build",
-                prob->precision);
+  if (prob->precision == DV_PREC_TF32)
+    return fail(DV_ERR_UNSUPPORTED, "TF32 operands are not available in this build");
+  if (prob->precision == DV_PREC_BF16 && !tc_supported(prob->K))
+    return fail(DV_ERR_UNSUPPORTED, "the BF16 tensor-core operator supports K = 9, 15, 31, 63");
   if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
 
@@ -488,7 +493,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   P->n_tc = prob->n_tc;
   P->T = P->n_tr * P->n_tc;
   P->path = DV_PATH_DIRECT;
-  P->fft_ok = prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
+  P->tc = prob->precision == DV_PREC_BF16;
+  P->fft_ok = !P->tc && prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
   {
     int dev = 0;
     DV_TRY_CUDA(cudaGetDevice(&dev));
@@ -620,6 +626,14 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     tb.nHtg = (int)w.size();
     DV_TRY(upload(P, &tb.Htg, w.data(), w.size(), s));
   }
+  if (P->tc) {
+    std::vector<uint2> fr;
+    tc_fragments(prob->psfs, G, K, true, fr);
+    DV_TRY(upload(P, &P->d_bfragH, fr.data(), fr.size(), s));
+    tc_fragments(prob->psfs, G, K, false, fr);
+    DV_TRY(upload(P, &P->d_bfragHt, fr.data(), fr.size(), s));
+    DV_TRY_CUDA(tc_prepare(K));
+  }
   if (P->fft_ok) {
     DV_TRY(alloc(P, &P->d_counter, 2));
     DV_TRY(alloc(P, &P->d_fft_scr, (size_t)P->n_sm * fft_size() * fft_size()));
@@ -701,6 +715,7 @@ dv_status release(dv_plan* P) {
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
+                  P->d_bfragH, P->d_bfragHt,
                   P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)

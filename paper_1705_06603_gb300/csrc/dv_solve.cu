@@ -195,7 +195,7 @@ dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
   DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
   DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, P->d_xg, nullptr, P->hy, P->wy,
                              P->rad, tmp, nullptr, s, nullptr));
-  DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_OBJ, tmp, nullptr, false), s));
+  DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_OBJ, tmp, nullptr, false), s, true));
   DV_TRY_CUDA(launch_huber_value(P->d_tiles, P->T, P->max_nxr, P->max_nxc, tmp, P->prob.delta,
                                  part_hub(P), s));
   const double* parts[4] = {part_data(P), part_hub(P), part_cons(P), part_cons(P) + ncons(P)};

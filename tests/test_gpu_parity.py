@@ -295,3 +295,49 @@ def test_autotuner_times_both_paths_and_keeps_the_faster(env):
     with pytest.raises(dv.DVError):
         dv.Plan(40, 40, big, path=FFT)
     plan.close()
+
+
+BF16_TOL = 3e-3   # operator relative L2 with BF16 operands and FP32 accumulation
+
+
+@pytest.mark.parametrize("hy,wy,K,G", [(130, 70, 9, (3, 3)), (200, 180, 31, (4, 3)),
+                                       (150, 97, 63, (2, 2)), (66, 64, 15, (1, 1))])
+def test_bf16_operator_matches_oracle(env, hy, wy, K, G):
+    torch, dv = env
+    g = np.random.default_rng(K + 1000)
+    psfs = random_psfs(g, G, K)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
+    r = g.standard_normal((hy, wy)).astype(np.float32)
+    plan = dv.Plan(hy, wy, psfs, precision=dv.DV_PREC_BF16)
+    yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
+    wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
+    ps = psfs.astype(np.float64)
+    assert rel_l2(yd, O.apply_H(x.astype(np.float64), ps, wr, wc)) <= BF16_TOL
+    assert rel_l2(gd, O.apply_Ht(r.astype(np.float64), ps, wr, wc)) <= BF16_TOL
+    plan.close()
+
+
+def test_bf16_solve_close_to_oracle(env):
+    """The 128x128 workload with the BF16 operator: the objective is evaluated
+    with the FP32 operator, the image stays within 1e-2 of the FP64 oracle."""
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, 10, 10, precision=2)
+    lay, xr, info = oracle_solve(w, psfs, y, 10, 10)
+    assert rel_l2(xd, xr) <= 1e-2
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
+    assert abs(st["objective"] - F) <= 1e-2 * F
+    plan.close()
+
+
+def test_unsupported_precisions_are_reported(env):
+    torch, dv = env
+    psfs = np.full((1, 1, 9, 9), 1 / 81.0, dtype=np.float32)
+    with pytest.raises(dv.DVError) as e:
+        dv.Plan(40, 40, psfs, precision=dv.DV_PREC_TF32)
+    assert e.value.code == dv.DV_ERR_UNSUPPORTED
+    with pytest.raises(dv.DVError) as e:
+        dv.Plan(40, 40, np.full((1, 1, 11, 11), 1 / 121.0, dtype=np.float32),
+                precision=dv.DV_PREC_BF16)
+    assert e.value.code == dv.DV_ERR_UNSUPPORTED
