@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16",
+                    help="lowest operand precision the chosen form may use for H / H^T "
+                         "(the autotuner picks the fastest allowed path)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
                          "short, fixed launch sequence for ncu captures); prints nothing")
@@ -309,8 +312,9 @@ def run_ours(args):
     # F <= F*(1 + 1e-4) (objective checked every 2 outer iterations)
     net, train_info = train_warmstart(dv, w, psfs, seed=rank)
     target = f_star * (1.0 + 1e-4)
+    prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=2 * w.n_outer, use_warmstart=1,
-                   check_every=2, target_objective=target, **common)
+                   check_every=2, target_objective=target, precision=prec, **common)
     dv.dv_plan_set_warmstart(plan.handle, net)
     st = dv.dv_stats()
     for i in range(args.warmup):
@@ -364,23 +368,46 @@ def run_ours(args):
     e2e = {"value": w.hy * w.wy * world / t_e2e / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1]}
 
-    # roofline of the dominant kernel (FP32 issue bound), live event timing
+    # roofline of the dominant kernel, live event timing
     info = dv.dv_plan_get_info(plan.handle)
     rows, cols, _ = dv.dv_layout_query(plan.problem)
     lay_tiles = [(r, c) for r in rows for c in cols]
     y_px = sum((r1 - r0) * (c1 - c0) for (r0, r1), (c0, c1) in lay_tiles)
     x_px = sum((r1 - r0 + w.K - 1) * (c1 - c0 + w.K - 1) for (r0, r1), (c0, c1) in lay_tiles)
-    fft = info.path == dv.DV_PATH_FFT
-    kH, kHt = (("fft_H_kernel", "fft_Ht_kernel") if fft else
-               (f"direct_H_kernel<{w.K}>", f"direct_Ht_kernel<{w.K}>"))
+    path = info.path
+    pname = {dv.DV_PATH_DIRECT: "direct", dv.DV_PATH_FFT: "block-FFT",
+             dv.DV_PATH_TENSOR: "tensor-core"}[path]
+    tc_prec = 0 if args.precision == "bf16" else 1
+    kH, kHt = {dv.DV_PATH_FFT: ("fft_H_kernel", "fft_Ht_kernel"),
+               dv.DV_PATH_DIRECT: (f"direct_H_kernel<{w.K}>", f"direct_Ht_kernel<{w.K}>"),
+               dv.DV_PATH_TENSOR: (f"tc_H_kernel<{tc_prec},{w.K}>",
+                                   f"tc_Ht_kernel<{tc_prec},{w.K}>")}[path]
     names = {0: f"{kH} (H_i with residual)", 1: f"{kHt} (H_i^T + fused prox step)",
              2: "consensus_kernel"}
     dom = max((0, 1), key=lambda k: ktime[k][0])
     ms_launch = ktime[dom][0] / max(ktime[dom][1], 1)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    if fft:
+    px = y_px if dom == 0 else x_px
+    if path == dv.DV_PATH_TENSOR:
+        # algorithmic: 2 K^2 flop per output pixel per active PSF, at most 4
+        # active PSFs (first-order interpolation); the tensor pipe also runs
+        # the zero band of the Toeplitz operand and the ragged block tails
+        flops = 8.0 * w.K * w.K * px
+        km = 16 if args.precision == "bf16" else 8
+        ks = (63 + w.K + km - 1) // km
+        executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 64
+        sus = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        peak = sus if args.precision == "bf16" else sus * 1.1 / 2.25
+        bound, unit = "tensor", "TFLOP/s"
+        peak_src = ("measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)"
+                    if args.precision == "bf16" else
+                    "measured sustained cuBLAS BF16 x nominal TF32/BF16 ratio 1.1/2.25")
+        alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
+               f"{px} pixels; executed MMA work {executed / 1e9:.1f} GFLOP per launch "
+               f"({info.block_psfs[dom]} block-PSF pairs x K x {ks * km} Toeplitz columns x "
+               f"2 x 128 x 64)")
+    elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
         # per 128 x 128 complex 2-D transform (N = 16384) and 8 flop per spectral
         # product; H runs one forward per PSF pair and one inverse per block,
@@ -388,19 +415,37 @@ def run_ours(args):
         n = 128 * 128
         f2d = 5.0 * n * np.log2(n)
         flops = (info.blocks[dom] + info.psf_pairs[dom]) * f2d + info.psf_pairs[dom] * 8.0 * n
+        peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        peak_src = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz "
+                    f"(unit counts and max SM clock)")
         alg = (f"5 N log2 N flop per 128x128 complex 2-D transform + 8 N per spectral product; "
                f"{info.blocks[dom]} blocks, {info.psf_pairs[dom]} PSF pairs per launch")
     else:
-        flops = 8.0 * w.K * w.K * (y_px if dom == 0 else x_px)
+        flops = 8.0 * w.K * w.K * px
+        peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        peak_src = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz "
+                    f"(unit counts and max SM clock)")
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
-               f"{(y_px if dom == 0 else x_px)} pixels")
+               f"{px} pixels")
     achieved = flops / (ms_launch * 1e-3) / 1e12
     kern = [kH, kHt][dom].split("<")[0]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic_for(kern), "kernel": names[dom],
-            "peak_source": f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x "
-                           f"{sm_max:.0f} MHz (unit counts and max SM clock)",
-            "algorithmic": alg}
+            "peak_source": peak_src, "algorithmic": alg}
+    # the HBM-bound consensus + dual update: read x_i, u_i and write u_i per
+    # tile pixel, read and write zbar_prev per global pixel (residuals tracked)
+    ms_cons = ktime[2][0] / max(ktime[2][1], 1)
+    cons_bytes = 12.0 * x_px + 8.0 * plan.nx[0] * plan.nx[1]
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    cons_gbs = cons_bytes / (ms_cons * 1e-3) / 1e9
+    roof_cons = {"bound": "hbm", "achieved": cons_gbs, "peak": hbm, "unit": "GB/s",
+                 "frac": cons_gbs / hbm, "traffic": traffic_for("consensus_kernel"),
+                 "kernel": "consensus_kernel",
+                 "algorithmic": f"12 B per tile pixel ({x_px}) + 8 B per global x pixel "
+                                f"({plan.nx[0] * plan.nx[1]}) = {cons_bytes / 1e6:.1f} MB per launch",
+                 "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
     kernels = {names[k]: {"launches": ktime[k][1], "ms_per_launch": ktime[k][0] / max(ktime[k][1], 1),
                           "share": ktime[k][0] / max(total_ms, 1e-9)} for k in (0, 1, 2)}
 
@@ -418,16 +463,20 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bf16" if args.precision == "bf16" else "tf32")
+            if path == dv.DV_PATH_TENSOR else "f32", "data": "synthetic",
             "config": {"workload": "stars2048: 2048x2048 star field (Poisson stars, power-law "
                                    "fluxes, elliptical blobs), 8x8 Moffat 31x31 PSFs, 4x4 tiles "
                                    "overlapping by 64 px, sigma 0.005; plain form 100 outer x 10 "
                                    "inner iterations",
-                       "chosen_form": "%s operator (autotuned: direct %.3f ms, FFT %.3f ms per "
-                                      "H + H^T), CUDA graph per local solve, learned warm start, "
-                                      "stop at F <= F*(1 + 1e-4) checked every 2 outer iterations"
-                                      % ("block-FFT" if fft else "direct", info.tune_ms_direct,
-                                         info.tune_ms_fft),
+                       "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
+                                      "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
+                                      "per local solve, learned warm start, stop at F <= "
+                                      "F*(1 + 1e-4) checked every 2 outer iterations; objective "
+                                      "with the FP32 operator"
+                                      % (pname, args.precision, info.tune_ms_direct,
+                                         info.tune_ms_fft, info.tune_ms_tensor),
                        "plain_form": "FP32 block-FFT at fixed S = 128, one launch per kernel, "
                                      "blurred-image start, 100 x 10 iterations",
                        "plain_value": plain_value, "plain_ms": ms_plain, "f_star": f_star,
@@ -436,7 +485,8 @@ def run_ours(args):
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "roofline": roof, "roofline_streaming": roof_cons, "kernels": kernels,
+            "cpu_baseline": cpu,
             "device_bytes": info.device_bytes,
         }
         print(json.dumps(out), flush=True)
@@ -447,8 +497,9 @@ def run_ours(args):
 
 
 def run_profile_case():
-    """Launch sequence for ncu: inputs, plan, then scatter, H, H^T (+ step),
-    consensus and assembly of one 1 x 1 solve, eagerly (no graphs)."""
+    """Launch sequence for ncu: inputs, a block-FFT plan (no autotuning), then
+    scatter, H, H^T (+ step), consensus and assembly of one 1 x 1 solve,
+    eagerly (no graphs)."""
     import torch
     torch.cuda.set_device(0)
     from paper_1705_06603_gb300 import build as dvbuild
@@ -459,7 +510,8 @@ def run_profile_case():
     psfs = psf_grid_for(w).astype(np.float32)
     y = make_inputs(torch, dv, w, psfs, 0)
     plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
-                   delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=1, n_inner=1, use_graphs=0)
+                   delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=1, n_inner=1, use_graphs=0,
+                   path=dv.DV_PATH_FFT, noise_sigma=w.noise_sigma)
     plan.solve(y, stats=False)
     torch.cuda.synchronize()
     plan.close()

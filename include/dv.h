@@ -59,8 +59,10 @@ typedef enum dv_status {
   DV_ERR_UNSUPPORTED = 5   /* valid request this build does not implement     */
 } dv_status;
 
-/* Arithmetic of the blur operator H and its adjoint (Sec. II-B).  Every other
- * step runs in FP32 with FP64 reductions. */
+/* Lowest operand precision allowed for the blur operator H and its adjoint
+ * (Sec. II-B) in the inner iterations.  BF16 / TF32 let the autotuner pick
+ * the tensor-core path when it is faster; the objective, the stopping test
+ * and every other step run in FP32 with FP64 reductions. */
 typedef enum dv_precision {
   DV_PREC_FP32 = 0,        /* FP32 operands, FP32 accumulation                 */
   DV_PREC_TF32 = 1,        /* TF32 operands on tensor cores, FP32 accumulation */
@@ -81,9 +83,12 @@ typedef enum dv_weight_kind {
 
 /* How H and H^T are computed; all give the same operator. */
 typedef enum dv_operator_path {
-  DV_PATH_AUTO = 0,        /* plan-time autotuner picks the fastest          */
-  DV_PATH_DIRECT = 1,      /* spatial-domain correlation                     */
-  DV_PATH_FFT = 2          /* block FFT (overlap-save)                       */
+  DV_PATH_AUTO = 0,        /* plan-time autotuner picks the fastest allowed  */
+  DV_PATH_DIRECT = 1,      /* spatial-domain correlation, FP32               */
+  DV_PATH_FFT = 2,         /* block FFT (overlap-save), FP32                 */
+  DV_PATH_TENSOR = 3       /* direct correlation on tensor cores (tcgen05)
+                            * with BF16 / TF32 operands as set by precision
+                            * (not FP32); K = 9, 15, 31 or 63               */
 } dv_operator_path;
 
 typedef struct dv_problem {
@@ -104,7 +109,8 @@ typedef struct dv_problem {
    * and block i starts at round(i (n - B)/(count - 1)).  Otherwise host arrays
    * of n_tr (rows) / n_tc (cols) half-open y-block bounds, sorted, covering
    * [0, hy) x [0, wy) with no gaps, and with each x-tile overlapping only its
-   * immediate neighbours along each axis. */
+   * immediate neighbours along each axis.  n_tr, n_tc <= 1024; x may have at
+   * most 65535 rows (hy + K - 1). */
   int32_t n_tr, n_tc;
   const int32_t* tile_r0;
   const int32_t* tile_r1;
@@ -224,7 +230,7 @@ dv_status dv_state_import(dv_plan* plan, const float* x_stack_dev, const float* 
 typedef struct dv_plan_info {
   int32_t nx_r, nx_c;      /* x size */
   int32_t n_tiles;
-  int32_t path;            /* dv_operator_path chosen (never AUTO) */
+  int32_t path;            /* dv_operator_path of the inner iterations (never AUTO) */
   int64_t stack_elems;     /* floats in one x-shaped tile stack */
   int64_t device_bytes;    /* device memory owned by the plan */
   double tau_min, tau_max; /* local step sizes */
@@ -237,8 +243,9 @@ typedef struct dv_plan_info {
   int64_t blocks[2];
   int64_t block_psfs[2];
   int64_t psf_pairs[2];
-  int32_t block_side;      /* output block side: 64 (direct) or 128 - K + 1 (FFT) */
-  int32_t pad;
+  int32_t block_side;      /* output block rows: 64 (direct), 128 - K + 1 (FFT), 128 (tensor) */
+  int32_t fp32_path;       /* FP32 operator of objective evaluations: DV_PATH_DIRECT or _FFT */
+  double tune_ms_tensor;   /* autotuner: tensor-core path (0 if not timed / not available) */
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

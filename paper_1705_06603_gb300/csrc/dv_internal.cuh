@@ -108,19 +108,22 @@ struct OpArgs {
   const float2* spec;     // FFT path: [Gr*Gc][S][S] PSF spectra / S^2
   int* counter;           // FFT path: work counter, zeroed before each launch
   float2* scratch;        // FFT path: one S x S spectrum per CTA of the launch grid
-  const uint2* bfrag;     // BF16 tensor-core path: MMA B fragments [G][K][KS][32]
+  const unsigned char* tcop;  // tensor-core path: tall B operands [G][K] (shared-memory images)
+  int32_t prec;           // tensor-core path: DV_PREC_BF16 or DV_PREC_TF32
+  int32_t pad3;
+  int* err;               // tensor-core path: nonzero after a bounded wait gave up
 };
 
 // Streaming kernels' shared view of the tile grid
 struct GridArgs {
   const TileDesc* tiles;
   const int2* rowcov;     // per global x row: covering tile rows (second = -1 if none)
-  const int2* colcov;
+  const int4* cseg;       // column segments {c0, c1, tile col, second tile col or -1}
   const float* omr;
   const float* omc;
   int32_t n_tc;
   int32_t nxr, nxc;
-  int32_t pad;
+  int32_t n_cseg;
 };
 
 // ---------------------------------------------------------------------------
@@ -141,7 +144,9 @@ cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma,
                              float rho, float* zbuf, double* partials, cudaStream_t s,
                              int* n_blocks_out);
-int consensus_blocks(int nxr, int nxc);
+int consensus_blocks(int nxr, int n_cseg);
+// longest column segment of the consensus / assembly blocks
+int row_segment_width();
 // x_hat = sum omega_i x_i / sum omega_i
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s);
 // FP64 block partials of the Huber prior over the tile stacks
@@ -163,10 +168,12 @@ void fft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
 cudaError_t launch_fft_H(const OpArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_fft_Ht(const OpArgs& a, cudaStream_t s, int grid);
 
-// BF16 tensor-core path (direct work tables)
+// Tensor-core path (tcgen05, BF16 / TF32 operands; its own work tables)
+int tc_block_m();
+int tc_block_n();
 bool tc_supported(int K);
-cudaError_t tc_prepare(int K);
-void tc_fragments(const float* psfs, int G, int K, bool flip, std::vector<uint2>& out);
+cudaError_t tc_prepare(int K, int prec);
+void tc_operands(const float* psfs, int G, int K, int prec, bool flip, std::vector<uint8_t>& out);
 cudaError_t launch_tc_H(const OpArgs& a, cudaStream_t s);
 cudaError_t launch_tc_Ht(const OpArgs& a, cudaStream_t s);
 
@@ -219,17 +226,19 @@ struct OpTables {
 struct dv_plan {
   dv_problem prob;        // copy with host pointers cleared
   int hy, wy, K, rad, Gr, Gc, nxr, nxc, n_tr, n_tc, T;
-  int path;               // operator path in use: DV_PATH_DIRECT or DV_PATH_FFT
-  dv::OpTables tab[2];    // [0] direct 64x64 blocks, [1] FFT b x b blocks (if supported)
+  int path;               // operator of the inner iterations: DV_PATH_DIRECT, _FFT or _TENSOR
+  int fpath;              // FP32 operator (objective, stopping test): DV_PATH_DIRECT or _FFT
+  bool tensor_ok = false;  // tensor-core tables and operands were built
+  dv::OpTables tab[3];    // [0] direct 64x64, [1] FFT b x b, [2] tensor 128x64 blocks
   bool fft_ok = false;
   float2* d_spec = nullptr;
   int* d_counter = nullptr;        // [0] H launches, [1] H^T launches (FFT path)
   float2* d_fft_scr = nullptr;     // FFT path: n_sm spectra of S x S
   int n_sm = 0;
-  bool tc = false;                 // operator on BF16 tensor cores
-  uint2* d_bfragH = nullptr;       // MMA B fragments (flipped PSFs, for H)
-  uint2* d_bfragHt = nullptr;      // MMA B fragments (PSFs, for H^T)
-  double tune_ms[2] = {0.0, 0.0};   // autotuner: one H + one H^T apply per path
+  unsigned char* d_tcopH = nullptr;   // tensor-core B operands (flipped PSFs, for H)
+  unsigned char* d_tcopHt = nullptr;  // tensor-core B operands (PSFs, for H^T)
+  int* d_err = nullptr;               // device error word of the tensor-core kernels
+  double tune_ms[3] = {0.0, 0.0, 0.0};  // autotuner: one H + one H^T apply per path
   dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
   float* d_desc = nullptr;         // per-PSF descriptors [G][3]
   float* d_feat = nullptr;         // warm-start features [nx][5] (lazy)
@@ -249,7 +258,8 @@ struct dv_plan {
   dv::TileDesc* d_tiles = nullptr;
   dv::TileDesc* d_gtile = nullptr;
   int2* d_rowcov = nullptr;
-  int2* d_colcov = nullptr;
+  int4* d_cseg = nullptr;
+  int n_cseg = 0;
   float* d_w[2] = {nullptr, nullptr};
   float* d_u = nullptr;
   float* d_r = nullptr;
@@ -278,15 +288,14 @@ struct dv_plan {
 namespace dv {
 dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0);
 void psf_descriptors(const float* psfs, int G, int K, std::vector<float>& out);
-// Operator launches on the plan's path; the H launch in OP_OBJ mode writes
-// obj_parts(P) FP64 partials.
-// fp32_only: use the plan's FP32 path even when the operator runs in BF16
-// (objective and stopping-test evaluation)
-cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s, bool fp32_only = false);
-cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s);
+// Operator launches on one path (DV_PATH_DIRECT, _FFT or _TENSOR; the args
+// must come from op_args_* of the same path).  The H launch in OP_OBJ mode
+// (FP32 paths) writes obj_parts(P) FP64 partials.
+cudaError_t launch_op_H(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s);
+cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s);
 int obj_parts(const dv_plan* P);
-dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global);
-dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
-                      const float* w, const float* u);
+dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, float* out, bool global);
+dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, float* out,
+                      bool global, const float* w, const float* u);
 dv::GridArgs grid_args(const dv_plan* p);
 }  // namespace dv

@@ -36,6 +36,8 @@ dv_status cuda_fail(cudaError_t e, const char* what, const char* file, int line)
 namespace {
 
 constexpr int kMaxK = 127;
+constexpr int kMaxTileGrid = 1024;   // row kernels stage one tile row pair per block in shared memory
+constexpr int kMaxRows = 65535;      // grid.y of the row kernels is one x row
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -181,6 +183,10 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
   if (p->grid_r < 1 || p->grid_c < 1) return fail(DV_ERR_INVALID_ARG, "PSF grid must be >= 1x1");
   if (!p->psfs) return fail(DV_ERR_INVALID_ARG, "psfs is NULL");
   if (p->n_tr < 1 || p->n_tc < 1) return fail(DV_ERR_INVALID_ARG, "tile grid must be >= 1x1");
+  if (p->n_tr > kMaxTileGrid || p->n_tc > kMaxTileGrid)
+    return fail(DV_ERR_INVALID_ARG, "tile grid must be at most %d x %d", kMaxTileGrid, kMaxTileGrid);
+  if ((int64_t)p->hy + p->K - 1 > kMaxRows)
+    return fail(DV_ERR_INVALID_ARG, "x must have at most %d rows", kMaxRows);
   if (!(p->lambda >= 0.0) || !(p->delta > 0.0) || !(p->gamma > 0.0))
     return fail(DV_ERR_INVALID_ARG, "need lambda >= 0, delta > 0, gamma > 0");
   if (!(p->rho > 0.0 && p->rho < 2.0)) return fail(DV_ERR_INVALID_ARG, "rho must be in (0, 2)");
@@ -195,7 +201,7 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
   if (p->precision != DV_PREC_FP32 && p->precision != DV_PREC_TF32 &&
       p->precision != DV_PREC_BF16)
     return fail(DV_ERR_INVALID_ARG, "unknown precision %d", p->precision);
-  if (p->path < DV_PATH_AUTO || p->path > DV_PATH_FFT)
+  if (p->path < DV_PATH_AUTO || p->path > DV_PATH_TENSOR)
     return fail(DV_ERR_INVALID_ARG, "unknown operator path %d", p->path);
   if (p->overlap < 0) return fail(DV_ERR_INVALID_ARG, "overlap must be >= 0");
   if (p->check_every < 0) return fail(DV_ERR_INVALID_ARG, "check_every must be >= 0");
@@ -315,9 +321,14 @@ void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const La
 
 }  // namespace
 
-dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bool global) {
+static int tab_index(int path) {
+  return path == DV_PATH_FFT ? 1 : (path == DV_PATH_TENSOR ? 2 : 0);
+}
+
+dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, float* out,
+                     bool global) {
   OpArgs a{};
-  const OpTables& tb = p->tab[p->path == DV_PATH_FFT ? 1 : 0];
+  const OpTables& tb = p->tab[tab_index(path)];
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Hg : tb.H;
   a.n_work = global ? tb.nHg : tb.nH;
@@ -337,23 +348,25 @@ dv::OpArgs op_args_H(const dv_plan* p, int mode, const float* in, float* out, bo
   a.spec = p->d_spec;
   a.counter = p->d_counter;
   a.scratch = p->d_fft_scr;
-  a.bfrag = p->d_bfragH;
+  a.tcop = p->d_tcopH;
+  a.prec = p->prob.precision;
+  a.err = p->d_err;
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
   return a;
 }
 
-dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, bool global,
-                      const float* w, const float* u) {
-  OpArgs a = op_args_H(p, mode, in, out, global);
-  const OpTables& tb = p->tab[p->path == DV_PATH_FFT ? 1 : 0];
+dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, float* out,
+                      bool global, const float* w, const float* u) {
+  OpArgs a = op_args_H(p, path, mode, in, out, global);
+  const OpTables& tb = p->tab[tab_index(path)];
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Htg : tb.Ht;
   a.n_work = global ? tb.nHtg : tb.nHt;
   a.psf = p->d_psf;
   a.counter = p->d_counter ? p->d_counter + 1 : nullptr;
-  a.bfrag = p->d_bfragHt;
+  a.tcop = p->d_tcopHt;
   a.w = w;
   a.u = u;
   a.omr = p->d_omr;
@@ -361,25 +374,24 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int mode, const float* in, float* out, b
   return a;
 }
 
-cudaError_t launch_op_H(const dv_plan* P, const OpArgs& a, cudaStream_t s, bool fp32_only) {
-  if (P->tc && !fp32_only) return launch_tc_H(a, s);
-  return P->path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
+cudaError_t launch_op_H(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
+  if (path == DV_PATH_TENSOR) return launch_tc_H(a, s);
+  return path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
 }
 
-cudaError_t launch_op_Ht(const dv_plan* P, const OpArgs& a, cudaStream_t s) {
-  if (P->tc) return launch_tc_Ht(a, s);
-  return P->path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
+cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
+  if (path == DV_PATH_TENSOR) return launch_tc_Ht(a, s);
+  return path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
 }
 
-int obj_parts(const dv_plan* P) {
-  return P->path == DV_PATH_FFT ? P->tab[1].nH : P->tab[0].nH;
-}
+int obj_parts(const dv_plan* P) { return P->tab[tab_index(P->fpath)].nH; }
 
 dv::GridArgs grid_args(const dv_plan* p) {
   GridArgs g{};
   g.tiles = p->d_tiles;
   g.rowcov = p->d_rowcov;
-  g.colcov = p->d_colcov;
+  g.cseg = p->d_cseg;
+  g.n_cseg = p->n_cseg;
   g.omr = p->d_omr;
   g.omc = p->d_omc;
   g.n_tc = p->n_tc;
@@ -435,44 +447,57 @@ extern "C" dv_status dv_layout_query(const dv_problem* prob, int32_t* tile_r0, i
 
 namespace dv {
 // Autotuner: times one H (with residual) and one H^T (with the fused step) on
-// the plan's tile stacks for each available path and keeps the faster one.
+// the plan's tile stacks for each candidate path.  The FP32 operator (used
+// for the objective and, unless the tensor path wins, the inner iterations)
+// is the faster of direct and block FFT; with BF16 / TF32 allowed the tensor
+// path competes for the inner iterations.
+static dv_status time_path(dv_plan* P, int path, cudaStream_t s, double& out) {
+  double best = 1e30;
+  for (int rep = 0; rep < 4; ++rep) {
+    DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
+    DV_TRY_CUDA(launch_op_H(P, path, op_args_H(P, path, OP_RESID, P->d_w[0], P->d_r, false), s));
+    DV_TRY_CUDA(launch_op_Ht(P, path, op_args_Ht(P, path, OP_STEP, P->d_r, P->d_w[1], false,
+                                                 P->d_w[0], P->d_u), s));
+    DV_TRY_CUDA(cudaEventRecord(P->ev1, s));
+    DV_TRY_CUDA(cudaEventSynchronize(P->ev1));
+    float ms = 0.f;
+    DV_TRY_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+    if (rep > 0) best = std::min(best, (double)ms);   // first repetition warms up
+  }
+  out = best;
+  return DV_OK;
+}
+
 static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
-  if (P->tc || requested == DV_PATH_DIRECT || !P->fft_ok) {
-    P->path = DV_PATH_DIRECT;
+  if (requested == DV_PATH_DIRECT || requested == DV_PATH_FFT) {
+    P->path = P->fpath = requested;
     return DV_OK;
   }
-  if (requested == DV_PATH_FFT) {
-    P->path = DV_PATH_FFT;
-    return DV_OK;
+  P->fpath = DV_PATH_DIRECT;
+  if (P->fft_ok) {
+    DV_TRY(time_path(P, DV_PATH_DIRECT, s, P->tune_ms[0]));
+    DV_TRY(time_path(P, DV_PATH_FFT, s, P->tune_ms[1]));
+    if (P->tune_ms[1] < P->tune_ms[0]) P->fpath = DV_PATH_FFT;
   }
-  const int paths[2] = {DV_PATH_DIRECT, DV_PATH_FFT};
-  for (int k = 0; k < 2; ++k) {
-    P->path = paths[k];
-    double best = 1e30;
-    for (int rep = 0; rep < 4; ++rep) {
-      DV_TRY_CUDA(cudaEventRecord(P->ev0, s));
-      DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_RESID, P->d_w[0], P->d_r, false), s));
-      DV_TRY_CUDA(launch_op_Ht(P, op_args_Ht(P, OP_STEP, P->d_r, P->d_w[1], false, P->d_w[0],
-                                            P->d_u), s));
-      DV_TRY_CUDA(cudaEventRecord(P->ev1, s));
-      DV_TRY_CUDA(cudaEventSynchronize(P->ev1));
-      float ms = 0.f;
-      DV_TRY_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-      if (rep > 0) best = std::min(best, (double)ms);   // first repetition warms up
-    }
-    P->tune_ms[k] = best;
+  P->path = P->fpath;
+  if (requested == DV_PATH_TENSOR) {
+    P->path = DV_PATH_TENSOR;
+  } else if (P->tensor_ok) {
+    DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms[2]));
+    const double fp32_ms = P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0];
+    if (fp32_ms == 0.0) DV_TRY(time_path(P, P->fpath, s, P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]));
+    if (P->tune_ms[2] < P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]) P->path = DV_PATH_TENSOR;
   }
-  P->path = P->tune_ms[1] < P->tune_ms[0] ? DV_PATH_FFT : DV_PATH_DIRECT;
   return DV_OK;
 }
 
 static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) {
   Layout L;
   DV_TRY(validate_and_layout(prob, L));
-  if (prob->precision == DV_PREC_TF32)
-    return fail(DV_ERR_UNSUPPORTED, "TF32 operands are not available in this build");
-  if (prob->precision == DV_PREC_BF16 && !tc_supported(prob->K))
-    return fail(DV_ERR_UNSUPPORTED, "the BF16 tensor-core operator supports K = 9, 15, 31, 63");
+  if (prob->path == DV_PATH_TENSOR && prob->precision == DV_PREC_FP32)
+    return fail(DV_ERR_INVALID_ARG, "the tensor-core path needs precision BF16 or TF32");
+  if (prob->path == DV_PATH_TENSOR && !tc_supported(prob->K))
+    return fail(DV_ERR_UNSUPPORTED, "the tensor-core operator supports K = 9, 15, 31, 63");
   if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
 
@@ -493,8 +518,10 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   P->n_tc = prob->n_tc;
   P->T = P->n_tr * P->n_tc;
   P->path = DV_PATH_DIRECT;
-  P->tc = prob->precision == DV_PREC_BF16;
-  P->fft_ok = !P->tc && prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
+  P->fpath = DV_PATH_DIRECT;
+  P->tensor_ok = prob->precision != DV_PREC_FP32 && tc_supported(prob->K) &&
+                 (prob->path == DV_PATH_AUTO || prob->path == DV_PATH_TENSOR);
+  P->fft_ok = prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
   {
     int dev = 0;
     DV_TRY_CUDA(cudaGetDevice(&dev));
@@ -586,11 +613,12 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   // host copy of the global tile for work-table construction
   std::vector<TileDesc> gtiles{gt};
 
-  // work tables: direct path always, FFT path when K allows it
+  // work tables: direct path always, FFT and tensor paths when available
   std::vector<WorkItem> w;
-  for (int k = 0; k < (P->fft_ok ? 2 : 1); ++k) {
-    const int bm = k == 0 ? direct_tile_m() : fft_block(K);
-    const int bn = k == 0 ? direct_tile_n() : fft_block(K);
+  for (int k = 0; k < 3; ++k) {
+    if ((k == 1 && !P->fft_ok) || (k == 2 && !P->tensor_ok)) continue;
+    const int bm = k == 0 ? direct_tile_m() : (k == 1 ? fft_block(K) : tc_block_m());
+    const int bn = k == 0 ? direct_tile_n() : (k == 1 ? fft_block(K) : tc_block_n());
     OpTables& tb = P->tab[k];
     // FFT items are handed out dynamically: heaviest (most PSF pairs) first
     auto order = [&](std::vector<WorkItem>& v) {
@@ -626,14 +654,16 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     tb.nHtg = (int)w.size();
     DV_TRY(upload(P, &tb.Htg, w.data(), w.size(), s));
   }
-  if (P->tc) {
-    std::vector<uint2> fr;
-    tc_fragments(prob->psfs, G, K, true, fr);
-    DV_TRY(upload(P, &P->d_bfragH, fr.data(), fr.size(), s));
-    tc_fragments(prob->psfs, G, K, false, fr);
-    DV_TRY(upload(P, &P->d_bfragHt, fr.data(), fr.size(), s));
-    DV_TRY_CUDA(tc_prepare(K));
+  if (P->tensor_ok) {
+    std::vector<uint8_t> op;
+    tc_operands(prob->psfs, G, K, prob->precision, true, op);
+    DV_TRY(upload(P, &P->d_tcopH, op.data(), op.size(), s));
+    tc_operands(prob->psfs, G, K, prob->precision, false, op);
+    DV_TRY(upload(P, &P->d_tcopHt, op.data(), op.size(), s));
+    DV_TRY_CUDA(tc_prepare(K, prob->precision));
   }
+  DV_TRY(alloc(P, &P->d_err, 1));
+  DV_TRY_CUDA(cudaMemsetAsync(P->d_err, 0, sizeof(int), s));
   if (P->fft_ok) {
     DV_TRY(alloc(P, &P->d_counter, 2));
     DV_TRY(alloc(P, &P->d_fft_scr, (size_t)P->n_sm * fft_size() * fft_size()));
@@ -650,7 +680,17 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   for (int tc = 0; tc < P->n_tc; ++tc)
     for (int C = L.yc0[tc]; C < L.yc1[tc] + K - 1; ++C) (cc[C].x < 0 ? cc[C].x : cc[C].y) = tc;
   DV_TRY(upload(P, &P->d_rowcov, rc.data(), rc.size(), s));
-  DV_TRY(upload(P, &P->d_colcov, cc.data(), cc.size(), s));
+  // column segments with a constant set of covering tile columns
+  std::vector<int4> seg;
+  for (int c = 0; c < P->nxc;) {
+    int e = c + 1;
+    while (e < P->nxc && cc[e].x == cc[c].x && cc[e].y == cc[c].y && e - c < row_segment_width())
+      ++e;
+    seg.push_back(make_int4(c, e, cc[c].x, cc[c].y));
+    c = e;
+  }
+  P->n_cseg = (int)seg.size();
+  DV_TRY(upload(P, &P->d_cseg, seg.data(), seg.size(), s));
 
   // iterates, dual variable, residuals, data, scratch
   DV_TRY(alloc(P, &P->d_w[0], P->xstack));
@@ -667,9 +707,9 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   if (prob->noise_w) DV_TRY(upload(P, &P->d_W, prob->noise_w, (size_t)P->hy * P->wy, s));
   DV_TRY(alloc(P, &P->d_z, (size_t)P->nxr * P->nxc));
   DV_TRY(alloc(P, &P->d_xg, (size_t)P->nxr * P->nxc));
-  const int64_t ncons = consensus_blocks(P->nxr, P->nxc);
+  const int64_t ncons = consensus_blocks(P->nxr, P->n_cseg);
   const int64_t nhub = huber_blocks(P->T, P->max_nxr, P->max_nxc);
-  P->n_part = std::max(P->tab[0].nH, P->tab[1].nH) + nhub + 2 * ncons;
+  P->n_part = std::max(std::max(P->tab[0].nH, P->tab[1].nH), P->tab[2].nH) + nhub + 2 * ncons;
   DV_TRY(alloc(P, &P->d_part, (size_t)P->n_part));
   DV_TRY(alloc(P, &P->d_scal, 8));
   DV_TRY_CUDA(cudaMallocHost((void**)&P->h_scal, 8 * sizeof(double)));
@@ -715,8 +755,9 @@ dv_status release(dv_plan* P) {
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
-                  P->d_bfragH, P->d_bfragHt,
-                  P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
+                  P->tab[2].H, P->tab[2].Ht, P->tab[2].Hg, P->tab[2].Htg,
+                  P->d_tcopH, P->d_tcopHt, P->d_err,
+                  P->d_rowcov, P->d_cseg, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -748,14 +789,15 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->kernel_launches = P->launches;
   info->tune_ms_direct = P->tune_ms[0];
   info->tune_ms_fft = P->tune_ms[1];
-  const int k = P->path == DV_PATH_FFT ? 1 : 0;
+  info->tune_ms_tensor = P->tune_ms[2];
+  info->fp32_path = P->fpath;
+  const int k = tab_index(P->path);
   info->blocks[0] = P->tab[k].nH;
   info->blocks[1] = P->tab[k].nHt;
   info->block_psfs[0] = P->tab[k].psfs[0];
   info->block_psfs[1] = P->tab[k].psfs[1];
   info->psf_pairs[0] = P->tab[k].pairs[0];
   info->psf_pairs[1] = P->tab[k].pairs[1];
-  info->block_side = k ? fft_block(P->K) : direct_tile_m();
-  info->pad = 0;
+  info->block_side = k == 1 ? fft_block(P->K) : (k == 2 ? tc_block_m() : direct_tile_m());
   return DV_OK;
 }

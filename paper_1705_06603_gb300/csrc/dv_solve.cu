@@ -13,9 +13,11 @@ namespace {
 enum Kind { KIND_H = 0, KIND_HT = 1, KIND_CONS = 2 };
 
 int nhub(const dv_plan* P) { return huber_blocks(P->T, P->max_nxr, P->max_nxc); }
-int ncons(const dv_plan* P) { return consensus_blocks(P->nxr, P->nxc); }
+int ncons(const dv_plan* P) { return consensus_blocks(P->nxr, P->n_cseg); }
 double* part_data(dv_plan* P) { return P->d_part; }
-int npart_data(const dv_plan* P) { return std::max(P->tab[0].nH, P->tab[1].nH); }
+int npart_data(const dv_plan* P) {
+  return std::max(std::max(P->tab[0].nH, P->tab[1].nH), P->tab[2].nH);
+}
 double* part_hub(dv_plan* P) { return P->d_part + npart_data(P); }
 double* part_cons(dv_plan* P) { return P->d_part + npart_data(P) + nhub(P); }
 
@@ -64,12 +66,14 @@ dv_status timed_launch(dv_plan* P, int kind, cudaStream_t s, F fn) {
 }
 
 cudaError_t launch_inner_H(dv_plan* P, int par, cudaStream_t s) {
-  return launch_op_H(P, op_args_H(P, OP_RESID, P->d_w[par], P->d_r, false), s);
+  return launch_op_H(P, P->path, op_args_H(P, P->path, OP_RESID, P->d_w[par], P->d_r, false), s);
 }
 
 cudaError_t launch_inner_Ht(dv_plan* P, int par, cudaStream_t s) {
-  return launch_op_Ht(
-      P, op_args_Ht(P, OP_STEP, P->d_r, P->d_w[par ^ 1], false, P->d_w[par], P->d_u), s);
+  return launch_op_Ht(P, P->path,
+                      op_args_Ht(P, P->path, OP_STEP, P->d_r, P->d_w[par ^ 1], false, P->d_w[par],
+                                 P->d_u),
+                      s);
 }
 
 dv_status capture_node(cudaStream_t cs, cudaGraphNode_t* node) {
@@ -195,7 +199,7 @@ dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
   DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
   DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, P->d_xg, nullptr, P->hy, P->wy,
                              P->rad, tmp, nullptr, s, nullptr));
-  DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_OBJ, tmp, nullptr, false), s, true));
+  DV_TRY_CUDA(launch_op_H(P, P->fpath, op_args_H(P, P->fpath, OP_OBJ, tmp, nullptr, false), s));
   DV_TRY_CUDA(launch_huber_value(P->d_tiles, P->T, P->max_nxr, P->max_nxc, tmp, P->prob.delta,
                                  part_hub(P), s));
   const double* parts[4] = {part_data(P), part_hub(P), part_cons(P), part_cons(P) + ncons(P)};
@@ -203,7 +207,11 @@ dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
   DV_TRY_CUDA(launch_reduce(parts, counts, residuals ? 4 : 2, P->d_scal, s));
   P->launches += 5;
   DV_TRY_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int* h_err = reinterpret_cast<int*>(P->h_scal + 6);
+  DV_TRY_CUDA(cudaMemcpyAsync(h_err, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   DV_TRY_CUDA(cudaStreamSynchronize(s));
+  if (*h_err != 0)
+    return fail(DV_ERR_TIMEOUT, "a tensor-core operator kernel gave up waiting on its pipeline");
   if (!residuals) P->h_scal[2] = P->h_scal[3] = NAN;
   return DV_OK;
 }
@@ -299,7 +307,8 @@ extern "C" dv_status dv_apply_H(dv_plan* P, const float* x_dev, float* y_dev, vo
   clear_error();
   DV_TRY(check_plan(P));
   if (!x_dev || !y_dev) return fail(DV_ERR_INVALID_ARG, "x_dev and y_dev must not be NULL");
-  DV_TRY_CUDA(launch_op_H(P, op_args_H(P, OP_PLAIN, x_dev, y_dev, true), (cudaStream_t)stream));
+  DV_TRY_CUDA(launch_op_H(P, P->path, op_args_H(P, P->path, OP_PLAIN, x_dev, y_dev, true),
+                          (cudaStream_t)stream));
   P->launches += 1;
   return DV_OK;
 }
@@ -308,7 +317,8 @@ extern "C" dv_status dv_apply_Ht(dv_plan* P, const float* r_dev, float* g_dev, v
   clear_error();
   DV_TRY(check_plan(P));
   if (!r_dev || !g_dev) return fail(DV_ERR_INVALID_ARG, "r_dev and g_dev must not be NULL");
-  DV_TRY_CUDA(launch_op_Ht(P, op_args_Ht(P, OP_PLAIN, r_dev, g_dev, true, nullptr, nullptr),
+  DV_TRY_CUDA(launch_op_Ht(P, P->path,
+                           op_args_Ht(P, P->path, OP_PLAIN, r_dev, g_dev, true, nullptr, nullptr),
                             (cudaStream_t)stream));
   P->launches += 1;
   return DV_OK;

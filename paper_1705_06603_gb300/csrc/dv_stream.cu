@@ -54,58 +54,107 @@ __global__ void scatter_kernel(const TileDesc* __restrict__ tiles, const float* 
   }
 }
 
+// The consensus and assembly kernels work on row segments: a block owns one
+// global x row R and one column segment [c0, c1) over which the covering tile
+// columns do not change (at most ROW_SEG columns), so the (at most 2 x 2)
+// covering tiles are fixed for the whole block and NBR threads stride over
+// the segment, every warp touching 32 consecutive pixels of each tile stack.
+constexpr int NBR = 128;     // threads per block of the row kernels
+constexpr int GRP = 4;       // pixels per thread and group: the group's loads are issued together
+constexpr int ROW_SEG = 1024;  // longest column segment of one block
+constexpr int HUB_ROWS = 4;  // tile rows per block of the prior kernel
+
+// The covering tiles of block (R, segment) as slots (i, j): tile row i of
+// the row cover, tile column j of the segment.  Per slot: stack offset of
+// global column 0 on row R, row factor of the profile times `scale`, offset
+// of global column 0 in the column profile.
+struct RowSlots {
+  int64_t base[4];
+  float row[4];
+  int omc[4];
+  bool valid[4];
+};
+
+__device__ __forceinline__ RowSlots row_slots(const GridArgs& G, int R, const int4& sg, float scale) {
+  RowSlots S;
+  const int2 rc = G.rowcov[R];
+#pragma unroll
+  for (int sl = 0; sl < 4; ++sl) {
+    const int tr = (sl >> 1) ? rc.y : rc.x, tc = (sl & 1) ? sg.w : sg.z;
+    S.valid[sl] = tr >= 0 && tc >= 0;
+    S.base[sl] = 0;
+    S.row[sl] = 0.f;
+    S.omc[sl] = 0;
+    if (S.valid[sl]) {
+      const TileDesc& td = G.tiles[tr * G.n_tc + tc];
+      const int lr = R - td.xr0;
+      S.base[sl] = td.xoff + (int64_t)lr * td.xpitch - td.xc0;
+      S.row[sl] = scale * G.omr[td.omr_off + lr];
+      S.omc[sl] = td.omc_off - td.xc0;
+    }
+  }
+  return S;
+}
+
 // Per global x pixel: zbar = sum_i alpha_i (2 x_i - u_i) / sum_i alpha_i over
 // the (at most 2 x 2) tiles covering it, then u_i <- u_i + rho (zbar - x_i).
-// With partials: FP64 block sums of (x_i - zbar)^2 and (zbar - zbar_prev)^2.
-__global__ void __launch_bounds__(NB) consensus_kernel(const GridArgs G, const float* __restrict__ x,
-                                                       float* __restrict__ u, float gamma, float rho,
-                                                       float* __restrict__ zg,
-                                                       double* __restrict__ partials) {
-  __shared__ double red[NB / 32];
+// With partials: FP64 block sums of (x_i - zbar)^2 and (zbar - zbar_prev)^2
+// (each thread adds a group's FP32 sum of at most 4 x 4 terms in FP64).
+__global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const float* __restrict__ x,
+                                                        float* __restrict__ u, float gamma, float rho,
+                                                        float* __restrict__ zg,
+                                                        double* __restrict__ partials) {
+  __shared__ double red[NBR / 32];
   const int R = blockIdx.y;
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  const int4 sg = G.cseg[blockIdx.x];
+  const RowSlots S = row_slots(G, R, sg, gamma);
   double pp = 0.0, dd = 0.0;
-  if (C < G.nxc) {
-    const int2 rc = G.rowcov[R], cc = G.colcov[C];
-    const int trs[2] = {rc.x, rc.y}, tcs[2] = {cc.x, cc.y};
-    float xv[4], uv[4];
-    int64_t idx[4];
-    int n = 0;
-    float num = 0.f, den = 0.f;
+  for (int cb = sg.x + threadIdx.x; cb < sg.y; cb += GRP * NBR) {
+    float xs[GRP][4], us[GRP][4], as[GRP][4], zp[GRP];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      if (trs[i] < 0) continue;
+    for (int k = 0; k < GRP; ++k) {
+      const int C = cb + k * NBR;
+      const bool in = C < sg.y;
+      zp[k] = (in && zg) ? zg[(int64_t)R * G.nxc + C] : 0.f;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        if (tcs[j] < 0) continue;
-        const TileDesc& td = G.tiles[trs[i] * G.n_tc + tcs[j]];
-        const int lr = R - td.xr0, lc = C - td.xc0;
-        const int64_t id = td.xoff + (int64_t)lr * td.xpitch + lc;
-        const float xa = x[id], ua = u[id];
-        const float al = gamma * G.omr[td.omr_off + lr] * G.omc[td.omc_off + lc];
-        num += al * (2.f * xa - ua);
-        den += al;
-        xv[n] = xa;
-        uv[n] = ua;
-        idx[n] = id;
-        ++n;
+      for (int sl = 0; sl < 4; ++sl) {
+        xs[k][sl] = us[k][sl] = as[k][sl] = 0.f;
+        if (in && S.valid[sl]) {
+          const int64_t id = S.base[sl] + C;
+          xs[k][sl] = x[id];
+          us[k][sl] = u[id];
+          as[k][sl] = S.row[sl] * G.omc[S.omc[sl] + C];
+        }
       }
     }
-    const float z = num / den;
+    float pg = 0.f, dg = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k < n) {
-        u[idx[k]] = uv[k] + rho * (z - xv[k]);
-        const double e = (double)xv[k] - (double)z;
-        pp += e * e;
+    for (int k = 0; k < GRP; ++k) {
+      const int C = cb + k * NBR;
+      if (C >= sg.y) continue;
+      float num = 0.f, den = 0.f;
+#pragma unroll
+      for (int sl = 0; sl < 4; ++sl) {
+        num += as[k][sl] * (2.f * xs[k][sl] - us[k][sl]);
+        den += as[k][sl];
+      }
+      const float z = num / den;
+#pragma unroll
+      for (int sl = 0; sl < 4; ++sl) {
+        if (S.valid[sl]) {
+          u[S.base[sl] + C] = us[k][sl] + rho * (z - xs[k][sl]);
+          const float d = xs[k][sl] - z;
+          pg = fmaf(d, d, pg);
+        }
+      }
+      if (zg) {
+        const float d = z - zp[k];
+        dg = fmaf(d, d, dg);
+        zg[(int64_t)R * G.nxc + C] = z;
       }
     }
-    if (zg) {
-      const int64_t gi = (int64_t)R * G.nxc + C;
-      const double e = (double)z - (double)zg[gi];
-      dd += e * e;
-      zg[gi] = z;
-    }
+    pp += (double)pg;
+    dd += (double)dg;
   }
   if (partials) {
     const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
@@ -117,52 +166,61 @@ __global__ void __launch_bounds__(NB) consensus_kernel(const GridArgs G, const f
 }
 
 // x_hat = sum_i omega_i x_i / sum_i omega_i over the tiles covering each pixel.
-__global__ void __launch_bounds__(NB) assemble_kernel(const GridArgs G, const float* __restrict__ x,
-                                                      float* __restrict__ out) {
+__global__ void __launch_bounds__(NBR) assemble_kernel(const GridArgs G, const float* __restrict__ x,
+                                                       float* __restrict__ out) {
   const int R = blockIdx.y;
-  const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= G.nxc) return;
-  const int2 rc = G.rowcov[R], cc = G.colcov[C];
-  const int trs[2] = {rc.x, rc.y}, tcs[2] = {cc.x, cc.y};
-  float num = 0.f, den = 0.f;
+  const int4 sg = G.cseg[blockIdx.x];
+  const RowSlots S = row_slots(G, R, sg, 1.f);
+  for (int cb = sg.x + threadIdx.x; cb < sg.y; cb += GRP * NBR) {
+    float num[GRP], den[GRP];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    if (trs[i] < 0) continue;
+    for (int k = 0; k < GRP; ++k) {
+      const int C = cb + k * NBR;
+      num[k] = den[k] = 0.f;
+      if (C >= sg.y) continue;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (tcs[j] < 0) continue;
-      const TileDesc& td = G.tiles[trs[i] * G.n_tc + tcs[j]];
-      const int lr = R - td.xr0, lc = C - td.xc0;
-      const float om = G.omr[td.omr_off + lr] * G.omc[td.omc_off + lc];
-      num += om * x[td.xoff + (int64_t)lr * td.xpitch + lc];
-      den += om;
+      for (int sl = 0; sl < 4; ++sl) {
+        if (S.valid[sl]) {
+          const float om = S.row[sl] * G.omc[S.omc[sl] + C];
+          num[k] += om * x[S.base[sl] + C];
+          den[k] += om;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < GRP; ++k) {
+      const int C = cb + k * NBR;
+      if (C < sg.y) out[(int64_t)R * G.nxc + C] = num[k] / den[k];
     }
   }
-  out[(int64_t)R * G.nxc + C] = num / den;
 }
 
 // FP64 block partials of sum_l hub(|grad x(l)|) over every tile of the stack
-// (forward differences, zero on each tile's last row / column).
-__global__ void __launch_bounds__(NB) huber_value_kernel(const TileDesc* __restrict__ tiles,
-                                                         const float* __restrict__ x, double delta,
-                                                         double* __restrict__ partials) {
-  __shared__ double red[NB / 32];
-  const TileDesc td = tiles[blockIdx.z];
-  const int R = blockIdx.y;
+// (forward differences, zero on each tile's last row / column).  A block owns
+// HUB_ROWS rows of one tile; each pixel's term is formed in FP32 and each
+// thread adds its FP32 row sum in FP64.
+__global__ void __launch_bounds__(NBR) huber_value_kernel(const TileDesc* __restrict__ tiles,
+                                                          const float* __restrict__ x, float delta,
+                                                          double* __restrict__ partials) {
+  __shared__ double red[NBR / 32];
+  const TileDesc td = tiles[blockIdx.y];
   double acc = 0.0;
-  if (R < td.nxr) {
-    for (int C = blockIdx.x * blockDim.x + threadIdx.x; C < td.nxc; C += gridDim.x * blockDim.x) {
-      const int64_t idx = td.xoff + (int64_t)R * td.xpitch + C;
-      const double c0 = x[idx];
-      const double dr = (R + 1 < td.nxr) ? (double)x[idx + td.xpitch] - c0 : 0.0;
-      const double dc = (C + 1 < td.nxc) ? (double)x[idx + 1] - c0 : 0.0;
-      const double s = sqrt(dr * dr + dc * dc);
-      acc += (s <= delta) ? 0.5 * s * s : delta * (s - 0.5 * delta);
+  const int r0 = blockIdx.x * HUB_ROWS, r1 = min(r0 + HUB_ROWS, td.nxr);
+  for (int R = r0; R < r1; ++R) {
+    const float* row = x + td.xoff + (int64_t)R * td.xpitch;
+    const bool down = R + 1 < td.nxr;
+    float racc = 0.f;
+    for (int C = threadIdx.x; C < td.nxc; C += NBR) {
+      const float c = row[C];
+      const float dr = down ? row[C + td.xpitch] - c : 0.f;
+      const float dc = (C + 1 < td.nxc) ? row[C + 1] - c : 0.f;
+      const float s2 = dr * dr + dc * dc;
+      racc += (s2 <= delta * delta) ? 0.5f * s2 : delta * (sqrtf(s2) - 0.5f * delta);
     }
+    acc += (double)racc;
   }
   const double t = block_sum(acc, red);
-  if (threadIdx.x == 0)
-    partials[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = t;
+  if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 struct ReduceArgs {
@@ -194,30 +252,34 @@ cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_
   return cudaGetLastError();
 }
 
+int row_segment_width() { return ROW_SEG; }
+
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma, float rho,
                              float* zbuf, double* partials, cudaStream_t s, int* n_blocks_out) {
-  dim3 grid(cdiv(g.nxc, NB), g.nxr);
+  dim3 grid(g.n_cseg, g.nxr);
   if (n_blocks_out) *n_blocks_out = grid.x * grid.y;
-  consensus_kernel<<<grid, NB, 0, s>>>(g, x, u, gamma, rho, zbuf, partials);
+  consensus_kernel<<<grid, NBR, 0, s>>>(g, x, u, gamma, rho, zbuf, partials);
   return cudaGetLastError();
 }
 
-int consensus_blocks(int nxr, int nxc) { return cdiv(nxc, NB) * nxr; }
+int consensus_blocks(int nxr, int n_cseg) { return n_cseg * nxr; }
 
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s) {
-  dim3 grid(cdiv(g.nxc, NB), g.nxr);
-  assemble_kernel<<<grid, NB, 0, s>>>(g, x, out);
+  dim3 grid(g.n_cseg, g.nxr);
+  assemble_kernel<<<grid, NBR, 0, s>>>(g, x, out);
   return cudaGetLastError();
 }
 
 int huber_blocks(int n_tiles, int max_nxr, int max_nxc) {
-  return cdiv(max_nxc, NB) * max_nxr * n_tiles;
+  (void)max_nxc;
+  return cdiv(max_nxr, HUB_ROWS) * n_tiles;
 }
 
 cudaError_t launch_huber_value(const TileDesc* tiles, int n_tiles, int max_nxr, int max_nxc,
                                const float* x, double delta, double* partials, cudaStream_t s) {
-  dim3 grid(cdiv(max_nxc, NB), max_nxr, n_tiles);
-  huber_value_kernel<<<grid, NB, 0, s>>>(tiles, x, delta, partials);
+  (void)max_nxc;
+  dim3 grid(cdiv(max_nxr, HUB_ROWS), n_tiles);
+  huber_value_kernel<<<grid, NBR, 0, s>>>(tiles, x, (float)delta, partials);
   return cudaGetLastError();
 }
 

@@ -1,18 +1,31 @@
-// BF16 tensor-core kernels of the shift-variant operator of Sec. II-B and its
-// adjoint (FP32 accumulation), on the direct path's 64x64 output blocks.
+// Tensor-core (tcgen05) kernels of the shift-variant operator of Sec. II-B
+// and its adjoint: BF16 or TF32 operands, FP32 accumulation in tensor memory.
 //
 // For one PSF and one filter row a, a correlation is a banded-Toeplitz
-// product:  Y[i][j] += sum_c S[i + a][c] T_a[c][j],  T_a[c][j] = f(a, c - j)
-// for 0 <= c - j < K, with S the staged input block and f the (flipped for H)
-// PSF.  Each warp owns 16 output rows x 64 columns = 8 tiles of the
-// m16n8k16 BF16 MMA; for tap row a and k-step ks, tile nt reads the 16
-// columns [8 nt + 16 ks, +16) of rows shifted by a.  A operands come from
-// shared memory with ldmatrix (any row shift is just another row address;
-// 8-column chunk q = nt + 2 ks is shared by several tiles), B fragments depend
-// only on (PSF, a, ks) and are precomputed on the host in bfloat16.
-//   H:   S = bf16(w_p . x); all PSFs accumulate into the same fragments.
-//   H^T: S = bf16(r) staged once; each PSF's correlation is weighted by w_p at
-//        the output (FP32) and summed.
+// product over the staged input block S:
+//     D[i][j] += sum_c S[i + a][c] T_a[c][j],   T_a[c][j] = f(a, c - j), 0 <= c - j < K,
+// with f the flipped PSF (H) or the PSF (H^T).  A CTA owns BM = 128 output
+// rows x BN = 64 output columns; one tcgen05.mma (M = 128, N = 64, 32 bytes
+// of K) covers the k-step ks of tap row a:
+//   A = rows i + a of S, columns [KM ks, KM ks + KM): shared memory, K-major,
+//       no swizzle, each 16-byte column chunk a panel of rows 16 bytes apart,
+//       so the row shift a is the start address plus 16 a;
+//   B = T_a on the same columns, N x KM, K-major: a 64-row window of one
+//       "tall" matrix per tap row, Bt[n'][k] = f(a, k + KM (KS - 1) - n'),
+//       two panels of (64 + KM (KS - 1)) x 16 bytes.  The tall matrices are
+//       precomputed on the host per PSF and streamed by cp.async.bulk into a
+//       ring of stages guarded by mbarriers.
+//   H:   S = w_p . x is restaged per PSF (double-buffered when it fits); all
+//        PSFs accumulate into one 128 x 64 FP32 accumulator in tensor memory.
+//   H^T: S = r is staged once; PSF p accumulates into tensor-memory buffer
+//        p & 1 and the epilogue warps add w_p . D_p into registers while the
+//        next PSF's MMAs run; the projected-gradient step is fused.
+// Warp roles: warps 0-3 stage operands and run the epilogue (warp w reads
+// tensor-memory lanes 32w .. 32w + 31, i.e. output rows); warp 4 allocates
+// tensor memory and one of its lanes issues every bulk copy and MMA.  Every
+// mbarrier wait gives up after about two seconds, records the timeout in the
+// plan's error word and sends the whole CTA to its teardown, which waits (with
+// its own bound) for the copies and MMAs it issued and frees tensor memory.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -23,156 +36,491 @@
 namespace dv {
 namespace {
 
-constexpr int TM = 64, TN = 64, NW = 4, NT = 32 * NW;
-constexpr int NTILE = TN / 8;     // 8 MMA tiles across a warp's 64 columns
+constexpr int BM = 128, BN = 64;
+constexpr int NWE = 4;                    // staging / epilogue warps
+constexpr int NTH = 32 * (NWE + 1);       // + the issuing warp
+constexpr int NST = 6;                    // B ring stages (one tap row each)
+constexpr int OPITCH = BN + 1;            // fp32 output staging pitch (floats)
+constexpr uint64_t kWaitNs = 2000000000ull;    // bound of a pipeline wait
+constexpr uint64_t kDrainNs = 200000000ull;    // bound of a teardown wait
 
-__host__ __device__ constexpr int ksteps(int K) { return (8 + K - 1 + 15) / 16; }
-// staged width (bf16 elements): chunks 0 .. 7 + 2 KS - 1, 8 columns each
-__host__ __device__ constexpr int swidth(int K) { return 8 * (NTILE + 2 * ksteps(K) - 1); }
+// PREC 0: BF16 (8 elements per 16-byte chunk, MMA K = 16); 1: TF32 (4, 8)
+template <int PREC>
+struct Elt {
+  static constexpr int bytes = PREC == 0 ? 2 : 4;
+  static constexpr int chunk = 16 / bytes;
+  static constexpr int km = 32 / bytes;
+};
 
-// Shared memory: [S (bf16) | B fragments of one PSF] at 0, reused by the
-// (TM+2) x (TN+2) fp32 halo of the step epilogue; the fp32 output staging
-// block after both.
-__host__ __device__ constexpr size_t tc_off_out(int K) {
-  return (((size_t)(TM + K - 1) * swidth(K) * 2 + (size_t)K * ksteps(K) * 32 * 8 >
-                   (size_t)(TM + 2) * (TN + 2) * 4
-               ? (size_t)(TM + K - 1) * swidth(K) * 2 + (size_t)K * ksteps(K) * 32 * 8
-               : (size_t)(TM + 2) * (TN + 2) * 4) +
-          15) / 16 * 16;
+template <int PREC, int K>
+struct Geo {
+  static constexpr int KM = Elt<PREC>::km;
+  static constexpr int CH = Elt<PREC>::chunk;
+  static constexpr int KS = (BN - 1 + K + KM - 1) / KM;   // MMAs per tap row
+  static constexpr int COLS = KS * KM;                    // staged input columns
+  static constexpr int NCH = COLS / CH;                   // 16-byte column panels
+  static constexpr int ROWS = BM + K - 1;                 // staged input rows
+  static constexpr int APANEL = ROWS * 16 + 16;           // + 16 spreads panels over banks
+  static constexpr int ABYTES = NCH * APANEL;
+  static constexpr int RB = BN + KM * (KS - 1);           // rows of the tall B operand
+  static constexpr int BPANEL = RB * 16;
+  static constexpr int BBYTES = 2 * BPANEL;               // one tap row
+  // epilogue (reuses the A region): fp32 output block, and for the H^T step
+  // the (BM + 2) x (BN + 2) halo of the iterate
+  static constexpr int OBYTES = BM * OPITCH * 4;
+  static constexpr int WBYTES = (BM + 2) * (BN + 2) * 4;
+  // H: two A buffers when they fit
+  static constexpr int NA = (2 * ABYTES + NST * BBYTES + 4096 <= 220 * 1024) ? 2 : 1;
+  static constexpr int AREG_H = NA * ABYTES > OBYTES ? NA * ABYTES : OBYTES;
+  static constexpr int AREG_HT = ABYTES > OBYTES + WBYTES ? ABYTES : OBYTES + WBYTES;
+};
+
+struct Bars {            // mbarriers etc., at the start of dynamic shared memory
+  uint64_t bfull[NST], bempty[NST];
+  uint64_t afull[2], aempty[2];
+  uint64_t dfull[2], dempty[2];
+  uint64_t fin;          // all MMAs of the CTA complete (teardown)
+  uint32_t tmem;         // tensor-memory base written by tcgen05.alloc
+  int abort;             // set by the first wait that gives up
+};
+constexpr int kHdr = 256;  // bytes reserved for Bars
+static_assert(sizeof(Bars) <= kHdr, "barrier header");
+
+template <int PREC, int K>
+constexpr size_t smem_H() {
+  using G = Geo<PREC, K>;
+  return kHdr + (size_t)G::AREG_H + (size_t)NST * G::BBYTES + (size_t)2 * (G::ROWS + G::COLS) * 4;
 }
-size_t tc_smem(int K) { return tc_off_out(K) + (size_t)TM * (TN + 4) * 4; }
+constexpr int kMaxWcol = 16;   // H^T: PSF grid columns whose output weights are staged
+template <int PREC, int K>
+constexpr size_t smem_Ht() {
+  using G = Geo<PREC, K>;
+  return kHdr + (size_t)G::AREG_HT + (size_t)NST * G::BBYTES + (size_t)kMaxWcol * BN * 4;
+}
+// Requests are padded so that at most 6 H CTAs (64 tensor-memory columns
+// each) or 3 H^T CTAs (128 each) share an SM: their allocations stay within
+// the 512 columns, so tcgen05.alloc never has to wait for another CTA.
+constexpr size_t kMinSmemH = 36 * 1024, kMinSmemHt = 58 * 1024;
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+// ----------------------------------------------------------------- PTX glue
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
-
-__device__ __forceinline__ void ldsm_x2(uint32_t& r0, uint32_t& r1, const void* p) {
-  const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r0), "=r"(r1)
-               : "r"(a));
-}
-
-// acc[nt][.] += sum_a sum_ks  A(rows + a, chunk nt + 2 ks) B(a, ks)
-template <int K>
-__device__ __forceinline__ void tc_corr(const __nv_bfloat16* sS, const uint2* sB, int row0,
-                                        float (&acc)[NTILE][4]) {
-  constexpr int KS = ksteps(K);
-  constexpr int W = swidth(K);
-  constexpr int NCH = NTILE + 2 * KS;   // chunks read per tap row
-  const int lane = threadIdx.x & 31;
-  const __nv_bfloat16* rowp = sS + (row0 + (lane & 15)) * W;
-#pragma unroll 1
-  for (int a = 0; a < K; ++a) {
-    uint32_t r0[NCH], r1[NCH];
-#pragma unroll
-    for (int q = 0; q < NCH - 1; ++q) ldsm_x2(r0[q], r1[q], rowp + a * W + 8 * q);
-    r0[NCH - 1] = r1[NCH - 1] = 0u;
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-      const uint2 b = sB[(a * KS + ks) * 32 + lane];
-#pragma unroll
-      for (int nt = 0; nt < NTILE; ++nt) {
-        const int q = nt + 2 * ks;
-        mma_bf16(acc[nt], r0[q], r1[q], r0[q + 1], r1[q + 1], b.x, b.y);
-      }
+// Pipeline wait: false after kWaitNs (the CTA-wide abort flag set and the
+// timeout recorded), or at once when another role has already given up.
+__device__ __noinline__ bool wait_bar(uint64_t* b, uint32_t parity, Bars* H, int* err) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (*(volatile int*)&H->abort) return false;
+    if (gtime() - t0 > kWaitNs) {
+      *(volatile int*)&H->abort = 1;
+      if (err) atomicExch(err, 1);
+      return false;
     }
   }
 }
-
-// Accumulator element (tile nt, slot e) -> (row, col) in the warp's 16 x 64 band
-__device__ __forceinline__ void frag_pos(int nt, int e, int& r, int& c) {
-  const int lane = threadIdx.x & 31;
-  r = (lane >> 2) + (e >= 2 ? 8 : 0);
-  c = 8 * nt + 2 * (lane & 3) + (e & 1);
+// Teardown wait for work this CTA issued: ignores the abort flag, own bound.
+__device__ __noinline__ bool drain_bar(uint64_t* b, uint32_t parity, int* err) {
+  const uint64_t t0 = gtime();
+  while (!mbar_try(b, parity)) {
+    if (gtime() - t0 > kDrainNs) {
+      if (err) atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          saddr(dst)),
+      "l"(src), "r"(bytes), "r"(saddr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   saddr(bar))
+               : "memory");
+}
+// Barrier of the four staging / epilogue warps, and the same barrier as an
+// AND-vote, so that all of them take the same branch after a wait.
+__device__ __forceinline__ void named_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * NWE) : "memory");
+}
+__device__ __forceinline__ bool named_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * NWE)
+      : "memory");
+  return r != 0;
 }
 
-template <int K>
-__global__ void __launch_bounds__(NT) tc_H_kernel(const OpArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int KS = ksteps(K), W = swidth(K), ROWS = TM + K - 1;
-  __nv_bfloat16* sS = reinterpret_cast<__nv_bfloat16*>(smem);
-  uint2* sB = reinterpret_cast<uint2*>(smem + (size_t)ROWS * W * 2);
-  float* sO = reinterpret_cast<float*>(smem + tc_off_out(K));
-  __shared__ float sWr[ROWS], sWc[W];
-  __shared__ double red[NW];
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, LBO =
+// byte distance between the two 16-byte K chunks, SBO = 128 (eight 16-byte
+// rows per core matrix, core matrices contiguous along M / N), version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor: FP32 accumulator, A and B BF16 (1) or TF32 (2),
+// both K-major, N = 64, M = 128.
+template <int PREC>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((PREC == 0 ? 1u : 2u) << 7) | ((PREC == 0 ? 1u : 2u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  if constexpr (PREC == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<0>()), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc<1>()), "r"(acc)
+        : "memory");
+  }
+}
+// 32 consecutive FP32 columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t base, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols)
+               : "memory");
+}
+
+// Operand chunk from FP32 values: BF16 round-to-nearest-even or TF32
+// round-to-nearest (ties away), 16 bytes.
+template <int PREC>
+__device__ __forceinline__ uint4 pack_chunk(const float* v) {
+  uint32_t w[4];
+  if constexpr (PREC == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(v[i]));
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int PREC, int K>
+__device__ __forceinline__ void put_chunk(unsigned char* abuf, int ir, int q, const float* v) {
+  using G = Geo<PREC, K>;
+  *reinterpret_cast<uint4*>(abuf + (size_t)q * G::APANEL + ir * 16) = pack_chunk<PREC>(v);
+}
+
+// The MMAs of one tap row: KS k-steps accumulating into tensor-memory column d.
+template <int PREC, int K>
+__device__ __forceinline__ void issue_row(uint32_t d, uint32_t a_base, int a, uint32_t b_stage,
+                                          bool first) {
+  using G = Geo<PREC, K>;
+#pragma unroll
+  for (int ks = 0; ks < G::KS; ++ks) {
+    const uint64_t ad = sdesc(a_base + (uint32_t)(2 * ks) * G::APANEL + 16u * a, G::APANEL);
+    const uint64_t bd = sdesc(b_stage + 16u * G::KM * (G::KS - 1 - ks), G::BPANEL);
+    mma<PREC>(d, ad, bd, (first && ks == 0) ? 0u : 1u);
+  }
+}
+
+// One lane of warp 4: streams the B tap rows of the PSFs (a_lo..a_hi) x
+// (b_lo..b_hi) through the ring and issues their MMAs.
+// H (ADJ = false): PSF p reads A buffer p % NA and accumulates into d0.
+// H^T (ADJ = true): PSF p reads the single A buffer and accumulates into
+// d0 + 64 (p & 1) once the epilogue has released that buffer.
+template <int PREC, int K, bool ADJ>
+__device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned char* areg,
+                       unsigned char* breg, uint32_t d0, int np) {
+  using G = Geo<PREC, K>;
+  const int nb = wi.b_hi - wi.b_lo + 1;
+  const int total = np * K;
+  const unsigned char* src0 = A.tcop;
+  auto src_of = [&](int it) {
+    const int p = it / K, a = it - p * K;
+    const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+    return src0 + ((size_t)(ga * A.Gc + gb) * K + a) * G::BBYTES;
+  };
+  const int pro = total < NST ? total : NST;
+  for (int it = 0; it < pro; ++it) {
+    mbar_expect_tx(&H->bfull[it], G::BBYTES);
+    bulk_g2s(breg + (size_t)it * G::BBYTES, src_of(it), G::BBYTES, &H->bfull[it]);
+  }
+  int issued = pro, consumed = 0;
+  bool ok = true;
+  for (int p = 0; p < np && ok; ++p) {
+    uint32_t a_base, d;
+    if constexpr (ADJ) {
+      a_base = saddr(areg);
+      d = d0 + 64u * (uint32_t)(p & 1);
+      if (p == 0) ok = wait_bar(&H->afull[0], 0, H, A.err);
+      if (ok && p >= 2) ok = wait_bar(&H->dempty[p & 1], (uint32_t)((p / 2 - 1) & 1), H, A.err);
+    } else {
+      const int ab = p % G::NA;
+      a_base = saddr(areg + (size_t)ab * G::ABYTES);
+      d = d0;
+      ok = wait_bar(&H->afull[ab], (uint32_t)((p / G::NA) & 1), H, A.err);
+    }
+    if (!ok) break;
+    tc_fence_after();
+    for (int a = 0; a < K; ++a) {
+      const int it = p * K + a, s = it % NST;
+      if (!wait_bar(&H->bfull[s], (uint32_t)((it / NST) & 1), H, A.err)) {
+        ok = false;
+        break;
+      }
+      consumed = it + 1;
+      tc_fence_after();
+      issue_row<PREC, K>(d, a_base, a, saddr(breg + (size_t)s * G::BBYTES),
+                         ADJ ? (a == 0) : (p == 0 && a == 0));
+      tc_commit(&H->bempty[s]);
+      // refill the stage of the previous tap row once its MMAs are done
+      if (it >= 1 && issued < total) {
+        const int prev = it - 1, s1 = prev % NST;
+        if (!wait_bar(&H->bempty[s1], (uint32_t)((prev / NST) & 1), H, A.err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&H->bfull[s1], G::BBYTES);
+        bulk_g2s(breg + (size_t)s1 * G::BBYTES, src_of(issued), G::BBYTES, &H->bfull[s1]);
+        ++issued;
+      }
+    }
+    if (!ok) break;
+    if constexpr (ADJ) {
+      tc_commit(&H->dfull[p & 1]);
+    } else {
+      tc_commit(&H->aempty[p % G::NA]);
+    }
+  }
+  if constexpr (!ADJ) {
+    if (ok && np > 0) tc_commit(&H->dfull[0]);
+  }
+  // teardown: the MMAs and bulk copies this lane issued must be complete
+  // before tensor memory is freed and the CTA exits
+  tc_commit(&H->fin);
+  drain_bar(&H->fin, 0, A.err);
+  for (int it = consumed; it < issued; ++it)
+    if (!drain_bar(&H->bfull[it % NST], (uint32_t)((it / NST) & 1), A.err)) break;
+}
+
+__device__ __forceinline__ void init_bars(Bars* H) {
+  for (int s = 0; s < NST; ++s) {
+    mbar_init(&H->bfull[s], 1);
+    mbar_init(&H->bempty[s], 1);
+  }
+  for (int b = 0; b < 2; ++b) {
+    mbar_init(&H->afull[b], 32 * NWE);
+    mbar_init(&H->aempty[b], 1);
+    mbar_init(&H->dfull[b], 1);
+    mbar_init(&H->dempty[b], 32 * NWE);
+  }
+  mbar_init(&H->fin, 1);
+  H->abort = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ H kernel
+template <int PREC, int K>
+__global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
+  using G = Geo<PREC, K>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  Bars* H = reinterpret_cast<Bars*>(smem);
+  unsigned char* areg = smem + kHdr;
+  unsigned char* breg = areg + G::AREG_H;
+  float* sWr = reinterpret_cast<float*>(breg + (size_t)NST * G::BBYTES);   // [2][ROWS]
+  float* sWc = sWr + 2 * G::ROWS;                                         // [2][COLS]
+  __shared__ double red[NWE];
   const WorkItem wi = A.work[blockIdx.x];
   const TileDesc td = A.tiles[wi.tile];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  float acc[NTILE][4];
-#pragma unroll
-  for (int nt = 0; nt < NTILE; ++nt)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) init_bars(H);
+  if (warp == NWE) tmem_alloc(&H->tmem, 64);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = H->tmem;
+  const int nb = wi.b_hi - wi.b_lo + 1;
+  const int np = (wi.a_hi - wi.a_lo + 1) * nb;
 
-  for (int a = wi.a_lo; a <= wi.a_hi; ++a) {
-    for (int b = wi.b_lo; b <= wi.b_hi; ++b) {
-      __syncthreads();
-      for (int e = tid; e < ROWS; e += NT) {
+  if (warp == NWE) {
+    if (lane == 0) issuer<PREC, K, false>(A, wi, H, areg, breg, tbase, np);
+    __syncwarp();
+  } else {
+    // stage S_p = w_p . x per PSF into A buffer p % NA
+    const float* xin = A.in + td.xoff;
+    const bool vec = ((td.xpitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(xin) & 15) == 0);
+    bool ok = true;
+    for (int p = 0; p < np && ok; ++p) {
+      const int ab = p % G::NA;
+      if (p >= G::NA) {
+        ok = named_all(wait_bar(&H->aempty[ab], (uint32_t)((p / G::NA - 1) & 1), H, A.err));
+        if (!ok) break;
+      }
+      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+      float* wr = sWr + ab * G::ROWS;
+      float* wc = sWc + ab * G::COLS;
+      for (int e = tid; e < G::ROWS; e += 32 * NWE) {
         const int R = wi.r0 + e;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], a) : 0.f;
+        wr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
       }
-      for (int e = tid; e < W; e += NT) {
+      for (int e = tid; e < G::COLS; e += 32 * NWE) {
         const int C = wi.c0 + e;
-        sWc[e] = (e < TN + K - 1 && C < td.nxc) ? wsel(A.wcol[td.xc0 + C], b) : 0.f;
+        wc[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
       }
-      const uint2* bsrc = A.bfrag + (size_t)(a * A.Gc + b) * K * KS * 32;
-      for (int e = tid; e < K * KS * 32; e += NT) sB[e] = bsrc[e];
-      __syncthreads();
-      for (int e = tid; e < ROWS * W; e += NT) {
-        const int ir = e / W, ic = e - ir * W;
-        const float wgt = sWr[ir] * sWc[ic];
-        float v = 0.f;
-        if (wgt != 0.f) v = wgt * A.in[td.xoff + (int64_t)(wi.r0 + ir) * td.xpitch + (wi.c0 + ic)];
-        sS[e] = __float2bfloat16_rn(v);
+      named_sync();
+      unsigned char* abuf = areg + (size_t)ab * G::ABYTES;
+      for (int e = tid; e < G::ROWS * G::NCH; e += 32 * NWE) {
+        const int ir = e / G::NCH, q = e - ir * G::NCH;
+        const int R = wi.r0 + ir, C0 = wi.c0 + q * G::CH;
+        float v[G::CH];
+        const float rw = wr[ir];
+        if (rw == 0.f || R >= td.nxr) {
+#pragma unroll
+          for (int i = 0; i < G::CH; ++i) v[i] = 0.f;
+        } else {
+          const float* src = xin + (int64_t)R * td.xpitch + C0;
+          if (vec && C0 + G::CH <= td.nxc) {
+#pragma unroll
+            for (int i = 0; i < G::CH; i += 4) {
+              const float4 t = __ldg(reinterpret_cast<const float4*>(src + i));
+              v[i] = t.x;
+              v[i + 1] = t.y;
+              v[i + 2] = t.z;
+              v[i + 3] = t.w;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < G::CH; ++i) v[i] = (C0 + i < td.nxc) ? __ldg(src + i) : 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < G::CH; ++i) v[i] *= rw * wc[q * G::CH + i];
+        }
+        put_chunk<PREC, K>(abuf, ir, q, v);
       }
-      __syncthreads();
-      tc_corr<K>(sS, sB, 16 * warp, acc);
+      fence_async_smem();
+      mbar_arrive(&H->afull[ab]);
+    }
+    // epilogue: accumulator row 32 warp + lane -> fp32 staging block
+    float* sO = reinterpret_cast<float*>(areg);
+    if (ok && np > 0) ok = named_all(wait_bar(&H->dfull[0], 0, H, A.err));
+    tc_fence_after();
+    named_sync();   // every staging thread is past its last A write
+    {
+      const int i = 32 * warp + lane;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float v[32];
+        if (ok && np > 0) {
+          tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + 32u * h, v);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sO[i * OPITCH + 32 * h + j] = v[j];
+      }
+    }
+    tc_fence_before();
+    named_sync();
+    double part = 0.0;
+    if (ok) {
+      for (int e = tid; e < BM * BN; e += 32 * NWE) {
+        const int il = e / BN, jl = e - il * BN;
+        const int i = wi.r0 + il, j = wi.c0 + jl;
+        if (i >= td.nyr || j >= td.nyc) continue;
+        const float v = sO[il * OPITCH + jl];
+        if (A.mode == OP_PLAIN) {
+          A.out[td.yoff + (int64_t)i * td.ypitch + j] = v;
+        } else {
+          const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + j);
+          const float wt = A.W ? A.W[gi] : 1.f;
+          const float d = v - A.y[gi];
+          if (A.mode == OP_RESID)
+            A.out[td.yoff + (int64_t)i * td.ypitch + j] = wt * d;
+          else
+            part += (double)wt * (double)d * (double)d;
+        }
+      }
+    }
+    if (A.mode == OP_OBJ) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+      if (lane == 0) red[warp] = part;
+      named_sync();
+      if (tid == 0) A.partials[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
     }
   }
+  tc_fence_before();
   __syncthreads();
-#pragma unroll
-  for (int nt = 0; nt < NTILE; ++nt)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int r, c;
-      frag_pos(nt, e, r, c);
-      sO[(16 * warp + r) * (TN + 4) + c] = acc[nt][e];
-    }
-  __syncthreads();
-  double part = 0.0;
-  for (int e = tid; e < TM * TN; e += NT) {
-    const int il = e / TN, jl = e - il * TN;
-    const int i = wi.r0 + il, j = wi.c0 + jl;
-    if (i >= td.nyr || j >= td.nyc) continue;
-    const float v = sO[il * (TN + 4) + jl];
-    if (A.mode == OP_PLAIN) {
-      A.out[td.yoff + (int64_t)i * td.ypitch + j] = v;
-    } else {
-      const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + j);
-      const float wt = A.W ? A.W[gi] : 1.f;
-      const float d = v - A.y[gi];
-      if (A.mode == OP_RESID)
-        A.out[td.yoff + (int64_t)i * td.ypitch + j] = wt * d;
-      else
-        part += (double)wt * (double)d * (double)d;
-    }
-  }
-  if (A.mode == OP_OBJ) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((tid & 31) == 0) red[warp] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < NW; ++i) s += red[i];
-      A.partials[blockIdx.x] = s;
-    }
+  if (warp == NWE) {
+    tc_fence_after();
+    tmem_free(tbase, 64);
   }
 }
 
@@ -193,116 +541,206 @@ __device__ __forceinline__ void huber_p(const float* sW, int SPW, int li, int lj
   pc = k * dc;
 }
 
-template <int K>
-__global__ void __launch_bounds__(NT) tc_Ht_kernel(const OpArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int KS = ksteps(K), W = swidth(K), ROWS = TM + K - 1;
-  __nv_bfloat16* sS = reinterpret_cast<__nv_bfloat16*>(smem);
-  uint2* sB = reinterpret_cast<uint2*>(smem + (size_t)ROWS * W * 2);
-  float* sO = reinterpret_cast<float*>(smem + tc_off_out(K));
+// ---------------------------------------------------------------- H^T kernel
+template <int PREC, int K>
+__global__ void __launch_bounds__(NTH, 3) tc_Ht_kernel(const OpArgs A) {
+  using G = Geo<PREC, K>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  Bars* H = reinterpret_cast<Bars*>(smem);
+  unsigned char* areg = smem + kHdr;
+  unsigned char* breg = areg + G::AREG_HT;
+  float* sWcol = reinterpret_cast<float*>(breg + (size_t)NST * G::BBYTES);   // [kMaxWcol][BN]
   const WorkItem wi = A.work[blockIdx.x];
   const TileDesc td = A.tiles[wi.tile];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // residual block, rows R0 - (K-1) .., columns C0 - (K-1) .., zero outside the y-block
-  for (int e = tid; e < ROWS * W; e += NT) {
-    const int ir = e / W, ic = e - ir * W;
-    const int ry = wi.r0 - (K - 1) + ir, rx = wi.c0 - (K - 1) + ic;
-    float v = 0.f;
-    if (ic < TN + K - 1 && ry >= 0 && ry < td.nyr && rx >= 0 && rx < td.nyc)
-      v = A.in[td.yoff + (int64_t)ry * td.ypitch + rx];
-    sS[e] = __float2bfloat16_rn(v);
-  }
-  float g[NTILE][4];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) init_bars(H);
+  if (warp == NWE) tmem_alloc(&H->tmem, 128);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = H->tmem;
+  const int nb = wi.b_hi - wi.b_lo + 1;
+  const int np = (wi.a_hi - wi.a_lo + 1) * nb;
+
+  if (warp == NWE) {
+    if (lane == 0) issuer<PREC, K, true>(A, wi, H, areg, breg, tbase, np);
+    __syncwarp();
+  } else {
+    // residual block: rows R0 - (K-1) .., columns C0 - (K-1) .., zero
+    // outside the y-block and beyond the BN + K - 1 columns a block reads
+    const float* rin = A.in + td.yoff;
+    for (int e = tid; e < G::ROWS * G::NCH; e += 32 * NWE) {
+      const int ir = e / G::NCH, q = e - ir * G::NCH;
+      const int ry = wi.r0 - (K - 1) + ir, rx0 = wi.c0 - (K - 1) + q * G::CH;
+      const bool row_ok = ry >= 0 && ry < td.nyr;
+      float v[G::CH];
 #pragma unroll
-  for (int nt = 0; nt < NTILE; ++nt)
+      for (int i = 0; i < G::CH; ++i) {
+        const int rx = rx0 + i;
+        v[i] = (row_ok && rx >= 0 && rx < td.nyc && q * G::CH + i < BN + K - 1)
+                   ? __ldg(rin + (int64_t)ry * td.ypitch + rx)
+                   : 0.f;
+      }
+      put_chunk<PREC, K>(areg, ir, q, v);
+    }
+    fence_async_smem();
+    mbar_arrive(&H->afull[0]);
+    // output column weights of the block's PSF grid columns
+    const bool wcol_staged = nb <= kMaxWcol;
+    if (wcol_staged) {
+      for (int e = tid; e < nb * BN; e += 32 * NWE) {
+        const int bi = e / BN, j = e - bi * BN;
+        const int C = wi.c0 + j;
+        sWcol[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], wi.b_lo + bi) : 0.f;
+      }
+    }
+    named_sync();
+
+    // g = sum_p w_p . D_p over this thread's output row, in registers
+    const int i = 32 * warp + lane;
+    const int R = wi.r0 + i;
+    float g[BN];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) g[nt][e] = 0.f;
-  // output weights of this thread's fragment rows / columns are looked up per PSF
-  for (int a = wi.a_lo; a <= wi.a_hi; ++a) {
-    for (int b = wi.b_lo; b <= wi.b_hi; ++b) {
-      __syncthreads();
-      const uint2* bsrc = A.bfrag + (size_t)(a * A.Gc + b) * K * KS * 32;
-      for (int e = tid; e < K * KS * 32; e += NT) sB[e] = bsrc[e];
-      __syncthreads();
-      float acc[NTILE][4];
-#pragma unroll
-      for (int nt = 0; nt < NTILE; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
-      tc_corr<K>(sS, sB, 16 * warp, acc);
-      const int lane = tid & 31;
-      float wr[2];
+    for (int j = 0; j < BN; ++j) g[j] = 0.f;
+    bool ok = true;
+    for (int p = 0; p < np; ++p) {
+      const int db = p & 1;
+      if (!named_all(wait_bar(&H->dfull[db], (uint32_t)((p / 2) & 1), H, A.err))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+      const float wr = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int R = wi.r0 + 16 * warp + (lane >> 2) + 8 * h;
-        wr[h] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], a) : 0.f;
-      }
+        float v[32];
+        tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + 64u * db + 32u * h, v);
+        const float* wcs = sWcol + (gb - wi.b_lo) * BN + 32 * h;
 #pragma unroll
-      for (int nt = 0; nt < NTILE; ++nt) {
-#pragma unroll
-        for (int e2 = 0; e2 < 2; ++e2) {
-          const int C = wi.c0 + 8 * nt + 2 * (lane & 3) + e2;
-          const float wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], b) : 0.f;
-          g[nt][e2] = fmaf(wr[0] * wc, acc[nt][e2], g[nt][e2]);
-          g[nt][e2 + 2] = fmaf(wr[1] * wc, acc[nt][e2 + 2], g[nt][e2 + 2]);
+        for (int j = 0; j < 32; ++j) {
+          float wc;
+          if (wcol_staged) {
+            wc = wcs[j];
+          } else {
+            const int C = wi.c0 + 32 * h + j;
+            wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+          }
+          g[32 * h + j] = fmaf(wr * wc, v[j], g[32 * h + j]);
         }
       }
+      tc_fence_before();
+      mbar_arrive(&H->dempty[db]);
     }
-  }
-  __syncthreads();
+    // once the last D buffer was full every MMA had completed: the A region
+    // is free for the fp32 output block and the iterate halo
+    float* sO = reinterpret_cast<float*>(areg);
+    float* sW = reinterpret_cast<float*>(areg + G::OBYTES);
+    named_sync();
+    if (ok) {
 #pragma unroll
-  for (int nt = 0; nt < NTILE; ++nt)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      int r, c;
-      frag_pos(nt, e, r, c);
-      sO[(16 * warp + r) * (TN + 4) + c] = g[nt][e];
+      for (int j = 0; j < BN; ++j) sO[i * OPITCH + j] = g[j];
     }
-  __syncthreads();
-  if (A.mode == OP_PLAIN) {
-    for (int e = tid; e < TM * TN; e += NT) {
-      const int il = e / TN, jl = e - il * TN;
-      const int R = wi.r0 + il, C = wi.c0 + jl;
-      if (R < td.nxr && C < td.nxc)
-        A.out[td.xoff + (int64_t)R * td.xpitch + C] = sO[il * (TN + 4) + jl];
+    named_sync();
+    if (ok && A.mode == OP_PLAIN) {
+      for (int e = tid; e < BM * BN; e += 32 * NWE) {
+        const int il = e / BN, jl = e - il * BN;
+        const int Ro = wi.r0 + il, Co = wi.c0 + jl;
+        if (Ro < td.nxr && Co < td.nxc)
+          A.out[td.xoff + (int64_t)Ro * td.xpitch + Co] = sO[il * OPITCH + jl];
+      }
+    } else if (ok) {
+      // OP_STEP: grad = g + lambda D^T psi(D w) + alpha (w - u); w_next = max(0, w - tau grad)
+      constexpr int SPW = BN + 2;
+      for (int e = tid; e < (BM + 2) * SPW; e += 32 * NWE) {
+        const int ir = e / SPW, ic = e - ir * SPW;
+        const int Rr = wi.r0 - 1 + ir, Cc = wi.c0 - 1 + ic;
+        float v = 0.f;
+        if (Rr >= 0 && Rr < td.nxr && Cc >= 0 && Cc < td.nxc)
+          v = A.w[td.xoff + (int64_t)Rr * td.xpitch + Cc];
+        sW[e] = v;
+      }
+      named_sync();
+      for (int e = tid; e < BM * BN; e += 32 * NWE) {
+        const int il = e / BN, jl = e - il * BN;
+        const int Ro = wi.r0 + il, Co = wi.c0 + jl;
+        if (Ro >= td.nxr || Co >= td.nxc) continue;
+        const int li = il + 1, lj = jl + 1;
+        float pr, pc, pru, pcu, prl, pcl;
+        huber_p(sW, SPW, li, lj, Ro, Co, td.nxr, td.nxc, A.delta, pr, pc);
+        huber_p(sW, SPW, li - 1, lj, Ro - 1, Co, td.nxr, td.nxc, A.delta, pru, pcu);
+        huber_p(sW, SPW, li, lj - 1, Ro, Co - 1, td.nxr, td.nxc, A.delta, prl, pcl);
+        const float hub = pru - pr + pcl - pc;
+        const float wv = sW[li * SPW + lj];
+        const float alpha = A.gamma * A.omr[td.omr_off + Ro] * A.omc[td.omc_off + Co];
+        const int64_t idx = td.xoff + (int64_t)Ro * td.xpitch + Co;
+        const float grad = sO[il * OPITCH + jl] + A.lambda * hub + alpha * (wv - A.u[idx]);
+        A.out[idx] = fmaxf(0.f, wv - td.tau * grad);
+      }
     }
-    return;
   }
-  // OP_STEP: grad = g + lambda D^T psi(D w) + alpha (w - u); w_next = max(0, w - tau grad)
-  float* sW = reinterpret_cast<float*>(smem);   // (TM+2) x (TN+2) halo of w (reuses S and B)
-  constexpr int SPW = TN + 2;
-  for (int e = tid; e < (TM + 2) * SPW; e += NT) {
-    const int ir = e / SPW, ic = e - ir * SPW;
-    const int R = wi.r0 - 1 + ir, C = wi.c0 - 1 + ic;
-    float v = 0.f;
-    if (R >= 0 && R < td.nxr && C >= 0 && C < td.nxc) v = A.w[td.xoff + (int64_t)R * td.xpitch + C];
-    sW[e] = v;
-  }
+  tc_fence_before();
   __syncthreads();
-  for (int e = tid; e < TM * TN; e += NT) {
-    const int il = e / TN, jl = e - il * TN;
-    const int R = wi.r0 + il, C = wi.c0 + jl;
-    if (R >= td.nxr || C >= td.nxc) continue;
-    const int li = il + 1, lj = jl + 1;
-    float pr, pc, pru, pcu, prl, pcl;
-    huber_p(sW, SPW, li, lj, R, C, td.nxr, td.nxc, A.delta, pr, pc);
-    huber_p(sW, SPW, li - 1, lj, R - 1, C, td.nxr, td.nxc, A.delta, pru, pcu);
-    huber_p(sW, SPW, li, lj - 1, R, C - 1, td.nxr, td.nxc, A.delta, prl, pcl);
-    const float hub = pru - pr + pcl - pc;
-    const float wv = sW[li * SPW + lj];
-    const float alpha = A.gamma * A.omr[td.omr_off + R] * A.omc[td.omc_off + C];
-    const int64_t idx = td.xoff + (int64_t)R * td.xpitch + C;
-    const float grad = sO[il * (TN + 4) + jl] + A.lambda * hub + alpha * (wv - A.u[idx]);
-    A.out[idx] = fmaxf(0.f, wv - td.tau * grad);
+  if (warp == NWE) {
+    tc_fence_after();
+    tmem_free(tbase, 128);
   }
 }
 
-template <int K>
+template <int PREC, int K>
+size_t sm_H() { return std::max(smem_H<PREC, K>(), kMinSmemH); }
+template <int PREC, int K>
+size_t sm_Ht() { return std::max(smem_Ht<PREC, K>(), kMinSmemHt); }
+
+template <int PREC, int K>
 cudaError_t prep_t() {
-  const int smem = (int)tc_smem(K);
-  cudaError_t e = cudaFuncSetAttribute(tc_H_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(tc_H_kernel<PREC, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sm_H<PREC, K>());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_Ht_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(tc_Ht_kernel<PREC, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sm_Ht<PREC, K>());
+}
+
+template <int PREC, int K>
+cudaError_t launch_t(const OpArgs& a, cudaStream_t s, bool adjoint) {
+  if (adjoint)
+    tc_Ht_kernel<PREC, K><<<a.n_work, NTH, sm_Ht<PREC, K>(), s>>>(a);
+  else
+    tc_H_kernel<PREC, K><<<a.n_work, NTH, sm_H<PREC, K>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t dispatch(const OpArgs& a, cudaStream_t s, bool adjoint) {
+  switch (a.K) {
+    case 9: return launch_t<PREC, 9>(a, s, adjoint);
+    case 15: return launch_t<PREC, 15>(a, s, adjoint);
+    case 31: return launch_t<PREC, 31>(a, s, adjoint);
+    case 63: return launch_t<PREC, 63>(a, s, adjoint);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PREC>
+cudaError_t prep_prec(int K) {
+  switch (K) {
+    case 9: return prep_t<PREC, 9>();
+    case 15: return prep_t<PREC, 15>();
+    case 31: return prep_t<PREC, 31>();
+    case 63: return prep_t<PREC, 63>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int PREC>
+int bbytes(int K) {
+  switch (K) {
+    case 9: return Geo<PREC, 9>::BBYTES;
+    case 15: return Geo<PREC, 15>::BBYTES;
+    case 31: return Geo<PREC, 31>::BBYTES;
+    case 63: return Geo<PREC, 63>::BBYTES;
+    default: return 0;
+  }
 }
 
 uint16_t to_bf16(float f) {
@@ -314,77 +752,66 @@ uint16_t to_bf16(float f) {
   return (uint16_t)(u >> 16);
 }
 
+uint32_t to_tf32(float f) {
+  // round to nearest, ties away from zero, keeping 10 mantissa bits
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return u & 0xffffe000u;
+  u += 0x1000u;
+  return u & 0xffffe000u;
+}
+
 }  // namespace
 
+int tc_block_m() { return BM; }
+int tc_block_n() { return BN; }
 bool tc_supported(int K) { return K == 9 || K == 15 || K == 31 || K == 63; }
 
-cudaError_t tc_prepare(int K) {
-  switch (K) {
-    case 9: return prep_t<9>();
-    case 15: return prep_t<15>();
-    case 31: return prep_t<31>();
-    case 63: return prep_t<63>();
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t tc_prepare(int K, int prec) {
+  return prec == DV_PREC_TF32 ? prep_prec<1>(K) : prep_prec<0>(K);
 }
 
-// B fragments of the m16n8k16 MMA for every PSF, filter row and k-step:
-// T[k][n] = f(a, k - n) for 0 <= k - n < K (f = flipped PSF for H, PSF for H^T);
-// lane l holds (T[2t + 16 ks][g], T[2t + 1 + 16 ks][g]) and the same for k + 8,
-// g = l / 4, t = l % 4, as bf16 pairs (lower k in the low half).
-void tc_fragments(const float* psfs, int G, int K, bool flip, std::vector<uint2>& out) {
-  const int KS = ksteps(K);
-  out.assign((size_t)G * K * KS * 32, make_uint2(0u, 0u));
+// Tall B operands of every PSF and tap row a, as the shared-memory image the
+// kernels copy: two panels (K chunks 0 and 1) of RB rows x 16 bytes, row n'
+// holding Bt[n'][k] = f(a, k + KM (KS - 1) - n') (zero outside [0, K));
+// f = flipped PSF for H, the PSF for H^T.
+void tc_operands(const float* psfs, int G, int K, int prec, bool flip, std::vector<uint8_t>& out) {
+  const bool tf = prec == DV_PREC_TF32;
+  const int bytes = tf ? 4 : 2, km = 32 / bytes, ch = 16 / bytes;
+  const int KS = (BN - 1 + K + km - 1) / km;
+  const int RB = BN + km * (KS - 1);
+  const int BB = tf ? bbytes<1>(K) : bbytes<0>(K);
+  out.assign((size_t)G * K * BB, 0);
   for (int p = 0; p < G; ++p) {
     const float* h = psfs + (size_t)p * K * K;
-    for (int a = 0; a < K; ++a)
-      for (int ks = 0; ks < KS; ++ks)
-        for (int l = 0; l < 32; ++l) {
-          const int gq = l >> 2, t = l & 3;
-          auto T = [&](int k) -> float {
-            const int d = k - gq;
-            if (d < 0 || d >= K) return 0.f;
-            return flip ? h[(K - 1 - a) * K + (K - 1 - d)] : h[a * K + d];
-          };
-          const int k0 = 2 * t + 16 * ks;
-          const uint32_t x = (uint32_t)to_bf16(T(k0)) | ((uint32_t)to_bf16(T(k0 + 1)) << 16);
-          const uint32_t y = (uint32_t)to_bf16(T(k0 + 8)) | ((uint32_t)to_bf16(T(k0 + 9)) << 16);
-          out[(((size_t)p * K + a) * KS + ks) * 32 + l] = make_uint2(x, y);
+    for (int a = 0; a < K; ++a) {
+      uint8_t* dst = out.data() + ((size_t)p * K + a) * BB;
+      for (int n = 0; n < RB; ++n)
+        for (int k = 0; k < km; ++k) {
+          const int d = k + km * (KS - 1) - n;
+          float v = 0.f;
+          if (d >= 0 && d < K) v = flip ? h[(K - 1 - a) * K + (K - 1 - d)] : h[a * K + d];
+          uint8_t* e = dst + (size_t)(k / ch) * RB * 16 + (size_t)n * 16 + (k % ch) * bytes;
+          if (tf) {
+            const uint32_t t = to_tf32(v);
+            std::memcpy(e, &t, 4);
+          } else {
+            const uint16_t t = to_bf16(v);
+            std::memcpy(e, &t, 2);
+          }
         }
+    }
   }
-}
-
-template <int K>
-cudaError_t launch_H_tc(const OpArgs& a, cudaStream_t s) {
-  tc_H_kernel<K><<<a.n_work, NT, tc_smem(K), s>>>(a);
-  return cudaGetLastError();
-}
-template <int K>
-cudaError_t launch_Ht_tc(const OpArgs& a, cudaStream_t s) {
-  tc_Ht_kernel<K><<<a.n_work, NT, tc_smem(K), s>>>(a);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tc_H(const OpArgs& a, cudaStream_t s) {
   if (a.n_work <= 0) return cudaSuccess;
-  switch (a.K) {
-    case 9: return launch_H_tc<9>(a, s);
-    case 15: return launch_H_tc<15>(a, s);
-    case 31: return launch_H_tc<31>(a, s);
-    case 63: return launch_H_tc<63>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return a.prec == DV_PREC_TF32 ? dispatch<1>(a, s, false) : dispatch<0>(a, s, false);
 }
 
 cudaError_t launch_tc_Ht(const OpArgs& a, cudaStream_t s) {
   if (a.n_work <= 0) return cudaSuccess;
-  switch (a.K) {
-    case 9: return launch_Ht_tc<9>(a, s);
-    case 15: return launch_Ht_tc<15>(a, s);
-    case 31: return launch_Ht_tc<31>(a, s);
-    case 63: return launch_Ht_tc<63>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return a.prec == DV_PREC_TF32 ? dispatch<1>(a, s, true) : dispatch<0>(a, s, true);
 }
 
 }  // namespace dv

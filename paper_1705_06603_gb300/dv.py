@@ -29,7 +29,7 @@ except OSError as e:  # pragma: no cover - depends on the machine
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_CUDA, DV_ERR_OOM, DV_ERR_TIMEOUT, DV_ERR_UNSUPPORTED = range(6)
 DV_PREC_FP32, DV_PREC_TF32, DV_PREC_BF16 = 0, 1, 2
 DV_WEIGHTS_BILINEAR, DV_WEIGHTS_SEPARABLE = 0, 1
-DV_PATH_AUTO, DV_PATH_DIRECT, DV_PATH_FFT = 0, 1, 2
+DV_PATH_AUTO, DV_PATH_DIRECT, DV_PATH_FFT, DV_PATH_TENSOR = 0, 1, 2, 3
 KERNEL_H, KERNEL_HT_STEP, KERNEL_CONSENSUS = 0, 1, 2
 
 _fp = C.POINTER(C.c_float)
@@ -68,7 +68,8 @@ class dv_plan_info(C.Structure):
                 ("kernel_launches", C.c_int64), ("tune_ms_direct", C.c_double),
                 ("tune_ms_fft", C.c_double), ("blocks", C.c_int64 * 2),
                 ("block_psfs", C.c_int64 * 2), ("psf_pairs", C.c_int64 * 2),
-                ("block_side", C.c_int32), ("pad", C.c_int32)]
+                ("block_side", C.c_int32), ("fp32_path", C.c_int32),
+                ("tune_ms_tensor", C.c_double)]
 
 
 _vp = C.c_void_p

@@ -83,6 +83,9 @@ def test_layout_with_noise_weights(dv):
     (dict(gamma=0.0), "gamma"),
     (dict(delta=-1.0), "delta"),
     (dict(n_outer=-1), "iteration"),
+    (dict(path=4), "operator path"),
+    (dict(precision=3), "precision"),
+    (dict(n_tc=1025), "tile grid"),
 ])
 def test_invalid_problems_rejected(dv, change, needle):
     psfs = np.full((1, 1, 3, 3), 1 / 9.0)
@@ -121,3 +124,13 @@ def test_separable_weights_validated(dv):
     p, keep = dv.make_problem(hy, wy, psfs, weights=(bad, wc))
     with pytest.raises(dv.DVError, match="at most two"):
         dv.dv_layout_query(p)
+
+
+@pytest.mark.parametrize("path,prec", [(0, 0), (1, 0), (2, 0), (3, 1), (3, 2), (0, 2)])
+def test_every_operator_path_is_a_valid_request(dv, path, prec):
+    """Host-side validation accepts every dv_operator_path / dv_precision
+    value (whether the tensor path applies to the PSF size is decided at plan
+    creation)."""
+    psfs = np.full((1, 1, 9, 9), 1 / 81.0)
+    p, keep = dv.make_problem(20, 20, psfs, path=path, precision=prec)
+    dv.dv_layout_query(p)
