@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--profile-case", action="store_true",
                     help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
                          "short, fixed launch sequence for ncu captures); prints nothing")
+    ap.add_argument("--profile-path", choices=["fft", "direct", "bf16", "tf32"], default="fft",
+                    help="operator of --profile-case: FP32 block FFT or direct, or the "
+                         "tensor-core path with BF16 / TF32 operands")
     return ap.parse_args()
 
 
@@ -496,8 +499,8 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_profile_case():
-    """Launch sequence for ncu: inputs, a block-FFT plan (no autotuning), then
+def run_profile_case(which):
+    """Launch sequence for ncu: inputs, a plan on the requested path (no autotuning), then
     scatter, H, H^T (+ step), consensus and assembly of one 1 x 1 solve,
     eagerly (no graphs)."""
     import torch
@@ -509,9 +512,12 @@ def run_profile_case():
     w = WORKLOADS[WORKLOAD]
     psfs = psf_grid_for(w).astype(np.float32)
     y = make_inputs(torch, dv, w, psfs, 0)
+    kw = {"fft": dict(path=dv.DV_PATH_FFT), "direct": dict(path=dv.DV_PATH_DIRECT),
+          "bf16": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_BF16),
+          "tf32": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_TF32)}[which]
     plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
                    delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=1, n_inner=1, use_graphs=0,
-                   path=dv.DV_PATH_FFT, noise_sigma=w.noise_sigma)
+                   noise_sigma=w.noise_sigma, **kw)
     plan.solve(y, stats=False)
     torch.cuda.synchronize()
     plan.close()
@@ -520,7 +526,7 @@ def run_profile_case():
 def main():
     args = parse()
     if args.profile_case:
-        run_profile_case()
+        run_profile_case(args.profile_path)
         return
     if args.impl == "reference":
         run_reference(args)

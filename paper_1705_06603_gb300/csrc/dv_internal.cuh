@@ -118,12 +118,12 @@ struct OpArgs {
 struct GridArgs {
   const TileDesc* tiles;
   const int2* rowcov;     // per global x row: covering tile rows (second = -1 if none)
-  const int4* cseg;       // column segments {c0, c1, tile col, second tile col or -1}
+  const int2* colcov;     // per global x column: covering tile columns
   const float* omr;
   const float* omc;
   int32_t n_tc;
   int32_t nxr, nxc;
-  int32_t n_cseg;
+  int32_t pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -144,9 +144,7 @@ cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma,
                              float rho, float* zbuf, double* partials, cudaStream_t s,
                              int* n_blocks_out);
-int consensus_blocks(int nxr, int n_cseg);
-// longest column segment of the consensus / assembly blocks
-int row_segment_width();
+int consensus_blocks(int nxr, int nxc);
 // x_hat = sum omega_i x_i / sum omega_i
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s);
 // FP64 block partials of the Huber prior over the tile stacks
@@ -258,8 +256,7 @@ struct dv_plan {
   dv::TileDesc* d_tiles = nullptr;
   dv::TileDesc* d_gtile = nullptr;
   int2* d_rowcov = nullptr;
-  int4* d_cseg = nullptr;
-  int n_cseg = 0;
+  int2* d_colcov = nullptr;
   float* d_w[2] = {nullptr, nullptr};
   float* d_u = nullptr;
   float* d_r = nullptr;

@@ -390,8 +390,7 @@ dv::GridArgs grid_args(const dv_plan* p) {
   GridArgs g{};
   g.tiles = p->d_tiles;
   g.rowcov = p->d_rowcov;
-  g.cseg = p->d_cseg;
-  g.n_cseg = p->n_cseg;
+  g.colcov = p->d_colcov;
   g.omr = p->d_omr;
   g.omc = p->d_omc;
   g.n_tc = p->n_tc;
@@ -680,17 +679,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   for (int tc = 0; tc < P->n_tc; ++tc)
     for (int C = L.yc0[tc]; C < L.yc1[tc] + K - 1; ++C) (cc[C].x < 0 ? cc[C].x : cc[C].y) = tc;
   DV_TRY(upload(P, &P->d_rowcov, rc.data(), rc.size(), s));
-  // column segments with a constant set of covering tile columns
-  std::vector<int4> seg;
-  for (int c = 0; c < P->nxc;) {
-    int e = c + 1;
-    while (e < P->nxc && cc[e].x == cc[c].x && cc[e].y == cc[c].y && e - c < row_segment_width())
-      ++e;
-    seg.push_back(make_int4(c, e, cc[c].x, cc[c].y));
-    c = e;
-  }
-  P->n_cseg = (int)seg.size();
-  DV_TRY(upload(P, &P->d_cseg, seg.data(), seg.size(), s));
+  DV_TRY(upload(P, &P->d_colcov, cc.data(), cc.size(), s));
 
   // iterates, dual variable, residuals, data, scratch
   DV_TRY(alloc(P, &P->d_w[0], P->xstack));
@@ -707,7 +696,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   if (prob->noise_w) DV_TRY(upload(P, &P->d_W, prob->noise_w, (size_t)P->hy * P->wy, s));
   DV_TRY(alloc(P, &P->d_z, (size_t)P->nxr * P->nxc));
   DV_TRY(alloc(P, &P->d_xg, (size_t)P->nxr * P->nxc));
-  const int64_t ncons = consensus_blocks(P->nxr, P->n_cseg);
+  const int64_t ncons = consensus_blocks(P->nxr, P->nxc);
   const int64_t nhub = huber_blocks(P->T, P->max_nxr, P->max_nxc);
   P->n_part = std::max(std::max(P->tab[0].nH, P->tab[1].nH), P->tab[2].nH) + nhub + 2 * ncons;
   DV_TRY(alloc(P, &P->d_part, (size_t)P->n_part));
@@ -757,7 +746,7 @@ dv_status release(dv_plan* P) {
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
                   P->tab[2].H, P->tab[2].Ht, P->tab[2].Hg, P->tab[2].Htg,
                   P->d_tcopH, P->d_tcopHt, P->d_err,
-                  P->d_rowcov, P->d_cseg, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
+                  P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
     if (b) cudaFree(b);

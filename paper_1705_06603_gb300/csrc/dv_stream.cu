@@ -54,46 +54,38 @@ __global__ void scatter_kernel(const TileDesc* __restrict__ tiles, const float* 
   }
 }
 
-// The consensus and assembly kernels work on row segments: a block owns one
-// global x row R and one column segment [c0, c1) over which the covering tile
-// columns do not change (at most ROW_SEG columns), so the (at most 2 x 2)
-// covering tiles are fixed for the whole block and NBR threads stride over
-// the segment, every warp touching 32 consecutive pixels of each tile stack.
-constexpr int NBR = 128;     // threads per block of the row kernels
-constexpr int GRP = 4;       // pixels per thread and group: the group's loads are issued together
-constexpr int ROW_SEG = 1024;  // longest column segment of one block
+// The consensus, assembly and prior kernels work row-wise: a block owns one
+// global x row (or a few tile rows) and NBR threads stride over its columns,
+// so every warp touches 32 consecutive pixels of each tile stack it reads.
+constexpr int NBR = 128;   // threads per block of the row kernels
+constexpr int GRP = 4;     // pixels per thread and group: loads of a group are issued together
 constexpr int HUB_ROWS = 4;  // tile rows per block of the prior kernel
 
-// The covering tiles of block (R, segment) as slots (i, j): tile row i of
-// the row cover, tile column j of the segment.  Per slot: stack offset of
-// global column 0 on row R, row factor of the profile times `scale`, offset
-// of global column 0 in the column profile.
-struct RowSlots {
-  int64_t base[4];
-  float row[4];
-  int omc[4];
-  bool valid[4];
-};
+// Column chunks of the row kernels: about 4096 columns each, a multiple of 32.
+__host__ __device__ inline int row_chunks(int nxc) { return (nxc + 4095) / 4096; }
+__host__ __device__ inline int row_chunk_width(int nxc) {
+  const int n = row_chunks(nxc);
+  return ((nxc + n - 1) / n + 31) / 32 * 32;
+}
 
-__device__ __forceinline__ RowSlots row_slots(const GridArgs& G, int R, const int4& sg, float scale) {
-  RowSlots S;
+// Per block: for the (one or two) tile rows covering global row R and every
+// tile column t, the stack offset of global column 0 on that row (sbase), the
+// row factor of the profile times `scale` (srow) and the offset of global
+// column 0 in the column profile (somc).  Returns the number of tile rows.
+__device__ __forceinline__ int stage_row(const GridArgs& G, int R, float scale, int64_t* sbase,
+                                         float* srow, int* somc) {
   const int2 rc = G.rowcov[R];
-#pragma unroll
-  for (int sl = 0; sl < 4; ++sl) {
-    const int tr = (sl >> 1) ? rc.y : rc.x, tc = (sl & 1) ? sg.w : sg.z;
-    S.valid[sl] = tr >= 0 && tc >= 0;
-    S.base[sl] = 0;
-    S.row[sl] = 0.f;
-    S.omc[sl] = 0;
-    if (S.valid[sl]) {
-      const TileDesc& td = G.tiles[tr * G.n_tc + tc];
-      const int lr = R - td.xr0;
-      S.base[sl] = td.xoff + (int64_t)lr * td.xpitch - td.xc0;
-      S.row[sl] = scale * G.omr[td.omr_off + lr];
-      S.omc[sl] = td.omc_off - td.xc0;
-    }
+  const int nr = rc.y >= 0 ? 2 : 1;
+  for (int e = threadIdx.x; e < nr * G.n_tc; e += blockDim.x) {
+    const int i = e / G.n_tc, t = e - i * G.n_tc;
+    const TileDesc td = G.tiles[(i ? rc.y : rc.x) * G.n_tc + t];
+    const int lr = R - td.xr0;
+    sbase[e] = td.xoff + (int64_t)lr * td.xpitch - td.xc0;
+    srow[e] = scale * G.omr[td.omr_off + lr];
+    somc[e] = td.omc_off - td.xc0;
   }
-  return S;
+  __syncthreads();
+  return nr;
 }
 
 // Per global x pixel: zbar = sum_i alpha_i (2 x_i - u_i) / sum_i alpha_i over
@@ -104,26 +96,36 @@ __global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const 
                                                         float* __restrict__ u, float gamma, float rho,
                                                         float* __restrict__ zg,
                                                         double* __restrict__ partials) {
+  extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ double red[NBR / 32];
+  const int ntc = G.n_tc;
+  int64_t* sbase = reinterpret_cast<int64_t*>(dsm);
+  float* srow = reinterpret_cast<float*>(sbase + 2 * ntc);
+  int* somc = reinterpret_cast<int*>(srow + 2 * ntc);
   const int R = blockIdx.y;
-  const int4 sg = G.cseg[blockIdx.x];
-  const RowSlots S = row_slots(G, R, sg, gamma);
+  const int nr = stage_row(G, R, gamma, sbase, srow, somc);
+  const int cw = row_chunk_width(G.nxc);
+  const int c0 = blockIdx.x * cw, c1 = min(c0 + cw, G.nxc);
   double pp = 0.0, dd = 0.0;
-  for (int cb = sg.x + threadIdx.x; cb < sg.y; cb += GRP * NBR) {
+  for (int cb = c0 + threadIdx.x; cb < c1; cb += GRP * NBR) {
     float xs[GRP][4], us[GRP][4], as[GRP][4], zp[GRP];
+    int2 cc[GRP];
 #pragma unroll
     for (int k = 0; k < GRP; ++k) {
       const int C = cb + k * NBR;
-      const bool in = C < sg.y;
+      const bool in = C < c1;
+      cc[k] = in ? G.colcov[C] : make_int2(-1, -1);
       zp[k] = (in && zg) ? zg[(int64_t)R * G.nxc + C] : 0.f;
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
+        const int i = sl >> 1, t = (sl & 1) ? cc[k].y : cc[k].x;
         xs[k][sl] = us[k][sl] = as[k][sl] = 0.f;
-        if (in && S.valid[sl]) {
-          const int64_t id = S.base[sl] + C;
+        if (in && i < nr && t >= 0) {
+          const int e = i * ntc + t;
+          const int64_t id = sbase[e] + C;
           xs[k][sl] = x[id];
           us[k][sl] = u[id];
-          as[k][sl] = S.row[sl] * G.omc[S.omc[sl] + C];
+          as[k][sl] = srow[e] * G.omc[somc[e] + C];
         }
       }
     }
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const 
 #pragma unroll
     for (int k = 0; k < GRP; ++k) {
       const int C = cb + k * NBR;
-      if (C >= sg.y) continue;
+      if (C >= c1) continue;
       float num = 0.f, den = 0.f;
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
@@ -141,8 +143,9 @@ __global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const 
       const float z = num / den;
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
-        if (S.valid[sl]) {
-          u[S.base[sl] + C] = us[k][sl] + rho * (z - xs[k][sl]);
+        if (as[k][sl] != 0.f) {
+          const int e = (sl >> 1) * ntc + ((sl & 1) ? cc[k].y : cc[k].x);
+          u[sbase[e] + C] = us[k][sl] + rho * (z - xs[k][sl]);
           const float d = xs[k][sl] - z;
           pg = fmaf(d, d, pg);
         }
@@ -168,21 +171,30 @@ __global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const 
 // x_hat = sum_i omega_i x_i / sum_i omega_i over the tiles covering each pixel.
 __global__ void __launch_bounds__(NBR) assemble_kernel(const GridArgs G, const float* __restrict__ x,
                                                        float* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int ntc = G.n_tc;
+  int64_t* sbase = reinterpret_cast<int64_t*>(dsm);
+  float* srow = reinterpret_cast<float*>(sbase + 2 * ntc);
+  int* somc = reinterpret_cast<int*>(srow + 2 * ntc);
   const int R = blockIdx.y;
-  const int4 sg = G.cseg[blockIdx.x];
-  const RowSlots S = row_slots(G, R, sg, 1.f);
-  for (int cb = sg.x + threadIdx.x; cb < sg.y; cb += GRP * NBR) {
+  const int nr = stage_row(G, R, 1.f, sbase, srow, somc);
+  const int cw = row_chunk_width(G.nxc);
+  const int c0 = blockIdx.x * cw, c1 = min(c0 + cw, G.nxc);
+  for (int cb = c0 + threadIdx.x; cb < c1; cb += GRP * NBR) {
     float num[GRP], den[GRP];
 #pragma unroll
     for (int k = 0; k < GRP; ++k) {
       const int C = cb + k * NBR;
       num[k] = den[k] = 0.f;
-      if (C >= sg.y) continue;
+      if (C >= c1) continue;
+      const int2 cc = G.colcov[C];
 #pragma unroll
       for (int sl = 0; sl < 4; ++sl) {
-        if (S.valid[sl]) {
-          const float om = S.row[sl] * G.omc[S.omc[sl] + C];
-          num[k] += om * x[S.base[sl] + C];
+        const int i = sl >> 1, t = (sl & 1) ? cc.y : cc.x;
+        if (i < nr && t >= 0) {
+          const int e = i * ntc + t;
+          const float om = srow[e] * G.omc[somc[e] + C];
+          num[k] += om * x[sbase[e] + C];
           den[k] += om;
         }
       }
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(NBR) assemble_kernel(const GridArgs G, const f
 #pragma unroll
     for (int k = 0; k < GRP; ++k) {
       const int C = cb + k * NBR;
-      if (C < sg.y) out[(int64_t)R * G.nxc + C] = num[k] / den[k];
+      if (C < c1) out[(int64_t)R * G.nxc + C] = num[k] / den[k];
     }
   }
 }
@@ -252,21 +264,21 @@ cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_
   return cudaGetLastError();
 }
 
-int row_segment_width() { return ROW_SEG; }
+size_t row_smem(int n_tc) { return (size_t)2 * n_tc * (sizeof(int64_t) + 2 * sizeof(float)); }
 
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma, float rho,
                              float* zbuf, double* partials, cudaStream_t s, int* n_blocks_out) {
-  dim3 grid(g.n_cseg, g.nxr);
+  dim3 grid(row_chunks(g.nxc), g.nxr);
   if (n_blocks_out) *n_blocks_out = grid.x * grid.y;
-  consensus_kernel<<<grid, NBR, 0, s>>>(g, x, u, gamma, rho, zbuf, partials);
+  consensus_kernel<<<grid, NBR, row_smem(g.n_tc), s>>>(g, x, u, gamma, rho, zbuf, partials);
   return cudaGetLastError();
 }
 
-int consensus_blocks(int nxr, int n_cseg) { return n_cseg * nxr; }
+int consensus_blocks(int nxr, int nxc) { return row_chunks(nxc) * nxr; }
 
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s) {
-  dim3 grid(g.n_cseg, g.nxr);
-  assemble_kernel<<<grid, NBR, 0, s>>>(g, x, out);
+  dim3 grid(row_chunks(g.nxc), g.nxr);
+  assemble_kernel<<<grid, NBR, row_smem(g.n_tc), s>>>(g, x, out);
   return cudaGetLastError();
 }
 

@@ -12,17 +12,22 @@
 //       so the row shift a is the start address plus 16 a;
 //   B = T_a on the same columns, N x KM, K-major: a 64-row window of one
 //       "tall" matrix per tap row, Bt[n'][k] = f(a, k + KM (KS - 1) - n'),
-//       two panels of (64 + KM (KS - 1)) x 16 bytes.  The tall matrices are
-//       precomputed on the host per PSF and streamed by cp.async.bulk into a
-//       ring of stages guarded by mbarriers.
-//   H:   S = w_p . x is restaged per PSF (double-buffered when it fits); all
-//        PSFs accumulate into one 128 x 64 FP32 accumulator in tensor memory.
-//   H^T: S = r is staged once; PSF p accumulates into tensor-memory buffer
-//        p & 1 and the epilogue warps add w_p . D_p into registers while the
-//        next PSF's MMAs run; the projected-gradient step is fused.
+//       two panels of (64 + KM (KS - 1)) x 16 bytes of which only K + CH - 1
+//       rows per panel are nonzero.  Those windows are precomputed on the
+//       host per PSF and tap row and streamed by cp.async.bulk into a ring of
+//       stages (zero outside the windows) guarded by mbarriers.
+// The FP32 input window (rows + K - 1, columns of all k-steps) is copied once
+// per CTA into shared memory by cp.async (zero-filled outside the tile), then
+// converted into the operand panels:
+//   H:   S = w_p . x per PSF (double-buffered when it fits); all PSFs
+//        accumulate into one 128 x 64 FP32 accumulator in tensor memory.
+//   H^T: S = r once; PSF p accumulates into tensor-memory buffer p & 1 and the
+//        epilogue warps add w_p . D_p into registers while the next PSF's
+//        MMAs run; the projected-gradient step is fused.
 // Warp roles: warps 0-3 stage operands and run the epilogue (warp w reads
 // tensor-memory lanes 32w .. 32w + 31, i.e. output rows); warp 4 allocates
-// tensor memory and one of its lanes issues every bulk copy and MMA.  Every
+// tensor memory and one of its lanes issues every MMA; one lane of warp 5
+// refills the B ring as soon as the MMAs of a stage have completed.  Every
 // mbarrier wait gives up after about two seconds, records the timeout in the
 // plan's error word and sends the whole CTA to its teardown, which waits (with
 // its own bound) for the copies and MMAs it issued and frees tensor memory.
@@ -38,8 +43,7 @@ namespace {
 
 constexpr int BM = 128, BN = 64;
 constexpr int NWE = 4;                    // staging / epilogue warps
-constexpr int NTH = 32 * (NWE + 1);       // + the issuing warp
-constexpr int NST = 6;                    // B ring stages (one tap row each)
+constexpr int NTH = 32 * (NWE + 2);       // + the MMA warp and the bulk-copy warp
 constexpr int OPITCH = BN + 1;            // fp32 output staging pitch (floats)
 constexpr uint64_t kWaitNs = 2000000000ull;    // bound of a pipeline wait
 constexpr uint64_t kDrainNs = 200000000ull;    // bound of a teardown wait
@@ -51,6 +55,11 @@ struct Elt {
   static constexpr int chunk = 16 / bytes;
   static constexpr int km = 32 / bytes;
 };
+
+constexpr int kSmemMax = 227 * 1024;      // dynamic shared memory per CTA
+constexpr int kHdrBytes = 512;            // mbarrier header at the start of it
+constexpr int kMaxWcol = 16;              // H^T: PSF grid columns whose output weights are staged
+constexpr int kMaxWcolBytes = kMaxWcol * BN * 4;
 
 template <int PREC, int K>
 struct Geo {
@@ -64,43 +73,53 @@ struct Geo {
   static constexpr int ABYTES = NCH * APANEL;
   static constexpr int RB = BN + KM * (KS - 1);           // rows of the tall B operand
   static constexpr int BPANEL = RB * 16;
-  static constexpr int BBYTES = 2 * BPANEL;               // one tap row
-  // epilogue (reuses the A region): fp32 output block, and for the H^T step
-  // the (BM + 2) x (BN + 2) halo of the iterate
+  static constexpr int BBYTES = 2 * BPANEL;               // one ring stage (one tap row)
+  static constexpr int WR = K + CH - 1;                   // nonzero rows per panel
+  static constexpr int S0 = KM * (KS - 1) - K + 1;        // first nonzero row of panel 0
+  static constexpr int WBYTES_TX = 2 * WR * 16;           // bytes streamed per tap row
+  static constexpr int XBYTES = ROWS * COLS * 4;          // FP32 input window
+  // epilogue: fp32 output block, and for the H^T step the (BM + 2) x (BN + 2)
+  // halo of the iterate
   static constexpr int OBYTES = BM * OPITCH * 4;
-  static constexpr int WBYTES = (BM + 2) * (BN + 2) * 4;
-  // H: two A buffers when they fit
-  static constexpr int NA = (2 * ABYTES + NST * BBYTES + 4096 <= 220 * 1024) ? 2 : 1;
+  static constexpr int HBYTES = (BM + 2) * (BN + 2) * 4;
+  // H: [A buffers (also the output block) | x window | B ring | weights]
+  static constexpr int WGT_H = 2 * (ROWS + COLS) * 4;
+  static constexpr int sz_h(int na, int nst) {
+    return kHdrBytes + (na * ABYTES > OBYTES ? na * ABYTES : OBYTES) + XBYTES + nst * BBYTES + WGT_H;
+  }
+  static constexpr int NA = sz_h(2, 8) <= kSmemMax ? 2 : 1;
+  static constexpr int NST_H = sz_h(NA, 16) <= kSmemMax ? 16 : (sz_h(NA, 8) <= kSmemMax ? 8 : 4);
   static constexpr int AREG_H = NA * ABYTES > OBYTES ? NA * ABYTES : OBYTES;
-  static constexpr int AREG_HT = ABYTES > OBYTES + WBYTES ? ABYTES : OBYTES + WBYTES;
+  // H^T: [A | x window, later output block + halo | B ring | column weights]
+  static constexpr int UREG_HT = XBYTES > OBYTES + HBYTES ? XBYTES : OBYTES + HBYTES;
+  static constexpr int sz_ht(int nst) {
+    return kHdrBytes + ABYTES + UREG_HT + nst * BBYTES + kMaxWcolBytes;
+  }
+  static constexpr int NST_HT = sz_ht(16) <= kSmemMax ? 16 : (sz_ht(8) <= kSmemMax ? 8 : 4);
+  static_assert(S0 >= 0 && S0 + CH + WR <= RB, "Toeplitz windows inside the panels");
+  static_assert(sz_h(NA, NST_H) <= kSmemMax && sz_ht(NST_HT) <= kSmemMax, "shared memory");
 };
 
+constexpr int NSTMAX = 16;
 struct Bars {            // mbarriers etc., at the start of dynamic shared memory
-  uint64_t bfull[NST], bempty[NST];
+  uint64_t bfull[NSTMAX], bempty[NSTMAX];
   uint64_t afull[2], aempty[2];
   uint64_t dfull[2], dempty[2];
   uint64_t fin;          // all MMAs of the CTA complete (teardown)
   uint32_t tmem;         // tensor-memory base written by tcgen05.alloc
   int abort;             // set by the first wait that gives up
 };
-constexpr int kHdr = 256;  // bytes reserved for Bars
-static_assert(sizeof(Bars) <= kHdr, "barrier header");
+static_assert(sizeof(Bars) <= kHdrBytes, "barrier header");
+constexpr int kHdr = kHdrBytes;
 
 template <int PREC, int K>
-constexpr size_t smem_H() {
-  using G = Geo<PREC, K>;
-  return kHdr + (size_t)G::AREG_H + (size_t)NST * G::BBYTES + (size_t)2 * (G::ROWS + G::COLS) * 4;
-}
-constexpr int kMaxWcol = 16;   // H^T: PSF grid columns whose output weights are staged
+constexpr size_t smem_H() { return (size_t)Geo<PREC, K>::sz_h(Geo<PREC, K>::NA, Geo<PREC, K>::NST_H); }
 template <int PREC, int K>
-constexpr size_t smem_Ht() {
-  using G = Geo<PREC, K>;
-  return kHdr + (size_t)G::AREG_HT + (size_t)NST * G::BBYTES + (size_t)kMaxWcol * BN * 4;
-}
-// Requests are padded so that at most 6 H CTAs (64 tensor-memory columns
-// each) or 3 H^T CTAs (128 each) share an SM: their allocations stay within
-// the 512 columns, so tcgen05.alloc never has to wait for another CTA.
-constexpr size_t kMinSmemH = 36 * 1024, kMinSmemHt = 58 * 1024;
+constexpr size_t smem_Ht() { return (size_t)Geo<PREC, K>::sz_ht(Geo<PREC, K>::NST_HT); }
+// Requests are at least this large so that at most 3 CTAs (128 tensor-memory
+// columns at most each) share an SM: their allocations stay within the 512
+// columns, so tcgen05.alloc never has to wait for another CTA.
+constexpr size_t kMinSmem = 58 * 1024;
 
 // ----------------------------------------------------------------- PTX glue
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -134,8 +153,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 }
 // Pipeline wait: false after kWaitNs (the CTA-wide abort flag set and the
 // timeout recorded), or at once when another role has already given up.
-__device__ __noinline__ bool wait_bar(uint64_t* b, uint32_t parity, Bars* H, int* err) {
-  if (mbar_try(b, parity)) return true;
+__device__ __noinline__ bool wait_bar_slow(uint64_t* b, uint32_t parity, Bars* H, int* err) {
   const uint64_t t0 = gtime();
   while (true) {
     if (mbar_try(b, parity)) return true;
@@ -146,6 +164,9 @@ __device__ __noinline__ bool wait_bar(uint64_t* b, uint32_t parity, Bars* H, int
       return false;
     }
   }
+}
+__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, Bars* H, int* err) {
+  return mbar_try(b, parity) || wait_bar_slow(b, parity, H, err);
 }
 // Teardown wait for work this CTA issued: ignores the abort flag, own bound.
 __device__ __noinline__ bool drain_bar(uint64_t* b, uint32_t parity, int* err) {
@@ -276,42 +297,58 @@ __device__ __forceinline__ void put_chunk(unsigned char* abuf, int ir, int q, co
   *reinterpret_cast<uint4*>(abuf + (size_t)q * G::APANEL + ir * 16) = pack_chunk<PREC>(v);
 }
 
-// The MMAs of one tap row: KS k-steps accumulating into tensor-memory column d.
+// The MMAs of one tap row: KS k-steps accumulating into tensor-memory column
+// d.  ad = descriptor of A at rows a .. (k-step 0), bd = descriptor of the B
+// stage at the window of k-step 0; the start-address field counts 16-byte
+// units and never carries out of its 14 bits (shared memory < 256 KB), so
+// the k-step descriptors are plain constant offsets.
 template <int PREC, int K>
-__device__ __forceinline__ void issue_row(uint32_t d, uint32_t a_base, int a, uint32_t b_stage,
-                                          bool first) {
+__device__ __forceinline__ void issue_row(uint32_t d, uint64_t ad, uint64_t bd, bool first) {
   using G = Geo<PREC, K>;
+  mma<PREC>(d, ad, bd, first ? 0u : 1u);
 #pragma unroll
-  for (int ks = 0; ks < G::KS; ++ks) {
-    const uint64_t ad = sdesc(a_base + (uint32_t)(2 * ks) * G::APANEL + 16u * a, G::APANEL);
-    const uint64_t bd = sdesc(b_stage + 16u * G::KM * (G::KS - 1 - ks), G::BPANEL);
-    mma<PREC>(d, ad, bd, (first && ks == 0) ? 0u : 1u);
-  }
+  for (int ks = 1; ks < G::KS; ++ks)
+    mma<PREC>(d, ad + (uint64_t)(2 * ks * (G::APANEL >> 4)), bd - (uint64_t)(ks * G::KM), 1u);
 }
 
-// One lane of warp 4: streams the B tap rows of the PSFs (a_lo..a_hi) x
-// (b_lo..b_hi) through the ring and issues their MMAs.
-// H (ADJ = false): PSF p reads A buffer p % NA and accumulates into d0.
-// H^T (ADJ = true): PSF p reads the single A buffer and accumulates into
-// d0 + 64 (p & 1) once the epilogue has released that buffer.
-template <int PREC, int K, bool ADJ>
-__device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned char* areg,
-                       unsigned char* breg, uint32_t d0, int np) {
+// One lane of warp 5: streams the B tap rows of the PSFs (a_lo..a_hi) x
+// (b_lo..b_hi), in the order the MMA lane consumes them, through the
+// NST-stage ring; a stage is refilled once the MMAs that read it completed.
+template <int PREC, int K, int NST>
+__device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned char* breg, int np) {
   using G = Geo<PREC, K>;
   const int nb = wi.b_hi - wi.b_lo + 1;
   const int total = np * K;
-  const unsigned char* src0 = A.tcop;
-  auto src_of = [&](int it) {
+  int issued = 0;
+  for (int it = 0; it < total; ++it) {
+    const int s = it % NST;
+    if (it >= NST && !wait_bar(&H->bempty[s], (uint32_t)((it / NST - 1) & 1), H, A.err)) break;
     const int p = it / K, a = it - p * K;
     const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-    return src0 + ((size_t)(ga * A.Gc + gb) * K + a) * G::BBYTES;
-  };
-  const int pro = total < NST ? total : NST;
-  for (int it = 0; it < pro; ++it) {
-    mbar_expect_tx(&H->bfull[it], G::BBYTES);
-    bulk_g2s(breg + (size_t)it * G::BBYTES, src_of(it), G::BBYTES, &H->bfull[it]);
+    const unsigned char* src = A.tcop + ((size_t)(ga * A.Gc + gb) * K + a) * G::WBYTES_TX;
+    unsigned char* dst = breg + (size_t)s * G::BBYTES;
+    mbar_expect_tx(&H->bfull[s], G::WBYTES_TX);
+    bulk_g2s(dst + G::S0 * 16, src, G::WR * 16, &H->bfull[s]);
+    bulk_g2s(dst + G::BPANEL + (G::S0 + G::CH) * 16, src + G::WR * 16, G::WR * 16, &H->bfull[s]);
+    issued = it + 1;
   }
-  int issued = pro, consumed = 0;
+  // teardown: every copy issued must have landed before the CTA exits
+  for (int it = (issued > NST ? issued - NST : 0); it < issued; ++it)
+    if (!drain_bar(&H->bfull[it % NST], (uint32_t)((it / NST) & 1), A.err)) break;
+}
+
+// One lane of warp 4: issues the MMAs of every tap row as soon as its B
+// stage has landed, and releases the stage with a commit (never waits for
+// MMA completion except at buffer hand-overs).
+// H (ADJ = false): PSF p reads A buffer p % NA and accumulates into d0.
+// H^T (ADJ = true): PSF p reads the single A buffer and accumulates into
+// d0 + 64 (p & 1) once the epilogue has released that buffer.
+template <int PREC, int K, bool ADJ, int NST>
+__device__ void issuer(const OpArgs& A, Bars* H, unsigned char* areg, unsigned char* breg,
+                       uint32_t d0, int np) {
+  using G = Geo<PREC, K>;
+  // B descriptor of stage 0 at the window of k-step 0
+  const uint64_t bd0 = sdesc(saddr(breg) + 16u * G::KM * (G::KS - 1), G::BPANEL);
   bool ok = true;
   for (int p = 0; p < np && ok; ++p) {
     uint32_t a_base, d;
@@ -328,27 +365,21 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
     }
     if (!ok) break;
     tc_fence_after();
+    const uint64_t ad0 = sdesc(a_base, G::APANEL);
+    int s = (p * K) % NST;
+    uint32_t ph = (uint32_t)(((p * K) / NST) & 1);
     for (int a = 0; a < K; ++a) {
-      const int it = p * K + a, s = it % NST;
-      if (!wait_bar(&H->bfull[s], (uint32_t)((it / NST) & 1), H, A.err)) {
+      if (!wait_bar(&H->bfull[s], ph, H, A.err)) {
         ok = false;
         break;
       }
-      consumed = it + 1;
       tc_fence_after();
-      issue_row<PREC, K>(d, a_base, a, saddr(breg + (size_t)s * G::BBYTES),
+      issue_row<PREC, K>(d, ad0 + (uint64_t)a, bd0 + (uint64_t)(s * (G::BBYTES >> 4)),
                          ADJ ? (a == 0) : (p == 0 && a == 0));
       tc_commit(&H->bempty[s]);
-      // refill the stage of the previous tap row once its MMAs are done
-      if (it >= 1 && issued < total) {
-        const int prev = it - 1, s1 = prev % NST;
-        if (!wait_bar(&H->bempty[s1], (uint32_t)((prev / NST) & 1), H, A.err)) {
-          ok = false;
-          break;
-        }
-        mbar_expect_tx(&H->bfull[s1], G::BBYTES);
-        bulk_g2s(breg + (size_t)s1 * G::BBYTES, src_of(issued), G::BBYTES, &H->bfull[s1]);
-        ++issued;
+      if (++s == NST) {
+        s = 0;
+        ph ^= 1u;
       }
     }
     if (!ok) break;
@@ -361,16 +392,47 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
   if constexpr (!ADJ) {
     if (ok && np > 0) tc_commit(&H->dfull[0]);
   }
-  // teardown: the MMAs and bulk copies this lane issued must be complete
-  // before tensor memory is freed and the CTA exits
+  // teardown: the MMAs this lane issued must be complete before tensor
+  // memory is freed and the CTA exits
   tc_commit(&H->fin);
   drain_bar(&H->fin, 0, A.err);
-  for (int it = consumed; it < issued; ++it)
-    if (!drain_bar(&H->bfull[it % NST], (uint32_t)((it / NST) & 1), A.err)) break;
+}
+
+// Zeroes the rows of the B ring outside the windows the bulk copies fill
+// (the staging threads, once per CTA, before the first MMA may run).
+template <int PREC, int K, int NST>
+__device__ __forceinline__ void zero_ring(unsigned char* breg, int tid) {
+  using G = Geo<PREC, K>;
+  for (int e = tid; e < NST * 2 * G::RB; e += 32 * NWE) {
+    const int s = e / (2 * G::RB), rem = e - s * 2 * G::RB, pn = rem / G::RB, n = rem - pn * G::RB;
+    const int w0 = G::S0 + pn * G::CH;
+    if (n < w0 || n >= w0 + G::WR)
+      *reinterpret_cast<uint4*>(breg + (size_t)s * G::BBYTES + pn * G::BPANEL + n * 16) =
+          make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// FP32 window rows r0 .., columns c0 .. of a pitched image into sX
+// [ROWS][COLS] by cp.async; elements outside [0, nr) x [0, nc) (and columns
+// past `cmax` of the window) are zero-filled.
+template <int PREC, int K>
+__device__ __forceinline__ void load_window(float* sX, const float* img, int64_t pitch, int r0, int c0,
+                                            int nr, int nc, int cmax, int tid) {
+  using G = Geo<PREC, K>;
+  for (int e = tid; e < G::ROWS * G::COLS; e += 32 * NWE) {
+    const int ir = e / G::COLS, ic = e - ir * G::COLS;
+    const int R = r0 + ir, C = c0 + ic;
+    const bool in = R >= 0 && R < nr && C >= 0 && C < nc && ic < cmax;
+    const float* src = in ? img + (int64_t)R * pitch + C : img;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(saddr(sX + e)), "l"(src),
+                 "r"(in ? 4 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 __device__ __forceinline__ void init_bars(Bars* H) {
-  for (int s = 0; s < NST; ++s) {
+  for (int s = 0; s < NSTMAX; ++s) {
     mbar_init(&H->bfull[s], 1);
     mbar_init(&H->bempty[s], 1);
   }
@@ -391,8 +453,10 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
   using G = Geo<PREC, K>;
   extern __shared__ __align__(1024) unsigned char smem[];
   Bars* H = reinterpret_cast<Bars*>(smem);
+  constexpr int NST = G::NST_H;
   unsigned char* areg = smem + kHdr;
-  unsigned char* breg = areg + G::AREG_H;
+  float* sX = reinterpret_cast<float*>(areg + G::AREG_H);                  // [ROWS][COLS]
+  unsigned char* breg = reinterpret_cast<unsigned char*>(sX) + G::XBYTES;
   float* sWr = reinterpret_cast<float*>(breg + (size_t)NST * G::BBYTES);   // [2][ROWS]
   float* sWc = sWr + 2 * G::ROWS;                                         // [2][COLS]
   __shared__ double red[NWE];
@@ -409,12 +473,17 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
   const int np = (wi.a_hi - wi.a_lo + 1) * nb;
 
   if (warp == NWE) {
-    if (lane == 0) issuer<PREC, K, false>(A, wi, H, areg, breg, tbase, np);
+    if (lane == 0) issuer<PREC, K, false, NST>(A, H, areg, breg, tbase, np);
+    __syncwarp();
+  } else if (warp == NWE + 1) {
+    if (lane == 0) producer<PREC, K, NST>(A, wi, H, breg, np);
     __syncwarp();
   } else {
-    // stage S_p = w_p . x per PSF into A buffer p % NA
-    const float* xin = A.in + td.xoff;
-    const bool vec = ((td.xpitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(xin) & 15) == 0);
+    // the x window (rows r0 .., columns c0 ..) once, then S_p = w_p . x per
+    // PSF into A buffer p % NA
+    zero_ring<PREC, K, NST>(breg, tid);
+    if (np > 0)
+      load_window<PREC, K>(sX, A.in + td.xoff, td.xpitch, wi.r0, wi.c0, td.nxr, td.nxc, G::COLS, tid);
     bool ok = true;
     for (int p = 0; p < np && ok; ++p) {
       const int ab = p % G::NA;
@@ -437,29 +506,17 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
       unsigned char* abuf = areg + (size_t)ab * G::ABYTES;
       for (int e = tid; e < G::ROWS * G::NCH; e += 32 * NWE) {
         const int ir = e / G::NCH, q = e - ir * G::NCH;
-        const int R = wi.r0 + ir, C0 = wi.c0 + q * G::CH;
         float v[G::CH];
         const float rw = wr[ir];
-        if (rw == 0.f || R >= td.nxr) {
+        const float4* src = reinterpret_cast<const float4*>(sX + ir * G::COLS + q * G::CH);
+        const float4* wcs = reinterpret_cast<const float4*>(wc + q * G::CH);
 #pragma unroll
-          for (int i = 0; i < G::CH; ++i) v[i] = 0.f;
-        } else {
-          const float* src = xin + (int64_t)R * td.xpitch + C0;
-          if (vec && C0 + G::CH <= td.nxc) {
-#pragma unroll
-            for (int i = 0; i < G::CH; i += 4) {
-              const float4 t = __ldg(reinterpret_cast<const float4*>(src + i));
-              v[i] = t.x;
-              v[i + 1] = t.y;
-              v[i + 2] = t.z;
-              v[i + 3] = t.w;
-            }
-          } else {
-#pragma unroll
-            for (int i = 0; i < G::CH; ++i) v[i] = (C0 + i < td.nxc) ? __ldg(src + i) : 0.f;
-          }
-#pragma unroll
-          for (int i = 0; i < G::CH; ++i) v[i] *= rw * wc[q * G::CH + i];
+        for (int i = 0; i < G::CH; i += 4) {
+          const float4 t = src[i / 4], c = wcs[i / 4];
+          v[i] = rw * c.x * t.x;
+          v[i + 1] = rw * c.y * t.y;
+          v[i + 2] = rw * c.z * t.z;
+          v[i + 3] = rw * c.w * t.w;
         }
         put_chunk<PREC, K>(abuf, ir, q, v);
       }
@@ -543,12 +600,14 @@ __device__ __forceinline__ void huber_p(const float* sW, int SPW, int li, int lj
 
 // ---------------------------------------------------------------- H^T kernel
 template <int PREC, int K>
-__global__ void __launch_bounds__(NTH, 3) tc_Ht_kernel(const OpArgs A) {
+__global__ void __launch_bounds__(NTH, 2) tc_Ht_kernel(const OpArgs A) {
   using G = Geo<PREC, K>;
   extern __shared__ __align__(1024) unsigned char smem[];
   Bars* H = reinterpret_cast<Bars*>(smem);
+  constexpr int NST = G::NST_HT;
   unsigned char* areg = smem + kHdr;
-  unsigned char* breg = areg + G::AREG_HT;
+  unsigned char* ureg = areg + G::ABYTES;      // r window, later output block + halo
+  unsigned char* breg = ureg + G::UREG_HT;
   float* sWcol = reinterpret_cast<float*>(breg + (size_t)NST * G::BBYTES);   // [kMaxWcol][BN]
   const WorkItem wi = A.work[blockIdx.x];
   const TileDesc td = A.tiles[wi.tile];
@@ -563,23 +622,30 @@ __global__ void __launch_bounds__(NTH, 3) tc_Ht_kernel(const OpArgs A) {
   const int np = (wi.a_hi - wi.a_lo + 1) * nb;
 
   if (warp == NWE) {
-    if (lane == 0) issuer<PREC, K, true>(A, wi, H, areg, breg, tbase, np);
+    if (lane == 0) issuer<PREC, K, true, NST>(A, H, areg, breg, tbase, np);
+    __syncwarp();
+  } else if (warp == NWE + 1) {
+    if (lane == 0) producer<PREC, K, NST>(A, wi, H, breg, np);
     __syncwarp();
   } else {
     // residual block: rows R0 - (K-1) .., columns C0 - (K-1) .., zero
     // outside the y-block and beyond the BN + K - 1 columns a block reads
-    const float* rin = A.in + td.yoff;
+    zero_ring<PREC, K, NST>(breg, tid);
+    float* sX = reinterpret_cast<float*>(ureg);
+    load_window<PREC, K>(sX, A.in + td.yoff, td.ypitch, wi.r0 - (K - 1), wi.c0 - (K - 1), td.nyr,
+                         td.nyc, BN + K - 1, tid);
+    named_sync();
     for (int e = tid; e < G::ROWS * G::NCH; e += 32 * NWE) {
       const int ir = e / G::NCH, q = e - ir * G::NCH;
-      const int ry = wi.r0 - (K - 1) + ir, rx0 = wi.c0 - (K - 1) + q * G::CH;
-      const bool row_ok = ry >= 0 && ry < td.nyr;
       float v[G::CH];
+      const float4* src = reinterpret_cast<const float4*>(sX + ir * G::COLS + q * G::CH);
 #pragma unroll
-      for (int i = 0; i < G::CH; ++i) {
-        const int rx = rx0 + i;
-        v[i] = (row_ok && rx >= 0 && rx < td.nyc && q * G::CH + i < BN + K - 1)
-                   ? __ldg(rin + (int64_t)ry * td.ypitch + rx)
-                   : 0.f;
+      for (int i = 0; i < G::CH; i += 4) {
+        const float4 t = src[i / 4];
+        v[i] = t.x;
+        v[i + 1] = t.y;
+        v[i + 2] = t.z;
+        v[i + 3] = t.w;
       }
       put_chunk<PREC, K>(areg, ir, q, v);
     }
@@ -632,10 +698,10 @@ __global__ void __launch_bounds__(NTH, 3) tc_Ht_kernel(const OpArgs A) {
       tc_fence_before();
       mbar_arrive(&H->dempty[db]);
     }
-    // once the last D buffer was full every MMA had completed: the A region
-    // is free for the fp32 output block and the iterate halo
-    float* sO = reinterpret_cast<float*>(areg);
-    float* sW = reinterpret_cast<float*>(areg + G::OBYTES);
+    // the r window is dead once A was converted (every thread passed the
+    // first D wait); the output block and the iterate halo reuse it
+    float* sO = reinterpret_cast<float*>(ureg);
+    float* sW = reinterpret_cast<float*>(ureg + G::OBYTES);
     named_sync();
     if (ok) {
 #pragma unroll
@@ -688,9 +754,9 @@ __global__ void __launch_bounds__(NTH, 3) tc_Ht_kernel(const OpArgs A) {
 }
 
 template <int PREC, int K>
-size_t sm_H() { return std::max(smem_H<PREC, K>(), kMinSmemH); }
+size_t sm_H() { return std::max(smem_H<PREC, K>(), kMinSmem); }
 template <int PREC, int K>
-size_t sm_Ht() { return std::max(smem_Ht<PREC, K>(), kMinSmemHt); }
+size_t sm_Ht() { return std::max(smem_Ht<PREC, K>(), kMinSmem); }
 
 template <int PREC, int K>
 cudaError_t prep_t() {
@@ -732,17 +798,6 @@ cudaError_t prep_prec(int K) {
   }
 }
 
-template <int PREC>
-int bbytes(int K) {
-  switch (K) {
-    case 9: return Geo<PREC, 9>::BBYTES;
-    case 15: return Geo<PREC, 15>::BBYTES;
-    case 31: return Geo<PREC, 31>::BBYTES;
-    case 63: return Geo<PREC, 63>::BBYTES;
-    default: return 0;
-  }
-}
-
 uint16_t to_bf16(float f) {
   // round to nearest even on the IEEE single-precision bit pattern
   uint32_t u;
@@ -771,33 +826,38 @@ cudaError_t tc_prepare(int K, int prec) {
   return prec == DV_PREC_TF32 ? prep_prec<1>(K) : prep_prec<0>(K);
 }
 
-// Tall B operands of every PSF and tap row a, as the shared-memory image the
-// kernels copy: two panels (K chunks 0 and 1) of RB rows x 16 bytes, row n'
-// holding Bt[n'][k] = f(a, k + KM (KS - 1) - n') (zero outside [0, K));
-// f = flipped PSF for H, the PSF for H^T.
+// B operands of every PSF and tap row a: the nonzero windows of the two
+// panels (K chunks 0 and 1) of the tall matrix Bt[n'][k] = f(a, k + KM (KS - 1)
+// - n') (f = flipped PSF for H, the PSF for H^T), rows S0 .. S0 + WR - 1 of
+// panel 0 then rows S0 + CH .. S0 + CH + WR - 1 of panel 1, 16 bytes per row,
+// exactly as the kernels copy them into their ring stages.
 void tc_operands(const float* psfs, int G, int K, int prec, bool flip, std::vector<uint8_t>& out) {
   const bool tf = prec == DV_PREC_TF32;
   const int bytes = tf ? 4 : 2, km = 32 / bytes, ch = 16 / bytes;
   const int KS = (BN - 1 + K + km - 1) / km;
-  const int RB = BN + km * (KS - 1);
-  const int BB = tf ? bbytes<1>(K) : bbytes<0>(K);
-  out.assign((size_t)G * K * BB, 0);
+  const int WR = K + ch - 1, S0 = km * (KS - 1) - K + 1;
+  const size_t per_row = (size_t)2 * WR * 16;
+  out.assign((size_t)G * K * per_row, 0);
   for (int p = 0; p < G; ++p) {
     const float* h = psfs + (size_t)p * K * K;
     for (int a = 0; a < K; ++a) {
-      uint8_t* dst = out.data() + ((size_t)p * K + a) * BB;
-      for (int n = 0; n < RB; ++n)
-        for (int k = 0; k < km; ++k) {
-          const int d = k + km * (KS - 1) - n;
-          float v = 0.f;
-          if (d >= 0 && d < K) v = flip ? h[(K - 1 - a) * K + (K - 1 - d)] : h[a * K + d];
-          uint8_t* e = dst + (size_t)(k / ch) * RB * 16 + (size_t)n * 16 + (k % ch) * bytes;
-          if (tf) {
-            const uint32_t t = to_tf32(v);
-            std::memcpy(e, &t, 4);
-          } else {
-            const uint16_t t = to_bf16(v);
-            std::memcpy(e, &t, 2);
+      uint8_t* dst = out.data() + ((size_t)p * K + a) * per_row;
+      for (int pn = 0; pn < 2; ++pn)
+        for (int r = 0; r < WR; ++r) {
+          const int n = S0 + pn * ch + r;
+          for (int kk = 0; kk < ch; ++kk) {
+            const int k = pn * ch + kk;
+            const int d = k + km * (KS - 1) - n;
+            float v = 0.f;
+            if (d >= 0 && d < K) v = flip ? h[(K - 1 - a) * K + (K - 1 - d)] : h[a * K + d];
+            uint8_t* e = dst + (size_t)pn * WR * 16 + (size_t)r * 16 + (size_t)kk * bytes;
+            if (tf) {
+              const uint32_t t = to_tf32(v);
+              std::memcpy(e, &t, 4);
+            } else {
+              const uint16_t t = to_bf16(v);
+              std::memcpy(e, &t, 2);
+            }
           }
         }
     }
