@@ -174,6 +174,15 @@ cudaError_t tc_prepare(int K, int prec);
 void tc_operands(const float* psfs, int G, int K, int prec, bool flip, std::vector<uint8_t>& out);
 cudaError_t launch_tc_H(const OpArgs& a, cudaStream_t s);
 cudaError_t launch_tc_Ht(const OpArgs& a, cudaStream_t s);
+// BF16 tensor-core path in the column-band layout: 128 output columns per
+// block, up to tcT_max_rows(K) output rows (WorkItem.pad = the block's rows,
+// a multiple of 16)
+int tcT_block_cols();
+int tcT_max_rows(int K);
+cudaError_t tcT_prepare(int K);
+void tcT_operands(const float* psfs, int G, int K, bool flip, std::vector<uint8_t>& out);
+cudaError_t launch_tcT_H(const OpArgs& a, cudaStream_t s);
+cudaError_t launch_tcT_Ht(const OpArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Plan

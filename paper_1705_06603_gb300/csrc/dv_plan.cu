@@ -294,22 +294,30 @@ dv_status alloc(dv_plan* P, T** dst, size_t n) {
 
 // Work items of one operator over the given tiles: output blocks of bm x bn,
 // with the PSF grid range active on the block's input (H) or output (H^T)
-// region.
+// region.  With max_rows > 0 the rows of each tile are split into the fewest
+// blocks of at most max_rows rows, each a multiple of 16 rows, and the
+// block's row count is stored in WorkItem.pad.
 void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const Layout& L, int bm,
-               int bn, std::vector<WorkItem>& out) {
+               int bn, std::vector<WorkItem>& out, int max_rows = 0) {
   out.clear();
   for (int t = 0; t < (int)tiles.size(); ++t) {
     const TileDesc& td = tiles[t];
     const int nr = adjoint ? td.nxr : td.nyr, nc = adjoint ? td.nxc : td.nyc;
-    for (int r0 = 0; r0 < nr; r0 += bm) {
+    int bmt = bm;
+    if (max_rows > 0) {
+      const int nblk = (nr + max_rows - 1) / max_rows;
+      bmt = (int)round_up((nr + nblk - 1) / nblk, 16);
+    }
+    for (int r0 = 0; r0 < nr; r0 += bmt) {
       for (int c0 = 0; c0 < nc; c0 += bn) {
         WorkItem w{};
         w.tile = t;
         w.r0 = r0;
         w.c0 = c0;
+        if (max_rows > 0) w.pad = (int)std::min<int64_t>(bmt, round_up(nr - r0, 16));
         // global x coordinate range whose weights matter
         const int rlo = td.xr0 + r0, clo = td.xc0 + c0;
-        const int rhi = td.xr0 + std::min(r0 + bm, nr) + (adjoint ? 0 : K - 1);
+        const int rhi = td.xr0 + std::min(r0 + bmt, nr) + (adjoint ? 0 : K - 1);
         const int chi = td.xc0 + std::min(c0 + bn, nc) + (adjoint ? 0 : K - 1);
         active_range(L.wrow, rlo, rhi, w.a_lo, w.a_hi);
         active_range(L.wcol, clo, chi, w.b_lo, w.b_hi);
@@ -375,12 +383,14 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, flo
 }
 
 cudaError_t launch_op_H(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
-  if (path == DV_PATH_TENSOR) return launch_tc_H(a, s);
+  if (path == DV_PATH_TENSOR)
+    return P->prob.precision == DV_PREC_BF16 ? launch_tcT_H(a, s) : launch_tc_H(a, s);
   return path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
 }
 
 cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
-  if (path == DV_PATH_TENSOR) return launch_tc_Ht(a, s);
+  if (path == DV_PATH_TENSOR)
+    return P->prob.precision == DV_PREC_BF16 ? launch_tcT_Ht(a, s) : launch_tc_Ht(a, s);
   return path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
 }
 
@@ -616,12 +626,18 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   std::vector<WorkItem> w;
   for (int k = 0; k < 3; ++k) {
     if ((k == 1 && !P->fft_ok) || (k == 2 && !P->tensor_ok)) continue;
+    // tensor path: BF16 column-band blocks (128 columns, rows per tile up to
+    // tcT_max_rows) or the TF32 row-band blocks
+    const bool band = k == 2 && prob->precision == DV_PREC_BF16;
     const int bm = k == 0 ? direct_tile_m() : (k == 1 ? fft_block(K) : tc_block_m());
-    const int bn = k == 0 ? direct_tile_n() : (k == 1 ? fft_block(K) : tc_block_n());
+    const int bn = k == 0 ? direct_tile_n()
+                          : (k == 1 ? fft_block(K) : (band ? tcT_block_cols() : tc_block_n()));
+    const int max_rows = band ? tcT_max_rows(K) : 0;
     OpTables& tb = P->tab[k];
-    // FFT items are handed out dynamically: heaviest (most PSF pairs) first
+    // FFT items are handed out dynamically, tensor items are long: heaviest
+    // (most PSFs) first
     auto order = [&](std::vector<WorkItem>& v) {
-      if (k == 1)
+      if (k >= 1)
         std::stable_sort(v.begin(), v.end(), [](const WorkItem& x, const WorkItem& y) {
           return (x.a_hi - x.a_lo + 1) * (x.b_hi - x.b_lo + 1) + 1 >
                  (y.a_hi - y.a_lo + 1) * (y.b_hi - y.b_lo + 1) + 1;
@@ -634,32 +650,36 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
         tb.pairs[k2] += (np + 1) / 2;
       }
     };
-    make_work(P->h_tiles, false, K, L, bm, bn, w);
+    make_work(P->h_tiles, false, K, L, bm, bn, w, max_rows);
     count(w, 0);
     order(w);
     tb.nH = (int)w.size();
     DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
-    make_work(P->h_tiles, true, K, L, bm, bn, w);
+    make_work(P->h_tiles, true, K, L, bm, bn, w, max_rows);
     count(w, 1);
     order(w);
     tb.nHt = (int)w.size();
     DV_TRY(upload(P, &tb.Ht, w.data(), w.size(), s));
-    make_work(gtiles, false, K, L, bm, bn, w);
+    make_work(gtiles, false, K, L, bm, bn, w, max_rows);
     order(w);
     tb.nHg = (int)w.size();
     DV_TRY(upload(P, &tb.Hg, w.data(), w.size(), s));
-    make_work(gtiles, true, K, L, bm, bn, w);
+    make_work(gtiles, true, K, L, bm, bn, w, max_rows);
     order(w);
     tb.nHtg = (int)w.size();
     DV_TRY(upload(P, &tb.Htg, w.data(), w.size(), s));
   }
   if (P->tensor_ok) {
     std::vector<uint8_t> op;
-    tc_operands(prob->psfs, G, K, prob->precision, true, op);
-    DV_TRY(upload(P, &P->d_tcopH, op.data(), op.size(), s));
-    tc_operands(prob->psfs, G, K, prob->precision, false, op);
-    DV_TRY(upload(P, &P->d_tcopHt, op.data(), op.size(), s));
-    DV_TRY_CUDA(tc_prepare(K, prob->precision));
+    const bool bf16 = prob->precision == DV_PREC_BF16;
+    for (int flip = 1; flip >= 0; --flip) {
+      if (bf16)
+        tcT_operands(prob->psfs, G, K, flip != 0, op);
+      else
+        tc_operands(prob->psfs, G, K, prob->precision, flip != 0, op);
+      DV_TRY(upload(P, flip ? &P->d_tcopH : &P->d_tcopHt, op.data(), op.size(), s));
+    }
+    DV_TRY_CUDA(bf16 ? tcT_prepare(K) : tc_prepare(K, prob->precision));
   }
   DV_TRY(alloc(P, &P->d_err, 1));
   DV_TRY_CUDA(cudaMemsetAsync(P->d_err, 0, sizeof(int), s));
@@ -787,6 +807,9 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->block_psfs[1] = P->tab[k].psfs[1];
   info->psf_pairs[0] = P->tab[k].pairs[0];
   info->psf_pairs[1] = P->tab[k].pairs[1];
-  info->block_side = k == 1 ? fft_block(P->K) : (k == 2 ? tc_block_m() : direct_tile_m());
+  info->block_side = k == 1 ? fft_block(P->K)
+                            : (k == 2 ? (P->prob.precision == DV_PREC_BF16 ? tcT_max_rows(P->K)
+                                                                          : tc_block_m())
+                                      : direct_tile_m());
   return DV_OK;
 }

@@ -37,6 +37,7 @@
 #include <cstring>
 
 #include "dv_internal.cuh"
+#include "dv_tcgen05.cuh"
 
 namespace dv {
 namespace {
@@ -45,8 +46,6 @@ constexpr int BM = 128, BN = 64;
 constexpr int NWE = 4;                    // staging / epilogue warps
 constexpr int NTH = 32 * (NWE + 2);       // + the MMA warp and the bulk-copy warp
 constexpr int OPITCH = BN + 1;            // fp32 output staging pitch (floats)
-constexpr uint64_t kWaitNs = 2000000000ull;    // bound of a pipeline wait
-constexpr uint64_t kDrainNs = 200000000ull;    // bound of a teardown wait
 
 // PREC 0: BF16 (8 elements per 16-byte chunk, MMA K = 16); 1: TF32 (4, 8)
 template <int PREC>
@@ -121,174 +120,16 @@ constexpr size_t smem_Ht() { return (size_t)Geo<PREC, K>::sz_ht(Geo<PREC, K>::NS
 // columns, so tcgen05.alloc never has to wait for another CTA.
 constexpr size_t kMinSmem = 58 * 1024;
 
-// ----------------------------------------------------------------- PTX glue
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(saddr(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Pipeline wait: false after kWaitNs (the CTA-wide abort flag set and the
-// timeout recorded), or at once when another role has already given up.
-__device__ __noinline__ bool wait_bar_slow(uint64_t* b, uint32_t parity, Bars* H, int* err) {
-  const uint64_t t0 = gtime();
-  while (true) {
-    if (mbar_try(b, parity)) return true;
-    if (*(volatile int*)&H->abort) return false;
-    if (gtime() - t0 > kWaitNs) {
-      *(volatile int*)&H->abort = 1;
-      if (err) atomicExch(err, 1);
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, Bars* H, int* err) {
-  return mbar_try(b, parity) || wait_bar_slow(b, parity, H, err);
-}
-// Teardown wait for work this CTA issued: ignores the abort flag, own bound.
-__device__ __noinline__ bool drain_bar(uint64_t* b, uint32_t parity, int* err) {
-  const uint64_t t0 = gtime();
-  while (!mbar_try(b, parity)) {
-    if (gtime() - t0 > kDrainNs) {
-      if (err) atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          saddr(dst)),
-      "l"(src), "r"(bytes), "r"(saddr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   saddr(bar))
-               : "memory");
-}
-// Barrier of the four staging / epilogue warps, and the same barrier as an
-// AND-vote, so that all of them take the same branch after a wait.
-__device__ __forceinline__ void named_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(32 * NWE) : "memory");
-}
-__device__ __forceinline__ bool named_all(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(32 * NWE)
-      : "memory");
-  return r != 0;
-}
+using namespace tcg;
 
-// Shared-memory matrix descriptor, K-major, no swizzle: start address, LBO =
-// byte distance between the two 16-byte K chunks, SBO = 128 (eight 16-byte
-// rows per core matrix, core matrices contiguous along M / N), version 1.
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
-}
-// Instruction descriptor: FP32 accumulator, A and B BF16 (1) or TF32 (2),
-// both K-major, N = 64, M = 128.
-template <int PREC>
-__host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | ((PREC == 0 ? 1u : 2u) << 7) | ((PREC == 0 ? 1u : 2u) << 10) |
-         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
+__device__ __forceinline__ void named_sync() { tcg::named_sync<32 * NWE>(); }
+__device__ __forceinline__ bool named_all(bool v) { return tcg::named_all<32 * NWE>(v); }
 template <int PREC>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  if constexpr (PREC == 0) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc<0>()), "r"(acc)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc<1>()), "r"(acc)
-        : "memory");
-  }
-}
-// 32 consecutive FP32 columns of this warp's 32 lanes
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_free(uint32_t base, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols)
-               : "memory");
-}
-
-// Operand chunk from FP32 values: BF16 round-to-nearest-even or TF32
-// round-to-nearest (ties away), 16 bytes.
-template <int PREC>
-__device__ __forceinline__ uint4 pack_chunk(const float* v) {
-  uint32_t w[4];
-  if constexpr (PREC == 0) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-      w[i] = *reinterpret_cast<const uint32_t*>(&h);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w[i]) : "f"(v[i]));
-  }
-  return make_uint4(w[0], w[1], w[2], w[3]);
+  if constexpr (PREC == 0)
+    mma_bf16(d, a, b, idesc(1, BM, BN), acc);
+  else
+    mma_tf32(d, a, b, idesc(2, BM, BN), acc);
 }
 
 template <int PREC, int K>
@@ -322,7 +163,7 @@ __device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned 
   int issued = 0;
   for (int it = 0; it < total; ++it) {
     const int s = it % NST;
-    if (it >= NST && !wait_bar(&H->bempty[s], (uint32_t)((it / NST - 1) & 1), H, A.err)) break;
+    if (it >= NST && !wait_bar(&H->bempty[s], (uint32_t)((it / NST - 1) & 1), &H->abort, A.err)) break;
     const int p = it / K, a = it - p * K;
     const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
     const unsigned char* src = A.tcop + ((size_t)(ga * A.Gc + gb) * K + a) * G::WBYTES_TX;
@@ -355,13 +196,13 @@ __device__ void issuer(const OpArgs& A, Bars* H, unsigned char* areg, unsigned c
     if constexpr (ADJ) {
       a_base = saddr(areg);
       d = d0 + 64u * (uint32_t)(p & 1);
-      if (p == 0) ok = wait_bar(&H->afull[0], 0, H, A.err);
-      if (ok && p >= 2) ok = wait_bar(&H->dempty[p & 1], (uint32_t)((p / 2 - 1) & 1), H, A.err);
+      if (p == 0) ok = wait_bar(&H->afull[0], 0, &H->abort, A.err);
+      if (ok && p >= 2) ok = wait_bar(&H->dempty[p & 1], (uint32_t)((p / 2 - 1) & 1), &H->abort, A.err);
     } else {
       const int ab = p % G::NA;
       a_base = saddr(areg + (size_t)ab * G::ABYTES);
       d = d0;
-      ok = wait_bar(&H->afull[ab], (uint32_t)((p / G::NA) & 1), H, A.err);
+      ok = wait_bar(&H->afull[ab], (uint32_t)((p / G::NA) & 1), &H->abort, A.err);
     }
     if (!ok) break;
     tc_fence_after();
@@ -369,7 +210,7 @@ __device__ void issuer(const OpArgs& A, Bars* H, unsigned char* areg, unsigned c
     int s = (p * K) % NST;
     uint32_t ph = (uint32_t)(((p * K) / NST) & 1);
     for (int a = 0; a < K; ++a) {
-      if (!wait_bar(&H->bfull[s], ph, H, A.err)) {
+      if (!wait_bar(&H->bfull[s], ph, &H->abort, A.err)) {
         ok = false;
         break;
       }
@@ -488,7 +329,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
     for (int p = 0; p < np && ok; ++p) {
       const int ab = p % G::NA;
       if (p >= G::NA) {
-        ok = named_all(wait_bar(&H->aempty[ab], (uint32_t)((p / G::NA - 1) & 1), H, A.err));
+        ok = named_all(wait_bar(&H->aempty[ab], (uint32_t)((p / G::NA - 1) & 1), &H->abort, A.err));
         if (!ok) break;
       }
       const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
@@ -525,7 +366,7 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
     }
     // epilogue: accumulator row 32 warp + lane -> fp32 staging block
     float* sO = reinterpret_cast<float*>(areg);
-    if (ok && np > 0) ok = named_all(wait_bar(&H->dfull[0], 0, H, A.err));
+    if (ok && np > 0) ok = named_all(wait_bar(&H->dfull[0], 0, &H->abort, A.err));
     tc_fence_after();
     named_sync();   // every staging thread is past its last A write
     {
@@ -579,23 +420,6 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
     tc_fence_after();
     tmem_free(tbase, 64);
   }
-}
-
-// p = kappa (dr, dc) of the Huber prior at tile pixel (R, C) from the staged
-// iterate (smem (li, lj), pitch SPW); zero above / left of the tile.
-__device__ __forceinline__ void huber_p(const float* sW, int SPW, int li, int lj, int R, int C,
-                                        int nxr, int nxc, float delta, float& pr, float& pc) {
-  if (R < 0 || C < 0) {
-    pr = pc = 0.f;
-    return;
-  }
-  const float c0 = sW[li * SPW + lj];
-  const float dr = (R + 1 < nxr) ? sW[(li + 1) * SPW + lj] - c0 : 0.f;
-  const float dc = (C + 1 < nxc) ? sW[li * SPW + lj + 1] - c0 : 0.f;
-  const float s2 = dr * dr + dc * dc;
-  const float k = (s2 <= delta * delta) ? 1.f : delta * rsqrtf(s2);
-  pr = k * dr;
-  pc = k * dc;
 }
 
 // ---------------------------------------------------------------- H^T kernel
@@ -671,7 +495,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_Ht_kernel(const OpArgs A) {
     bool ok = true;
     for (int p = 0; p < np; ++p) {
       const int db = p & 1;
-      if (!named_all(wait_bar(&H->dfull[db], (uint32_t)((p / 2) & 1), H, A.err))) {
+      if (!named_all(wait_bar(&H->dfull[db], (uint32_t)((p / 2) & 1), &H->abort, A.err))) {
         ok = false;
         break;
       }

@@ -319,7 +319,7 @@ def test_tensor_operator_matches_oracle(env, prec, hy, wy, K, G):
     x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
     r = g.standard_normal((hy, wy)).astype(np.float32)
     plan = dv.Plan(hy, wy, psfs, precision=prec, path=TENSOR)
-    assert plan.info.path == TENSOR and plan.info.block_side == 128
+    assert plan.info.path == TENSOR and plan.info.block_side in (128, 256)
     yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
     gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
     wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
