@@ -383,8 +383,9 @@ def run_ours(args):
     tc_prec = 0 if args.precision == "bf16" else 1
     kH, kHt = {dv.DV_PATH_FFT: ("fft_H_kernel", "fft_Ht_kernel"),
                dv.DV_PATH_DIRECT: (f"direct_H_kernel<{w.K}>", f"direct_Ht_kernel<{w.K}>"),
-               dv.DV_PATH_TENSOR: (f"tc_H_kernel<{tc_prec},{w.K}>",
-                                   f"tc_Ht_kernel<{tc_prec},{w.K}>")}[path]
+               dv.DV_PATH_TENSOR: ((f"tcT_H_kernel<{w.K}>", f"tcT_Ht_kernel<{w.K}>")
+                                   if args.precision == "bf16" else
+                                   (f"tc_H_kernel<1,{w.K}>", f"tc_Ht_kernel<1,{w.K}>"))}[path]
     names = {0: f"{kH} (H_i with residual)", 1: f"{kHt} (H_i^T + fused prox step)",
              2: "consensus_kernel"}
     dom = max((0, 1), key=lambda k: ktime[k][0])
@@ -397,9 +398,18 @@ def run_ours(args):
         # active PSFs (first-order interpolation); the tensor pipe also runs
         # the zero band of the Toeplitz operand and the ragged block tails
         flops = 8.0 * w.K * w.K * px
-        km = 16 if args.precision == "bf16" else 8
-        ks = (63 + w.K + km - 1) // km
-        executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 64
+        # executed MMA work: per (block, PSF) pair and tap row, KS k-steps of
+        # 128 x N x KM; BF16 column-band blocks: N = the block's rows (up to
+        # 256), K-extent 127 + K; TF32 row-band blocks: 128 x 64, K-extent 63 + K
+        if args.precision == "bf16":
+            km, band = 16, 127 + w.K
+            ks = (band + km - 1) // km
+            mean_rows = (y_px if dom == 0 else x_px) / max(info.blocks[dom], 1) / 128.0
+            executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 16 * np.ceil(mean_rows / 16)
+        else:
+            km, band = 8, 63 + w.K
+            ks = (band + km - 1) // km
+            executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 64
         sus = float(peaks.get("bf16_tflops_sustained", 1700.0))
         peak = sus if args.precision == "bf16" else sus * 1.1 / 2.25
         bound, unit = "tensor", "TFLOP/s"

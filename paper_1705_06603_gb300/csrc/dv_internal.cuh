@@ -114,6 +114,21 @@ struct OpArgs {
   int* err;               // tensor-core path: nonzero after a bounded wait gave up
 };
 
+// One item of the consensus / assembly kernels: a rectangle of the global x
+// grid (at most 8 rows x 512 columns) over which the covering tiles do not
+// change, with per covering tile ("slot", tile rows outer, tile columns
+// inner): the stack offset of (r0, global column 0), the row pitch, and the
+// indices of global row 0 / column 0 in the consensus profiles.
+struct ConsItem {
+  int32_t r0, nrow, c0, ncol;
+  int32_t ns, pad[3];
+  int64_t base[4];
+  int32_t pitch[4];
+  int32_t obr[4];
+  int32_t obc[4];
+};
+static_assert(sizeof(ConsItem) == 112, "ConsItem layout");
+
 // Streaming kernels' shared view of the tile grid
 struct GridArgs {
   const TileDesc* tiles;
@@ -123,7 +138,8 @@ struct GridArgs {
   const float* omc;
   int32_t n_tc;
   int32_t nxr, nxc;
-  int32_t pad;
+  int32_t n_citems;
+  const ConsItem* citems;
 };
 
 // ---------------------------------------------------------------------------
@@ -144,7 +160,10 @@ cudaError_t launch_scatter(const GridArgs& g, int n_tiles, int max_nxr, int max_
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma,
                              float rho, float* zbuf, double* partials, cudaStream_t s,
                              int* n_blocks_out);
-int consensus_blocks(int nxr, int nxc);
+int consensus_blocks(int n_citems);
+// rows / columns of the largest consensus item
+int cons_item_rows();
+int cons_item_cols();
 // x_hat = sum omega_i x_i / sum omega_i
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s);
 // FP64 block partials of the Huber prior over the tile stacks
@@ -266,6 +285,8 @@ struct dv_plan {
   dv::TileDesc* d_gtile = nullptr;
   int2* d_rowcov = nullptr;
   int2* d_colcov = nullptr;
+  dv::ConsItem* d_citems = nullptr;
+  int n_citems = 0;
   float* d_w[2] = {nullptr, nullptr};
   float* d_u = nullptr;
   float* d_r = nullptr;

@@ -401,6 +401,8 @@ dv::GridArgs grid_args(const dv_plan* p) {
   g.tiles = p->d_tiles;
   g.rowcov = p->d_rowcov;
   g.colcov = p->d_colcov;
+  g.citems = p->d_citems;
+  g.n_citems = p->n_citems;
   g.omr = p->d_omr;
   g.omc = p->d_omc;
   g.n_tc = p->n_tc;
@@ -700,6 +702,45 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     for (int C = L.yc0[tc]; C < L.yc1[tc] + K - 1; ++C) (cc[C].x < 0 ? cc[C].x : cc[C].y) = tc;
   DV_TRY(upload(P, &P->d_rowcov, rc.data(), rc.size(), s));
   DV_TRY(upload(P, &P->d_colcov, cc.data(), cc.size(), s));
+  // consensus / assembly items: rectangles of constant cover, cut into at
+  // most cons_item_rows() x cons_item_cols() pixels
+  {
+    std::vector<ConsItem> items;
+    auto bands = [](const std::vector<int2>& cov) {
+      std::vector<std::pair<int, int>> b;
+      for (int i = 0; i < (int)cov.size();) {
+        int e = i + 1;
+        while (e < (int)cov.size() && cov[e].x == cov[i].x && cov[e].y == cov[i].y) ++e;
+        b.push_back({i, e});
+        i = e;
+      }
+      return b;
+    };
+    for (const auto& rb : bands(rc))
+      for (const auto& cb : bands(cc))
+        for (int r0 = rb.first; r0 < rb.second; r0 += cons_item_rows())
+          for (int c0 = cb.first; c0 < cb.second; c0 += cons_item_cols()) {
+            ConsItem it{};
+            it.r0 = r0;
+            it.nrow = std::min(cons_item_rows(), rb.second - r0);
+            it.c0 = c0;
+            it.ncol = std::min(cons_item_cols(), cb.second - c0);
+            const int trs[2] = {rc[r0].x, rc[r0].y}, tcs[2] = {cc[c0].x, cc[c0].y};
+            for (int i = 0; i < 2; ++i)
+              for (int j = 0; j < 2; ++j) {
+                if (trs[i] < 0 || tcs[j] < 0) continue;
+                const TileDesc& td = P->h_tiles[(size_t)trs[i] * P->n_tc + tcs[j]];
+                const int sl = it.ns++;
+                it.base[sl] = td.xoff + (int64_t)(r0 - td.xr0) * td.xpitch - td.xc0;
+                it.pitch[sl] = td.xpitch;
+                it.obr[sl] = td.omr_off - td.xr0;
+                it.obc[sl] = td.omc_off - td.xc0;
+              }
+            items.push_back(it);
+          }
+    P->n_citems = (int)items.size();
+    DV_TRY(upload(P, &P->d_citems, items.data(), items.size(), s));
+  }
 
   // iterates, dual variable, residuals, data, scratch
   DV_TRY(alloc(P, &P->d_w[0], P->xstack));
@@ -716,7 +757,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   if (prob->noise_w) DV_TRY(upload(P, &P->d_W, prob->noise_w, (size_t)P->hy * P->wy, s));
   DV_TRY(alloc(P, &P->d_z, (size_t)P->nxr * P->nxc));
   DV_TRY(alloc(P, &P->d_xg, (size_t)P->nxr * P->nxc));
-  const int64_t ncons = consensus_blocks(P->nxr, P->nxc);
+  const int64_t ncons = consensus_blocks(P->n_citems);
   const int64_t nhub = huber_blocks(P->T, P->max_nxr, P->max_nxc);
   P->n_part = std::max(std::max(P->tab[0].nH, P->tab[1].nH), P->tab[2].nH) + nhub + 2 * ncons;
   DV_TRY(alloc(P, &P->d_part, (size_t)P->n_part));
@@ -766,7 +807,7 @@ dv_status release(dv_plan* P) {
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
                   P->tab[2].H, P->tab[2].Ht, P->tab[2].Hg, P->tab[2].Htg,
                   P->d_tcopH, P->d_tcopHt, P->d_err,
-                  P->d_rowcov, P->d_colcov, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
+                  P->d_rowcov, P->d_colcov, P->d_citems, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
     if (b) cudaFree(b);

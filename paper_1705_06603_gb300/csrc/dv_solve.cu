@@ -13,7 +13,7 @@ namespace {
 enum Kind { KIND_H = 0, KIND_HT = 1, KIND_CONS = 2 };
 
 int nhub(const dv_plan* P) { return huber_blocks(P->T, P->max_nxr, P->max_nxc); }
-int ncons(const dv_plan* P) { return consensus_blocks(P->nxr, P->nxc); }
+int ncons(const dv_plan* P) { return consensus_blocks(P->n_citems); }
 double* part_data(dv_plan* P) { return P->d_part; }
 int npart_data(const dv_plan* P) {
   return std::max(std::max(P->tab[0].nH, P->tab[1].nH), P->tab[2].nH);

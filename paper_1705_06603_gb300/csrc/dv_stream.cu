@@ -54,104 +54,66 @@ __global__ void scatter_kernel(const TileDesc* __restrict__ tiles, const float* 
   }
 }
 
-// The consensus, assembly and prior kernels work row-wise: a block owns one
-// global x row (or a few tile rows) and NBR threads stride over its columns,
-// so every warp touches 32 consecutive pixels of each tile stack it reads.
-constexpr int NBR = 128;   // threads per block of the row kernels
-constexpr int GRP = 4;     // pixels per thread and group: loads of a group are issued together
-constexpr int HUB_ROWS = 4;  // tile rows per block of the prior kernel
-
-// Column chunks of the row kernels: about 4096 columns each, a multiple of 32.
-__host__ __device__ inline int row_chunks(int nxc) { return (nxc + 4095) / 4096; }
-__host__ __device__ inline int row_chunk_width(int nxc) {
-  const int n = row_chunks(nxc);
-  return ((nxc + n - 1) / n + 31) / 32 * 32;
-}
-
-// Per block: for the (one or two) tile rows covering global row R and every
-// tile column t, the stack offset of global column 0 on that row (sbase), the
-// row factor of the profile times `scale` (srow) and the offset of global
-// column 0 in the column profile (somc).  Returns the number of tile rows.
-__device__ __forceinline__ int stage_row(const GridArgs& G, int R, float scale, int64_t* sbase,
-                                         float* srow, int* somc) {
-  const int2 rc = G.rowcov[R];
-  const int nr = rc.y >= 0 ? 2 : 1;
-  for (int e = threadIdx.x; e < nr * G.n_tc; e += blockDim.x) {
-    const int i = e / G.n_tc, t = e - i * G.n_tc;
-    const TileDesc td = G.tiles[(i ? rc.y : rc.x) * G.n_tc + t];
-    const int lr = R - td.xr0;
-    sbase[e] = td.xoff + (int64_t)lr * td.xpitch - td.xc0;
-    srow[e] = scale * G.omr[td.omr_off + lr];
-    somc[e] = td.omc_off - td.xc0;
-  }
-  __syncthreads();
-  return nr;
-}
+// The consensus and assembly kernels run over items: rectangles of at most
+// CI_ROWS x CI_COLS global pixels with a fixed set of covering tiles, so the
+// tile offsets are uniform per block and every load of a pixel group is
+// independent of the others.  Thread t owns columns t, t + 128, t + 256,
+// t + 384 of every row of its item.
+constexpr int NBR = 128;        // threads per block of the row kernels
+constexpr int CI_ROWS = 8, CI_COLS = 4 * NBR;
+constexpr int HUB_ROWS = 4;     // tile rows per block of the prior kernel
 
 // Per global x pixel: zbar = sum_i alpha_i (2 x_i - u_i) / sum_i alpha_i over
-// the (at most 2 x 2) tiles covering it, then u_i <- u_i + rho (zbar - x_i).
-// With partials: FP64 block sums of (x_i - zbar)^2 and (zbar - zbar_prev)^2
-// (each thread adds a group's FP32 sum of at most 4 x 4 terms in FP64).
-__global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const float* __restrict__ x,
-                                                        float* __restrict__ u, float gamma, float rho,
-                                                        float* __restrict__ zg,
-                                                        double* __restrict__ partials) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ double red[NBR / 32];
-  const int ntc = G.n_tc;
-  int64_t* sbase = reinterpret_cast<int64_t*>(dsm);
-  float* srow = reinterpret_cast<float*>(sbase + 2 * ntc);
-  int* somc = reinterpret_cast<int*>(srow + 2 * ntc);
-  const int R = blockIdx.y;
-  const int nr = stage_row(G, R, gamma, sbase, srow, somc);
-  const int cw = row_chunk_width(G.nxc);
-  const int c0 = blockIdx.x * cw, c1 = min(c0 + cw, G.nxc);
-  double pp = 0.0, dd = 0.0;
-  for (int cb = c0 + threadIdx.x; cb < c1; cb += GRP * NBR) {
-    float xs[GRP][4], us[GRP][4], as[GRP][4], zp[GRP];
-    int2 cc[GRP];
+// the NS tiles covering it, then u_i <- u_i + rho (zbar - x_i).  With
+// partials: FP64 block sums of (x_i - zbar)^2 and (zbar - zbar_prev)^2 (each
+// thread adds a group's FP32 sum in FP64).
+template <int NS>
+__device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem& it,
+                                               const float* __restrict__ x, float* __restrict__ u,
+                                               float gamma, float rho, float* __restrict__ zg,
+                                               double& pp, double& dd) {
+  constexpr int GP = 16 / NS;      // pixels per group
+  const int tx = threadIdx.x;
+  for (int k0 = 0; k0 < 4 * it.nrow; k0 += GP) {
+    float xs[GP][NS], us[GP][NS], as[GP][NS], zp[GP];
 #pragma unroll
-    for (int k = 0; k < GRP; ++k) {
-      const int C = cb + k * NBR;
-      const bool in = C < c1;
-      cc[k] = in ? G.colcov[C] : make_int2(-1, -1);
-      zp[k] = (in && zg) ? zg[(int64_t)R * G.nxc + C] : 0.f;
+    for (int g = 0; g < GP; ++g) {
+      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
+      const bool in = r < it.nrow && cl < it.ncol;
+      const int R = it.r0 + r, C = it.c0 + cl;
+      zp[g] = (in && zg) ? zg[(int64_t)R * G.nxc + C] : 0.f;
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        const int i = sl >> 1, t = (sl & 1) ? cc[k].y : cc[k].x;
-        xs[k][sl] = us[k][sl] = as[k][sl] = 0.f;
-        if (in && i < nr && t >= 0) {
-          const int e = i * ntc + t;
-          const int64_t id = sbase[e] + C;
-          xs[k][sl] = x[id];
-          us[k][sl] = u[id];
-          as[k][sl] = srow[e] * G.omc[somc[e] + C];
+      for (int s = 0; s < NS; ++s) {
+        xs[g][s] = us[g][s] = as[g][s] = 0.f;
+        if (in) {
+          const int64_t id = it.base[s] + (int64_t)r * it.pitch[s] + C;
+          xs[g][s] = x[id];
+          us[g][s] = u[id];
+          as[g][s] = gamma * G.omr[it.obr[s] + R] * G.omc[it.obc[s] + C];
         }
       }
     }
     float pg = 0.f, dg = 0.f;
 #pragma unroll
-    for (int k = 0; k < GRP; ++k) {
-      const int C = cb + k * NBR;
-      if (C >= c1) continue;
+    for (int g = 0; g < GP; ++g) {
+      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
+      if (r >= it.nrow || cl >= it.ncol) continue;
+      const int R = it.r0 + r, C = it.c0 + cl;
       float num = 0.f, den = 0.f;
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        num += as[k][sl] * (2.f * xs[k][sl] - us[k][sl]);
-        den += as[k][sl];
+      for (int s = 0; s < NS; ++s) {
+        num += as[g][s] * (2.f * xs[g][s] - us[g][s]);
+        den += as[g][s];
       }
       const float z = num / den;
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        if (as[k][sl] != 0.f) {
-          const int e = (sl >> 1) * ntc + ((sl & 1) ? cc[k].y : cc[k].x);
-          u[sbase[e] + C] = us[k][sl] + rho * (z - xs[k][sl]);
-          const float d = xs[k][sl] - z;
-          pg = fmaf(d, d, pg);
-        }
+      for (int s = 0; s < NS; ++s) {
+        u[it.base[s] + (int64_t)r * it.pitch[s] + C] = us[g][s] + rho * (z - xs[g][s]);
+        const float d = xs[g][s] - z;
+        pg = fmaf(d, d, pg);
       }
       if (zg) {
-        const float d = z - zp[k];
+        const float d = z - zp[g];
         dg = fmaf(d, d, dg);
         zg[(int64_t)R * G.nxc + C] = z;
       }
@@ -159,52 +121,68 @@ __global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const 
     pp += (double)pg;
     dd += (double)dg;
   }
+}
+
+__global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const float* __restrict__ x,
+                                                        float* __restrict__ u, float gamma, float rho,
+                                                        float* __restrict__ zg,
+                                                        double* __restrict__ partials) {
+  __shared__ double red[NBR / 32];
+  const ConsItem it = G.citems[blockIdx.x];
+  double pp = 0.0, dd = 0.0;
+  if (it.ns == 1)
+    consensus_item<1>(G, it, x, u, gamma, rho, zg, pp, dd);
+  else if (it.ns == 2)
+    consensus_item<2>(G, it, x, u, gamma, rho, zg, pp, dd);
+  else
+    consensus_item<4>(G, it, x, u, gamma, rho, zg, pp, dd);
   if (partials) {
-    const int blk = blockIdx.y * gridDim.x + blockIdx.x, nblk = gridDim.x * gridDim.y;
     const double sp = block_sum(pp, red);
-    if (threadIdx.x == 0) partials[blk] = sp;
+    if (threadIdx.x == 0) partials[blockIdx.x] = sp;
     const double sd = block_sum(dd, red);
-    if (threadIdx.x == 0) partials[nblk + blk] = sd;
+    if (threadIdx.x == 0) partials[gridDim.x + blockIdx.x] = sd;
   }
 }
 
 // x_hat = sum_i omega_i x_i / sum_i omega_i over the tiles covering each pixel.
-__global__ void __launch_bounds__(NBR) assemble_kernel(const GridArgs G, const float* __restrict__ x,
-                                                       float* __restrict__ out) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  const int ntc = G.n_tc;
-  int64_t* sbase = reinterpret_cast<int64_t*>(dsm);
-  float* srow = reinterpret_cast<float*>(sbase + 2 * ntc);
-  int* somc = reinterpret_cast<int*>(srow + 2 * ntc);
-  const int R = blockIdx.y;
-  const int nr = stage_row(G, R, 1.f, sbase, srow, somc);
-  const int cw = row_chunk_width(G.nxc);
-  const int c0 = blockIdx.x * cw, c1 = min(c0 + cw, G.nxc);
-  for (int cb = c0 + threadIdx.x; cb < c1; cb += GRP * NBR) {
-    float num[GRP], den[GRP];
+template <int NS>
+__device__ __forceinline__ void assemble_item(const GridArgs& G, const ConsItem& it,
+                                              const float* __restrict__ x, float* __restrict__ out) {
+  constexpr int GP = 16 / NS;
+  const int tx = threadIdx.x;
+  for (int k0 = 0; k0 < 4 * it.nrow; k0 += GP) {
+    float num[GP], den[GP];
 #pragma unroll
-    for (int k = 0; k < GRP; ++k) {
-      const int C = cb + k * NBR;
-      num[k] = den[k] = 0.f;
-      if (C >= c1) continue;
-      const int2 cc = G.colcov[C];
+    for (int g = 0; g < GP; ++g) {
+      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
+      num[g] = den[g] = 0.f;
+      if (r >= it.nrow || cl >= it.ncol) continue;
+      const int R = it.r0 + r, C = it.c0 + cl;
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        const int i = sl >> 1, t = (sl & 1) ? cc.y : cc.x;
-        if (i < nr && t >= 0) {
-          const int e = i * ntc + t;
-          const float om = srow[e] * G.omc[somc[e] + C];
-          num[k] += om * x[sbase[e] + C];
-          den[k] += om;
-        }
+      for (int s = 0; s < NS; ++s) {
+        const float om = G.omr[it.obr[s] + R] * G.omc[it.obc[s] + C];
+        num[g] += om * x[it.base[s] + (int64_t)r * it.pitch[s] + C];
+        den[g] += om;
       }
     }
 #pragma unroll
-    for (int k = 0; k < GRP; ++k) {
-      const int C = cb + k * NBR;
-      if (C < c1) out[(int64_t)R * G.nxc + C] = num[k] / den[k];
+    for (int g = 0; g < GP; ++g) {
+      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
+      if (r < it.nrow && cl < it.ncol)
+        out[(int64_t)(it.r0 + r) * G.nxc + it.c0 + cl] = num[g] / den[g];
     }
   }
+}
+
+__global__ void __launch_bounds__(NBR) assemble_kernel(const GridArgs G, const float* __restrict__ x,
+                                                       float* __restrict__ out) {
+  const ConsItem it = G.citems[blockIdx.x];
+  if (it.ns == 1)
+    assemble_item<1>(G, it, x, out);
+  else if (it.ns == 2)
+    assemble_item<2>(G, it, x, out);
+  else
+    assemble_item<4>(G, it, x, out);
 }
 
 // FP64 block partials of sum_l hub(|grad x(l)|) over every tile of the stack
@@ -268,17 +246,17 @@ size_t row_smem(int n_tc) { return (size_t)2 * n_tc * (sizeof(int64_t) + 2 * siz
 
 cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float gamma, float rho,
                              float* zbuf, double* partials, cudaStream_t s, int* n_blocks_out) {
-  dim3 grid(row_chunks(g.nxc), g.nxr);
-  if (n_blocks_out) *n_blocks_out = grid.x * grid.y;
-  consensus_kernel<<<grid, NBR, row_smem(g.n_tc), s>>>(g, x, u, gamma, rho, zbuf, partials);
+  if (n_blocks_out) *n_blocks_out = g.n_citems;
+  consensus_kernel<<<g.n_citems, NBR, 0, s>>>(g, x, u, gamma, rho, zbuf, partials);
   return cudaGetLastError();
 }
 
-int consensus_blocks(int nxr, int nxc) { return row_chunks(nxc) * nxr; }
+int consensus_blocks(int n_citems) { return n_citems; }
+int cons_item_rows() { return CI_ROWS; }
+int cons_item_cols() { return CI_COLS; }
 
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s) {
-  dim3 grid(row_chunks(g.nxc), g.nxr);
-  assemble_kernel<<<grid, NBR, row_smem(g.n_tc), s>>>(g, x, out);
+  assemble_kernel<<<g.n_citems, NBR, 0, s>>>(g, x, out);
   return cudaGetLastError();
 }
 
