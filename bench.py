@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16",
                     help="lowest operand precision the chosen form may use for H / H^T "
                          "(the autotuner picks the fastest allowed path)")
+    ap.add_argument("--ws-pairs", type=int, default=24,
+                    help="warm-start training pairs made by the plain method")
+    ap.add_argument("--ws-steps", type=int, default=2000, help="warm-start Adam steps")
     ap.add_argument("--profile-case", action="store_true",
                     help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
                          "short, fixed launch sequence for ncu captures); prints nothing")
@@ -313,7 +316,8 @@ def run_ours(args):
 
     # chosen form: autotuned operator, CUDA graphs, learned warm start, stops at
     # F <= F*(1 + 1e-4) (objective checked every 2 outer iterations)
-    net, train_info = train_warmstart(dv, w, psfs, seed=rank)
+    net, train_info = train_warmstart(dv, w, psfs, seed=rank, n_pairs=args.ws_pairs,
+                                      steps=args.ws_steps)
     target = f_star * (1.0 + 1e-4)
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=2 * w.n_outer, use_warmstart=1,

@@ -468,6 +468,54 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
     mbar_arrive(&H->sfull);
     sync_stage();
 
+    float* sT = sU;                      // [32][TP]
+    float* sH = sU + 32 * TP;            // [34][HW] halo of the iterate
+    constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
+    const bool step = A.mode != OP_PLAIN;
+    // OP_STEP splits w_next = max(0, w - tau (g + lambda D^T psi(D w) + alpha (w - u)))
+    // into q = w - tau (lambda D^T psi(D w) + alpha (w - u)), which does not
+    // need g and is computed into the output while the MMAs run, and the
+    // final max(0, q - tau g).
+    auto q_chunk = [&](int i0) {
+      for (int e = tid; e < 34 * HW; e += NT) {
+        const int ir = e / HW, ic = e - ir * HW;
+        const int Rr = wi.r0 + i0 - 1 + ir, Cc = wi.c0 - 1 + ic;
+        const bool in = Rr >= 0 && Rr < td.nxr && Cc >= 0 && Cc < td.nxc;
+        cp_async4(sH + e, in ? A.w + td.xoff + (int64_t)Rr * td.xpitch + Cc : A.w, in);
+      }
+      float uv[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
+        const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
+        uv[u] = (i0 + il < nrow && Ro < td.nxr && Co < td.nxc)
+                    ? __ldg(A.u + td.xoff + (int64_t)Ro * td.xpitch + Co)
+                    : 0.f;
+      }
+      cp_async_wait_all();
+      sync_stage();
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
+        const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
+        if (i0 + il >= nrow || Ro >= td.nxr || Co >= td.nxc) continue;
+        const int li = il + 1, lj = jl + 1;
+        float pr, pc, pru, pcu, prl, pcl;
+        huber_p(sH, HW, li, lj, Ro, Co, td.nxr, td.nxc, A.delta, pr, pc);
+        huber_p(sH, HW, li - 1, lj, Ro - 1, Co, td.nxr, td.nxc, A.delta, pru, pcu);
+        huber_p(sH, HW, li, lj - 1, Ro, Co - 1, td.nxr, td.nxc, A.delta, prl, pcl);
+        const float hub = pru - pr + pcl - pc;
+        const float wv = sH[li * HW + lj];
+        const float alpha = sOr[i0 + il] * sOc[jl];
+        A.out[td.xoff + (int64_t)Ro * td.xpitch + Co] =
+            wv - td.tau * (A.lambda * hub + alpha * (wv - uv[u]));
+      }
+      sync_stage();
+    };
+    const int nck = (nrow + 31) / 32;
+    const int qper = np > 0 ? (nck + np - 1) / np : nck;   // q chunks per PSF interval
+    int qc = 0;
+
     // G (tensor-memory columns NR ..) = sum_p w_p . D_p; each warp covers 16
     // rows of every 32-row chunk for its 32 columns, D and G loaded together
     const int j = 32 * (warp & 3) + lane, hf = warp >> 2;
@@ -475,6 +523,8 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = true;
     for (int p = 0; p < np; ++p) {
+      if (step)
+        for (int k = 0; k < qper && qc < nck; ++k) q_chunk(32 * qc++);
       if (!all_stage(wait_bar(&H->dfull[0], (uint32_t)(p & 1), &H->abort, A.err))) {
         ok = false;
         break;
@@ -505,19 +555,10 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
       tc_fence_before();
       mbar_arrive(&H->dempty[0]);
     }
-    float* sT = sU;                      // [32][TP]
-    float* sH = sU + 32 * TP;            // [34][HW] halo of the iterate
-    constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
+    if (step && ok)
+      while (qc < nck) q_chunk(32 * qc++);
+    // final pass: g out of tensor memory (transposed through shared memory)
     for (int i0 = 0; i0 < nrow && ok; i0 += 32) {
-      // halo of the iterate for this chunk (OP_STEP), in flight while G is read
-      if (A.mode != OP_PLAIN) {
-        for (int e = tid; e < 34 * HW; e += NT) {
-          const int ir = e / HW, ic = e - ir * HW;
-          const int Rr = wi.r0 + i0 - 1 + ir, Cc = wi.c0 - 1 + ic;
-          const bool in = Rr >= 0 && Rr < td.nxr && Cc >= 0 && Cc < td.nxc;
-          cp_async4(sH + e, in ? A.w + td.xoff + (int64_t)Rr * td.xpitch + Cc : A.w, in);
-        }
-      }
       uint32_t gv[16];
       if (np > 0) {
         tmem_ld16_nowait(tbase + lanes + (uint32_t)(G::NR + i0 + 16 * hf), gv);
@@ -528,44 +569,32 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
       }
 #pragma unroll
       for (int t = 0; t < 16; ++t) sT[(16 * hf + t) * TP + j] = __uint_as_float(gv[t]);
-      if (A.mode == OP_PLAIN) {
-        sync_stage();
+      sync_stage();
+      if (!step) {
         for (int e = tid; e < 32 * MC; e += NT) {
           const int il = e / MC, jl = e - il * MC;
           const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
           if (i0 + il < nrow && Ro < td.nxr && Co < td.nxc)
             A.out[td.xoff + (int64_t)Ro * td.xpitch + Co] = sT[il * TP + jl];
         }
-        sync_stage();
-        continue;
-      }
-      // OP_STEP: grad = g + lambda D^T psi(D w) + alpha (w - u); w_next = max(0, w - tau grad)
-      float uv[PER];
+      } else {
+        float qv[PER];
 #pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
-        const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
-        uv[u] = (i0 + il < nrow && Ro < td.nxr && Co < td.nxc)
-                    ? __ldg(A.u + td.xoff + (int64_t)Ro * td.xpitch + Co)
-                    : 0.f;
-      }
-      cp_async_wait_all();
-      sync_stage();
+        for (int u = 0; u < PER; ++u) {
+          const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
+          const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
+          qv[u] = (i0 + il < nrow && Ro < td.nxr && Co < td.nxc)
+                      ? A.out[td.xoff + (int64_t)Ro * td.xpitch + Co]
+                      : 0.f;
+        }
 #pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
-        const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
-        if (i0 + il >= nrow || Ro >= td.nxr || Co >= td.nxc) continue;
-        const int li = il + 1, lj = jl + 1;
-        float pr, pc, pru, pcu, prl, pcl;
-        huber_p(sH, HW, li, lj, Ro, Co, td.nxr, td.nxc, A.delta, pr, pc);
-        huber_p(sH, HW, li - 1, lj, Ro - 1, Co, td.nxr, td.nxc, A.delta, pru, pcu);
-        huber_p(sH, HW, li, lj - 1, Ro, Co - 1, td.nxr, td.nxc, A.delta, prl, pcl);
-        const float hub = pru - pr + pcl - pc;
-        const float wv = sH[li * HW + lj];
-        const float alpha = sOr[i0 + il] * sOc[jl];
-        const float grad = sT[il * TP + jl] + A.lambda * hub + alpha * (wv - uv[u]);
-        A.out[td.xoff + (int64_t)Ro * td.xpitch + Co] = fmaxf(0.f, wv - td.tau * grad);
+        for (int u = 0; u < PER; ++u) {
+          const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
+          const int Ro = wi.r0 + i0 + il, Co = wi.c0 + jl;
+          if (i0 + il < nrow && Ro < td.nxr && Co < td.nxc)
+            A.out[td.xoff + (int64_t)Ro * td.xpitch + Co] =
+                fmaxf(0.f, qv[u] - td.tau * sT[il * TP + jl]);
+        }
       }
       sync_stage();
     }
