@@ -60,6 +60,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(values, world, device="cuda"):
+    """Element-wise maximum of per-rank timings over all ranks (every rank gets
+    the result); identity when world == 1."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def aggregate_rate(pixels_per_rank, world, seconds):
+    """Whole-job Mpixel/s: every rank solves its own image of pixels_per_rank
+    observed pixels; seconds is the slowest rank's time per step."""
+    return pixels_per_rank * world / seconds / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -349,13 +367,10 @@ def run_ours(args):
     ktime = {k: dv.dv_plan_kernel_time(plan.handle, k) for k in (0, 1, 2)}
     dv.dv_plan_set_timing(plan.handle, 0)
     reached = all(o <= target for o in objs)
-    if world > 1:
-        t = torch.tensor([total_ms, ms_plain], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, ms_plain = float(t[0].item()), float(t[1].item())
+    total_ms, ms_plain = max_over_ranks([total_ms, ms_plain], world)
     ms_step = total_ms / args.steps
-    value = w.hy * w.wy * world / (ms_step * 1e-3) / 1e6
-    plain_value = w.hy * w.wy * world / (ms_plain * 1e-3) / 1e6
+    value = aggregate_rate(w.hy * w.wy, world, ms_step * 1e-3)
+    plain_value = aggregate_rate(w.hy * w.wy, world, ms_plain * 1e-3)
 
     # end to end: host buffers through dv_consensus_solve_host (H2D + solve + D2H)
     yh = torch.empty((w.hy, w.wy), dtype=torch.float32, pin_memory=True)
@@ -368,11 +383,8 @@ def run_ours(args):
     for _ in range(args.e2e_steps):
         dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream)
     t_e2e = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": w.hy * w.wy * world / t_e2e / 1e6, "unit": UNIT,
+    t_e2e = max_over_ranks([t_e2e], world)[0]
+    e2e = {"value": aggregate_rate(w.hy * w.wy, world, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1]}
 
     # roofline of the dominant kernel, live event timing
