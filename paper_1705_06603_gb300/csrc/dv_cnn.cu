@@ -7,6 +7,9 @@
 //   - backward data (the forward kernel on flipped, transposed weights, with
 //     the ReLU mask of the layer input fused in), backward weights (per-tile
 //     partial sums reduced in a fixed order), mean-squared-error loss, Adam.
+// Inference (the solve's warm start and dv_cnn_forward) runs the same layers
+// as implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32
+// accumulators in tensor memory).
 // Architecture: 5 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, ReLU between
 // layers, none after the last.  The first layer's 5 input channels are padded
 // to 8 with zeros.
@@ -18,6 +21,7 @@
 #include <random>
 
 #include "dv_internal.cuh"
+#include "dv_tcgen05.cuh"
 
 namespace dv {
 namespace {
@@ -285,6 +289,166 @@ __global__ void apply_warm_kernel(const float* __restrict__ f, const float* __re
   if (i < n) x0[i] = fmaxf(0.f, f[i * DV_CNN_IN_CH] + d[i]);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core 3x3 convolution (inference).  A CTA owns 4 image rows x 128
+// pixels; per output row r, tap (dy, dx) and 16-channel k-step, one
+// tcgen05.mma (M = 128 pixels, N = NP output channels, K = 16 channels):
+//   A = staged input pixels of row r + dy starting at column dx, K-major, no
+//       swizzle: the 6 x 130 staged pixels of each 8-channel chunk form a
+//       panel with pixels 16 bytes apart, so (r + dy, dx) is a start offset;
+//   B = the layer's weights of that tap and k-step, NP rows x 16 channels,
+//       resident in shared memory for the whole CTA.
+// Accumulator row r lives in tensor-memory columns [r NP, r NP + NP); lane =
+// pixel.  Thread 0 issues the MMAs; the 4 warps stage and run the epilogue
+// (bias, ReLU, BF16 or FP32 NHWC store).
+constexpr int TCR = 4;              // output rows per CTA
+constexpr int TCW = 128;            // output pixels per row (MMA M)
+constexpr int TCSP = (TCR + 2) * (TCW + 2);   // staged pixels
+constexpr int TCTH = 128;
+
+template <int CINP, int NP>
+struct ConvTC {
+  static constexpr int NPAN = CINP / 8;                 // 8-channel panels of A
+  static constexpr int APANEL = TCSP * 16 + 16;
+  static constexpr int KS = CINP / 16;                  // k-steps per tap
+  static constexpr int BSTEP = 2 * NP * 16;             // bytes of B per (tap, k-step)
+  static constexpr int BBYTES = 9 * KS * BSTEP;
+  // padded so that at most 4 CTAs (128 tensor-memory columns at most each)
+  // share an SM and tcgen05.alloc never waits
+  static constexpr int SMEM0 = 64 + NPAN * APANEL + BBYTES + NP * 4;
+  static constexpr int SMEM = SMEM0 > 58 * 1024 ? SMEM0 : 58 * 1024;
+  static constexpr int TMEM = TCR * NP <= 32 ? 32 : (TCR * NP <= 64 ? 64 : 128);
+};
+
+// B images of one layer: [tap][k-step][panel][o < NP][8 channels] BF16 from
+// the BF16-rounded forward weights wf[tap][i < cin_p][o < cout] (zero beyond).
+__global__ void pack_tc_kernel(const float* __restrict__ wf, int cin_p, int cout, int cinp_tc, int np,
+                               bf16* __restrict__ out) {
+  const int ks_n = cinp_tc / 16;
+  const int n = 9 * ks_n * 2 * np * 8;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int ch = e % 8, o = (e / 8) % np, pn = (e / (8 * np)) % 2, ks = (e / (16 * np)) % ks_n,
+            tap = e / (16 * np * ks_n);
+  const int i = 16 * ks + 8 * pn + ch;
+  out[e] = __float2bfloat16_rn(i < cin_p && o < cout ? wf[(tap * cin_p + i) * cout + o] : 0.f);
+}
+
+template <int CINP, int NP, int COUT, bool RELU, bool OUTF32>
+__global__ void __launch_bounds__(TCTH) tconv_kernel(const bf16* __restrict__ in, int cin,
+                                                     const bf16* __restrict__ wtc,
+                                                     const float* __restrict__ bias,
+                                                     void* __restrict__ out, int H, int W,
+                                                     int* err) {
+  using G = ConvTC<CINP, NP>;
+  using namespace tcg;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tsm);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tsm + 8);
+  int* abort_flag = reinterpret_cast<int*>(tsm + 16);
+  unsigned char* sA = tsm + 64;
+  unsigned char* sB = sA + G::NPAN * G::APANEL;
+  float* sBias = reinterpret_cast<float*>(sB + G::BBYTES);
+  const int n = blockIdx.z, y0 = blockIdx.y * TCR, x0 = blockIdx.x * TCW;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, G::TMEM);
+  // weights and bias
+  for (int e = tid; e < G::BBYTES / 16; e += TCTH)
+    reinterpret_cast<uint4*>(sB)[e] = reinterpret_cast<const uint4*>(wtc)[e];
+  for (int e = tid; e < NP; e += TCTH) sBias[e] = e < COUT ? bias[e] : 0.f;
+  // input pixels (rows y0 - 1 .. y0 + TCR, columns x0 - 1 .. x0 + TCW), 8 channels per panel
+  for (int e = tid; e < TCSP * G::NPAN; e += TCTH) {
+    const int p = e / G::NPAN, q = e - p * G::NPAN;
+    const int yy = y0 - 1 + p / (TCW + 2), xx = x0 - 1 + p % (TCW + 2);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (yy >= 0 && yy < H && xx >= 0 && xx < W && 8 * q < cin)
+      v = *reinterpret_cast<const uint4*>(in + (((int64_t)n * H + yy) * W + xx) * cin + 8 * q);
+    *reinterpret_cast<uint4*>(sA + (size_t)q * G::APANEL + p * 16) = v;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  if (tid == 0) {
+    const uint32_t id = idesc(1, TCW, NP);
+    const uint64_t a0 = sdesc(saddr(sA), G::APANEL);
+    const uint64_t b0 = sdesc(saddr(sB), NP * 16);
+    for (int r = 0; r < TCR; ++r) {
+      bool first = true;
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap - 3 * dy;
+#pragma unroll
+        for (int ks = 0; ks < G::KS; ++ks) {
+          const uint64_t ad = a0 + (uint64_t)(2 * ks * (G::APANEL >> 4) + (r + dy) * (TCW + 2) + dx);
+          const uint64_t bd = b0 + (uint64_t)((tap * G::KS + ks) * (G::BSTEP >> 4));
+          mma_bf16(tbase + (uint32_t)(r * NP), ad, bd, id, first ? 0u : 1u);
+          first = false;
+        }
+      }
+    }
+    tc_commit(bar);
+  }
+  __syncwarp();
+  const bool ok = wait_bar(bar, 0, abort_flag, err);
+  tc_fence_after();
+  const int xx = x0 + 32 * warp + lane;
+  const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+  for (int r = 0; r < TCR && ok; ++r) {
+    float v[NP];
+    if constexpr (NP == 32) {
+      float t[32];
+      tmem_ld32(tbase + lanes + (uint32_t)(r * NP), t);
+#pragma unroll
+      for (int o = 0; o < 32; ++o) v[o] = t[o];
+    } else {
+      uint32_t t[16];
+      tmem_ld16_nowait(tbase + lanes + (uint32_t)(r * NP), t);
+      tmem_wait_ld();
+#pragma unroll
+      for (int o = 0; o < 16; ++o) v[o] = __uint_as_float(t[o]);
+    }
+    const int yy = y0 + r;
+    if (yy >= H || xx >= W) continue;
+    const int64_t pix = ((int64_t)n * H + yy) * W + xx;
+    if constexpr (OUTF32) {
+      float* o = reinterpret_cast<float*>(out) + pix * COUT;
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) o[c] = RELU ? fmaxf(v[c] + sBias[c], 0.f) : v[c] + sBias[c];
+    } else {
+      static_assert(COUT % 8 == 0, "BF16 output in 16-byte groups");
+      uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(out) + pix * COUT);
+#pragma unroll
+      for (int g = 0; g < COUT / 8; ++g) {
+        uint32_t wv[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          float a = v[8 * g + 2 * h] + sBias[8 * g + 2 * h];
+          float b = v[8 * g + 2 * h + 1] + sBias[8 * g + 2 * h + 1];
+          if (RELU) {
+            a = fmaxf(a, 0.f);
+            b = fmaxf(b, 0.f);
+          }
+          const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
+          wv[h] = *reinterpret_cast<const uint32_t*>(&hb);
+        }
+        o[g] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_free(tbase, G::TMEM);
+  }
+}
+
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
@@ -299,6 +463,8 @@ struct dv_cnn {
   float* d_v = nullptr;
   float* d_wf[dv::NLAYER] = {};  // bfloat16-rounded compute weights
   float* d_wt[dv::NLAYER] = {};
+  dv::bf16* d_wtc[dv::NLAYER] = {};   // tensor-core B images (inference)
+  int* d_err = nullptr;               // bounded-wait error word of the tensor-core kernels
   int64_t step = 0;
   // activation buffers (grown on demand)
   int64_t cap_pix = 0;
@@ -381,14 +547,55 @@ dv_status ensure_capacity(dv_cnn* c, int64_t npix, int64_t nblk) {
   return DV_OK;
 }
 
+__host__ __device__ constexpr int tc_cinp(int l) { return l == 0 ? 16 : WID; }
+__host__ __device__ constexpr int tc_np(int l) { return l == NLAYER - 1 ? 16 : WID; }
+
 dv_status pack(dv_cnn* c, cudaStream_t s) {
   for (int l = 0; l < NLAYER; ++l) {
     const int n = 9 * layer_cin(l) * layer_cout(l);
     pack_kernel<<<cdiv(n, NB), NB, 0, s>>>(c->d_p + c->off_w[l], layer_cin_logical(l), layer_cin(l),
                                            layer_cout(l), c->d_wf[l], c->d_wt[l]);
     DV_TRY_CUDA(cudaGetLastError());
+    const int nt = 9 * tc_cinp(l) * tc_np(l);
+    pack_tc_kernel<<<cdiv(nt, NB), NB, 0, s>>>(c->d_wf[l], layer_cin(l), layer_cout(l), tc_cinp(l),
+                                               tc_np(l), c->d_wtc[l]);
+    DV_TRY_CUDA(cudaGetLastError());
   }
   c->packed = true;
+  return DV_OK;
+}
+
+template <int CINP, int NP, int COUT, bool RELU, bool OUTF32>
+cudaError_t tconv_launch(const bf16* in, int cin, const bf16* wtc, const float* b, void* out, int N,
+                         int H, int W, int* err, cudaStream_t s) {
+  using G = ConvTC<CINP, NP>;
+  cudaError_t e = cudaFuncSetAttribute(tconv_kernel<CINP, NP, COUT, RELU, OUTF32>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(cdiv(W, TCW), cdiv(H, TCR), N);
+  tconv_kernel<CINP, NP, COUT, RELU, OUTF32><<<grid, TCTH, G::SMEM, s>>>(in, cin, wtc, b, out, H, W, err);
+  return cudaGetLastError();
+}
+
+// Inference pass on tensor cores (same layers; activations in the training
+// buffers, not kept consistent with the backward pass).
+dv_status forward_tc(dv_cnn* c, const float* in, int N, int H, int W, float* out, int* err,
+                     cudaStream_t s) {
+  const int64_t npix = (int64_t)N * H * W;
+  DV_TRY(ensure_capacity(c, npix, (int64_t)N * cdiv(H, TS) * cdiv(W, TS)));
+  if (!c->packed) DV_TRY(pack(c, s));
+  input_kernel<<<cdiv(npix * CIN0, NB), NB, 0, s>>>(in, npix, c->d_act[0]);
+  DV_TRY_CUDA(cudaGetLastError());
+  DV_TRY_CUDA((tconv_launch<16, WID, WID, true, false>(c->d_act[0], CIN0, c->d_wtc[0],
+                                                      c->d_p + c->off_b[0], c->d_act[1], N, H, W,
+                                                      err, s)));
+  for (int l = 1; l < NLAYER - 1; ++l)
+    DV_TRY_CUDA((tconv_launch<WID, WID, WID, true, false>(c->d_act[l], WID, c->d_wtc[l],
+                                                         c->d_p + c->off_b[l], c->d_act[l + 1], N,
+                                                         H, W, err, s)));
+  DV_TRY_CUDA((tconv_launch<WID, 16, 1, false, true>(c->d_act[NLAYER - 1], WID, c->d_wtc[NLAYER - 1],
+                                                    c->d_p + c->off_b[NLAYER - 1],
+                                                    out ? out : c->d_out, N, H, W, err, s)));
   return DV_OK;
 }
 
@@ -473,7 +680,8 @@ dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0) {
   for (int r0 = 0; r0 < nxr; r0 += strip) {
     const int r1 = std::min(nxr, r0 + strip);
     const int a = std::max(0, r0 - NLAYER), b = std::min(nxr, r1 + NLAYER);
-    DV_TRY(forward(c, P->d_feat + (int64_t)a * nxc * DV_CNN_IN_CH, 1, b - a, nxc, nullptr, s));
+    DV_TRY(forward_tc(c, P->d_feat + (int64_t)a * nxc * DV_CNN_IN_CH, 1, b - a, nxc, nullptr,
+                      P->d_err, s));
     DV_TRY_CUDA(cudaMemcpyAsync(P->d_wsd + (int64_t)r0 * nxc, c->d_out + (int64_t)(r0 - a) * nxc,
                                 (size_t)(r1 - r0) * nxc * sizeof(float), cudaMemcpyDeviceToDevice, s));
   }
@@ -521,8 +729,10 @@ void free_cnn(dv_cnn* c) {
   for (int l = 0; l < NLAYER; ++l) {
     if (c->d_wf[l]) cudaFree(c->d_wf[l]);
     if (c->d_wt[l]) cudaFree(c->d_wt[l]);
+    if (c->d_wtc[l]) cudaFree(c->d_wtc[l]);
     if (c->d_act[l]) cudaFree(c->d_act[l]);
   }
+  if (c->d_err) cudaFree(c->d_err);
   if (c->d_lpart) cudaFree(c->d_lpart);
   if (c->d_loss) cudaFree(c->d_loss);
   if (c->h_loss) cudaFreeHost(c->h_loss);
@@ -567,10 +777,15 @@ extern "C" dv_status dv_cnn_create(int32_t width, int32_t depth, uint64_t seed, 
       return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
   for (int l = 0; l < NLAYER; ++l) {
     const size_t n = (size_t)9 * layer_cin(l) * layer_cout(l);
+    const size_t nt = (size_t)9 * tc_cinp(l) * tc_np(l);
     if ((e = cudaMalloc(&c->d_wf[l], n * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_wt[l], n * sizeof(float))) != cudaSuccess)
+        (e = cudaMalloc(&c->d_wt[l], n * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_wtc[l], nt * sizeof(bf16))) != cudaSuccess)
       return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
   }
+  if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) != cudaSuccess)
+    return cleanup(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
   if ((e = cudaMalloc(&c->d_lpart, 1024 * sizeof(double))) != cudaSuccess ||
       (e = cudaMalloc(&c->d_loss, sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&c->h_loss, sizeof(double))) != cudaSuccess)
@@ -615,7 +830,7 @@ extern "C" dv_status dv_cnn_forward(dv_cnn* c, const float* in_dev, int32_t N, i
   clear_error();
   if (!c || !in_dev || !out_dev) return fail(DV_ERR_INVALID_ARG, "NULL argument");
   DV_TRY(check_shape(N, H, W));
-  return forward(c, in_dev, N, H, W, out_dev, (cudaStream_t)stream);
+  return forward_tc(c, in_dev, N, H, W, out_dev, c->d_err, (cudaStream_t)stream);
 }
 
 extern "C" dv_status dv_cnn_gradients(dv_cnn* c, const float* in_dev, const float* target_dev,
