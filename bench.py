@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--ws-pairs", type=int, default=24,
                     help="warm-start training pairs made by the plain method")
     ap.add_argument("--ws-steps", type=int, default=2000, help="warm-start Adam steps")
+    ap.add_argument("--check-every", type=int, default=2,
+                    help="outer iterations between objective checks of the chosen form")
+    ap.add_argument("--inner", type=int, default=0,
+                    help="projected-gradient steps per outer iteration of the chosen form "
+                         "(0: the workload's count)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
                          "short, fixed launch sequence for ncu captures); prints nothing")
@@ -338,8 +343,10 @@ def run_ours(args):
                                       steps=args.ws_steps)
     target = f_star * (1.0 + 1e-4)
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
-    plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=2 * w.n_outer, use_warmstart=1,
-                   check_every=2, target_objective=target, precision=prec, **common)
+    chosen = dict(common, n_inner=args.inner) if args.inner > 0 else common
+    plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=4 * w.n_outer, use_warmstart=1,
+                   check_every=args.check_every, target_objective=target, precision=prec,
+                   **chosen)
     dv.dv_plan_set_warmstart(plan.handle, net)
     st = dv.dv_stats()
     for i in range(args.warmup):
@@ -501,11 +508,14 @@ def run_ours(args):
                                    "inner iterations",
                        "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
                                       "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
-                                      "per local solve, learned warm start, stop at F <= "
-                                      "F*(1 + 1e-4) checked every 2 outer iterations; objective "
-                                      "with the FP32 operator"
+                                      "per local solve, learned warm start (%d pairs, %d Adam "
+                                      "steps), %d projected-gradient steps per outer iteration, "
+                                      "stop at F <= F*(1 + 1e-4) checked every %d outer "
+                                      "iterations; objective with the FP32 operator"
                                       % (pname, args.precision, info.tune_ms_direct,
-                                         info.tune_ms_fft, info.tune_ms_tensor),
+                                         info.tune_ms_fft, info.tune_ms_tensor, args.ws_pairs,
+                                         args.ws_steps, args.inner or w.n_inner,
+                                         args.check_every),
                        "plain_form": "FP32 block-FFT at fixed S = 128, one launch per kernel, "
                                      "blurred-image start, 100 x 10 iterations",
                        "plain_value": plain_value, "plain_ms": ms_plain, "f_star": f_star,

@@ -76,6 +76,7 @@ struct GeoT {
   static_assert(SMEM_H <= kSmemMax && SMEM_HT <= kSmemMax, "shared memory");
   static_assert(SBYTES >= 32 * TP * 4 && UBYTES >= 32 * TP * 4 + 34 * HW * 4, "epilogue tiles");
   static_assert(UBYTES >= (COLS + 4) * 4 && SBYTES >= (COLS + 4) * 4, "staging chunk");
+  static_assert(XBYTES >= 4 * 32 * MC * 4, "H epilogue prefetch buffers in the x-window region");
   // 16-byte alignment of every region accessed with 16-byte vectors or bulk copies
   static_assert(SPANEL % 16 == 0 && SBYTES % 16 == 0 && XBYTES % 16 == 0 && APANEL % 16 == 0 &&
                     (COLS * 2) % 16 == 0 && (COLS * 4) % 16 == 0 && (WCOFF * 4) % 16 == 0 &&
@@ -337,16 +338,40 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       mbar_arrive(&H->sfull);
     }
     // epilogue: 32-row chunks of the accumulator, transposed through shared
-    // memory (the S panels are free once every MMA has completed); each
-    // thread's 16 observed values of a chunk are loaded before any is used
+    // memory (the S panels are free once every MMA has completed).  The
+    // observed image (and noise weights) of chunk c + 1 are copied into the
+    // freed x-window region by cp.async while chunk c is written; chunk 0's
+    // copy overlaps the last PSF's MMAs.
+    constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
+    const bool obs = A.mode != OP_PLAIN;
+    float* sYb = reinterpret_cast<float*>(sXb);          // [2][32 * MC] observed image
+    float* sWb = sYb + 2 * 32 * MC;                      // [2][32 * MC] noise weights
+    auto prefetch = [&](int i0, int buf) {
+      if (obs) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
+          const int i = wi.r0 + i0 + il, jj = wi.c0 + jl;
+          const bool in = i0 + il < nrow && i < td.nyr && jj < td.nyc;
+          const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
+          cp_async4(sYb + buf * 32 * MC + e, in ? A.y + gi : A.y, in);
+          if (A.W) cp_async4(sWb + buf * 32 * MC + e, in ? A.W + gi : A.W, in);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (ok && np > 0) prefetch(0, 0);
     if (ok && np > 0) ok = all_stage(wait_bar(&H->dfull[0], 0, &H->abort, A.err));
+    if (ok && np == 0) prefetch(0, 0);
     tc_fence_after();
     sync_stage();
     float* sT = reinterpret_cast<float*>(sS);
     const int j = 32 * (warp & 3) + lane, hf = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     double part = 0.0;
-    for (int i0 = 0; i0 < nrow && ok; i0 += 32) {
+    for (int i0 = 0, c = 0; i0 < nrow && ok; i0 += 32, ++c) {
+      if (i0 + 32 < nrow) prefetch(i0 + 32, (c + 1) & 1);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
       uint32_t v[16];
       if (np > 0) {
         tmem_ld16_nowait(tbase + lanes + (uint32_t)(i0 + 16 * hf), v);
@@ -357,36 +382,30 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       }
 #pragma unroll
       for (int t = 0; t < 16; ++t) sT[(16 * hf + t) * TP + j] = __uint_as_float(v[t]);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");   // chunk c has landed
       sync_stage();
-      constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
-      float yv[PER], wv[PER];
-#pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
-        const int i = wi.r0 + i0 + il, jj = wi.c0 + jl;
-        const bool in = i0 + il < nrow && i < td.nyr && jj < td.nyc;
-        const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
-        yv[u] = (in && A.mode != OP_PLAIN) ? __ldg(A.y + gi) : 0.f;
-        wv[u] = (in && A.mode != OP_PLAIN && A.W) ? __ldg(A.W + gi) : 1.f;
-      }
+      const float* yb = sYb + (c & 1) * 32 * MC;
+      const float* wb = sWb + (c & 1) * 32 * MC;
 #pragma unroll
       for (int u = 0; u < PER; ++u) {
         const int e = tid + u * NT, il = e / MC, jl = e - il * MC;
         const int i = wi.r0 + i0 + il, jj = wi.c0 + jl;
         if (i0 + il >= nrow || i >= td.nyr || jj >= td.nyc) continue;
         const float y = sT[il * TP + jl];
-        if (A.mode == OP_PLAIN) {
+        if (!obs) {
           A.out[td.yoff + (int64_t)i * td.ypitch + jj] = y;
         } else {
-          const float dd = y - yv[u];
+          const float dd = y - yb[e];
+          const float wt = A.W ? wb[e] : 1.f;
           if (A.mode == OP_RESID)
-            A.out[td.yoff + (int64_t)i * td.ypitch + jj] = wv[u] * dd;
+            A.out[td.yoff + (int64_t)i * td.ypitch + jj] = wt * dd;
           else
-            part += (double)wv[u] * (double)dd * (double)dd;
+            part += (double)wt * (double)dd * (double)dd;
         }
       }
       sync_stage();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     if (A.mode == OP_OBJ) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
