@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--ws-pairs", type=int, default=24,
                     help="warm-start training pairs made by the plain method")
     ap.add_argument("--ws-steps", type=int, default=2000, help="warm-start Adam steps")
+    ap.add_argument("--rho", type=float, default=0.0,
+                    help="relaxation of the chosen form's dual update (0: the workload's)")
+    ap.add_argument("--gamma", type=float, default=0.0,
+                    help="proximal weight gamma of the chosen form (0: the workload's)")
     ap.add_argument("--check-every", type=int, default=2,
                     help="outer iterations between objective checks of the chosen form")
     ap.add_argument("--inner", type=int, default=0,
@@ -343,7 +347,13 @@ def run_ours(args):
                                       steps=args.ws_steps)
     target = f_star * (1.0 + 1e-4)
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
-    chosen = dict(common, n_inner=args.inner) if args.inner > 0 else common
+    chosen = dict(common)
+    if args.inner > 0:
+        chosen["n_inner"] = args.inner
+    if args.rho > 0:
+        chosen["rho"] = args.rho
+    if args.gamma > 0:
+        chosen["gamma"] = args.gamma
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=4 * w.n_outer, use_warmstart=1,
                    check_every=args.check_every, target_objective=target, precision=prec,
                    **chosen)
@@ -510,12 +520,13 @@ def run_ours(args):
                                       "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
                                       "per local solve, learned warm start (%d pairs, %d Adam "
                                       "steps), %d projected-gradient steps per outer iteration, "
+                                      "gamma %.3g, rho %.3g, "
                                       "stop at F <= F*(1 + 1e-4) checked every %d outer "
                                       "iterations; objective with the FP32 operator"
                                       % (pname, args.precision, info.tune_ms_direct,
                                          info.tune_ms_fft, info.tune_ms_tensor, args.ws_pairs,
                                          args.ws_steps, args.inner or w.n_inner,
-                                         args.check_every),
+                                         chosen["gamma"], chosen["rho"], args.check_every),
                        "plain_form": "FP32 block-FFT at fixed S = 128, one launch per kernel, "
                                      "blurred-image start, 100 x 10 iterations",
                        "plain_value": plain_value, "plain_ms": ms_plain, "f_star": f_star,
