@@ -1,10 +1,17 @@
 """Benchmark of the consensus deblurring hot path (Algorithm 1 on the GPU).
 
-One step = one dv_consensus_solve of the 2048x2048 star-field workload
-(8x8 grid of 31x31 Moffat PSFs, 4x4 tiles overlapping by 64 px, 100 consensus
-iterations x 10 projected-gradient steps): start, all local solves, consensus
-and dual updates, assembly of x_hat.  Inputs are resident in HBM when the timed
-region starts; L2 is flushed (256 MB write) before every timed step.
+Workload: the 2048x2048 star field (8x8 grid of 31x31 Moffat PSFs, 4x4 tiles
+overlapping by 64 px).  The plain form (FP32 block-FFT operator, one launch per
+kernel, blurred-image start, 100 consensus iterations x 10 projected-gradient
+steps) sets the target objective F*.  One step = one dv_consensus_solve of the
+chosen form (autotuned operator with BF16 operands allowed, CUDA graph per
+local solve, learned warm start, 3 projected-gradient steps per outer
+iteration, gamma 0.2, rho 1.8) until F <= F*(1 + 1e-4): start, local solves,
+consensus and dual updates, objective checks, assembly of x_hat.  Inputs are
+resident in HBM when the timed region starts; L2 is flushed (256 MB write)
+before every timed step.  The Douglas-Rachford fixed point does not depend on
+gamma, rho or the inner step count, so the chosen form reaches the same
+minimiser as the plain form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,14 +57,14 @@ def parse():
                          "(the autotuner picks the fastest allowed path)")
     ap.add_argument("--ws-pairs", type=int, default=24,
                     help="warm-start training pairs made by the plain method")
-    ap.add_argument("--ws-steps", type=int, default=2000, help="warm-start Adam steps")
-    ap.add_argument("--rho", type=float, default=0.0,
+    ap.add_argument("--ws-steps", type=int, default=24000, help="warm-start Adam steps")
+    ap.add_argument("--rho", type=float, default=1.8,
                     help="relaxation of the chosen form's dual update (0: the workload's)")
-    ap.add_argument("--gamma", type=float, default=0.0,
+    ap.add_argument("--gamma", type=float, default=0.2,
                     help="proximal weight gamma of the chosen form (0: the workload's)")
-    ap.add_argument("--check-every", type=int, default=2,
+    ap.add_argument("--check-every", type=int, default=4,
                     help="outer iterations between objective checks of the chosen form")
-    ap.add_argument("--inner", type=int, default=0,
+    ap.add_argument("--inner", type=int, default=3,
                     help="projected-gradient steps per outer iteration of the chosen form "
                          "(0: the workload's count)")
     ap.add_argument("--profile-case", action="store_true",
@@ -452,7 +459,7 @@ def run_ours(args):
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
                f"{px} pixels; executed MMA work {executed / 1e9:.1f} GFLOP per launch "
                f"({info.block_psfs[dom]} block-PSF pairs x K x {ks * km} Toeplitz columns x "
-               f"2 x 128 x 64)")
+               f"2 x 128 x {'block rows' if args.precision == 'bf16' else '64'})")
     elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
         # per 128 x 128 complex 2-D transform (N = 16384) and 8 flop per spectral
