@@ -438,18 +438,23 @@ def run_ours(args):
         # active PSFs (first-order interpolation); the tensor pipe also runs
         # the zero band of the Toeplitz operand and the ragged block tails
         flops = 8.0 * w.K * w.K * px
-        # executed MMA work: per (block, PSF) pair and tap row, KS k-steps of
+        # executed MMA work: per (block, PSF) pair and tap row, k-steps of
         # 128 x N x KM; BF16 column-band blocks: N = the block's rows (up to
-        # 256), K-extent 127 + K; TF32 row-band blocks: 128 x 64, K-extent 63 + K
+        # 256), at most ceil((127 + K) / 16) k-steps, those where the PSF's
+        # column weight vanishes skipped (the plan reports the sum);
+        # TF32 row-band blocks: 128 x 64, ceil((63 + K) / 8) k-steps
         if args.precision == "bf16":
-            km, band = 16, 127 + w.K
-            ks = (band + km - 1) // km
+            km = 16
             mean_rows = (y_px if dom == 0 else x_px) / max(info.blocks[dom], 1) / 128.0
-            executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 16 * np.ceil(mean_rows / 16)
+            executed = info.mma_ksteps[dom] * w.K * km * 2.0 * 128 * 16 * np.ceil(mean_rows / 16)
+            work_note = (f"{info.mma_ksteps[dom]} (block, PSF) k-steps per tap row x K x 16 x "
+                         f"2 x 128 x block rows")
         else:
             km, band = 8, 63 + w.K
             ks = (band + km - 1) // km
             executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 64
+            work_note = (f"{info.block_psfs[dom]} block-PSF pairs x K x {ks * km} Toeplitz "
+                         f"columns x 2 x 128 x 64")
         sus = float(peaks.get("bf16_tflops_sustained", 1700.0))
         peak = sus if args.precision == "bf16" else sus * 1.1 / 2.25
         bound, unit = "tensor", "TFLOP/s"
@@ -458,8 +463,7 @@ def run_ours(args):
                     "measured sustained cuBLAS BF16 x nominal TF32/BF16 ratio 1.1/2.25")
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
                f"{px} pixels; executed MMA work {executed / 1e9:.1f} GFLOP per launch "
-               f"({info.block_psfs[dom]} block-PSF pairs x K x {ks * km} Toeplitz columns x "
-               f"2 x 128 x {'block rows' if args.precision == 'bf16' else '64'})")
+               f"({work_note})")
     elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
         # per 128 x 128 complex 2-D transform (N = 16384) and 8 flop per spectral

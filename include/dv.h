@@ -246,6 +246,12 @@ typedef struct dv_plan_info {
   int32_t block_side;      /* output block rows: 64 (direct), 128 - K + 1 (FFT), 128 (tensor) */
   int32_t fp32_path;       /* FP32 operator of objective evaluations: DV_PATH_DIRECT or _FFT */
   double tune_ms_tensor;   /* autotuner: tensor-core path (0 if not timed / not available) */
+  /* BF16 tensor-core path: k-steps per PSF tap row one tile-mode launch of H
+   * [0] and H^T [1] issues, summed over (block, PSF) pairs -- each k-step is
+   * one 128 x rows x 16 MMA per tap row, so K times this is the MMA count.
+   * Steps where a PSF's column weight is zero on the whole step are skipped.
+   * 0 on the other paths. */
+  int64_t mma_ksteps[2];
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

@@ -80,6 +80,10 @@ enum OpMode : int32_t {
   OP_STEP = 3     // H^T: fused projected-gradient step into w_next
 };
 
+// BF16 tensor-core path: PSF grid columns per work item with a k-step range
+// of their own (further columns run every k-step)
+constexpr int kTcMaxB = 16;
+
 struct OpArgs {
   const TileDesc* tiles;
   const WorkItem* work;
@@ -112,6 +116,7 @@ struct OpArgs {
   int32_t prec;           // tensor-core path: DV_PREC_BF16 or DV_PREC_TF32
   int32_t pad3;
   int* err;               // tensor-core path: nonzero after a bounded wait gave up
+  const uint16_t* ksr;    // BF16 tensor-core path: [n_work][kTcMaxB] k-step ranges (lo | hi << 8)
 };
 
 // One item of the consensus / assembly kernels: a rectangle of the global x
@@ -200,6 +205,11 @@ int tcT_block_cols();
 int tcT_max_rows(int K);
 cudaError_t tcT_prepare(int K);
 void tcT_operands(const float* psfs, int G, int K, bool flip, std::vector<uint8_t>& out);
+// k-step ranges of the items of one work table (kTcMaxB entries per item,
+// lo | hi << 8); returns the k-steps per tap row summed over (item, PSF)
+int64_t tcT_kstep_ranges(const std::vector<TileDesc>& tiles, const std::vector<WorkItem>& items,
+                         const std::vector<WTab>& wcol, int K, bool adjoint,
+                         std::vector<uint16_t>& out);
 cudaError_t launch_tcT_H(const OpArgs& a, cudaStream_t s);
 cudaError_t launch_tcT_Ht(const OpArgs& a, cudaStream_t s);
 
@@ -246,6 +256,13 @@ struct OpTables {
   WorkItem* Hg = nullptr;
   WorkItem* Htg = nullptr;
   int nH = 0, nHt = 0, nHg = 0, nHtg = 0;
+  // BF16 tensor-core path: per-item k-step ranges and the k-steps one
+  // tile-mode launch runs per tap row, summed over (block, PSF) pairs
+  uint16_t* ksH = nullptr;
+  uint16_t* ksHt = nullptr;
+  uint16_t* ksHg = nullptr;
+  uint16_t* ksHtg = nullptr;
+  int64_t ksteps[2] = {0, 0};
 };
 }  // namespace dv
 

@@ -339,6 +339,7 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
   const OpTables& tb = p->tab[tab_index(path)];
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Hg : tb.H;
+  a.ksr = global ? tb.ksHg : tb.ksH;
   a.n_work = global ? tb.nHg : tb.nH;
   a.mode = mode;
   a.wrow = p->d_wrow;
@@ -371,6 +372,7 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, flo
   const OpTables& tb = p->tab[tab_index(path)];
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Htg : tb.Ht;
+  a.ksr = global ? tb.ksHtg : tb.ksHt;
   a.n_work = global ? tb.nHtg : tb.nHt;
   a.psf = p->d_psf;
   a.counter = p->d_counter ? p->d_counter + 1 : nullptr;
@@ -652,24 +654,36 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
         tb.pairs[k2] += (np + 1) / 2;
       }
     };
+    // BF16 tensor path: per-item k-step ranges of the PSF grid columns
+    std::vector<uint16_t> ks;
+    auto ranges = [&](const std::vector<TileDesc>& tl, bool adj, uint16_t** dst) -> dv_status {
+      if (!band) return DV_OK;
+      const int64_t steps = tcT_kstep_ranges(tl, w, L.wcol, K, adj, ks);
+      if (&tl == &P->h_tiles) tb.ksteps[adj ? 1 : 0] = steps;
+      return upload(P, dst, ks.data(), ks.size(), s);
+    };
     make_work(P->h_tiles, false, K, L, bm, bn, w, max_rows);
     count(w, 0);
     order(w);
     tb.nH = (int)w.size();
     DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
+    DV_TRY(ranges(P->h_tiles, false, &tb.ksH));
     make_work(P->h_tiles, true, K, L, bm, bn, w, max_rows);
     count(w, 1);
     order(w);
     tb.nHt = (int)w.size();
     DV_TRY(upload(P, &tb.Ht, w.data(), w.size(), s));
+    DV_TRY(ranges(P->h_tiles, true, &tb.ksHt));
     make_work(gtiles, false, K, L, bm, bn, w, max_rows);
     order(w);
     tb.nHg = (int)w.size();
     DV_TRY(upload(P, &tb.Hg, w.data(), w.size(), s));
+    DV_TRY(ranges(gtiles, false, &tb.ksHg));
     make_work(gtiles, true, K, L, bm, bn, w, max_rows);
     order(w);
     tb.nHtg = (int)w.size();
     DV_TRY(upload(P, &tb.Htg, w.data(), w.size(), s));
+    DV_TRY(ranges(gtiles, true, &tb.ksHtg));
   }
   if (P->tensor_ok) {
     std::vector<uint8_t> op;
@@ -806,6 +820,7 @@ dv_status release(dv_plan* P) {
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
                   P->tab[2].H, P->tab[2].Ht, P->tab[2].Hg, P->tab[2].Htg,
+                  P->tab[2].ksH, P->tab[2].ksHt, P->tab[2].ksHg, P->tab[2].ksHtg,
                   P->d_tcopH, P->d_tcopHt, P->d_err,
                   P->d_rowcov, P->d_colcov, P->d_citems, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
@@ -848,6 +863,8 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->block_psfs[1] = P->tab[k].psfs[1];
   info->psf_pairs[0] = P->tab[k].pairs[0];
   info->psf_pairs[1] = P->tab[k].pairs[1];
+  info->mma_ksteps[0] = P->tab[k].ksteps[0];
+  info->mma_ksteps[1] = P->tab[k].ksteps[1];
   info->block_side = k == 1 ? fft_block(P->K)
                             : (k == 2 ? (P->prob.precision == DV_PREC_BF16 ? tcT_max_rows(P->K)
                                                                           : tc_block_m())

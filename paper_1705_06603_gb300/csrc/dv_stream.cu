@@ -72,7 +72,7 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
                                                const float* __restrict__ x, float* __restrict__ u,
                                                float gamma, float rho, float* __restrict__ zg,
                                                double& pp, double& dd) {
-  constexpr int GP = 16 / NS;      // pixels per group
+  constexpr int GP = 8 / NS;       // pixels per group
   const int tx = threadIdx.x;
   for (int k0 = 0; k0 < 4 * it.nrow; k0 += GP) {
     float xs[GP][NS], us[GP][NS], as[GP][NS], zp[GP];
@@ -123,7 +123,7 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
   }
 }
 
-__global__ void __launch_bounds__(NBR) consensus_kernel(const GridArgs G, const float* __restrict__ x,
+__global__ void __launch_bounds__(NBR, 8) consensus_kernel(const GridArgs G, const float* __restrict__ x,
                                                         float* __restrict__ u, float gamma, float rho,
                                                         float* __restrict__ zg,
                                                         double* __restrict__ partials) {

@@ -15,8 +15,9 @@
 //   B = rows i + a of S, the same columns: shared memory, K-major, no
 //       swizzle, rows 16 bytes apart in each column panel, so the row shift a
 //       is the start address plus 16 a.
-//   H:   S = bf16(w_p . x) restaged per PSF from a BF16 copy of the x window;
-//        all PSFs accumulate into one accumulator in tensor memory.
+//   H:   S = bf16(w_p . x), built per PSF from x in global memory (L2) into
+//        one of two S buffers while the MMAs of the previous PSF read the
+//        other; all PSFs accumulate into one accumulator in tensor memory.
 //   H^T: S = bf16(r) staged once; PSF p accumulates into D, and the epilogue
 //        warps add w_p . D into a second tensor-memory region G; the
 //        projected-gradient step is fused into the write-out.
@@ -26,6 +27,7 @@
 // one of its lanes issues the MMAs, one lane of warp 9 refills the ring.
 // Every wait is bounded (see dv_tcgen05.cuh).
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 #include "dv_internal.cuh"
@@ -45,7 +47,7 @@ constexpr int NST = 4;                    // ring stages (one tap row each)
 constexpr int TP = MC + 1;                // fp32 transposition tile pitch (floats)
 constexpr int HW = MC + 2;                // halo tile pitch (floats)
 constexpr int kHdr = 512;
-constexpr int kMaxArows = 4;              // H^T: PSF grid rows whose row weights are staged
+constexpr int kMaxB = kTcMaxB;            // PSF grid columns with a k-step range of their own
 constexpr int kSmemMax = 227 * 1024;
 
 template <int K>
@@ -57,7 +59,6 @@ struct GeoT {
   static constexpr int ROWS = NR + K - 1;                 // staged input rows
   static constexpr int SPANEL = ROWS * 16 + 16;
   static constexpr int SBYTES = NCH * SPANEL;
-  static constexpr int XBYTES = ROWS * COLS * 2;          // H: BF16 x window, row-major
   static constexpr int RA = MC + KM * (KS - 1);           // rows of the tall Toeplitz operand
   static constexpr int APANEL = RA * 16;
   static constexpr int ABYTES = 2 * APANEL;               // one ring stage
@@ -66,9 +67,9 @@ struct GeoT {
   static constexpr int WTX = 2 * WR * 16;                 // bytes streamed per tap row
   static constexpr int UBYTES = 64 * 1024;                // H^T: fp32 staging / epilogue tiles
   static constexpr int WCOFF = (ROWS + 3) / 4 * 4;        // H: sWc after sWr, 16-byte aligned
-  static constexpr int SMEM_H = kHdr + SBYTES + XBYTES + NST * ABYTES + (WCOFF + COLS) * 4;
-  // H^T: [... | row weights [kMaxArows][NR] | omega rows [NR] | omega columns [MC]]
-  static constexpr int SMEM_HT = kHdr + SBYTES + UBYTES + NST * ABYTES + kMaxArows * NR * 4 +
+  static constexpr int SMEM_H = kHdr + 2 * SBYTES + NST * ABYTES + (WCOFF + COLS) * 4;
+  // H^T: [... | row weights of two PSF grid rows [2][NR] | omega rows [NR] | omega columns [MC]]
+  static constexpr int SMEM_HT = kHdr + SBYTES + UBYTES + NST * ABYTES + 2 * NR * 4 +
                                  (NR + MC) * 4;
   static constexpr int TMEM_H = NR;
   static constexpr int TMEM_HT = 2 * NR;                  // accumulator D and sum G
@@ -76,9 +77,9 @@ struct GeoT {
   static_assert(SMEM_H <= kSmemMax && SMEM_HT <= kSmemMax, "shared memory");
   static_assert(SBYTES >= 32 * TP * 4 && UBYTES >= 32 * TP * 4 + 34 * HW * 4, "epilogue tiles");
   static_assert(UBYTES >= (COLS + 4) * 4 && SBYTES >= (COLS + 4) * 4, "staging chunk");
-  static_assert(XBYTES >= 4 * 32 * MC * 4, "H epilogue prefetch buffers in the x-window region");
+  static_assert(SBYTES >= 4 * 32 * MC * 4, "H epilogue prefetch buffers in a free S buffer");
   // 16-byte alignment of every region accessed with 16-byte vectors or bulk copies
-  static_assert(SPANEL % 16 == 0 && SBYTES % 16 == 0 && XBYTES % 16 == 0 && APANEL % 16 == 0 &&
+  static_assert(SPANEL % 16 == 0 && SBYTES % 16 == 0 && APANEL % 16 == 0 &&
                     (COLS * 2) % 16 == 0 && (COLS * 4) % 16 == 0 && (WCOFF * 4) % 16 == 0 &&
                     (S0 * 16) % 16 == 0 && UBYTES % 16 == 0 && kHdr % 16 == 0,
                 "alignment");
@@ -86,11 +87,12 @@ struct GeoT {
 
 struct Bars {
   uint64_t rfull[NST], rempty[NST];
-  uint64_t sfull, sempty;     // S panels staged / consumed (H: per PSF)
+  uint64_t sfull[2], sempty[2];  // S buffer staged / consumed (H: per PSF, H^T: buffer 0 once)
   uint64_t dfull[2], dempty[2];  // accumulator buffer complete / read (H: buffer 0 only)
   uint64_t fin;
   uint32_t tmem;
   int abort;
+  int ksr[kMaxB];             // k-step range of PSF grid column b_lo + b: lo | hi << 8
 };
 static_assert(sizeof(Bars) <= kHdr, "barrier header");
 
@@ -102,8 +104,10 @@ __device__ __forceinline__ void init_bars(Bars* H) {
     mbar_init(&H->rfull[s], 1);
     mbar_init(&H->rempty[s], 1);
   }
-  mbar_init(&H->sfull, NT);
-  mbar_init(&H->sempty, 1);
+  for (int b = 0; b < 2; ++b) {
+    mbar_init(&H->sfull[b], NT);
+    mbar_init(&H->sempty[b], 1);
+  }
   for (int b = 0; b < 2; ++b) {
     mbar_init(&H->dfull[b], 1);
     mbar_init(&H->dempty[b], NT);
@@ -138,42 +142,75 @@ __device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned 
     if (!drain_bar(&H->rfull[it % NST], (uint32_t)((it / NST) & 1), A.err)) break;
 }
 
+// K-step ranges of the block's PSF grid columns (computed on the host by
+// tcT_kstep_ranges), copied into the barrier header by warp NWE.
+__device__ __forceinline__ void load_ranges(const OpArgs& A, Bars* H, int lane) {
+  if (lane < kMaxB) H->ksr[lane] = A.ksr[(size_t)blockIdx.x * kMaxB + lane];
+  __syncwarp();
+}
+
+// One tap row: N k-steps from the start descriptors, as a straight run of
+// MMAs with constant descriptor offsets (a runtime loop or a branch per MMA
+// issues noticeably slower than the tensor pipe retires them).
+template <int N, int SB>
+__device__ __forceinline__ void issue_row(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id,
+                                          uint32_t acc) {
+  mma_bf16(d, ad, bd, id, acc);
+#pragma unroll
+  for (int i = 1; i < N; ++i) mma_bf16(d, ad - (uint64_t)(i * KM), bd + (uint64_t)(i * SB), id, 1u);
+}
+
+template <int N, int SB>
+__device__ __forceinline__ void issue_n(int n, uint32_t d, uint64_t ad, uint64_t bd, uint32_t id,
+                                        uint32_t acc) {
+  if (n == N) {
+    issue_row<N, SB>(d, ad, bd, id, acc);
+  } else if constexpr (N > 1) {
+    issue_n<N - 1, SB>(n, d, ad, bd, id, acc);
+  }
+}
+
 // MMA lane.  H (ADJ = false): every PSF accumulates into D once its S is
 // staged, and S is released after its MMAs.  H^T: S is staged once; PSF p
 // overwrites D once the epilogue has folded PSF p - 1 into G.
 template <int K, bool ADJ>
-__device__ void issuer(const OpArgs& A, Bars* H, unsigned char* sS, unsigned char* ring, uint32_t d,
-                       int np, int nrow) {
+__device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned char* sS,
+                       unsigned char* ring, uint32_t d, int np, int nrow) {
   using G = GeoT<K>;
   const uint32_t id = idesc(1, MC, nrow);
   const uint64_t ad0 = sdesc(saddr(ring) + 16u * KM * (G::KS - 1), G::APANEL);
-  const uint64_t bd0 = sdesc(saddr(sS), G::SPANEL);
+  const int nb = wi.b_hi - wi.b_lo + 1;
   int s = 0;
   uint32_t ph = 0;
   bool ok = true;
+  bool fresh = true;   // the next MMA overwrites the accumulator
   for (int p = 0; p < np && ok; ++p) {
     if (ADJ) {
-      ok = p == 0 ? wait_bar(&H->sfull, 0, &H->abort, A.err)
+      ok = p == 0 ? wait_bar(&H->sfull[0], 0, &H->abort, A.err)
                   : wait_bar(&H->dempty[0], (uint32_t)((p - 1) & 1), &H->abort, A.err);
     } else {
-      ok = wait_bar(&H->sfull, (uint32_t)(p & 1), &H->abort, A.err);
+      ok = wait_bar(&H->sfull[p & 1], (uint32_t)((p >> 1) & 1), &H->abort, A.err);
     }
     if (!ok) break;
     tc_fence_after();
     const uint32_t dp = d;
+    const int b = p % nb;
+    const int kr = b < kMaxB ? H->ksr[b] : (G::KS - 1) << 8;
+    const int klo = kr & 0xff, nks = (kr >> 8) - klo + 1;
+    const uint64_t adk = ad0 - (uint64_t)(klo * KM);
+    const uint64_t bdk = sdesc(saddr(sS + (ADJ ? 0 : (p & 1) * G::SBYTES)), G::SPANEL) +
+                         (uint64_t)(2 * klo * (G::SPANEL >> 4));
+    if (ADJ) fresh = true;
     for (int a = 0; a < K; ++a) {
       if (!wait_bar(&H->rfull[s], ph, &H->abort, A.err)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint64_t ad = ad0 + (uint64_t)(s * (G::ABYTES >> 4));
-      const uint64_t bd = bd0 + (uint64_t)a;
-      const bool first = ADJ ? a == 0 : (p == 0 && a == 0);
-      mma_bf16(dp, ad, bd, id, first ? 0u : 1u);
-#pragma unroll
-      for (int ks = 1; ks < G::KS; ++ks)
-        mma_bf16(dp, ad - (uint64_t)(ks * KM), bd + (uint64_t)(2 * ks * (G::SPANEL >> 4)), id, 1u);
+      const uint64_t ad = adk + (uint64_t)(s * (G::ABYTES >> 4));
+      const uint64_t bd = bdk + (uint64_t)a;
+      issue_n<G::KS, 2 * (G::SPANEL >> 4)>(nks, dp, ad, bd, id, fresh ? 0u : 1u);
+      fresh = false;
       tc_commit(&H->rempty[s]);
       if (++s == NST) {
         s = 0;
@@ -181,7 +218,7 @@ __device__ void issuer(const OpArgs& A, Bars* H, unsigned char* sS, unsigned cha
       }
     }
     if (!ok) break;
-    tc_commit(ADJ ? &H->dfull[0] : &H->sempty);
+    tc_commit(ADJ ? &H->dfull[0] : &H->sempty[p & 1]);
   }
   if (!ADJ && ok && np > 0) tc_commit(&H->dfull[0]);
   tc_commit(&H->fin);
@@ -255,15 +292,69 @@ __device__ __forceinline__ void put_s(unsigned char* sS, int ir, int q, const fl
   *reinterpret_cast<uint4*>(sS + (size_t)q * G::SPANEL + ir * 16) = pack_chunk<0>(v);
 }
 
+// H: S = bf16((w_r w_c) x) on window rows [0, ROWS) and the 8-column chunks
+// [qlo, qlo + nq) the PSF's k-steps read, straight from the FP32 x tile
+// (zero outside [0, nr) x [0, nc) and on rows of zero weight).  Loads are
+// issued U items at a time (16-byte loads where the rows are aligned).
+template <int K>
+__device__ __forceinline__ void restage_h(unsigned char* sb, const float* __restrict__ img,
+                                          int64_t pitch, bool al, int r0, int c0, int nr, int nc,
+                                          const float* sWr, const float* sWc, int qlo, int nq,
+                                          int tid) {
+  using G = GeoT<K>;
+  constexpr int U = 4;
+  const int total = G::ROWS * nq;
+  for (int e0 = tid; e0 < total; e0 += U * NT) {
+    float v[U][CH];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+#pragma unroll
+      for (int t = 0; t < CH; ++t) v[u][t] = 0.f;
+      if (e < total) {
+        const int ir = e / nq, q = qlo + (e - ir * nq);
+        const int R = r0 + ir, C = c0 + q * CH;
+        if (R < nr && sWr[ir] != 0.f) {
+          const float* src = img + (int64_t)R * pitch + C;
+          if (al && C + CH <= nc) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(src) + 1);
+            v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+            v[u][4] = b.x; v[u][5] = b.y; v[u][6] = b.z; v[u][7] = b.w;
+          } else {
+#pragma unroll
+            for (int t = 0; t < CH; ++t)
+              if (C + t < nc) v[u][t] = __ldg(src + t);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * NT;
+      if (e < total) {
+        const int ir = e / nq, q = qlo + (e - ir * nq);
+        const float rw = sWr[ir];
+        const float4 w0 = *reinterpret_cast<const float4*>(sWc + q * CH);
+        const float4 w1 = *reinterpret_cast<const float4*>(sWc + q * CH + 4);
+        const float cw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        float o[8];
+#pragma unroll
+        for (int t = 0; t < CH; ++t) o[t] = rw * cw[t] * v[u][t];
+        put_s<K>(sb, ir, q, o);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ H kernel
 template <int K>
 __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
   using G = GeoT<K>;
   extern __shared__ __align__(1024) unsigned char smem[];
   Bars* H = reinterpret_cast<Bars*>(smem);
-  unsigned char* sS = smem + kHdr;
-  __nv_bfloat16* sXb = reinterpret_cast<__nv_bfloat16*>(sS + G::SBYTES);   // [ROWS][COLS]
-  unsigned char* ring = reinterpret_cast<unsigned char*>(sXb) + G::XBYTES;
+  unsigned char* sS = smem + kHdr;                                        // [2][SBYTES]
+  unsigned char* ring = sS + 2 * G::SBYTES;
   float* sWr = reinterpret_cast<float*>(ring + (size_t)NST * G::ABYTES);   // [ROWS]
   float* sWc = sWr + G::WCOFF;                                            // [COLS]
   __shared__ double red[NWE];
@@ -272,7 +363,10 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
   const int nrow = wi.pad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) init_bars(H);
-  if (warp == NWE) tmem_alloc(&H->tmem, G::TMEM_H);
+  if (warp == NWE) {
+    tmem_alloc(&H->tmem, G::TMEM_H);
+    load_ranges(A, H, lane);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -281,29 +375,21 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
   const int np = (wi.a_hi - wi.a_lo + 1) * nb;
 
   if (warp == NWE) {
-    if (lane == 0) issuer<K, false>(A, H, sS, ring, tbase, np, nrow);
+    if (lane == 0) issuer<K, false>(A, wi, H, sS, ring, tbase, np, nrow);
     __syncwarp();
   } else if (warp == NWE + 1) {
     if (lane == 0) producer<K>(A, wi, H, ring, np);
     __syncwarp();
   } else {
     zero_ring<K>(ring, tid);
-    // BF16 copy of the x window, staged through the (not yet used) S panels
-    if (np > 0)
-      stream_window<K>(reinterpret_cast<float*>(sS), G::SBYTES / ((G::COLS + 4) * 4), A.in + td.xoff,
-                       td.xpitch, wi.r0, wi.c0, td.nxr, td.nxc, G::COLS, tid,
-                       [&](int ir, int ic, const float* v) {
-                         __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(sXb + ir * G::COLS + ic);
-#pragma unroll
-                         for (int i = 0; i < 4; ++i) o[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-                       });
+    const float* img = A.in + td.xoff;
+    const bool al = (td.xpitch & 3) == 0 && (reinterpret_cast<uintptr_t>(img) & 15) == 0;
     bool ok = true;
     for (int p = 0; p < np && ok; ++p) {
-      if (p >= 1) {
-        ok = all_stage(wait_bar(&H->sempty, (uint32_t)((p - 1) & 1), &H->abort, A.err));
-        if (!ok) break;
-      }
-      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+      const int ga = wi.a_lo + p / nb, b = p % nb, gb = wi.b_lo + b;
+      const int kr = b < kMaxB ? H->ksr[b] : (G::KS - 1) << 8;
+      const int qlo = 2 * (kr & 0xff), nq = 2 * ((kr >> 8) - (kr & 0xff) + 1);
+      sync_stage();   // the previous PSF's weights are no longer read
       for (int e = tid; e < G::ROWS; e += NT) {
         const int R = wi.r0 + e;
         sWr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
@@ -313,38 +399,26 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
         sWc[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
       }
       sync_stage();
-      for (int e = tid; e < G::ROWS * G::NCH; e += NT) {
-        const int ir = e / G::NCH, q = e - ir * G::NCH;
-        const float rw = sWr[ir];
-        float v[8];
-        if (rw == 0.f) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) v[i] = 0.f;
-        } else {
-          const uint4 xb = *reinterpret_cast<const uint4*>(sXb + ir * G::COLS + q * CH);
-          const float4* wc4 = reinterpret_cast<const float4*>(sWc + q * CH);
-          const float4 c0 = wc4[0], c1 = wc4[1];
-          const float cw[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-          const uint32_t xw[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            v[2 * i] = rw * cw[2 * i] * __uint_as_float(xw[i] << 16);
-            v[2 * i + 1] = rw * cw[2 * i + 1] * __uint_as_float(xw[i] & 0xffff0000u);
-          }
-        }
-        put_s<K>(sS, ir, q, v);
+      // S buffer p & 1 was last read by PSF p - 2
+      if (p >= 2) {
+        ok = all_stage(wait_bar(&H->sempty[p & 1], (uint32_t)(((p >> 1) - 1) & 1), &H->abort, A.err));
+        if (!ok) break;
       }
+      restage_h<K>(sS + (p & 1) * G::SBYTES, img, td.xpitch, al, wi.r0, wi.c0, td.nxr, td.nxc, sWr,
+                   sWc, qlo, nq, tid);
       fence_async_smem();
-      mbar_arrive(&H->sfull);
+      mbar_arrive(&H->sfull[p & 1]);
     }
-    // epilogue: 32-row chunks of the accumulator, transposed through shared
-    // memory (the S panels are free once every MMA has completed).  The
+    // epilogue: 32-row chunks of the accumulator, transposed through the S
+    // buffer of the last PSF (free once every MMA has completed).  The
     // observed image (and noise weights) of chunk c + 1 are copied into the
-    // freed x-window region by cp.async while chunk c is written; chunk 0's
-    // copy overlaps the last PSF's MMAs.
+    // other S buffer by cp.async while chunk c is written; chunk 0's copy
+    // overlaps the last PSF's MMAs.
     constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
     const bool obs = A.mode != OP_PLAIN;
-    float* sYb = reinterpret_cast<float*>(sXb);          // [2][32 * MC] observed image
+    if (ok && np >= 2)   // the other buffer was last read by PSF np - 2
+      ok = all_stage(wait_bar(&H->sempty[np & 1], (uint32_t)(((np - 2) >> 1) & 1), &H->abort, A.err));
+    float* sYb = reinterpret_cast<float*>(sS + (np & 1) * G::SBYTES);   // [2][32 * MC] observed image
     float* sWb = sYb + 2 * 32 * MC;                      // [2][32 * MC] noise weights
     auto prefetch = [&](int i0, int buf) {
       if (obs) {
@@ -365,7 +439,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
     if (ok && np == 0) prefetch(0, 0);
     tc_fence_after();
     sync_stage();
-    float* sT = reinterpret_cast<float*>(sS);
+    float* sT = reinterpret_cast<float*>(sS + ((np + 1) & 1) * G::SBYTES);
     const int j = 32 * (warp & 3) + lane, hf = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     double part = 0.0;
@@ -435,15 +509,18 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
   unsigned char* sS = smem + kHdr;
   float* sU = reinterpret_cast<float*>(sS + G::SBYTES);                 // staging / epilogue
   unsigned char* ring = reinterpret_cast<unsigned char*>(sU) + G::UBYTES;
-  float* sWr = reinterpret_cast<float*>(ring + (size_t)NST * G::ABYTES); // [kMaxArows][NR]
-  float* sOr = sWr + kMaxArows * G::NR;                                  // gamma omega rows [NR]
+  float* sWr = reinterpret_cast<float*>(ring + (size_t)NST * G::ABYTES); // [2][NR]
+  float* sOr = sWr + 2 * G::NR;                                          // gamma omega rows [NR]
   float* sOc = sOr + G::NR;                                              // omega columns [MC]
   const WorkItem wi = A.work[blockIdx.x];
   const TileDesc td = A.tiles[wi.tile];
   const int nrow = wi.pad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) init_bars(H);
-  if (warp == NWE) tmem_alloc(&H->tmem, G::TMEM_HT);
+  if (warp == NWE) {
+    tmem_alloc(&H->tmem, G::TMEM_HT);
+    load_ranges(A, H, lane);
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -453,7 +530,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
   const int np = na * nb;
 
   if (warp == NWE) {
-    if (lane == 0) issuer<K, true>(A, H, sS, ring, tbase, np, nrow);
+    if (lane == 0) issuer<K, true>(A, wi, H, sS, ring, tbase, np, nrow);
     __syncwarp();
   } else if (warp == NWE + 1) {
     if (lane == 0) producer<K>(A, wi, H, ring, np);
@@ -465,14 +542,6 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
     stream_window<K>(sU, G::UBYTES / ((G::COLS + 4) * 4), A.in + td.yoff, td.ypitch, wi.r0 - (K - 1),
                      wi.c0 - (K - 1), td.nyr, td.nyc, MC - 1 + K, tid,
                      [&](int ir, int ic, const float* v) { put_s<K>(sS, ir, ic / CH, v); });
-    const bool wr_staged = na <= kMaxArows;
-    if (wr_staged) {
-      for (int e = tid; e < na * G::NR; e += NT) {
-        const int ai = e / G::NR, i = e - ai * G::NR;
-        const int R = wi.r0 + i;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], wi.a_lo + ai) : 0.f;
-      }
-    }
     if (A.mode != OP_PLAIN) {   // consensus profiles of the step epilogue
       for (int e = tid; e < G::NR; e += NT) {
         const int R = wi.r0 + e;
@@ -484,7 +553,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
       }
     }
     fence_async_smem();
-    mbar_arrive(&H->sfull);
+    mbar_arrive(&H->sfull[0]);
     sync_stage();
 
     float* sT = sU;                      // [32][TP]
@@ -542,6 +611,17 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     bool ok = true;
     for (int p = 0; p < np; ++p) {
+      const int ai = p / nb, gb = wi.b_lo + p % nb;
+      // column weight of the PSF and, for the first PSF of a grid row, the
+      // row weights (buffer ai & 1: the fold of the previous grid row reads
+      // the other one), fetched while its MMAs run
+      const float wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+      float* wrow = sWr + (ai & 1) * G::NR;
+      if (p % nb == 0)
+        for (int e = tid; e < G::NR; e += NT) {
+          const int R = wi.r0 + e;
+          wrow[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], wi.a_lo + ai) : 0.f;
+        }
       if (step)
         for (int k = 0; k < qper && qc < nck; ++k) q_chunk(32 * qc++);
       if (!all_stage(wait_bar(&H->dfull[0], (uint32_t)(p & 1), &H->abort, A.err))) {
@@ -549,26 +629,35 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
         break;
       }
       tc_fence_after();
-      const int ai = p / nb, gb = wi.b_lo + p % nb;
-      const float wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+      // software-pipelined: the loads of the next 16 rows are issued before
+      // the sums of the current ones are stored
+      uint32_t dv[16], gv[16];
+      if (16 * hf < nrow) {
+        tmem_ld16_nowait(tbase + lanes + (uint32_t)(16 * hf), dv);
+        if (p > 0) tmem_ld16_nowait(tbase + lanes + (uint32_t)(G::NR + 16 * hf), gv);
+      }
       for (int i0 = 16 * hf; i0 < nrow; i0 += 32) {
-        uint32_t dv[16], gv[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)i0, dv);
-        if (p > 0) tmem_ld16_nowait(tbase + lanes + (uint32_t)(G::NR + i0), gv);
         tmem_wait_ld();
+        uint32_t ov[16];
+        float wr[16];
+#pragma unroll
+        for (int t = 0; t < 16; t += 4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wrow + i0 + t);
+          wr[t] = w4.x;
+          wr[t + 1] = w4.y;
+          wr[t + 2] = w4.z;
+          wr[t + 3] = w4.w;
+        }
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
-          float wr;
-          if (wr_staged) {
-            wr = sWr[ai * G::NR + i0 + t];
-          } else {
-            const int R = wi.r0 + i0 + t;
-            wr = R < td.nxr ? wsel(A.wrow[td.xr0 + R], wi.a_lo + ai) : 0.f;
-          }
           const float dd = __uint_as_float(dv[t]);
-          gv[t] = __float_as_uint(p > 0 ? fmaf(wr * wc, dd, __uint_as_float(gv[t])) : wr * wc * dd);
+          ov[t] = __float_as_uint(p > 0 ? fmaf(wr[t] * wc, dd, __uint_as_float(gv[t])) : wr[t] * wc * dd);
         }
-        tmem_st16_nowait(tbase + lanes + (uint32_t)(G::NR + i0), gv);
+        if (i0 + 32 < nrow) {
+          tmem_ld16_nowait(tbase + lanes + (uint32_t)(i0 + 32), dv);
+          if (p > 0) tmem_ld16_nowait(tbase + lanes + (uint32_t)(G::NR + i0 + 32), gv);
+        }
+        tmem_st16_nowait(tbase + lanes + (uint32_t)(G::NR + i0), ov);
       }
       tmem_wait_st();
       tc_fence_before();
@@ -667,6 +756,57 @@ uint16_t to_bf16(float f) {
 
 int tcT_block_cols() { return MC; }
 int tcT_max_rows(int K) { return K <= 31 ? 256 : 128; }
+
+// A k-step covers staged columns [16 ks, 16 ks + 16) and so reaches output
+// columns 16 ks - K + 1 .. 16 ks + 15 of the block.  H: S = w_p . x is zero
+// where the PSF's column weight is zero, so steps outside its support add
+// zeros, and steps reaching no valid output column are not needed.  H^T: the
+// weight multiplies the output, so only steps reaching an output column of
+// nonzero weight count, and steps whose staged residual columns are all zero
+// (outside the y tile) add nothing.  An empty range falls back to every step.
+int64_t tcT_kstep_ranges(const std::vector<TileDesc>& tiles, const std::vector<WorkItem>& items,
+                         const std::vector<WTab>& wcol, int K, bool adjoint,
+                         std::vector<uint16_t>& out) {
+  const int KS = (MC - 1 + K + KM - 1) / KM, COLS = KS * KM;
+  out.assign(items.size() * kMaxB, (uint16_t)((KS - 1) << 8));
+  int64_t steps = 0;
+  for (size_t it = 0; it < items.size(); ++it) {
+    const WorkItem& wi = items[it];
+    const TileDesc& td = tiles[wi.tile];
+    const int nb = wi.b_hi - wi.b_lo + 1, na = wi.a_hi - wi.a_lo + 1;
+    const int ncv = std::min(MC, (adjoint ? td.nxc : td.nyc) - wi.c0);
+    const int span = adjoint ? ncv : std::min(COLS, std::min(ncv + K - 1, td.nxc - wi.c0));
+    for (int b = 0; b < nb; ++b) {
+      int klo = 0, khi = KS - 1;
+      if (b < kMaxB) {
+        const int gb = wi.b_lo + b;
+        int lo = INT_MAX, hi = -1;
+        for (int c = 0; c < span; ++c)
+          if (wsel(wcol[td.xc0 + wi.c0 + c], gb) != 0.f) {
+            lo = std::min(lo, c);
+            hi = std::max(hi, c);
+          }
+        if (hi >= 0) {
+          if (adjoint) {
+            // staged residual column c holds y column c0 - (K - 1) + c
+            const int slo = std::max(0, K - 1 - wi.c0);
+            const int shi = std::min(MC - 2 + K, td.nyc - 1 - wi.c0 + K - 1);
+            const int wlo = lo / KM, whi = std::min(KS - 1, (hi + K - 1) / KM);
+            const int l2 = std::max(wlo, slo / KM), h2 = std::min(whi, shi / KM);
+            klo = l2 <= h2 ? l2 : wlo;
+            khi = l2 <= h2 ? h2 : whi;
+          } else {
+            klo = lo / KM;
+            khi = std::min(KS - 1, hi / KM);
+          }
+        }
+        out[it * kMaxB + b] = (uint16_t)(klo | (khi << 8));
+      }
+      steps += (int64_t)na * (khi - klo + 1);
+    }
+  }
+  return steps;
+}
 
 cudaError_t tcT_prepare(int K) {
   switch (K) {
