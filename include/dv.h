@@ -252,15 +252,24 @@ typedef struct dv_plan_info {
    * Steps where a PSF's column weight is zero on the whole step are skipped.
    * 0 on the other paths. */
   int64_t mma_ksteps[2];
+  /* tile groups whose inner iterations the captured local solve runs on
+   * concurrent streams (tensor path with CUDA graphs; 1 = one launch per
+   * operator over every tile) */
+  int32_t tile_groups;
+  int32_t reserved;
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);
 
 /* Per-kernel CUDA-event timing of the solve's launches (off by default).
  * kind: 0 = operator H with residual, 1 = operator H^T with fused prox step,
- * 2 = consensus + dual update.  Reports the summed duration (ms) and launch
- * count since the last reset; dv_consensus_solve must have returned (stats or
- * a synchronised stream) before reading. */
+ * 2 = consensus + dual update, 3 = one whole local solve (n_inner x {H, H^T}
+ * over every tile) when the captured local solve runs its tile groups
+ * concurrently (dv_plan_info.tile_groups > 1; kinds 0 and 1 then see only
+ * eager launches).  Reports the summed duration (ms) and the number of timed
+ * launches (local solves for kind 3) since the last reset;
+ * dv_consensus_solve must have returned (stats or a synchronised stream)
+ * before reading. */
 dv_status dv_plan_set_timing(dv_plan* plan, int32_t enable);
 dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int64_t* launches);
 

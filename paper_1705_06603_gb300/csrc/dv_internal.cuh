@@ -84,6 +84,11 @@ enum OpMode : int32_t {
 // of their own (further columns run every k-step)
 constexpr int kTcMaxB = 16;
 
+// Tile groups of the captured local solve: each group's H / H^T chain runs
+// on a stream of its own, so one group's blocks fill the SMs another group's
+// last blocks leave idle (the tiles are independent between consensus steps)
+constexpr int kMaxGroups = 4;
+
 struct OpArgs {
   const TileDesc* tiles;
   const WorkItem* work;
@@ -239,8 +244,8 @@ struct KernelTimer {
   std::vector<cudaEvent_t> placeholders;
   std::vector<Pending> pending;
   size_t next = 0;
-  double total_ms[3] = {0, 0, 0};
-  int64_t count[3] = {0, 0, 0};
+  double total_ms[4] = {0, 0, 0, 0};
+  int64_t count[4] = {0, 0, 0, 0};
 };
 
 }  // namespace dv
@@ -263,6 +268,9 @@ struct OpTables {
   uint16_t* ksHg = nullptr;
   uint16_t* ksHtg = nullptr;
   int64_t ksteps[2] = {0, 0};
+  // tile-mode items grouped by tile group: group g owns items [gH[g], gH[g + 1])
+  int gH[kMaxGroups + 1] = {};
+  int gHt[kMaxGroups + 1] = {};
 };
 }  // namespace dv
 
@@ -326,6 +334,9 @@ struct dv_plan {
   dv::KernelTimer timer;
   std::vector<dv::GraphEntry> graphs;
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  int ngrp = 1;                       // tile groups of the captured local solve
+  cudaStream_t grp_stream[dv::kMaxGroups] = {};
+  cudaEvent_t grp_fork = nullptr, grp_join[dv::kMaxGroups] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -342,4 +353,6 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
 dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, float* out,
                       bool global, const float* w, const float* u);
 dv::GridArgs grid_args(const dv_plan* p);
+// the tile-mode arguments restricted to the items of tile group g
+dv::OpArgs group_args(const dv_plan* p, int path, dv::OpArgs a, bool adjoint, int g);
 }  // namespace dv

@@ -398,6 +398,15 @@ cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream
 
 int obj_parts(const dv_plan* P) { return P->tab[tab_index(P->fpath)].nH; }
 
+dv::OpArgs group_args(const dv_plan* p, int path, dv::OpArgs a, bool adjoint, int g) {
+  const OpTables& tb = p->tab[tab_index(path)];
+  const int* b = adjoint ? tb.gHt : tb.gH;
+  a.work += b[g];
+  a.n_work = b[g + 1] - b[g];
+  if (a.ksr) a.ksr += (size_t)b[g] * kTcMaxB;
+  return a;
+}
+
 dv::GridArgs grid_args(const dv_plan* p) {
   GridArgs g{};
   g.tiles = p->d_tiles;
@@ -628,6 +637,23 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
 
   // work tables: direct path always, FFT and tensor paths when available
   std::vector<WorkItem> w;
+  // tile groups of the captured local solve on the tensor path, balanced by
+  // the tiles' (block, active PSF) pairs (largest tile to the lightest group)
+  std::vector<int> tgroup(P->h_tiles.size(), 0);
+  P->ngrp = (P->tensor_ok && prob->use_graphs) ? std::min<int>(kMaxGroups, (int)P->h_tiles.size()) : 1;
+  if (P->ngrp > 1) {
+    make_work(P->h_tiles, false, K, L, direct_tile_m(), direct_tile_n(), w);
+    std::vector<int64_t> cost(P->h_tiles.size(), 0), load(P->ngrp, 0);
+    for (const WorkItem& it : w) cost[it.tile] += (int64_t)(it.a_hi - it.a_lo + 1) * (it.b_hi - it.b_lo + 1);
+    std::vector<int> idx(P->h_tiles.size());
+    for (size_t t = 0; t < idx.size(); ++t) idx[t] = (int)t;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int t : idx) {
+      const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      tgroup[t] = g;
+      load[g] += cost[t];
+    }
+  }
   for (int k = 0; k < 3; ++k) {
     if ((k == 1 && !P->fft_ok) || (k == 2 && !P->tensor_ok)) continue;
     // tensor path: BF16 column-band blocks (128 columns, rows per tile up to
@@ -647,6 +673,20 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
                  (y.a_hi - y.a_lo + 1) * (y.b_hi - y.b_lo + 1) + 1;
         });
     };
+    // tensor path, tile mode: items grouped by tile group (heaviest first
+    // within a group); bounds[g] = first item of group g
+    auto group = [&](std::vector<WorkItem>& v, int* bounds) {
+      std::fill(bounds, bounds + kMaxGroups + 1, (int)v.size());
+      bounds[0] = 0;
+      if (k != 2 || P->ngrp <= 1) return;
+      std::stable_sort(v.begin(), v.end(), [&](const WorkItem& x, const WorkItem& y) {
+        return tgroup[x.tile] < tgroup[y.tile];
+      });
+      for (int g = 1; g <= P->ngrp; ++g)
+        bounds[g] = (int)(std::partition_point(v.begin(), v.end(), [&](const WorkItem& x) {
+                            return tgroup[x.tile] < g;
+                          }) - v.begin());
+    };
     auto count = [&](const std::vector<WorkItem>& v, int k2) {
       for (const WorkItem& it : v) {
         const int64_t np = (int64_t)(it.a_hi - it.a_lo + 1) * (it.b_hi - it.b_lo + 1);
@@ -665,12 +705,14 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     make_work(P->h_tiles, false, K, L, bm, bn, w, max_rows);
     count(w, 0);
     order(w);
+    group(w, tb.gH);
     tb.nH = (int)w.size();
     DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
     DV_TRY(ranges(P->h_tiles, false, &tb.ksH));
     make_work(P->h_tiles, true, K, L, bm, bn, w, max_rows);
     count(w, 1);
     order(w);
+    group(w, tb.gHt);
     tb.nHt = (int)w.size();
     DV_TRY(upload(P, &tb.Ht, w.data(), w.size(), s));
     DV_TRY(ranges(P->h_tiles, true, &tb.ksHt));
@@ -779,6 +821,13 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   DV_TRY_CUDA(cudaMallocHost((void**)&P->h_scal, 8 * sizeof(double)));
   DV_TRY_CUDA(direct_prepare(K));
   DV_TRY_CUDA(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  if (P->ngrp > 1) {
+    DV_TRY_CUDA(cudaEventCreateWithFlags(&P->grp_fork, cudaEventDisableTiming));
+    for (int g = 0; g < P->ngrp; ++g) {
+      DV_TRY_CUDA(cudaStreamCreateWithFlags(&P->grp_stream[g], cudaStreamNonBlocking));
+      DV_TRY_CUDA(cudaEventCreateWithFlags(&P->grp_join[g], cudaEventDisableTiming));
+    }
+  }
   DV_TRY_CUDA(cudaEventCreate(&P->ev0));
   DV_TRY_CUDA(cudaEventCreate(&P->ev1));
   DV_TRY_CUDA(cudaMemsetAsync(P->d_y, 0, (size_t)P->hy * P->wy * sizeof(float), s));
@@ -828,6 +877,11 @@ dv_status release(dv_plan* P) {
     if (b) cudaFree(b);
   if (P->h_scal) cudaFreeHost(P->h_scal);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  for (int g = 0; g < kMaxGroups; ++g) {
+    if (P->grp_stream[g]) cudaStreamDestroy(P->grp_stream[g]);
+    if (P->grp_join[g]) cudaEventDestroy(P->grp_join[g]);
+  }
+  if (P->grp_fork) cudaEventDestroy(P->grp_fork);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   delete P;
@@ -865,6 +919,8 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->psf_pairs[1] = P->tab[k].pairs[1];
   info->mma_ksteps[0] = P->tab[k].ksteps[0];
   info->mma_ksteps[1] = P->tab[k].ksteps[1];
+  info->tile_groups = (P->ngrp > 1 && P->path == DV_PATH_TENSOR) ? P->ngrp : 1;
+  info->reserved = 0;
   info->block_side = k == 1 ? fft_block(P->K)
                             : (k == 2 ? (P->prob.precision == DV_PREC_BF16 ? tcT_max_rows(P->K)
                                                                           : tc_block_m())

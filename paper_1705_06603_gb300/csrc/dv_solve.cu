@@ -10,7 +10,10 @@
 namespace dv {
 namespace {
 
-enum Kind { KIND_H = 0, KIND_HT = 1, KIND_CONS = 2 };
+enum Kind { KIND_H = 0, KIND_HT = 1, KIND_CONS = 2, KIND_LOCAL = 3 };
+
+// Whether the captured local solve runs the tile groups concurrently.
+bool grouped(const dv_plan* P) { return P->ngrp > 1 && P->path == DV_PATH_TENSOR; }
 
 int nhub(const dv_plan* P) { return huber_blocks(P->T, P->max_nxr, P->max_nxc); }
 int ncons(const dv_plan* P) { return consensus_blocks(P->n_citems); }
@@ -76,6 +79,41 @@ cudaError_t launch_inner_Ht(dv_plan* P, int par, cudaStream_t s) {
                       s);
 }
 
+// Tile group g of the inner iterations: the same kernels on the group's items.
+cudaError_t launch_group_H(dv_plan* P, int par, int g, cudaStream_t s) {
+  return launch_op_H(P, P->path,
+                     group_args(P, P->path, op_args_H(P, P->path, OP_RESID, P->d_w[par], P->d_r, false),
+                                false, g),
+                     s);
+}
+
+cudaError_t launch_group_Ht(dv_plan* P, int par, int g, cudaStream_t s) {
+  return launch_op_Ht(P, P->path,
+                      group_args(P, P->path,
+                                 op_args_Ht(P, P->path, OP_STEP, P->d_r, P->d_w[par ^ 1], false,
+                                            P->d_w[par], P->d_u),
+                                 true, g),
+                      s);
+}
+
+// Captures the n_inner iterations of every tile group on a stream of its own
+// (fork from and join back into the capture stream).
+dv_status capture_groups(dv_plan* P, cudaStream_t cs, int par, int n_inner) {
+  DV_TRY_CUDA(cudaEventRecord(P->grp_fork, cs));
+  for (int g = 0; g < P->ngrp; ++g) DV_TRY_CUDA(cudaStreamWaitEvent(P->grp_stream[g], P->grp_fork, 0));
+  for (int g = 0; g < P->ngrp; ++g) {
+    int pg = par;
+    for (int i = 0; i < n_inner; ++i) {
+      DV_TRY_CUDA(launch_group_H(P, pg, g, P->grp_stream[g]));
+      DV_TRY_CUDA(launch_group_Ht(P, pg, g, P->grp_stream[g]));
+      pg ^= 1;
+    }
+    DV_TRY_CUDA(cudaEventRecord(P->grp_join[g], P->grp_stream[g]));
+    DV_TRY_CUDA(cudaStreamWaitEvent(cs, P->grp_join[g], 0));
+  }
+  return DV_OK;
+}
+
 dv_status capture_node(cudaStream_t cs, cudaGraphNode_t* node) {
   cudaStreamCaptureStatus st;
   const cudaGraphNode_t* deps = nullptr;
@@ -98,7 +136,11 @@ dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
   DV_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   dv_status st = DV_OK;
   int par = g.parity;
-  for (int i = 0; i < g.n_inner && st == DV_OK; ++i) {
+  // the tensor path runs its tile groups concurrently (timed as one local
+  // solve); otherwise one launch per operator, each with its own event nodes
+  const bool grp = grouped(P);
+  if (grp) st = capture_groups(P, cs, par, g.n_inner);
+  for (int i = 0; i < g.n_inner && st == DV_OK && !grp; ++i) {
     for (int k = 0; k < 2 && st == DV_OK; ++k) {
       cudaGraphNode_t n0 = nullptr, n1 = nullptr;
       if (g.timed) {
@@ -156,6 +198,18 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
   if (P->prob.use_graphs) {
     GraphEntry* g = nullptr;
     DV_TRY(get_graph(P, n_inner, P->cur, &g));
+    if (g->timed && grouped(P)) {
+      int e0, e1;
+      DV_TRY(pool_event(P, &e0));
+      DV_TRY(pool_event(P, &e1));
+      DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e0], s));
+      DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
+      DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e1], s));
+      P->timer.pending.push_back(Pending{KIND_LOCAL, e0, e1});
+      P->launches += 2 * n_inner * P->ngrp;
+      P->cur ^= (n_inner & 1);
+      return DV_OK;
+    }
     if (g->timed) {
       for (size_t j = 0; j < g->kinds.size(); ++j) {
         int e0, e1;
@@ -167,7 +221,7 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
       }
     }
     DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
-    P->launches += 2 * n_inner;
+    P->launches += 2 * n_inner * (grouped(P) ? P->ngrp : 1);
   } else {
     int par = P->cur;
     for (int i = 0; i < n_inner; ++i) {
@@ -414,7 +468,7 @@ extern "C" dv_status dv_plan_set_timing(dv_plan* P, int32_t enable) {
   DV_TRY(check_plan(P));
   DV_TRY(harvest(P));
   P->timing = enable != 0;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     P->timer.total_ms[k] = 0.0;
     P->timer.count[k] = 0;
   }
@@ -425,7 +479,7 @@ extern "C" dv_status dv_plan_kernel_time(dv_plan* P, int32_t kind, double* total
                                          int64_t* launches) {
   clear_error();
   DV_TRY(check_plan(P));
-  if (kind < 0 || kind > 2) return fail(DV_ERR_INVALID_ARG, "kind must be 0, 1 or 2");
+  if (kind < 0 || kind > 3) return fail(DV_ERR_INVALID_ARG, "kind must be 0, 1, 2 or 3");
   DV_TRY(harvest(P));
   if (total_ms) *total_ms = P->timer.total_ms[kind];
   if (launches) *launches = P->timer.count[kind];

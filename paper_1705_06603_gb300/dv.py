@@ -69,7 +69,8 @@ class dv_plan_info(C.Structure):
                 ("tune_ms_fft", C.c_double), ("blocks", C.c_int64 * 2),
                 ("block_psfs", C.c_int64 * 2), ("psf_pairs", C.c_int64 * 2),
                 ("block_side", C.c_int32), ("fp32_path", C.c_int32),
-                ("tune_ms_tensor", C.c_double), ("mma_ksteps", C.c_int64 * 2)]
+                ("tune_ms_tensor", C.c_double), ("mma_ksteps", C.c_int64 * 2),
+                ("tile_groups", C.c_int32), ("reserved", C.c_int32)]
 
 
 _vp = C.c_void_p

@@ -345,6 +345,30 @@ def test_tensor_solve_close_to_oracle(env, prec):
     plan.close()
 
 
+def test_grouped_tensor_solve_is_bit_identical_to_eager(env):
+    """The captured local solve of the tensor path runs its tile groups on
+    concurrent streams; the result equals one launch per operator over every
+    tile (eager), and event timing counts whole local solves (kind 3)."""
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    p1, x1, s1 = _gpu_solve(env, w, psfs, y, 4, 3, use_graphs=1, path=TENSOR, precision=BF16)
+    p2, x2, s2 = _gpu_solve(env, w, psfs, y, 4, 3, use_graphs=0, path=TENSOR, precision=BF16)
+    assert p1.info.tile_groups == 4 and p2.info.tile_groups == 1
+    np.testing.assert_array_equal(x1, x2)
+    assert s1["objective"] == s2["objective"]
+    dv.dv_plan_set_timing(p1.handle, 1)
+    xd, _ = p1.solve(torch.from_numpy(y).cuda(), stats=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(xd.cpu().numpy(), x1)
+    ms, cnt = dv.dv_plan_kernel_time(p1.handle, 3)
+    assert cnt == 4 and ms > 0.0
+    assert dv.dv_plan_kernel_time(p1.handle, 0)[1] == 0
+    assert dv.dv_plan_kernel_time(p1.handle, 2)[1] == 4
+    dv.dv_plan_set_timing(p1.handle, 0)
+    p1.close()
+    p2.close()
+
+
 def test_autotuner_weighs_the_tensor_path(env):
     torch, dv = env
     w, psfs, y, _ = workload_case("disks128")
