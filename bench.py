@@ -57,7 +57,9 @@ def parse():
                          "(the autotuner picks the fastest allowed path)")
     ap.add_argument("--ws-pairs", type=int, default=24,
                     help="warm-start training pairs made by the plain method")
-    ap.add_argument("--ws-steps", type=int, default=24000, help="warm-start Adam steps")
+    ap.add_argument("--ws-steps", type=int, default=40000, help="warm-start Adam steps")
+    ap.add_argument("--ws-schedule", choices=["const", "cosine"], default="cosine",
+                    help="warm-start learning-rate schedule")
     ap.add_argument("--rho", type=float, default=1.8,
                     help="relaxation of the chosen form's dual update (0: the workload's)")
     ap.add_argument("--gamma", type=float, default=0.2,
@@ -283,7 +285,7 @@ def run_reference(args):
 # --------------------------------------------------------------------------- GPU arm
 
 
-def train_warmstart(dv, w, psfs, seed=0, n_pairs=24, size=256, steps=2000):
+def train_warmstart(dv, w, psfs, seed=0, n_pairs=24, size=256, steps=2000, schedule="const"):
     """Trains the warm-start network on pairs the plain method produces from
     other seeded scenes with the workload's PSF grid and noise level."""
     from paper_1705_06603_gb300 import warmstart as WS
@@ -296,8 +298,9 @@ def train_warmstart(dv, w, psfs, seed=0, n_pairs=24, size=256, steps=2000):
                                 sigma=w.noise_sigma)
         pairs.append((f, t))
     net = dv.Cnn(seed=seed)
-    losses = WS.train(net, pairs, steps=steps, batch=16, crop=64, lr=1e-3, seed=seed)
-    return net, {"pairs": n_pairs, "pair_size": size, "steps": steps,
+    losses = WS.train(net, pairs, steps=steps, batch=16, crop=64, lr=1e-3, seed=seed,
+                      schedule=schedule)
+    return net, {"pairs": n_pairs, "pair_size": size, "steps": steps, "schedule": schedule,
                  "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:])),
                  "seconds": time.perf_counter() - t0}
 
@@ -351,7 +354,7 @@ def run_ours(args):
     # chosen form: autotuned operator, CUDA graphs, learned warm start, stops at
     # F <= F*(1 + 1e-4) (objective checked every 2 outer iterations)
     net, train_info = train_warmstart(dv, w, psfs, seed=rank, n_pairs=args.ws_pairs,
-                                      steps=args.ws_steps)
+                                      steps=args.ws_steps, schedule=args.ws_schedule)
     target = f_star * (1.0 + 1e-4)
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
     chosen = dict(common)

@@ -314,6 +314,20 @@ dv_status dv_cnn_gradients(dv_cnn* cnn, const float* in_dev, const float* target
  * batch; loss_host (optional) receives the loss before the step (synchronises). */
 dv_status dv_cnn_train_step(dv_cnn* cnn, const float* in_dev, const float* target_dev, int32_t N,
                             int32_t H, int32_t W, float lr, double* loss_host, void* stream);
+/* n_steps Adam steps on crops of a stack of training pairs, queued on stream
+ * without host synchronisation between steps.  Step t trains on the batch of
+ * the `batch` crops crops_host[t][b] = {pair, r0, c0} (host, int32), each
+ * crop x crop pixels of feats_dev [n_pairs][H][W][5] and targets_dev
+ * [n_pairs][H][W] (device, float32), with learning rate lr_host[t] (host).
+ * The same as n_steps calls of dv_cnn_train_step on the gathered crops, bit
+ * for bit.  losses_host (optional, n_steps doubles) receives each step's loss
+ * before its update.  Synchronises stream once, at the end.  A crop outside
+ * its pair or a pair index out of range: DV_ERR_INVALID_ARG before any work.
+ * Allocates (and frees) device memory for the crop table and one batch. */
+dv_status dv_cnn_train_crops(dv_cnn* cnn, const float* feats_dev, const float* targets_dev,
+                             int32_t n_pairs, int32_t H, int32_t W, const int32_t* crops_host,
+                             int32_t n_steps, int32_t batch, int32_t crop, const float* lr_host,
+                             double* losses_host, void* stream);
 dv_status dv_cnn_destroy(dv_cnn* cnn);
 /* Attaches a network to the plan (borrowed; keep it alive while the plan
  * uses it).  With use_warmstart = 1 and no x0, dv_consensus_solve starts from

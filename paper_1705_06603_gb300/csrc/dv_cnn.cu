@@ -252,6 +252,23 @@ __global__ void input_kernel(const float* __restrict__ in, int64_t npix, bf16* _
   out[i] = __float2bfloat16_rn(c < DV_CNN_IN_CH ? in[p * DV_CNN_IN_CH + c] : 0.f);
 }
 
+// One training batch from a crop table: xb [b][r][c][5] and tb [b][r][c] =
+// the crop x crop window at (r0, c0) of pair crops[b] = {pair, r0, c0}.
+__global__ void gather_crops_kernel(const float* __restrict__ feats, const float* __restrict__ targets,
+                                    int H, int W, const int* __restrict__ crops, int batch, int crop,
+                                    float* __restrict__ xb, float* __restrict__ tb) {
+  const int64_t n = (int64_t)batch * crop * crop;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = (int)(i / ((int64_t)crop * crop));
+  const int rem = (int)(i - (int64_t)b * crop * crop), r = rem / crop, c = rem - r * crop;
+  const int* cb = crops + 3 * b;
+  const int64_t src = ((int64_t)cb[0] * H + cb[1] + r) * W + cb[2] + c;
+  tb[i] = targets[src];
+#pragma unroll
+  for (int ch = 0; ch < DV_CNN_IN_CH; ++ch) xb[i * DV_CNN_IN_CH + ch] = feats[src * DV_CNN_IN_CH + ch];
+}
+
 // Warm-start features of the global x grid (reading of the inputs in the
 // header): [y edge-replicated, 3 interpolated PSF descriptors, 100 sigma].
 __global__ void features_kernel(const float* __restrict__ y, int hy, int wy, int rad,
@@ -874,6 +891,83 @@ extern "C" dv_status dv_cnn_train_step(dv_cnn* c, const float* in_dev, const flo
     *loss_host = 0.5 * *c->h_loss / ((double)N * H * W);
   }
   return DV_OK;
+}
+
+extern "C" dv_status dv_cnn_train_crops(dv_cnn* c, const float* feats_dev, const float* targets_dev,
+                                       int32_t n_pairs, int32_t H, int32_t W, const int32_t* crops_host,
+                                       int32_t n_steps, int32_t batch, int32_t crop,
+                                       const float* lr_host, double* losses_host, void* stream) {
+  clear_error();
+  if (!c || !feats_dev || !targets_dev || !crops_host || !lr_host)
+    return fail(DV_ERR_INVALID_ARG, "NULL argument");
+  if (n_pairs < 1 || H < 1 || W < 1 || n_steps < 0 || batch < 1 || crop < 1 || crop > H || crop > W)
+    return fail(DV_ERR_INVALID_ARG, "bad pair stack %d x %d x %d or crop %d x %d", n_pairs, H, W,
+                batch, crop);
+  DV_TRY(check_shape(batch, crop, crop));
+  for (int64_t k = 0; k < (int64_t)n_steps * batch; ++k) {
+    const int32_t* cb = crops_host + 3 * k;
+    if (cb[0] < 0 || cb[0] >= n_pairs || cb[1] < 0 || cb[1] > H - crop || cb[2] < 0 || cb[2] > W - crop)
+      return fail(DV_ERR_INVALID_ARG, "crop %lld = {%d, %d, %d} outside the pairs", (long long)k,
+                  cb[0], cb[1], cb[2]);
+  }
+  for (int t = 0; t < n_steps; ++t)
+    if (!(lr_host[t] > 0.f)) return fail(DV_ERR_INVALID_ARG, "learning rate of step %d is not positive", t);
+  if (n_steps == 0) return DV_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t npix = (int64_t)batch * crop * crop;
+  int* d_crops = nullptr;
+  float* d_xb = nullptr;
+  double* d_losses = nullptr;
+  auto done = [&](dv_status st) {
+    if (st == DV_OK) {
+      const cudaError_t e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize", __FILE__, __LINE__);
+    } else {
+      cudaStreamSynchronize(s);
+    }
+    cudaFree(d_crops);
+    cudaFree(d_xb);
+    cudaFree(d_losses);
+    return st;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&d_crops, (size_t)n_steps * batch * 3 * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&d_xb, (size_t)npix * (DV_CNN_IN_CH + 1) * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&d_losses, (size_t)n_steps * sizeof(double))) != cudaSuccess)
+    return done(cuda_fail(e, "cudaMalloc", __FILE__, __LINE__));
+  float* d_tb = d_xb + npix * DV_CNN_IN_CH;
+  if ((e = cudaMemcpyAsync(d_crops, crops_host, (size_t)n_steps * batch * 3 * sizeof(int),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return done(cuda_fail(e, "upload", __FILE__, __LINE__));
+  const float b1 = 0.9f, b2 = 0.999f;
+  for (int t = 0; t < n_steps; ++t) {
+    gather_crops_kernel<<<cdiv(npix, NB), NB, 0, s>>>(feats_dev, targets_dev, H, W,
+                                                      d_crops + (int64_t)t * batch * 3, batch, crop,
+                                                      d_xb, d_tb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_fail(e, "gather", __FILE__, __LINE__));
+    dv_status st = forward(c, d_xb, batch, crop, crop, nullptr, s);
+    if (st == DV_OK) st = backward(c, d_tb, batch, crop, crop, s);
+    if (st != DV_OK) return done(st);
+    if ((e = cudaMemcpyAsync(d_losses + t, c->d_loss, sizeof(double), cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return done(cuda_fail(e, "loss copy", __FILE__, __LINE__));
+    c->step += 1;
+    const float c1 = 1.f - (float)std::pow((double)b1, (double)c->step);
+    const float c2 = 1.f - (float)std::pow((double)b2, (double)c->step);
+    adam_kernel<<<cdiv(c->nparam, NB), NB, 0, s>>>(c->d_p, c->d_g, c->d_m, c->d_v, c->nparam, lr_host[t],
+                                                   b1, b2, 1e-8f, c1, c2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_fail(e, "adam", __FILE__, __LINE__));
+    if ((st = pack(c, s)) != DV_OK) return done(st);
+  }
+  if (losses_host) {
+    if ((e = cudaMemcpyAsync(losses_host, d_losses, (size_t)n_steps * sizeof(double),
+                             cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return done(cuda_fail(e, "loss download", __FILE__, __LINE__));
+  }
+  const dv_status st = done(DV_OK);
+  if (st == DV_OK && losses_host)
+    for (int t = 0; t < n_steps; ++t) losses_host[t] *= 0.5 / (double)npix;
+  return st;
 }
 
 extern "C" dv_status dv_cnn_destroy(dv_cnn* c) {

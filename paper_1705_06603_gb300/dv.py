@@ -100,6 +100,8 @@ _sigs = {
                                    C.POINTER(C.c_double), _vp]),
     "dv_cnn_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, C.c_float,
                                     C.POINTER(C.c_double), _vp]),
+    "dv_cnn_train_crops": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, _vp,
+                                     C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "dv_cnn_destroy": (C.c_int, [_vp]),
     "dv_plan_set_warmstart": (C.c_int, [_vp, _vp]),
     "dv_warmstart_features": (C.c_int, [_vp, _vp, _vp, _vp]),
@@ -340,6 +342,25 @@ class Cnn:
         _check(_lib.dv_cnn_train_step(self._h, _dptr(x, "x"), _dptr(target, "target"), N, H, W,
                                       float(lr), C.byref(loss), _stream_handle(self.stream)))
         return loss.value
+
+    def train_crops(self, feats, targets, crops, crop, lrs):
+        """len(lrs) Adam steps on crops of stacked pairs: feats [P][H][W][5] and
+        targets [P][H][W] (float32 CUDA), crops int32 [steps][batch][3] =
+        (pair, r0, c0), lrs float32 [steps]; returns the per-step losses."""
+        P, H, W, _ = feats.shape
+        _dptr(feats, "feats")
+        _dptr(targets, "targets", (P, H, W))
+        crops = np.ascontiguousarray(crops, dtype=np.int32)
+        lrs = np.ascontiguousarray(lrs, dtype=np.float32)
+        steps, batch, three = crops.shape
+        if three != 3 or lrs.shape != (steps,):
+            raise ValueError("crops must be [steps][batch][3] and lrs [steps]")
+        losses = np.empty(steps, dtype=np.float64)
+        _check(_lib.dv_cnn_train_crops(self._h, _dptr(feats, "feats"), _dptr(targets, "targets"),
+                                       P, H, W, C.c_void_p(crops.ctypes.data), steps, batch,
+                                       int(crop), C.c_void_p(lrs.ctypes.data),
+                                       C.c_void_p(losses.ctypes.data), _stream_handle(self.stream)))
+        return losses
 
     def close(self):
         if self._h is not None and self._h.value:

@@ -50,23 +50,36 @@ def make_pair(seed, size=96, K=15, grid=(3, 3), n_tiles=(2, 2), overlap=16, n_ou
     return feat, xhat - feat[..., 0], y, psfs, sigma
 
 
-def train(cnn, pairs, steps, batch=8, crop=64, lr=1e-3, seed=0, log_every=0):
-    """Adam on random crops of the pairs; returns the loss history."""
+def train(cnn, pairs, steps, batch=8, crop=64, lr=1e-3, seed=0, log_every=0, schedule="const",
+          chunk=4000):
+    """Adam on random crops of the pairs; returns the loss history.  schedule:
+    "const" keeps lr; "cosine" anneals it as lr (1 + cos(pi t / steps)) / 2.
+    The crop table is drawn on the host (pair, then row, then column per crop)
+    and the steps run inside libdv, `chunk` steps per call."""
+    import math
     import torch
+    if schedule not in ("const", "cosine"):
+        raise ValueError(f"unknown schedule {schedule!r}")
+    H, W = pairs[0][1].shape
+    if any(t.shape != (H, W) for _, t in pairs):
+        raise ValueError("training pairs must share one size")
+    feats = torch.stack([f for f, _ in pairs]).contiguous()
+    targets = torch.stack([t for _, t in pairs]).contiguous()
     g = rng(30_000 + seed)
-    losses = []
+    crops = np.empty((steps, batch, 3), dtype=np.int32)
     for it in range(steps):
-        xs, ts = [], []
-        for _ in range(batch):
-            f, t = pairs[int(g.integers(len(pairs)))]
-            H, W = t.shape
-            r0 = int(g.integers(0, H - crop + 1))
-            c0 = int(g.integers(0, W - crop + 1))
-            xs.append(f[r0:r0 + crop, c0:c0 + crop])
-            ts.append(t[r0:r0 + crop, c0:c0 + crop])
-        xb = torch.stack(xs).contiguous()
-        tb = torch.stack(ts).contiguous()
-        losses.append(cnn.train_step(xb, tb, lr))
-        if log_every and (it + 1) % log_every == 0:
-            print(f"step {it + 1}: loss {np.mean(losses[-log_every:]):.3e}")
+        for b in range(batch):
+            crops[it, b, 0] = int(g.integers(len(pairs)))
+            crops[it, b, 1] = int(g.integers(0, H - crop + 1))
+            crops[it, b, 2] = int(g.integers(0, W - crop + 1))
+    t = np.arange(steps)
+    lrs = (np.full(steps, lr) if schedule == "const"
+           else 0.5 * lr * (1.0 + np.cos(math.pi * t / max(steps, 1))))
+    lrs = np.maximum(lrs, 1e-3 * lr).astype(np.float32)
+    losses = []
+    for s0 in range(0, steps, chunk):
+        s1 = min(steps, s0 + chunk)
+        losses.extend(cnn.train_crops(feats, targets, crops[s0:s1], crop, lrs[s0:s1]).tolist())
+        if log_every:
+            print(f"step {s1}: loss {np.mean(losses[-log_every:]):.3e}")
     return losses

@@ -89,6 +89,39 @@ def test_adam_step_matches_oracle(env):
     net.close()
 
 
+def test_train_crops_equals_single_steps(env):
+    """dv_cnn_train_crops (crop gather and the step loop inside libdv, no host
+    synchronisation) gives the same parameters and losses, bit for bit, as one
+    dv_cnn_train_step per step on the same crops; bad crops are refused."""
+    torch, dv = env
+    g = np.random.default_rng(5)
+    P, H, W, crop, batch, steps = 3, 40, 36, 16, 4, 6
+    feats = torch.from_numpy(g.uniform(0, 1, (P, H, W, 5)).astype(np.float32)).cuda()
+    targets = torch.from_numpy(g.uniform(-0.2, 0.2, (P, H, W)).astype(np.float32)).cuda()
+    crops = np.stack([g.integers(0, P, (steps, batch)), g.integers(0, H - crop + 1, (steps, batch)),
+                      g.integers(0, W - crop + 1, (steps, batch))], axis=-1).astype(np.int32)
+    lrs = np.linspace(2e-3, 5e-4, steps).astype(np.float32)
+    a, b = dv.Cnn(seed=3), dv.Cnn(seed=3)
+    la = a.train_crops(feats, targets, crops, crop, lrs)
+    lb = []
+    for t in range(steps):
+        xb = torch.stack([feats[p, r:r + crop, c:c + crop] for p, r, c in crops[t]]).contiguous()
+        tb = torch.stack([targets[p, r:r + crop, c:c + crop] for p, r, c in crops[t]]).contiguous()
+        lb.append(b.train_step(xb, tb, float(lrs[t])))
+    pa, sa = a.get_params()
+    pb, sb = b.get_params()
+    assert sa == sb == steps
+    np.testing.assert_array_equal(pa, pb)
+    np.testing.assert_array_equal(la, np.array(lb))
+    bad = crops.copy()
+    bad[2, 1, 1] = H - crop + 1
+    with pytest.raises(dv.DVError):
+        a.train_crops(feats, targets, bad, crop, lrs)
+    assert a.get_params()[1] == steps     # refused before any step
+    a.close()
+    b.close()
+
+
 def test_features_match_oracle(env):
     torch, dv = env
     g = np.random.default_rng(3)
