@@ -78,7 +78,19 @@ typedef enum dv_weight_kind {
   /* Caller-given separable profiles weights_r [G_r][hy+K-1] and
    * weights_c [G_c][wy+K-1]; at most two neighbouring grid points may be
    * nonzero at any coordinate (first-order interpolation). */
-  DV_WEIGHTS_SEPARABLE = 1
+  DV_WEIGHTS_SEPARABLE = 1,
+  /* One PSF per block, the paper's own layout (Sec. III-A, III-C): the PSF
+   * grid is the tile grid (grid_r = n_tr, grid_c = n_tc) and tile (tr, tc)
+   * blurs with PSF (tr, tc) alone, weight 1 on the whole tile (the local
+   * operators H_i = C_i H_i of Sec. III-A).  Without explicit tile bounds,
+   * x-tile i spans the grid points i - 1 .. i + 1 of the bilinear grid
+   * (c_a = a (n - 1)/(G - 1)): [ceil(c_{i-1}), ceil(c_{i+1})) with c_{-1} = 0 and
+   * c_G = n; the y-block is the x-tile less K - 1 at its end.  Neighbours then
+   * overlap by half a block and the consensus weights omega_i are the
+   * first-order interpolation tents.  dv_apply_H / dv_apply_Ht and the warm
+   * start use the bilinear interpolation of the same PSFs (the paper's data
+   * model, Sec. II-B).  No weight arrays. */
+  DV_WEIGHTS_PER_TILE = 2
 } dv_weight_kind;
 
 /* How H and H^T are computed; all give the same operator. */

@@ -60,6 +60,14 @@ Readings taken where the paper is silent, ambiguous or garbled:
  R10 Noise weights W: 1 for uniform Gaussian noise, so lambda is relative to
      the unweighted data term; a per-pixel W (0 for unmeasured pixels) may be
      given.
+ R11 One PSF per block (weights="per_tile", the paper's own layout, Sec.
+     III-A and III-C): the PSF grid is the tile grid and tile (tr, tc) blurs
+     with PSF (tr, tc) alone, weight 1 on the whole tile; its step uses L_H of
+     that PSF alone.  Blocks: G equal cells per axis of the x grid, x-tile i
+     spanning cells i - 1 .. i + 1 (clipped to the image), the y-block being the
+     x-tile less K - 1 rows (columns) at its end.  Neighbours share one cell,
+     half an interior block, and with R4 the consensus weights become the
+     first-order interpolation tents of the paper.
 
 Pins: every function here is checked by the "not gpu" tests against closed
 forms, library routines on special cases, invariants or brute force; none is
@@ -325,8 +333,39 @@ def make_layout(hy, wy, K, n_tr, n_tc, overlap, yrows=None, ycols=None) -> Layou
     return Layout(hy, wy, K, list(map(tuple, yrows)), list(map(tuple, ycols)))
 
 
+def paper_blocks(ny: int, K: int, G: int):
+    """[start, end) y-blocks of reading R11 on one axis: x-tile i covers cells
+    i - 1 .. i + 1 of G equal cells of the n = ny + K - 1 x coordinates."""
+    n = ny + K - 1
+    cell = n / G
+    out = []
+    for i in range(G):
+        x0 = 0 if i == 0 else int(np.floor((i - 0.5) * cell + 1e-9))
+        x1 = n if i == G - 1 else int(np.floor((i + 1.5) * cell + 1e-9))
+        out.append((x0, x1 - (K - 1)))
+    return out
+
+
+def paper_layout(hy, wy, K, Gr, Gc) -> "Layout":
+    """Tile layout of reading R11 (one block per PSF grid point)."""
+    return Layout(hy, wy, K, paper_blocks(hy, K, Gr), paper_blocks(wy, K, Gc))
+
+
+def tile_operator(layout: "Layout", tr, tc, psfs, weights):
+    """(PSFs, row weights, column weights) of tile (tr, tc)'s operator H_i:
+    the interpolated operator restricted to the tile, or with
+    weights == "per_tile" its own PSF alone with weight 1 (reading R11)."""
+    if isinstance(weights, str):
+        assert weights == "per_tile"
+        (r0, r1), (c0, c1) = layout.xrows[tr], layout.xcols[tc]
+        return psfs[tr:tr + 1, tc:tc + 1], np.ones((1, r1 - r0)), np.ones((1, c1 - c0))
+    wr, wc = weights
+    return (psfs,) + tile_weights(layout, tr, tc, wr, wc)
+
+
 def tile_step(layout: Layout, tr, tc, psfs, W, lam, gamma) -> float:
-    """tau_i of reading R5 (1 / Lipschitz bound of grad Phi_i)."""
+    """tau_i of reading R5 (1 / Lipschitz bound of grad Phi_i); psfs are the
+    PSFs of the tile's operator."""
     Wmax = 1.0 if W is None else float(np.max(W[layout.yslice(tr, tc)]))
     omax = float(layout.omega_r[tr].max() * layout.omega_c[tc].max())
     return 1.0 / (Wmax * lipschitz_bound_H(psfs) + 8.0 * lam + gamma * omax)
@@ -391,14 +430,16 @@ def tile_weights(layout: Layout, tr, tc, wr, wc):
 
 def objective(xhat, y, psfs, layout: Layout, lam, delta, W=None, weights=None):
     """F = sum_i [1/2 ||y_i - H_i C_i x||^2_W + lam phi(D C_i x)] (Eq. (4) at a
-    consensus point).  Returns (F, data term, prior sum)."""
-    wr, wc = weights if weights is not None else (bilinear_weights(layout.nx[0], psfs.shape[0]),
-                                                  bilinear_weights(layout.nx[1], psfs.shape[1]))
+    consensus point).  weights: (wr, wc) profiles, None (bilinear) or
+    "per_tile" (reading R11).  Returns (F, data term, prior sum)."""
+    if weights is None:
+        weights = (bilinear_weights(layout.nx[0], psfs.shape[0]),
+                   bilinear_weights(layout.nx[1], psfs.shape[1]))
     data = prior = 0.0
     for tr, tc in layout.tiles:
         xi = xhat[layout.xslice(tr, tc)]
-        wri, wci = tile_weights(layout, tr, tc, wr, wc)
-        ri = apply_H(xi, psfs, wri, wci) - y[layout.yslice(tr, tc)]
+        pi, wri, wci = tile_operator(layout, tr, tc, psfs, weights)
+        ri = apply_H(xi, pi, wri, wci) - y[layout.yslice(tr, tc)]
         Wi = 1.0 if W is None else W[layout.yslice(tr, tc)]
         data += 0.5 * float(np.sum(Wi * ri * ri))
         prior += huber_value(xi, delta)
@@ -421,25 +462,27 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
       x_i   <- Local-Solver(u_i; alpha_i, f_i)                    (all tiles)
       zbar  <- sum alpha_i (2 x_i - u_i) / sum alpha_i             (Lemma 1)
       u_i   <- u_i + rho (zbar - x_i)
-    repeated n_outer times.  Returns (x_hat, SolveInfo)."""
+    repeated n_outer times.  weights: (wr, wc) profiles, None (bilinear) or
+    "per_tile" (reading R11).  Returns (x_hat, SolveInfo)."""
     K = psfs.shape[2]
     nxr, nxc = layout.nx
-    wr, wc = weights if weights is not None else (bilinear_weights(nxr, psfs.shape[0]),
-                                                  bilinear_weights(nxc, psfs.shape[1]))
+    if weights is None:
+        weights = (bilinear_weights(nxr, psfs.shape[0]), bilinear_weights(nxc, psfs.shape[1]))
+    ops = [tile_operator(layout, tr, tc, psfs, weights) for tr, tc in layout.tiles]
     x0 = start_image(y, K) if x0 is None else np.asarray(x0, dtype=np.float64)
     tiles = layout.tiles
     xs = [x0[layout.xslice(tr, tc)].copy() for tr, tc in tiles]
     us = [x.copy() for x in xs]
     alphas = [gamma * layout.omega(tr, tc) for tr, tc in tiles]
-    taus = [tile_step(layout, tr, tc, psfs, W, lam, gamma) for tr, tc in tiles]
+    taus = [tile_step(layout, tr, tc, op[0], W, lam, gamma) for op, (tr, tc) in zip(ops, tiles)]
     info = SolveInfo(taus=taus)
     zprev = x0
     for k in range(n_outer):
         ni = n_inner + k * inner_increment
         for n, (tr, tc) in enumerate(tiles):
-            wri, wci = tile_weights(layout, tr, tc, wr, wc)
+            pi, wri, wci = ops[n]
             Wi = None if W is None else W[layout.yslice(tr, tc)]
-            xs[n] = local_solve(xs[n], us[n], y[layout.yslice(tr, tc)], Wi, psfs, wri, wci,
+            xs[n] = local_solve(xs[n], us[n], y[layout.yslice(tr, tc)], Wi, pi, wri, wci,
                                 alphas[n], lam, delta, taus[n], ni)
         zbar = consensus_average(layout, [2.0 * x - u for x, u in zip(xs, us)], alphas)
         info.primal.append(float(np.sqrt(sum(np.sum((x - zbar[layout.xslice(tr, tc)]) ** 2)
@@ -449,6 +492,6 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
         us = [u + rho * (zbar[layout.xslice(tr, tc)] - x) for u, x, (tr, tc) in zip(us, xs, tiles)]
         if history:
             info.objective.append(objective(assemble(layout, xs), y, psfs, layout, lam, delta,
-                                            W, (wr, wc))[0])
+                                            W, weights)[0])
     info.xs, info.us = xs, us
     return assemble(layout, xs), info

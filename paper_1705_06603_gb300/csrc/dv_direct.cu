@@ -151,11 +151,11 @@ __global__ void __launch_bounds__(NT) direct_H_kernel(const OpArgs A) {
       __syncthreads();
       for (int e = tid; e < ROWS; e += NT) {
         const int R = wi.r0 + e;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], a) : 0.f;
+        sWr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], a) : 0.f;
       }
       for (int e = tid; e < SP; e += NT) {
         const int C = wi.c0 + e;
-        sWc[e] = (e < TN + K - 1 && C < td.nxc) ? wsel(A.wcol[td.xc0 + C], b) : 0.f;
+        sWc[e] = (e < TN + K - 1 && C < td.nxc) ? wsel(A.wcol[td.wc0 + C], b) : 0.f;
       }
       const float* f = A.psf + (size_t)(a * A.Gc + b) * K * KP;
       for (int e = tid; e < K * KP; e += NT) sF[e] = f[e];
@@ -274,10 +274,10 @@ __global__ void __launch_bounds__(NT) direct_Ht_kernel(const OpArgs A) {
       float wr[RT], wc[CT];
 #pragma unroll
       for (int q = 0; q < RT; ++q)
-        wr[q] = (R0 + q < td.nxr) ? wsel(A.wrow[td.xr0 + R0 + q], a) : 0.f;
+        wr[q] = (R0 + q < td.nxr) ? wsel(A.wrow[td.wr0 + R0 + q], a) : 0.f;
 #pragma unroll
       for (int c = 0; c < CT; ++c)
-        wc[c] = (C0 + c < td.nxc) ? wsel(A.wcol[td.xc0 + C0 + c], b) : 0.f;
+        wc[c] = (C0 + c < td.nxc) ? wsel(A.wcol[td.wc0 + C0 + c], b) : 0.f;
 #pragma unroll
       for (int q = 0; q < RT; ++q)
 #pragma unroll

@@ -339,8 +339,8 @@ __global__ void __launch_bounds__(NT, 1) fft_H_kernel(const OpArgs A) {
       for (int e = threadIdx.x; e < S; e += NT) {
         const int R = wi.r0 + e, C = wi.c0 + e;
         const bool rin = R < td.nxr, cin = C < td.nxc;
-        const WTab tr = rin ? A.wrow[td.xr0 + R] : WTab{0, 0.f, 0.f, 0};
-        const WTab tc = cin ? A.wcol[td.xc0 + C] : WTab{0, 0.f, 0.f, 0};
+        const WTab tr = rin ? A.wrow[td.wr0 + R] : WTab{0, 0.f, 0.f, 0};
+        const WTab tc = cin ? A.wcol[td.wc0 + C] : WTab{0, 0.f, 0.f, 0};
         sw[0][e] = rin ? wsel(tr, a1) : 0.f;
         sw[1][e] = cin ? wsel(tc, b1) : 0.f;
         sw[2][e] = (rin && two) ? wsel(tr, a2) : 0.f;
@@ -470,8 +470,8 @@ __global__ void __launch_bounds__(NT, 1) fft_Ht_kernel(const OpArgs A) {
       for (int e = threadIdx.x; e < S; e += NT) {
         const int R = wi.r0 + e, C = wi.c0 + e;
         const bool rin = e < b && R < td.nxr, cin = e < b && C < td.nxc;
-        const WTab tr = rin ? A.wrow[td.xr0 + R] : WTab{0, 0.f, 0.f, 0};
-        const WTab tc = cin ? A.wcol[td.xc0 + C] : WTab{0, 0.f, 0.f, 0};
+        const WTab tr = rin ? A.wrow[td.wr0 + R] : WTab{0, 0.f, 0.f, 0};
+        const WTab tc = cin ? A.wcol[td.wc0 + C] : WTab{0, 0.f, 0.f, 0};
         sw[0][e] = rin ? wsel(tr, a1) : 0.f;
         sw[1][e] = cin ? wsel(tc, b1) : 0.f;
         sw[2][e] = (rin && two) ? wsel(tr, a2) : 0.f;

@@ -46,7 +46,8 @@ struct TileDesc {
   int32_t omr_off, omc_off;  // offsets of this tile's consensus profiles
   int32_t tr, tc;
   float tau;             // local projected-gradient step
-  int32_t pad[3];
+  int32_t wr0, wc0;      // index of x-tile row / column 0 in the weight tables
+  int32_t pad;
 };
 static_assert(sizeof(TileDesc) == 80, "TileDesc layout");
 

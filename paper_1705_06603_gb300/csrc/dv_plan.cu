@@ -171,9 +171,40 @@ void active_range(const std::vector<WTab>& tab, int lo, int hi, int& amin, int& 
 struct Layout {
   std::vector<int> yr0, yr1, yc0, yc1;
   std::vector<std::vector<double>> omr, omc;
+  // weight tables: the global x grid first, then (one PSF per tile) one table
+  // per tile row / column; wr0[tr] / wc0[tc] = index of the tile's x row /
+  // column 0 in them
   std::vector<WTab> wrow, wcol;
+  std::vector<int> wr0, wc0;
   std::vector<double> tau;
 };
+
+// The paper's blocks on one axis (Sec. III-C) for one PSF per block: G equal
+// cells of the x axis (n = ny + K - 1 coordinates), x-tile i spanning cells
+// i - 1 .. i + 1, i.e. [(2i - 1) n / 2G, (2i + 3) n / 2G) clipped to [0, n);
+// y-block i = the x-tile less K - 1 coordinates at its end.
+void grid_blocks(int ny, int K, int G, std::vector<int>& s, std::vector<int>& e) {
+  const int64_t n = (int64_t)ny + K - 1;
+  s.assign(G, 0);
+  e.assign(G, ny);
+  for (int i = 0; i < G; ++i) {
+    const int64_t x0 = std::max<int64_t>(0, (2 * (int64_t)i - 1) * n / (2 * G));
+    const int64_t x1 = std::min<int64_t>(n, (2 * (int64_t)i + 3) * n / (2 * G));
+    s[i] = (int)x0;
+    e[i] = i == G - 1 ? ny : (int)(x1 - (K - 1));
+  }
+}
+
+// One table per tile row (or column): every coordinate of the x-tile gives
+// weight 1 to the tile's own PSF row (column) and 0 to the others.
+void tile_tables(const std::vector<int>& y0, const std::vector<int>& y1, int K,
+                 std::vector<WTab>& tab, std::vector<int>& off) {
+  off.resize(y0.size());
+  for (size_t t = 0; t < y0.size(); ++t) {
+    off[t] = (int)tab.size();
+    for (int c = 0; c < y1[t] - y0[t] + K - 1; ++c) tab.push_back(WTab{(int)t, 1.f, 0.f, 0});
+  }
+}
 
 dv_status validate_and_layout(const dv_problem* p, Layout& L) {
   if (!p) return fail(DV_ERR_INVALID_ARG, "problem is NULL");
@@ -192,12 +223,18 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
   if (!(p->rho > 0.0 && p->rho < 2.0)) return fail(DV_ERR_INVALID_ARG, "rho must be in (0, 2)");
   if (p->n_outer < 0 || p->n_inner < 0 || p->inner_increment < 0)
     return fail(DV_ERR_INVALID_ARG, "iteration counts must be >= 0");
-  if (p->weight_kind != DV_WEIGHTS_BILINEAR && p->weight_kind != DV_WEIGHTS_SEPARABLE)
+  if (p->weight_kind != DV_WEIGHTS_BILINEAR && p->weight_kind != DV_WEIGHTS_SEPARABLE &&
+      p->weight_kind != DV_WEIGHTS_PER_TILE)
     return fail(DV_ERR_INVALID_ARG, "unknown weight_kind %d", p->weight_kind);
   if (p->weight_kind == DV_WEIGHTS_SEPARABLE && (!p->weights_r || !p->weights_c))
     return fail(DV_ERR_INVALID_ARG, "separable weights need weights_r and weights_c");
-  if (p->weight_kind == DV_WEIGHTS_BILINEAR && (p->weights_r || p->weights_c))
-    return fail(DV_ERR_INVALID_ARG, "bilinear weights take no weight arrays");
+  if (p->weight_kind != DV_WEIGHTS_SEPARABLE && (p->weights_r || p->weights_c))
+    return fail(DV_ERR_INVALID_ARG, "bilinear and per-tile weights take no weight arrays");
+  const bool per_tile = p->weight_kind == DV_WEIGHTS_PER_TILE;
+  if (per_tile && (p->grid_r != p->n_tr || p->grid_c != p->n_tc))
+    return fail(DV_ERR_INVALID_ARG,
+                "one PSF per tile needs the PSF grid (%d x %d) to equal the tile grid (%d x %d)",
+                p->grid_r, p->grid_c, p->n_tr, p->n_tc);
   if (p->precision != DV_PREC_FP32 && p->precision != DV_PREC_TF32 &&
       p->precision != DV_PREC_BF16)
     return fail(DV_ERR_INVALID_ARG, "unknown precision %d", p->precision);
@@ -220,8 +257,13 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
   } else {
     if (p->n_tr > p->hy || p->n_tc > p->wy)
       return fail(DV_ERR_INVALID_ARG, "more tiles than pixels");
-    uniform_blocks(p->hy, p->n_tr, p->overlap, L.yr0, L.yr1);
-    uniform_blocks(p->wy, p->n_tc, p->overlap, L.yc0, L.yc1);
+    if (per_tile) {
+      grid_blocks(p->hy, K, p->n_tr, L.yr0, L.yr1);
+      grid_blocks(p->wy, K, p->n_tc, L.yc0, L.yc1);
+    } else {
+      uniform_blocks(p->hy, p->n_tr, p->overlap, L.yr0, L.yr1);
+      uniform_blocks(p->wy, p->n_tc, p->overlap, L.yc0, L.yc1);
+    }
   }
   DV_TRY(check_blocks("row", p->hy, K, L.yr0, L.yr1));
   DV_TRY(check_blocks("column", p->wy, K, L.yc0, L.yc1));
@@ -236,6 +278,13 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
                       p->weight_kind == DV_WEIGHTS_SEPARABLE ? p->weights_r : nullptr, L.wrow));
   DV_TRY(weight_table("column", nxc, p->grid_c,
                       p->weight_kind == DV_WEIGHTS_SEPARABLE ? p->weights_c : nullptr, L.wcol));
+  if (per_tile) {
+    tile_tables(L.yr0, L.yr1, K, L.wrow, L.wr0);
+    tile_tables(L.yc0, L.yc1, K, L.wcol, L.wc0);
+  } else {
+    L.wr0 = L.yr0;
+    L.wc0 = L.yc0;
+  }
 
   // Lipschitz bound of the data gradient: ||H||^2 <= (max_p sum|h_p|)(sum_k max_p |h_p(k)|)
   const int G = p->grid_r * p->grid_c, KK = K * K;
@@ -252,7 +301,13 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     colmax = std::max(colmax, s);
   }
   for (int k = 0; k < KK; ++k) rowsum += kmax[k];
-  const double LH = colmax * rowsum;
+  // one PSF per tile: the tile's own PSF alone, (sum |h_i|)^2
+  auto tile_lh = [&](int tr, int tc) {
+    if (!per_tile) return colmax * rowsum;
+    double s1 = 0.0;
+    for (int k = 0; k < KK; ++k) s1 += std::fabs((double)p->psfs[((size_t)tr * p->n_tc + tc) * KK + k]);
+    return s1 * s1;
+  };
   L.tau.assign((size_t)p->n_tr * p->n_tc, 0.0);
   for (int tr = 0; tr < p->n_tr; ++tr) {
     for (int tc = 0; tc < p->n_tc; ++tc) {
@@ -269,7 +324,8 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
       }
       const double omax = *std::max_element(L.omr[tr].begin(), L.omr[tr].end()) *
                           *std::max_element(L.omc[tc].begin(), L.omc[tc].end());
-      L.tau[(size_t)tr * p->n_tc + tc] = 1.0 / (wmax * LH + 8.0 * p->lambda + p->gamma * omax);
+      L.tau[(size_t)tr * p->n_tc + tc] =
+          1.0 / (wmax * tile_lh(tr, tc) + 8.0 * p->lambda + p->gamma * omax);
     }
   }
   return DV_OK;
@@ -315,10 +371,10 @@ void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const La
         w.r0 = r0;
         w.c0 = c0;
         if (max_rows > 0) w.pad = (int)std::min<int64_t>(bmt, round_up(nr - r0, 16));
-        // global x coordinate range whose weights matter
-        const int rlo = td.xr0 + r0, clo = td.xc0 + c0;
-        const int rhi = td.xr0 + std::min(r0 + bmt, nr) + (adjoint ? 0 : K - 1);
-        const int chi = td.xc0 + std::min(c0 + bn, nc) + (adjoint ? 0 : K - 1);
+        // weight-table coordinate range whose weights matter
+        const int rlo = td.wr0 + r0, clo = td.wc0 + c0;
+        const int rhi = td.wr0 + std::min(r0 + bmt, nr) + (adjoint ? 0 : K - 1);
+        const int chi = td.wc0 + std::min(c0 + bn, nc) + (adjoint ? 0 : K - 1);
         active_range(L.wrow, rlo, rhi, w.a_lo, w.a_hi);
         active_range(L.wcol, clo, chi, w.b_lo, w.b_hi);
         out.push_back(w);
@@ -613,6 +669,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
       d.omc_off = omc_off[tc];
       d.tr = tr;
       d.tc = tc;
+      d.wr0 = L.wr0[tr];
+      d.wc0 = L.wc0[tc];
       d.tau = (float)L.tau[(size_t)tr * P->n_tc + tc];
       P->max_nxr = std::max(P->max_nxr, d.nxr);
       P->max_nxc = std::max(P->max_nxc, d.nxc);

@@ -337,11 +337,11 @@ __global__ void __launch_bounds__(NTH, 1) tc_H_kernel(const OpArgs A) {
       float* wc = sWc + ab * G::COLS;
       for (int e = tid; e < G::ROWS; e += 32 * NWE) {
         const int R = wi.r0 + e;
-        wr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
+        wr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
       }
       for (int e = tid; e < G::COLS; e += 32 * NWE) {
         const int C = wi.c0 + e;
-        wc[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+        wc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
       }
       named_sync();
       unsigned char* abuf = areg + (size_t)ab * G::ABYTES;
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_Ht_kernel(const OpArgs A) {
       for (int e = tid; e < nb * BN; e += 32 * NWE) {
         const int bi = e / BN, j = e - bi * BN;
         const int C = wi.c0 + j;
-        sWcol[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], wi.b_lo + bi) : 0.f;
+        sWcol[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], wi.b_lo + bi) : 0.f;
       }
     }
     named_sync();
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_Ht_kernel(const OpArgs A) {
       }
       tc_fence_after();
       const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      const float wr = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
+      const float wr = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         float v[32];
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(NTH, 2) tc_Ht_kernel(const OpArgs A) {
             wc = wcs[j];
           } else {
             const int C = wi.c0 + 32 * h + j;
-            wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+            wc = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
           }
           g[32 * h + j] = fmaf(wr * wc, v[j], g[32 * h + j]);
         }

@@ -392,11 +392,11 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       sync_stage();   // the previous PSF's weights are no longer read
       for (int e = tid; e < G::ROWS; e += NT) {
         const int R = wi.r0 + e;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], ga) : 0.f;
+        sWr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
       }
       for (int e = tid; e < G::COLS; e += NT) {
         const int C = wi.c0 + e;
-        sWc[e] = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+        sWc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
       }
       sync_stage();
       // S buffer p & 1 was last read by PSF p - 2
@@ -615,12 +615,12 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
       // column weight of the PSF and, for the first PSF of a grid row, the
       // row weights (buffer ai & 1: the fold of the previous grid row reads
       // the other one), fetched while its MMAs run
-      const float wc = C < td.nxc ? wsel(A.wcol[td.xc0 + C], gb) : 0.f;
+      const float wc = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
       float* wrow = sWr + (ai & 1) * G::NR;
       if (p % nb == 0)
         for (int e = tid; e < G::NR; e += NT) {
           const int R = wi.r0 + e;
-          wrow[e] = R < td.nxr ? wsel(A.wrow[td.xr0 + R], wi.a_lo + ai) : 0.f;
+          wrow[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], wi.a_lo + ai) : 0.f;
         }
       if (step)
         for (int k = 0; k < qper && qc < nck; ++k) q_chunk(32 * qc++);
@@ -782,7 +782,7 @@ int64_t tcT_kstep_ranges(const std::vector<TileDesc>& tiles, const std::vector<W
         const int gb = wi.b_lo + b;
         int lo = INT_MAX, hi = -1;
         for (int c = 0; c < span; ++c)
-          if (wsel(wcol[td.xc0 + wi.c0 + c], gb) != 0.f) {
+          if (wsel(wcol[td.wc0 + wi.c0 + c], gb) != 0.f) {
             lo = std::min(lo, c);
             hi = std::max(hi, c);
           }

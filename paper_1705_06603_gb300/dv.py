@@ -28,7 +28,7 @@ except OSError as e:  # pragma: no cover - depends on the machine
 
 DV_OK, DV_ERR_INVALID_ARG, DV_ERR_CUDA, DV_ERR_OOM, DV_ERR_TIMEOUT, DV_ERR_UNSUPPORTED = range(6)
 DV_PREC_FP32, DV_PREC_TF32, DV_PREC_BF16 = 0, 1, 2
-DV_WEIGHTS_BILINEAR, DV_WEIGHTS_SEPARABLE = 0, 1
+DV_WEIGHTS_BILINEAR, DV_WEIGHTS_SEPARABLE, DV_WEIGHTS_PER_TILE = 0, 1, 2
 DV_PATH_AUTO, DV_PATH_DIRECT, DV_PATH_FFT, DV_PATH_TENSOR = 0, 1, 2, 3
 KERNEL_H, KERNEL_HT_STEP, KERNEL_CONSENSUS = 0, 1, 2
 
@@ -167,8 +167,11 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
                  n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
                  use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1,
                  noise_sigma=0.0):
-    """Builds a dv_problem.  Returns (problem, keepalive) where keepalive holds
-    the host arrays the struct points to until dv_plan_create has copied them."""
+    """Builds a dv_problem.  weights: None (bilinear tents), (weights_r,
+    weights_c) separable profiles, or "per_tile" (one PSF per tile, the PSF
+    grid being the tile grid).  Returns (problem, keepalive) where keepalive
+    holds the host arrays the struct points to until dv_plan_create has copied
+    them."""
     p = dv_problem()
     _lib.dv_problem_init(C.byref(p))
     psfs = np.ascontiguousarray(psfs, dtype=np.float32)
@@ -178,7 +181,11 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
     keep = [psfs]
     p.hy, p.wy, p.grid_r, p.grid_c, p.K = hy, wy, Gr, Gc, K
     p.psfs = psfs.ctypes.data_as(_fp)
-    if weights is not None:
+    if isinstance(weights, str):
+        if weights != "per_tile":
+            raise ValueError(f"unknown weights {weights!r}")
+        p.weight_kind = DV_WEIGHTS_PER_TILE
+    elif weights is not None:
         wr = np.ascontiguousarray(weights[0], dtype=np.float32)
         wc = np.ascontiguousarray(weights[1], dtype=np.float32)
         keep += [wr, wc]

@@ -134,3 +134,31 @@ def test_every_operator_path_is_a_valid_request(dv, path, prec):
     psfs = np.full((1, 1, 9, 9), 1 / 81.0)
     p, keep = dv.make_problem(20, 20, psfs, path=path, precision=prec)
     dv.dv_layout_query(p)
+
+
+@pytest.mark.parametrize("hy,wy,K,G", [(128, 128, 9, (3, 3)), (2048, 2048, 31, (8, 8)),
+                                       (200, 150, 15, (4, 2)), (97, 301, 9, (1, 5)),
+                                       (8192, 8192, 63, (16, 16))])
+def test_paper_layout_and_steps_match_oracle(dv, hy, wy, K, G):
+    """One PSF per tile (reading R11): the library's blocks and per-tile steps
+    equal the oracle's independent construction."""
+    g = np.random.default_rng(K)
+    psfs = g.uniform(0.0, 1.0, (G[0], G[1], K, K)).astype(np.float32)
+    psfs /= psfs.sum(axis=(2, 3), keepdims=True)
+    p, keep = dv.make_problem(hy, wy, psfs, n_tiles=G, weights="per_tile", lam=2e-3, gamma=0.3)
+    rows, cols, tau = dv.dv_layout_query(p)
+    lay = O.paper_layout(hy, wy, K, *G)
+    assert rows == [tuple(r) for r in lay.yrows]
+    assert cols == [tuple(c) for c in lay.ycols]
+    ps = psfs.astype(np.float64)
+    for tr, tc in lay.tiles:
+        op = O.tile_operator(lay, tr, tc, ps, "per_tile")
+        ref = O.tile_step(lay, tr, tc, op[0], None, 2e-3, 0.3)
+        assert abs(tau[tr, tc] - ref) <= 1e-12 * ref
+
+
+def test_per_tile_weights_need_the_tile_grid(dv):
+    psfs = np.full((3, 3, 9, 9), 1.0 / 81, dtype=np.float32)
+    p, keep = dv.make_problem(128, 128, psfs, n_tiles=(2, 3), weights="per_tile")
+    with pytest.raises(dv.DVError, match="tile grid"):
+        dv.dv_layout_query(p)

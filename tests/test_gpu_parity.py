@@ -345,6 +345,39 @@ def test_tensor_solve_close_to_oracle(env, prec):
     plan.close()
 
 
+@pytest.mark.parametrize("path,prec,tol", [(DIRECT, 0, 1e-5), (FFT, 0, 1e-5), (TENSOR, BF16, 1e-2),
+                                           (TENSOR, TF32, 2e-3)])
+def test_paper_mode_solve_matches_oracle(env, path, prec, tol):
+    """One PSF per block, the paper's own layout (reading R11): the 3 x 3 PSF
+    grid of the 128^2 workload gives 3 x 3 blocks that overlap by half, each
+    blurred by its own PSF; the increasing inner schedule 3 + 2k of Sec. IV-B.
+    The GPU solve and its objective match the oracle on every operator path,
+    and dv_apply_H keeps the interpolated model."""
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    G = psfs.shape[:2]
+    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=G, weights="per_tile", lam=w.lam, delta=w.delta,
+                   gamma=w.gamma, rho=w.rho, n_outer=4, n_inner=3, inner_increment=2, path=path,
+                   precision=prec)
+    assert plan.info.path == path
+    xd, st = plan.solve(torch.from_numpy(y).cuda())
+    torch.cuda.synchronize()
+    lay = O.paper_layout(w.hy, w.wy, w.K, *G)
+    ps, y64 = psfs.astype(np.float64), y.astype(np.float64)
+    xr, info = O.solve(y64, ps, lay, w.lam, w.delta, w.gamma, w.rho, 4, 3, inner_increment=2,
+                       weights="per_tile")
+    assert rel_l2(xd.cpu().numpy(), xr) <= tol
+    F = O.objective(xr, y64, ps, lay, w.lam, w.delta, weights="per_tile")[0]
+    assert abs(st["objective"] - F) <= tol * F
+    assert st["inner_done"] == 3 + 5 + 7 + 9
+    g = np.random.default_rng(9)
+    x = g.uniform(0, 1, plan.nx).astype(np.float32)
+    hx = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    wr, wc = O.bilinear_weights(plan.nx[0], G[0]), O.bilinear_weights(plan.nx[1], G[1])
+    assert rel_l2(hx, O.apply_H(x.astype(np.float64), ps, wr, wc)) <= max(tol, 1e-5)
+    plan.close()
+
+
 def test_grouped_tensor_solve_is_bit_identical_to_eager(env):
     """The captured local solve of the tensor path runs its tile groups on
     concurrent streams; the result equals one launch per operator over every
