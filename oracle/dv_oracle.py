@@ -60,7 +60,7 @@ Readings taken where the paper is silent, ambiguous or garbled:
  R10 Noise weights W: 1 for uniform Gaussian noise, so lambda is relative to
      the unweighted data term; a per-pixel W (0 for unmeasured pixels) may be
      given.
- R11 One PSF per block (weights="per_tile", the paper's own layout, Sec.
+ R18 One PSF per block (weights="per_tile", the paper's own layout, Sec.
      III-A and III-C): the PSF grid is the tile grid and tile (tr, tc) blurs
      with PSF (tr, tc) alone, weight 1 on the whole tile; its step uses L_H of
      that PSF alone.  Blocks: G equal cells per axis of the x grid, x-tile i
@@ -334,7 +334,7 @@ def make_layout(hy, wy, K, n_tr, n_tc, overlap, yrows=None, ycols=None) -> Layou
 
 
 def paper_blocks(ny: int, K: int, G: int):
-    """[start, end) y-blocks of reading R11 on one axis: x-tile i covers cells
+    """[start, end) y-blocks of reading R18 on one axis: x-tile i covers cells
     i - 1 .. i + 1 of G equal cells of the n = ny + K - 1 x coordinates."""
     n = ny + K - 1
     cell = n / G
@@ -347,14 +347,14 @@ def paper_blocks(ny: int, K: int, G: int):
 
 
 def paper_layout(hy, wy, K, Gr, Gc) -> "Layout":
-    """Tile layout of reading R11 (one block per PSF grid point)."""
+    """Tile layout of reading R18 (one block per PSF grid point)."""
     return Layout(hy, wy, K, paper_blocks(hy, K, Gr), paper_blocks(wy, K, Gc))
 
 
 def tile_operator(layout: "Layout", tr, tc, psfs, weights):
     """(PSFs, row weights, column weights) of tile (tr, tc)'s operator H_i:
     the interpolated operator restricted to the tile, or with
-    weights == "per_tile" its own PSF alone with weight 1 (reading R11)."""
+    weights == "per_tile" its own PSF alone with weight 1 (reading R18)."""
     if isinstance(weights, str):
         assert weights == "per_tile"
         (r0, r1), (c0, c1) = layout.xrows[tr], layout.xcols[tc]
@@ -431,7 +431,7 @@ def tile_weights(layout: Layout, tr, tc, wr, wc):
 def objective(xhat, y, psfs, layout: Layout, lam, delta, W=None, weights=None):
     """F = sum_i [1/2 ||y_i - H_i C_i x||^2_W + lam phi(D C_i x)] (Eq. (4) at a
     consensus point).  weights: (wr, wc) profiles, None (bilinear) or
-    "per_tile" (reading R11).  Returns (F, data term, prior sum)."""
+    "per_tile" (reading R18).  Returns (F, data term, prior sum)."""
     if weights is None:
         weights = (bilinear_weights(layout.nx[0], psfs.shape[0]),
                    bilinear_weights(layout.nx[1], psfs.shape[1]))
@@ -463,7 +463,7 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
       zbar  <- sum alpha_i (2 x_i - u_i) / sum alpha_i             (Lemma 1)
       u_i   <- u_i + rho (zbar - x_i)
     repeated n_outer times.  weights: (wr, wc) profiles, None (bilinear) or
-    "per_tile" (reading R11).  Returns (x_hat, SolveInfo)."""
+    "per_tile" (reading R18).  Returns (x_hat, SolveInfo)."""
     K = psfs.shape[2]
     nxr, nxc = layout.nx
     if weights is None:

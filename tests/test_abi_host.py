@@ -140,7 +140,7 @@ def test_every_operator_path_is_a_valid_request(dv, path, prec):
                                        (200, 150, 15, (4, 2)), (97, 301, 9, (1, 5)),
                                        (8192, 8192, 63, (16, 16))])
 def test_paper_layout_and_steps_match_oracle(dv, hy, wy, K, G):
-    """One PSF per tile (reading R11): the library's blocks and per-tile steps
+    """One PSF per tile (reading R18): the library's blocks and per-tile steps
     equal the oracle's independent construction."""
     g = np.random.default_rng(K)
     psfs = g.uniform(0.0, 1.0, (G[0], G[1], K, K)).astype(np.float32)

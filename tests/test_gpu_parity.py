@@ -348,7 +348,7 @@ def test_tensor_solve_close_to_oracle(env, prec):
 @pytest.mark.parametrize("path,prec,tol", [(DIRECT, 0, 1e-5), (FFT, 0, 1e-5), (TENSOR, BF16, 1e-2),
                                            (TENSOR, TF32, 2e-3)])
 def test_paper_mode_solve_matches_oracle(env, path, prec, tol):
-    """One PSF per block, the paper's own layout (reading R11): the 3 x 3 PSF
+    """One PSF per block, the paper's own layout (reading R18): the 3 x 3 PSF
     grid of the 128^2 workload gives 3 x 3 blocks that overlap by half, each
     blurred by its own PSF; the increasing inner schedule 3 + 2k of Sec. IV-B.
     The GPU solve and its objective match the oracle on every operator path,

@@ -1,4 +1,4 @@
-"""Pins of the oracle's one-PSF-per-block mode (reading R11, Sec. III-A and
+"""Pins of the oracle's one-PSF-per-block mode (reading R18, Sec. III-A and
 III-C): the block geometry, the tile operator against scipy's valid
 convolution, the reduction to the interpolated model when every PSF is the
 same, and the consensus weights as first-order interpolation tents."""
