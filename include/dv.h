@@ -307,6 +307,21 @@ dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int
 dv_status dv_prior_value_noalloc(const float* x_dev, int32_t rows, int32_t cols, double delta,
                                  double* value_dev, void* stream);
 
+/* Image quality of x against a reference image, the measures of the
+ * paper's evaluation (Sec. V) on synthetic stand-ins: out_dev[0] = SNR =
+ * 10 log10(sum ref^2 / sum (x - ref)^2) dB over all pixels (+inf if x == ref),
+ * out_dev[1] = the mean structural similarity (Wang et al. 2004) over every
+ * 11 x 11 window inside the image: separable unit-sum Gaussian window of
+ * standard deviation 1.5, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with
+ * L = dynamic_range; local moments in FP32, sums in FP64 in a fixed order
+ * (deterministic).  x_dev, ref_dev: device float32 [rows][cols], rows and
+ * cols >= 11; work_dev: device scratch of dv_image_quality_workspace(rows,
+ * cols) doubles; out_dev: device, two doubles.  Stream-ordered: no
+ * allocation, no synchronisation. */
+int64_t dv_image_quality_workspace(int32_t rows, int32_t cols);
+dv_status dv_image_quality(const float* x_dev, const float* ref_dev, int32_t rows, int32_t cols,
+                           double dynamic_range, double* work_dev, double* out_dev, void* stream);
+
 /* Creates the warm-start network (width 32, depth 6 are the only supported
  * values) with He-normal weights drawn from seed; synchronises stream. */
 dv_status dv_cnn_create(int32_t width, int32_t depth, uint64_t seed, void* stream, dv_cnn** out);

@@ -60,6 +60,11 @@ Readings taken where the paper is silent, ambiguous or garbled:
  R10 Noise weights W: 1 for uniform Gaussian noise, so lambda is relative to
      the unweighted data term; a per-pixel W (0 for unmeasured pixels) may be
      given.
+ R19 Evaluation measures (Sec. V names SNR and SSIM, citing Wang et al.
+     2004, without formulas): SNR = 10 log10(||ref||^2 / ||x - ref||^2) dB over
+     all pixels; SSIM as Wang et al. define it, averaged over every 11 x 11
+     window inside the image (unit-sum Gaussian window of standard deviation
+     1.5, C1 = (0.01 L)^2, C2 = (0.03 L)^2, L the dynamic range).
  R18 One PSF per block (weights="per_tile", the paper's own layout, Sec.
      III-A and III-C): the PSF grid is the tile grid and tile (tr, tc) blurs
      with PSF (tr, tc) alone, weight 1 on the whole tile; its step uses L_H of
@@ -495,3 +500,40 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
                                             W, weights)[0])
     info.xs, info.us = xs, us
     return assemble(layout, xs), info
+
+
+# ---------------------------------------------------------------------------
+# Evaluation measures (Sec. V), reading R19
+# ---------------------------------------------------------------------------
+
+
+def snr_db(x: np.ndarray, ref: np.ndarray) -> float:
+    """10 log10(||ref||^2 / ||x - ref||^2)."""
+    x, ref = np.asarray(x, np.float64), np.asarray(ref, np.float64)
+    err = float(np.sum((x - ref) ** 2))
+    return float("inf") if err == 0.0 else 10.0 * np.log10(float(np.sum(ref * ref)) / err)
+
+
+def ssim_window() -> np.ndarray:
+    """11 x 11 circular Gaussian window, standard deviation 1.5, unit sum."""
+    t = np.arange(11) - 5.0
+    g = np.exp(-(t[:, None] ** 2 + t[None, :] ** 2) / (2 * 1.5 ** 2))
+    return g / g.sum()
+
+
+def ssim_map(x: np.ndarray, ref: np.ndarray, L: float = 1.0) -> np.ndarray:
+    """SSIM of every 11 x 11 window inside the image (one value per window
+    centre, shape (rows - 10, cols - 10)); local moments under ssim_window."""
+    from scipy.signal import correlate2d
+    x, ref = np.asarray(x, np.float64), np.asarray(ref, np.float64)
+    w = ssim_window()
+    mom = lambda a: correlate2d(a, w, mode="valid")
+    mx, mr = mom(x), mom(ref)
+    vx, vr, cxr = mom(x * x) - mx * mx, mom(ref * ref) - mr * mr, mom(x * ref) - mx * mr
+    c1, c2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    return (2 * mx * mr + c1) * (2 * cxr + c2) / ((mx * mx + mr * mr + c1) * (vx + vr + c2))
+
+
+def ssim(x: np.ndarray, ref: np.ndarray, L: float = 1.0) -> float:
+    """Mean SSIM over the windows inside the image."""
+    return float(np.mean(ssim_map(x, ref, L)))

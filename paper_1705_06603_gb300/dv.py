@@ -103,6 +103,8 @@ _sigs = {
     "dv_cnn_train_crops": (C.c_int, [_vp, _vp, _vp, C.c_int32, C.c_int32, C.c_int32, _vp,
                                      C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "dv_cnn_destroy": (C.c_int, [_vp]),
+    "dv_image_quality_workspace": (C.c_int64, [C.c_int32, C.c_int32]),
+    "dv_image_quality": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32, C.c_double, _vp, _vp, _vp]),
     "dv_plan_set_warmstart": (C.c_int, [_vp, _vp]),
     "dv_warmstart_features": (C.c_int, [_vp, _vp, _vp, _vp]),
     "dv_destroy": (C.c_int, [_vp]),
@@ -280,6 +282,33 @@ def dv_plan_kernel_time(plan, kind):
     ms, n = C.c_double(), C.c_int64()
     _check(_lib.dv_plan_kernel_time(plan, int(kind), C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def image_quality_async(x, ref, work, out, dynamic_range=1.0, stream=None):
+    """Stream-ordered dv_image_quality into out (float64 CUDA tensor of 2);
+    work: float64 CUDA tensor of dv_image_quality_workspace(rows, cols)."""
+    import torch
+    rows, cols = ref.shape
+    for t, name, n in ((work, "work", int(_lib.dv_image_quality_workspace(rows, cols))),
+                       (out, "out", 2)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.is_contiguous() and t.numel() >= n):
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor of >= {n} elements")
+    _check(_lib.dv_image_quality(_dptr(x, "x", (rows, cols)), _dptr(ref, "ref", (rows, cols)),
+                                 rows, cols, float(dynamic_range), C.c_void_p(work.data_ptr()),
+                                 C.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+
+def image_quality(x, ref, dynamic_range=1.0, stream=None):
+    """(SNR in dB, mean SSIM) of the 2-D float32 CUDA tensor x against ref."""
+    import torch
+    rows, cols = ref.shape
+    work = torch.empty(max(1, int(_lib.dv_image_quality_workspace(rows, cols))),
+                       dtype=torch.float64, device=ref.device)
+    out = torch.empty(2, dtype=torch.float64, device=ref.device)
+    image_quality_async(x, ref, work, out, dynamic_range, stream)
+    snr, ssim = out.cpu().tolist()
+    return snr, ssim
 
 
 def dv_prior_value_noalloc(x, delta, value, stream=None):

@@ -167,7 +167,7 @@ def test_checkpoint_resume_equals_uninterrupted(env):
 
 
 @pytest.mark.parametrize("case", ["one_tile", "no_inner", "no_outer", "uneven_tiles",
-                                  "noise_weights", "no_prior", "paper_schedule"])
+                                  "noise_weights", "no_prior", "paper_schedule", "independent"])
 def test_edge_cases_match_oracle(env, case):
     torch, dv = env
     g = np.random.default_rng(17)
@@ -201,6 +201,9 @@ def test_edge_cases_match_oracle(env, case):
     elif case == "paper_schedule":
         kw["inner_increment"] = 2
         okw["inner_increment"] = 2
+    elif case == "independent":
+        # Sec. V's "independent" method: tiles solved alone, then blended
+        kw.update(gamma=1e-9, n_outer=1, n_inner=40)
     plan = dv.Plan(hy, wy, psfs, **kw)
     xd, st = plan.solve(torch.from_numpy(y).cuda())
     xd = xd.cpu().numpy()
@@ -376,6 +379,29 @@ def test_paper_mode_solve_matches_oracle(env, path, prec, tol):
     wr, wc = O.bilinear_weights(plan.nx[0], G[0]), O.bilinear_weights(plan.nx[1], G[1])
     assert rel_l2(hx, O.apply_H(x.astype(np.float64), ps, wr, wc)) <= max(tol, 1e-5)
     plan.close()
+
+
+@pytest.mark.parametrize("shape,kind", [((11, 11), "uniform"), ((100, 77), "uniform"),
+                                        ((531, 1040), "uniform"), ((300, 257), "stars")])
+def test_image_quality_matches_oracle(env, shape, kind):
+    """dv_image_quality (SNR over all pixels, mean SSIM over the 11 x 11
+    windows, reading R19) against the FP64 oracle, on noise and on a blurred
+    star field with a small perturbation."""
+    torch, dv = env
+    g = np.random.default_rng(shape[0])
+    if kind == "uniform":
+        ref = g.uniform(0, 1, shape).astype(np.float32)
+        x = np.clip(ref + g.normal(0, 0.1, shape), 0, 1).astype(np.float32)
+    else:
+        from paper_1705_06603_gb300.synth import star_field
+        ref = star_field(shape, 5).astype(np.float32)
+        x = (ref + g.normal(0, 0.003, shape)).astype(np.float32)
+    snr, ssim = dv.image_quality(torch.from_numpy(x).cuda(), torch.from_numpy(ref).cuda())
+    x64, r64 = x.astype(np.float64), ref.astype(np.float64)
+    assert snr == pytest.approx(O.snr_db(x64, r64), rel=1e-9)
+    assert abs(ssim - O.ssim(x64, r64)) <= 2e-5
+    s2, q2 = dv.image_quality(torch.from_numpy(ref).cuda(), torch.from_numpy(ref).cuda())
+    assert s2 == float("inf") and abs(q2 - 1.0) <= 1e-5
 
 
 def test_grouped_tensor_solve_is_bit_identical_to_eager(env):
