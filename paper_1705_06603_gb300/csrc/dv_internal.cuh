@@ -126,7 +126,7 @@ struct OpArgs {
 };
 
 // One item of the consensus / assembly kernels: a rectangle of the global x
-// grid (at most 8 rows x 512 columns) over which the covering tiles do not
+// grid (at most 2048 pixels, at most 512 columns wide) over which the covering tiles do not
 // change, with per covering tile ("slot", tile rows outer, tile columns
 // inner): the stack offset of (r0, global column 0), the row pitch, and the
 // indices of global row 0 / column 0 in the consensus profiles.
@@ -173,7 +173,7 @@ cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float 
                              int* n_blocks_out);
 int consensus_blocks(int n_citems);
 // rows / columns of the largest consensus item
-int cons_item_rows();
+int cons_item_pixels();
 int cons_item_cols();
 // x_hat = sum omega_i x_i / sum omega_i
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s);

@@ -816,8 +816,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     for (int C = L.yc0[tc]; C < L.yc1[tc] + K - 1; ++C) (cc[C].x < 0 ? cc[C].x : cc[C].y) = tc;
   DV_TRY(upload(P, &P->d_rowcov, rc.data(), rc.size(), s));
   DV_TRY(upload(P, &P->d_colcov, cc.data(), cc.size(), s));
-  // consensus / assembly items: rectangles of constant cover, cut into at
-  // most cons_item_rows() x cons_item_cols() pixels
+  // consensus / assembly items: rectangles of constant cover, cut into
+  // pieces of at most cons_item_cols() columns and cons_item_pixels() pixels
   {
     std::vector<ConsItem> items;
     auto bands = [](const std::vector<int2>& cov) {
@@ -832,13 +832,15 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     };
     for (const auto& rb : bands(rc))
       for (const auto& cb : bands(cc))
-        for (int r0 = rb.first; r0 < rb.second; r0 += cons_item_rows())
-          for (int c0 = cb.first; c0 < cb.second; c0 += cons_item_cols()) {
+        for (int c0 = cb.first; c0 < cb.second; c0 += cons_item_cols()) {
+          const int ncol = std::min(cons_item_cols(), cb.second - c0);
+          const int rows = std::max(1, cons_item_pixels() / ncol);
+          for (int r0 = rb.first; r0 < rb.second; r0 += rows) {
             ConsItem it{};
             it.r0 = r0;
-            it.nrow = std::min(cons_item_rows(), rb.second - r0);
+            it.nrow = std::min(rows, rb.second - r0);
             it.c0 = c0;
-            it.ncol = std::min(cons_item_cols(), cb.second - c0);
+            it.ncol = ncol;
             const int trs[2] = {rc[r0].x, rc[r0].y}, tcs[2] = {cc[c0].x, cc[c0].y};
             for (int i = 0; i < 2; ++i)
               for (int j = 0; j < 2; ++j) {
@@ -852,6 +854,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
               }
             items.push_back(it);
           }
+        }
     P->n_citems = (int)items.size();
     DV_TRY(upload(P, &P->d_citems, items.data(), items.size(), s));
   }

@@ -55,12 +55,22 @@ __global__ void scatter_kernel(const TileDesc* __restrict__ tiles, const float* 
 }
 
 // The consensus and assembly kernels run over items: rectangles of at most
-// CI_ROWS x CI_COLS global pixels with a fixed set of covering tiles, so the
+// CI_PIX global pixels (at most CI_COLS wide) with a fixed set of covering tiles, so the
 // tile offsets are uniform per block and every load of a pixel group is
-// independent of the others.  Thread t owns columns t, t + 128, t + 256,
-// t + 384 of every row of its item.
+// independent of the others.  The item's pixels are numbered row by row and
+// thread t owns pixels t, t + 128, t + 256, ..., so every thread of a block
+// has work whatever the item's shape (the overlap bands are narrow).
 constexpr int NBR = 128;        // threads per block of the row kernels
-constexpr int CI_ROWS = 8, CI_COLS = 4 * NBR;
+constexpr int CI_PIX = 2048, CI_COLS = 512;   // pixels / columns per item at most
+
+// Row and column of pixel p of an item with ncol columns (p < 2^20; inv =
+// 1 / ncol in FP32, corrected to the exact quotient).
+__device__ __forceinline__ void item_rc(int p, int ncol, float inv, int& r, int& c) {
+  r = __float2int_rz((float)p * inv);
+  if (r * ncol > p) --r;
+  else if ((r + 1) * ncol <= p) ++r;
+  c = p - r * ncol;
+}
 constexpr int HUB_ROWS = 4;     // tile rows per block of the prior kernel
 
 // Per global x pixel: zbar = sum_i alpha_i (2 x_i - u_i) / sum_i alpha_i over
@@ -74,13 +84,18 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
                                                double& pp, double& dd) {
   constexpr int GP = 8 / NS;       // pixels per group
   const int tx = threadIdx.x;
-  for (int k0 = 0; k0 < 4 * it.nrow; k0 += GP) {
+  const int npix = it.nrow * it.ncol;
+  const float inv = 1.f / (float)it.ncol;
+  for (int p0 = 0; p0 < npix; p0 += GP * NBR) {
     float xs[GP][NS], us[GP][NS], as[GP][NS], zp[GP];
+    int rs[GP], cs[GP];
 #pragma unroll
     for (int g = 0; g < GP; ++g) {
-      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
-      const bool in = r < it.nrow && cl < it.ncol;
-      const int R = it.r0 + r, C = it.c0 + cl;
+      const int p = p0 + g * NBR + tx;
+      const bool in = p < npix;
+      item_rc(in ? p : 0, it.ncol, inv, rs[g], cs[g]);
+      const int r = rs[g];
+      const int R = it.r0 + r, C = it.c0 + cs[g];
       zp[g] = (in && zg) ? zg[(int64_t)R * G.nxc + C] : 0.f;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
@@ -96,9 +111,9 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
     float pg = 0.f, dg = 0.f;
 #pragma unroll
     for (int g = 0; g < GP; ++g) {
-      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
-      if (r >= it.nrow || cl >= it.ncol) continue;
-      const int R = it.r0 + r, C = it.c0 + cl;
+      if (p0 + g * NBR + tx >= npix) continue;
+      const int r = rs[g];
+      const int R = it.r0 + r, C = it.c0 + cs[g];
       float num = 0.f, den = 0.f;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
@@ -150,14 +165,19 @@ __device__ __forceinline__ void assemble_item(const GridArgs& G, const ConsItem&
                                               const float* __restrict__ x, float* __restrict__ out) {
   constexpr int GP = 16 / NS;
   const int tx = threadIdx.x;
-  for (int k0 = 0; k0 < 4 * it.nrow; k0 += GP) {
+  const int npix = it.nrow * it.ncol;
+  const float inv = 1.f / (float)it.ncol;
+  for (int p0 = 0; p0 < npix; p0 += GP * NBR) {
     float num[GP], den[GP];
+    int rs[GP], cs[GP];
 #pragma unroll
     for (int g = 0; g < GP; ++g) {
-      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
+      const int p = p0 + g * NBR + tx;
       num[g] = den[g] = 0.f;
-      if (r >= it.nrow || cl >= it.ncol) continue;
-      const int R = it.r0 + r, C = it.c0 + cl;
+      item_rc(p < npix ? p : 0, it.ncol, inv, rs[g], cs[g]);
+      if (p >= npix) continue;
+      const int r = rs[g];
+      const int R = it.r0 + r, C = it.c0 + cs[g];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         const float om = G.omr[it.obr[s] + R] * G.omc[it.obc[s] + C];
@@ -166,11 +186,9 @@ __device__ __forceinline__ void assemble_item(const GridArgs& G, const ConsItem&
       }
     }
 #pragma unroll
-    for (int g = 0; g < GP; ++g) {
-      const int k = k0 + g, r = k >> 2, cl = tx + NBR * (k & 3);
-      if (r < it.nrow && cl < it.ncol)
-        out[(int64_t)(it.r0 + r) * G.nxc + it.c0 + cl] = num[g] / den[g];
-    }
+    for (int g = 0; g < GP; ++g)
+      if (p0 + g * NBR + tx < npix)
+        out[(int64_t)(it.r0 + rs[g]) * G.nxc + it.c0 + cs[g]] = num[g] / den[g];
   }
 }
 
@@ -252,7 +270,7 @@ cudaError_t launch_consensus(const GridArgs& g, const float* x, float* u, float 
 }
 
 int consensus_blocks(int n_citems) { return n_citems; }
-int cons_item_rows() { return CI_ROWS; }
+int cons_item_pixels() { return CI_PIX; }
 int cons_item_cols() { return CI_COLS; }
 
 cudaError_t launch_assemble(const GridArgs& g, const float* x, float* out, cudaStream_t s) {
