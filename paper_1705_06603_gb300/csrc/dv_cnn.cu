@@ -1,15 +1,13 @@
 // Learned warm start of Algorithm 1: a small convolutional network that maps
 // the observed image and PSF descriptor maps to a correction of the start
-// image, x0 = max(0, y_pad + net(features)).  Hand-written training and
-// inference kernels:
-//   - 3x3 convolutions with zero padding, NHWC tensors, bfloat16 weights and
-//     activations, FP32 accumulation (CUDA cores);
-//   - backward data (the forward kernel on flipped, transposed weights, with
-//     the ReLU mask of the layer input fused in), backward weights (per-tile
-//     partial sums reduced in a fixed order), mean-squared-error loss, Adam.
-// Inference (the solve's warm start and dv_cnn_forward) runs the same layers
-// as implicit GEMMs on the tensor cores (tcgen05, BF16 operands, FP32
-// accumulators in tensor memory).
+// image, x0 = max(0, y_pad + net(features)).  Hand-written kernels:
+//   - the forward pass, in training and inference alike (the solve's warm
+//     start, dv_cnn_forward), as implicit GEMMs on the tensor cores (tcgen05,
+//     BF16 weights and activations, FP32 accumulators in tensor memory);
+//   - backward data (a 3x3 convolution on CUDA cores with the flipped,
+//     transposed weights and the ReLU mask of the layer input fused in),
+//     backward weights (per-tile partial sums reduced in a fixed order),
+//     mean-squared-error loss, Adam.
 // Architecture: 5 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, ReLU between
 // layers, none after the last.  The first layer's 5 input channels are padded
 // to 8 with zeros.
@@ -42,7 +40,6 @@ constexpr int layer_cin_logical(int l) { return l == 0 ? DV_CNN_IN_CH : WID; }
 
 __device__ __forceinline__ float tof(const bf16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float tof(const float v) { return v; }
-__device__ __forceinline__ void store(bf16* p, float v) { *p = __float2bfloat16_rn(v); }
 __device__ __forceinline__ void store(float* p, float v) { *p = v; }
 
 size_t conv_smem(int cin, int cout) {
@@ -207,12 +204,19 @@ __global__ void __launch_bounds__(NB) mse_kernel(const float* __restrict__ out,
   }
 }
 
-__global__ void sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+// *out = sum of the n partials (one block of NB threads, fixed order).
+__global__ void __launch_bounds__(NB) sum_kernel(const double* __restrict__ part, int n,
+                                                 double* __restrict__ out) {
+  __shared__ double red[NB];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < n; i += NB) t += part[i];
+  red[threadIdx.x] = t;
+  __syncthreads();
+  for (int w = NB / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Adam on the FP32 master parameters (bias-corrected; t counts from 1).
@@ -616,31 +620,13 @@ dv_status forward_tc(dv_cnn* c, const float* in, int N, int H, int W, float* out
   return DV_OK;
 }
 
-// Forward pass on N x H x W pixels; activations kept for the backward pass.
-dv_status forward(dv_cnn* c, const float* in, int N, int H, int W, float* out, cudaStream_t s) {
-  const int64_t npix = (int64_t)N * H * W;
-  DV_TRY(ensure_capacity(c, npix, (int64_t)N * cdiv(H, TS) * cdiv(W, TS)));
-  if (!c->packed) DV_TRY(pack(c, s));
-  input_kernel<<<cdiv(npix * CIN0, NB), NB, 0, s>>>(in, npix, c->d_act[0]);
-  DV_TRY_CUDA(cudaGetLastError());
-  DV_TRY_CUDA((conv_launch<CIN0, WID, bf16, bf16, true, false>(
-      c->d_act[0], c->d_wf[0], c->d_p + c->off_b[0], nullptr, c->d_act[1], N, H, W, s)));
-  for (int l = 1; l < NLAYER - 1; ++l)
-    DV_TRY_CUDA((conv_launch<WID, WID, bf16, bf16, true, false>(
-        c->d_act[l], c->d_wf[l], c->d_p + c->off_b[l], nullptr, c->d_act[l + 1], N, H, W, s)));
-  DV_TRY_CUDA((conv_launch<WID, 1, bf16, float, false, false>(
-      c->d_act[NLAYER - 1], c->d_wf[NLAYER - 1], c->d_p + c->off_b[NLAYER - 1], nullptr,
-      out ? out : c->d_out, N, H, W, s)));
-  return DV_OK;
-}
-
 // Loss and gradients (into d_g) for the last forward pass.
 dv_status backward(dv_cnn* c, const float* target, int N, int H, int W, cudaStream_t s) {
   const int64_t npix = (int64_t)N * H * W;
   const int grid = std::min(cdiv(npix, NB), 1024);
   mse_kernel<<<grid, NB, 0, s>>>(c->d_out, target, npix, c->d_dz[0], c->d_lpart);
   DV_TRY_CUDA(cudaGetLastError());
-  sum_kernel<<<1, 1, 0, s>>>(c->d_lpart, grid, c->d_loss);
+  sum_kernel<<<1, NB, 0, s>>>(c->d_lpart, grid, c->d_loss);
   DV_TRY_CUDA(cudaGetLastError());
   const int nblk = N * cdiv(H, TS) * cdiv(W, TS);
   int cur = 0;   // d_dz[cur] holds dL/dz of layer l
@@ -857,7 +843,7 @@ extern "C" dv_status dv_cnn_gradients(dv_cnn* c, const float* in_dev, const floa
   if (!c || !in_dev || !target_dev) return fail(DV_ERR_INVALID_ARG, "NULL argument");
   DV_TRY(check_shape(N, H, W));
   cudaStream_t s = (cudaStream_t)stream;
-  DV_TRY(forward(c, in_dev, N, H, W, nullptr, s));
+  DV_TRY(forward_tc(c, in_dev, N, H, W, nullptr, c->d_err, s));
   DV_TRY(backward(c, target_dev, N, H, W, s));
   DV_TRY_CUDA(cudaMemcpyAsync(c->h_loss, c->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   if (grad_host)
@@ -875,7 +861,7 @@ extern "C" dv_status dv_cnn_train_step(dv_cnn* c, const float* in_dev, const flo
   if (!c || !in_dev || !target_dev || !(lr > 0.f)) return fail(DV_ERR_INVALID_ARG, "bad argument");
   DV_TRY(check_shape(N, H, W));
   cudaStream_t s = (cudaStream_t)stream;
-  DV_TRY(forward(c, in_dev, N, H, W, nullptr, s));
+  DV_TRY(forward_tc(c, in_dev, N, H, W, nullptr, c->d_err, s));
   DV_TRY(backward(c, target_dev, N, H, W, s));
   c->step += 1;
   const float b1 = 0.9f, b2 = 0.999f;
@@ -945,7 +931,7 @@ extern "C" dv_status dv_cnn_train_crops(dv_cnn* c, const float* feats_dev, const
                                                       d_crops + (int64_t)t * batch * 3, batch, crop,
                                                       d_xb, d_tb);
     if ((e = cudaGetLastError()) != cudaSuccess) return done(cuda_fail(e, "gather", __FILE__, __LINE__));
-    dv_status st = forward(c, d_xb, batch, crop, crop, nullptr, s);
+    dv_status st = forward_tc(c, d_xb, batch, crop, crop, nullptr, c->d_err, s);
     if (st == DV_OK) st = backward(c, d_tb, batch, crop, crop, s);
     if (st != DV_OK) return done(st);
     if ((e = cudaMemcpyAsync(d_losses + t, c->d_loss, sizeof(double), cudaMemcpyDeviceToDevice, s)) !=
@@ -964,7 +950,12 @@ extern "C" dv_status dv_cnn_train_crops(dv_cnn* c, const float* feats_dev, const
                              cudaMemcpyDeviceToHost, s)) != cudaSuccess)
       return done(cuda_fail(e, "loss download", __FILE__, __LINE__));
   }
+  int h_err = 0;
+  if ((e = cudaMemcpyAsync(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return done(cuda_fail(e, "error word", __FILE__, __LINE__));
   const dv_status st = done(DV_OK);
+  if (st == DV_OK && h_err)
+    return fail(DV_ERR_TIMEOUT, "a tensor-core wait of the training forward pass gave up (%d)", h_err);
   if (st == DV_OK && losses_host)
     for (int t = 0; t < n_steps; ++t) losses_host[t] *= 0.5 / (double)npix;
   return st;

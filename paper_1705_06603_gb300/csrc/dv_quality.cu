@@ -10,7 +10,7 @@
 // (x, r, x^2, r^2, x r) into shared memory, then the vertical pass and the
 // SSIM per centre; FP64 partial sums per CTA, summed in a fixed order.
 #include <cmath>
-#include <vector>
+
 
 #include "dv_internal.cuh"
 
