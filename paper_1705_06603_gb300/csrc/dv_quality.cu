@@ -11,7 +11,6 @@
 // SSIM per centre; FP64 partial sums per CTA, summed in a fixed order.
 #include <cmath>
 
-
 #include "dv_internal.cuh"
 
 namespace dv {
