@@ -419,6 +419,27 @@ def run_ours(args):
     e2e = {"value": aggregate_rate(w.hy * w.wy, world, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1]}
 
+    # operator rates (m / t(H apply), m / t(H^T apply)): one whole-image
+    # launch of each on the plan's path, outside the timed region
+    xs_in = torch.rand(w.nx, device="cuda")
+    rs_in = torch.rand((w.hy, w.wy), device="cuda")
+    op_ms = {}
+    for nm, fn, arg in (("H", plan.apply_H, xs_in), ("Ht", plan.apply_Ht, rs_in)):
+        fn(arg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            fn(arg)
+        e1.record(stream)
+        e1.synchronize()
+        op_ms[nm] = e0.elapsed_time(e1) / 10
+    operator = {"H_ms": op_ms["H"], "Ht_ms": op_ms["Ht"],
+                "H_mpix_s": w.hy * w.wy / (op_ms["H"] * 1e-3) / 1e6,
+                "Ht_mpix_s": w.hy * w.wy / (op_ms["Ht"] * 1e-3) / 1e6,
+                "note": "dv_apply_H / dv_apply_Ht: one launch over the whole image on the "
+                        "plan's operator path, 10 back-to-back calls (output allocation included), "
+                        "inputs resident"}
+
     # roofline of the dominant kernel, live event timing
     info = dv.dv_plan_get_info(plan.handle)
     rows, cols, _ = dv.dv_layout_query(plan.problem)
@@ -581,6 +602,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches,
             "roofline": roof, "roofline_streaming": roof_cons, "kernels": kernels,
+            "operator": operator,
             "cpu_baseline": cpu,
             "device_bytes": info.device_bytes,
         }
