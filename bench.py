@@ -848,6 +848,9 @@ def run_compare(args):
         "paper_literal": dict(n_tiles=w.grid, weights="per_tile", gamma=w.gamma,
                               n_outer=PAPER_OUTER, n_inner=PAPER_INNER,
                               inner_increment=PAPER_INCR),
+        "paper_literal_vmlmb": dict(n_tiles=w.grid, weights="per_tile", gamma=w.gamma,
+                                    n_outer=PAPER_OUTER, n_inner=PAPER_INNER,
+                                    inner_increment=PAPER_INCR, local_solver=1, vm_memory=5),
     }
     desc = {"proposed": f"D-R consensus, {w.n_tiles[0]}x{w.n_tiles[1]} tiles / {w.overlap} px, "
                         f"{w.n_outer} x {w.n_inner}",
@@ -855,7 +858,10 @@ def run_compare(args):
             "independent": f"{w.n_tiles[0]}x{w.n_tiles[1]} tiles solved alone "
                            f"({w.n_outer * w.n_inner} steps, no consensus), omega-blended",
             "paper_literal": f"{w.grid[0]}x{w.grid[1]} blocks, one PSF each, {PAPER_OUTER} x "
-                             f"({PAPER_INNER} + {PAPER_INCR}k)"}
+                             f"({PAPER_INNER} + {PAPER_INCR}k)",
+            "paper_literal_vmlmb": f"as paper_literal with the paper's Local-Solver, VMLM-B "
+                                   f"(5 pairs): {PAPER_OUTER} x ({PAPER_INNER} + {PAPER_INCR}k) "
+                                   f"VMLM-B iterations"}
     x_out = torch.empty(w.nx, device="cuda")
     qwork = torch.empty(int(dv._lib.dv_image_quality_workspace(*w.nx)), dtype=torch.float64,
                         device="cuda")

@@ -103,6 +103,21 @@ typedef enum dv_operator_path {
                             * (not FP32); K = 9, 15, 31 or 63               */
 } dv_operator_path;
 
+/* Local-Solver of Algorithm 1 (Sec. IV-B). */
+typedef enum dv_local_solver {
+  /* projected gradient with the step tau_i (the default; captured in CUDA
+   * graphs, fused into the H^T kernels) */
+  DV_SOLVER_PG = 0,
+  /* VMLM-B, the paper's solver: limited-memory variable metric (vm_memory
+   * pairs, reset at every local solve) on the free variables, projected
+   * Armijo line search (c1 = 1e-4, halving, at most 20 trials); the
+   * projected-gradient step when memory is empty or the direction is not a
+   * descent direction.  One inner iteration = one VMLM-B iteration.  Runs
+   * eagerly, driven from the host with per-tile scalars (use_graphs does not
+   * apply). */
+  DV_SOLVER_VMLMB = 1
+} dv_local_solver;
+
 typedef struct dv_problem {
   /* observed image size (Eq. (2)); x is (hy + K - 1) x (wy + K - 1) */
   int32_t hy, wy;
@@ -148,7 +163,9 @@ typedef struct dv_problem {
   int32_t use_graphs;      /* 1: replay each outer iteration as a CUDA graph */
   /* noise standard deviation of y, an input of the learned warm start only */
   double noise_sigma;
-  int32_t reserved[5];
+  int32_t local_solver;    /* dv_local_solver */
+  int32_t vm_memory;       /* VMLM-B memory pairs, 1..32 (0: 5) */
+  int32_t reserved[3];
 } dv_problem;
 
 typedef struct dv_stats {

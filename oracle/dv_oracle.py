@@ -65,6 +65,17 @@ Readings taken where the paper is silent, ambiguous or garbled:
      all pixels; SSIM as Wang et al. define it, averaged over every 11 x 11
      window inside the image (unit-sum Gaussian window of standard deviation
      1.5, C1 = (0.01 L)^2, C2 = (0.03 L)^2, L the dynamic range).
+ R20 VMLM-B Local-Solver (local_solver="vmlmb"; the paper's solver, Sec. IV-B,
+     whose steps the paper does not spell out): per tile, a limited-memory
+     variable metric on Phi_i with m pairs, emptied at every local solve.
+     Free set F = {w > 0 or g < 0}; two-loop recursion on the gradient
+     restricted to F with full-vector pair products and H0 = (s'y / y'y) I of
+     the newest pair; the direction is zeroed outside F.  With no pairs, or
+     when g'd >= 0 (memory emptied), d = -tau_i (g on F): the projected-gradient
+     step.  Armijo along w(a) = max(0, w + a d): Phi(w(a)) <= Phi(w) +
+     1e-4 g'(w(a) - w), a = 1, 1/2, ..., at most 20 trials; no acceptance: stay
+     and empty the memory.  The pair (s, y) is kept if s'y > 0 (the oldest of
+     m + 1 dropped), else the memory is emptied.
  R18 One PSF per block (weights="per_tile", the paper's own layout, Sec.
      III-A and III-C): the PSF grid is the tile grid and tile (tr, tc) blurs
      with PSF (tr, tc) alone, weight 1 on the whole tile; its step uses L_H of
@@ -402,6 +413,60 @@ def local_solve(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau, n_in
     return w
 
 
+def local_solve_vmlmb(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau, n_iter, m=5):
+    """n_iter VMLM-B iterations of reading R20 on Phi_i from w."""
+    def phi(v):
+        return prox_objective(v, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta)
+
+    def grad(v):
+        r = apply_H(v, psfs, wr_i, wc_i) - y_i
+        if W_i is not None:
+            r = W_i * r
+        return apply_Ht(r, psfs, wr_i, wc_i) + lam * huber_gradient(v, delta) + alpha_i * (v - u)
+
+    pairs = []            # (s, y, 1 / s'y), oldest first
+    h0 = 1.0
+    f, g = phi(w), grad(w)
+    for _ in range(n_iter):
+        free = (w > 0) | (g < 0)
+        q = np.where(free, g, 0.0)
+        a = []
+        for s, y, rho in reversed(pairs):
+            ai = rho * float(np.sum(s * q))
+            q = q - ai * y
+            a.append(ai)
+        if pairs:
+            q = h0 * q
+        for (s, y, rho), ai in zip(pairs, reversed(a)):
+            b = rho * float(np.sum(y * q))
+            q = q + (ai - b) * s
+        d = np.where(free, -(1.0 if pairs else tau) * q, 0.0)
+        if not float(np.sum(g * d)) < 0.0:
+            pairs = []
+            d = np.where(free, -tau * g, 0.0)
+        step, wt, ft = 1.0, None, None
+        for _ in range(20):
+            cand = np.maximum(0.0, w + step * d)
+            fc = phi(cand)
+            if fc <= f + 1e-4 * float(np.sum(g * (cand - w))):
+                wt, ft = cand, fc
+                break
+            step *= 0.5
+        if wt is None:
+            pairs = []
+            wt, ft = w.copy(), f
+        gt = grad(wt)
+        s, y = wt - w, gt - g
+        sy, yy = float(np.sum(s * y)), float(np.sum(y * y))
+        if sy > 0.0 and yy > 0.0:
+            pairs = (pairs + [(s, y, 1.0 / sy)])[-m:]
+            h0 = sy / yy
+        else:
+            pairs = []
+        w, g, f = wt, gt, ft
+    return w
+
+
 # ---------------------------------------------------------------------------
 # Consensus prox (Lemma 1) and dual update (Sec. III-B)
 # ---------------------------------------------------------------------------
@@ -462,13 +527,15 @@ class SolveInfo:
 
 
 def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
-          inner_increment=0, W=None, x0=None, weights=None, history=False):
+          inner_increment=0, W=None, x0=None, weights=None, history=False,
+          local_solver="pg", vm_memory=5):
     """Algorithm 1 with the explicit D-R updates of Sec. III-B:
       x_i   <- Local-Solver(u_i; alpha_i, f_i)                    (all tiles)
       zbar  <- sum alpha_i (2 x_i - u_i) / sum alpha_i             (Lemma 1)
       u_i   <- u_i + rho (zbar - x_i)
     repeated n_outer times.  weights: (wr, wc) profiles, None (bilinear) or
     "per_tile" (reading R18).  Returns (x_hat, SolveInfo)."""
+    assert local_solver in ("pg", "vmlmb"), local_solver
     K = psfs.shape[2]
     nxr, nxc = layout.nx
     if weights is None:
@@ -487,8 +554,10 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
         for n, (tr, tc) in enumerate(tiles):
             pi, wri, wci = ops[n]
             Wi = None if W is None else W[layout.yslice(tr, tc)]
-            xs[n] = local_solve(xs[n], us[n], y[layout.yslice(tr, tc)], Wi, pi, wri, wci,
-                                alphas[n], lam, delta, taus[n], ni)
+            solver = local_solve if local_solver == "pg" else local_solve_vmlmb
+            extra = {} if local_solver == "pg" else {"m": vm_memory}
+            xs[n] = solver(xs[n], us[n], y[layout.yslice(tr, tc)], Wi, pi, wri, wci,
+                           alphas[n], lam, delta, taus[n], ni, **extra)
         zbar = consensus_average(layout, [2.0 * x - u for x, u in zip(xs, us)], alphas)
         info.primal.append(float(np.sqrt(sum(np.sum((x - zbar[layout.xslice(tr, tc)]) ** 2)
                                              for x, (tr, tc) in zip(xs, tiles)))))

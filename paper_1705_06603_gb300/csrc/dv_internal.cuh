@@ -269,6 +269,8 @@ struct OpTables {
   uint16_t* ksHg = nullptr;
   uint16_t* ksHtg = nullptr;
   int64_t ksteps[2] = {0, 0};
+  // host copy of the tile of every tile-mode H item (per-tile sums of its partials)
+  std::vector<int32_t> tileH;
   // tile-mode items grouped by tile group: group g owns items [gH[g], gH[g + 1])
   int gH[kMaxGroups + 1] = {};
   int gHt[kMaxGroups + 1] = {};
@@ -339,10 +341,26 @@ struct dv_plan {
   cudaStream_t grp_stream[dv::kMaxGroups] = {};
   cudaEvent_t grp_fork = nullptr, grp_join[dv::kMaxGroups] = {};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // VMLM-B Local-Solver (dv_problem.local_solver = DV_SOLVER_VMLMB), lazy
+  int vm_m = 5;                          // memory pairs
+  float* d_vg = nullptr;                 // gradient at the iterate
+  float* d_vgt = nullptr;                // gradient at the new iterate
+  float* d_vd = nullptr;                 // search direction
+  float* d_vq = nullptr;                 // two-loop work vector
+  float* d_vht = nullptr;                // H_i^T r
+  float* d_vs = nullptr;                 // [m] pairs s
+  float* d_vy = nullptr;                 // [m] pairs y
+  double* d_vpart = nullptr;             // per (tile, row chunk) partials
+  double* d_vhub = nullptr;              // Huber partials per (tile, row block)
+  float* d_vcoef = nullptr;              // per-tile coefficients
 };
 
 namespace dv {
 dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0);
+// VMLM-B Local-Solver: n_iter iterations on every tile (the projected-gradient
+// solver's buffer convention: d_w[cur] in, d_w[cur ^ (n_iter & 1)] out)
+dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s);
+int tab_index_of(int path);
 void psf_descriptors(const float* psfs, int G, int K, std::vector<float>& out);
 // Operator launches on one path (DV_PATH_DIRECT, _FFT or _TENSOR; the args
 // must come from op_args_* of the same path).  The H launch in OP_OBJ mode

@@ -242,6 +242,10 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     return fail(DV_ERR_INVALID_ARG, "unknown operator path %d", p->path);
   if (p->overlap < 0) return fail(DV_ERR_INVALID_ARG, "overlap must be >= 0");
   if (p->check_every < 0) return fail(DV_ERR_INVALID_ARG, "check_every must be >= 0");
+  if (p->local_solver != DV_SOLVER_PG && p->local_solver != DV_SOLVER_VMLMB)
+    return fail(DV_ERR_INVALID_ARG, "unknown local_solver %d", p->local_solver);
+  if (p->vm_memory < 0 || p->vm_memory > 32)
+    return fail(DV_ERR_INVALID_ARG, "vm_memory must be in [0, 32] (0: 5)");
   if (!(p->noise_sigma >= 0.0)) return fail(DV_ERR_INVALID_ARG, "noise_sigma must be >= 0");
 
   const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
@@ -388,6 +392,8 @@ void make_work(const std::vector<TileDesc>& tiles, bool adjoint, int K, const La
 static int tab_index(int path) {
   return path == DV_PATH_FFT ? 1 : (path == DV_PATH_TENSOR ? 2 : 0);
 }
+
+int tab_index_of(int path) { return tab_index(path); }
 
 dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, float* out,
                      bool global) {
@@ -580,6 +586,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
 
   P->prob = *prob;
+  P->vm_m = prob->vm_memory > 0 ? prob->vm_memory : 5;
   P->prob.psfs = nullptr;
   P->prob.weights_r = P->prob.weights_c = nullptr;
   P->prob.tile_r0 = P->prob.tile_r1 = P->prob.tile_c0 = P->prob.tile_c1 = nullptr;
@@ -765,6 +772,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     order(w);
     group(w, tb.gH);
     tb.nH = (int)w.size();
+    tb.tileH.resize(w.size());
+    for (size_t i = 0; i < w.size(); ++i) tb.tileH[i] = w[i].tile;
     DV_TRY(upload(P, &tb.H, w.data(), w.size(), s));
     DV_TRY(ranges(P->h_tiles, false, &tb.ksH));
     make_work(P->h_tiles, true, K, L, bm, bn, w, max_rows);
@@ -925,6 +934,10 @@ dv_status release(dv_plan* P) {
   }
   for (cudaEvent_t e : P->timer.pool) cudaEventDestroy(e);
   for (cudaEvent_t e : P->timer.placeholders) cudaEventDestroy(e);
+  void* vbufs[] = {P->d_vg, P->d_vgt, P->d_vd, P->d_vq, P->d_vht, P->d_vs, P->d_vy,
+                   P->d_vpart, P->d_vhub, P->d_vcoef};
+  for (void* b : vbufs)
+    if (b) cudaFree(b);
   void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,

@@ -195,6 +195,11 @@ dv_status get_graph(dv_plan* P, int n_inner, int par, GraphEntry** out) {
 // w <- max(0, w - tau (H_i^T r + lambda D^T psi(D w) + alpha (w - u)))}.
 dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
   if (n_inner <= 0) return DV_OK;
+  if (P->prob.local_solver == DV_SOLVER_VMLMB) {
+    DV_TRY(vmlmb_local_solve(P, n_inner, s));
+    P->cur ^= (n_inner & 1);
+    return DV_OK;
+  }
   if (P->prob.use_graphs) {
     GraphEntry* g = nullptr;
     DV_TRY(get_graph(P, n_inner, P->cur, &g));

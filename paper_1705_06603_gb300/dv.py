@@ -30,6 +30,7 @@ DV_OK, DV_ERR_INVALID_ARG, DV_ERR_CUDA, DV_ERR_OOM, DV_ERR_TIMEOUT, DV_ERR_UNSUP
 DV_PREC_FP32, DV_PREC_TF32, DV_PREC_BF16 = 0, 1, 2
 DV_WEIGHTS_BILINEAR, DV_WEIGHTS_SEPARABLE, DV_WEIGHTS_PER_TILE = 0, 1, 2
 DV_PATH_AUTO, DV_PATH_DIRECT, DV_PATH_FFT, DV_PATH_TENSOR = 0, 1, 2, 3
+DV_SOLVER_PG, DV_SOLVER_VMLMB = 0, 1
 KERNEL_H, KERNEL_HT_STEP, KERNEL_CONSENSUS = 0, 1, 2
 
 _fp = C.POINTER(C.c_float)
@@ -51,7 +52,8 @@ class dv_problem(C.Structure):
                 ("precision", C.c_int32), ("path", C.c_int32), ("use_warmstart", C.c_int32),
                 ("check_every", C.c_int32), ("target_objective", C.c_double),
                 ("use_graphs", C.c_int32), ("noise_sigma", C.c_double),
-                ("reserved", C.c_int32 * 5)]
+                ("local_solver", C.c_int32), ("vm_memory", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class dv_stats(C.Structure):
@@ -168,7 +170,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
                  noise_w=None, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, rho=1.0, n_outer=30,
                  n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
                  use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1,
-                 noise_sigma=0.0):
+                 noise_sigma=0.0, local_solver=0, vm_memory=0):
     """Builds a dv_problem.  weights: None (bilinear tents), (weights_r,
     weights_c) separable profiles, or "per_tile" (one PSF per tile, the PSF
     grid being the tile grid).  Returns (problem, keepalive) where keepalive
@@ -210,6 +212,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
     p.precision, p.path, p.use_warmstart = precision, path, use_warmstart
     p.check_every, p.target_objective, p.use_graphs = check_every, target_objective, use_graphs
     p.noise_sigma = noise_sigma
+    p.local_solver, p.vm_memory = local_solver, vm_memory
     return p, keep
 
 

@@ -404,6 +404,21 @@ def test_image_quality_matches_oracle(env, shape, kind):
     assert s2 == float("inf") and abs(q2 - 1.0) <= 1e-5
 
 
+@pytest.mark.parametrize("path", [DIRECT, FFT])
+def test_vmlmb_solve_matches_oracle(env, path):
+    """VMLM-B Local-Solver (reading R20: the paper's solver) through the C ABI:
+    3 outer iterations of 4 VMLM-B iterations with 3 memory pairs on the 128^2
+    workload, against the FP64 oracle running the same steps."""
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 4, path=path, local_solver=1, vm_memory=3)
+    assert st["inner_done"] == 12
+    lay, xr, info = oracle_solve(w, psfs, y, 3, 4, local_solver="vmlmb", vm_memory=3)
+    assert rel_l2(xd, xr) <= 1e-4
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
+    assert abs(st["objective"] - F) <= 1e-5 * F
+    plan.close()
+
+
 def test_grouped_tensor_solve_is_bit_identical_to_eager(env):
     """The captured local solve of the tensor path runs its tile groups on
     concurrent streams; the result equals one launch per operator over every
