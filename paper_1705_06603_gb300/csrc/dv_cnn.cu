@@ -666,6 +666,7 @@ dv_status check_shape(int N, int H, int W) {
 // Forward pass of the whole global x grid in row strips (halo of NLAYER rows,
 // so every kept row is exact); writes x0 = max(0, y_pad + net(features)).
 dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0) {
+  Range range("dv warm start");
   dv_cnn* c = P->cnn;
   const int nxr = P->nxr, nxc = P->nxc;
   const int64_t n = (int64_t)nxr * nxc;
@@ -883,6 +884,7 @@ extern "C" dv_status dv_cnn_train_crops(dv_cnn* c, const float* feats_dev, const
                                        int32_t n_pairs, int32_t H, int32_t W, const int32_t* crops_host,
                                        int32_t n_steps, int32_t batch, int32_t crop,
                                        const float* lr_host, double* losses_host, void* stream) {
+  Range range("dv cnn training");
   clear_error();
   if (!c || !feats_dev || !targets_dev || !crops_host || !lr_host)
     return fail(DV_ERR_INVALID_ARG, "NULL argument");

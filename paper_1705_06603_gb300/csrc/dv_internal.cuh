@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -356,6 +357,16 @@ struct dv_plan {
 };
 
 namespace dv {
+// Named host range of one phase (solve, local solve, consensus, objective,
+// warm start, plan, training) for profiler timelines; NVTX without an
+// attached tool costs a few nanoseconds.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 dv_status warmstart_x0(dv_plan* P, cudaStream_t s, float* x0);
 // VMLM-B Local-Solver: n_iter iterations on every tile (the projected-gradient
 // solver's buffer convention: d_w[cur] in, d_w[cur ^ (n_iter & 1)] out)

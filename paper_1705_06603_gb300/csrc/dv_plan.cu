@@ -909,6 +909,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
 }  // namespace dv
 
 extern "C" dv_status dv_plan_create(const dv_problem* prob, void* stream, dv_plan** out) {
+  Range range("dv plan");
   clear_error();
   if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;

@@ -194,6 +194,7 @@ dv_status get_graph(dv_plan* P, int n_inner, int par, GraphEntry** out) {
 // The Local-Solver of Algorithm 1 on every tile: n_inner x {r = W (H_i w - y_i);
 // w <- max(0, w - tau (H_i^T r + lambda D^T psi(D w) + alpha (w - u)))}.
 dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
+  Range range("dv local solve");
   if (n_inner <= 0) return DV_OK;
   if (P->prob.local_solver == DV_SOLVER_VMLMB) {
     DV_TRY(vmlmb_local_solve(P, n_inner, s));
@@ -240,6 +241,7 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
 }
 
 dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t s) {
+  Range range("dv consensus");
   const GridArgs g = grid_args(P);
   return timed_launch(P, KIND_CONS, s, [&](cudaStream_t st) {
     return launch_consensus(g, P->d_w[P->cur], P->d_u, (float)P->prob.gamma, (float)P->prob.rho,
@@ -253,6 +255,7 @@ dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t 
 // h_scal[1] = sum_i phi(D C_i x_hat), and (when the last consensus step wrote
 // them) h_scal[2..3] = the squared primal / dual residuals.  Synchronises the stream.
 dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
+  Range range("dv objective");
   const GridArgs g = grid_args(P);
   float* tmp = P->d_w[P->cur ^ 1];
   DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
@@ -340,6 +343,7 @@ dv_status check_plan(const dv_plan* P) {
 // Algorithm 1 from the start image; y is already in P->d_y.
 dv_status solve_internal(dv_plan* P, const float* x0, float* x_out, dv_stats* st, cudaStream_t s,
                          int64_t l0) {
+  Range range("dv solve");
   const GridArgs g = grid_args(P);
   const bool track_z = st || P->prob.check_every > 0;
   if (!x0 && P->prob.use_warmstart) {
