@@ -54,7 +54,7 @@ def parse():
                     help="chosen: the headline metric; paper: the paper-literal solve (one PSF "
                          "per block, 25 outer iterations, 10 + 10k inner steps); compare: SNR / "
                          "SSIM against the ground truth of the proposed, centralized, "
-                         "independent and paper-literal methods (Sec. V)")
+                         "independent and paper-literal methods (Sec. IV)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16",
@@ -807,14 +807,14 @@ def run_paper(args):
     plan.close()
 
 
-# --------------------------------------------------------------------------- comparison (Sec. V)
+# --------------------------------------------------------------------------- comparison (Sec. IV)
 
 COMPARE_METRIC = ("SNR (dB) against the ground truth of the proposed D-R consensus solve "
                   "(centralized, independent and paper-literal methods beside it)")
 
 
 def run_compare(args):
-    """The paper's evaluation protocol (Sec. V) on the stars2048 stand-in:
+    """The paper's evaluation protocol (Sec. IV, IV-C) on the stars2048 stand-in:
     every method deblurs the same observation with the FP32 operator and is
     scored by SNR and mean SSIM against the synthetic ground truth."""
     import torch

@@ -325,7 +325,7 @@ dv_status dv_prior_value_noalloc(const float* x_dev, int32_t rows, int32_t cols,
                                  double* value_dev, void* stream);
 
 /* Image quality of x against a reference image, the measures of the
- * paper's evaluation (Sec. V) on synthetic stand-ins: out_dev[0] = SNR =
+ * paper's evaluation (Sec. IV-C) on synthetic stand-ins: out_dev[0] = SNR =
  * 10 log10(sum ref^2 / sum (x - ref)^2) dB over all pixels (+inf if x == ref),
  * out_dev[1] = the mean structural similarity (Wang et al. 2004) over every
  * 11 x 11 window inside the image: separable unit-sum Gaussian window of

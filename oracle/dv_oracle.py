@@ -60,7 +60,7 @@ Readings taken where the paper is silent, ambiguous or garbled:
  R10 Noise weights W: 1 for uniform Gaussian noise, so lambda is relative to
      the unweighted data term; a per-pixel W (0 for unmeasured pixels) may be
      given.
- R19 Evaluation measures (Sec. V names SNR and SSIM, citing Wang et al.
+ R19 Evaluation measures (Sec. IV-C names SNR and SSIM, citing Wang et al.
      2004, without formulas): SNR = 10 log10(||ref||^2 / ||x - ref||^2) dB over
      all pixels; SSIM as Wang et al. define it, averaged over every 11 x 11
      window inside the image (unit-sum Gaussian window of standard deviation
@@ -572,7 +572,7 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
 
 
 # ---------------------------------------------------------------------------
-# Evaluation measures (Sec. V), reading R19
+# Evaluation measures (Sec. IV-C), reading R19
 # ---------------------------------------------------------------------------
 
 

@@ -1,5 +1,5 @@
 // Image quality against a reference, the measures of the paper's evaluation
-// (Sec. V): SNR = 10 log10(sum ref^2 / sum (x - ref)^2) over all pixels and
+// (Sec. IV-C): SNR = 10 log10(sum ref^2 / sum (x - ref)^2) over all pixels and
 // the mean structural similarity (Wang, Bovik, Sheikh, Simoncelli 2004) over
 // every 11 x 11 window inside the image:
 //   SSIM = (2 mu_x mu_r + C1)(2 s_xr + C2) / ((mu_x^2 + mu_r^2 + C1)(s_x^2 + s_r^2 + C2)),

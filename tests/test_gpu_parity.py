@@ -202,7 +202,7 @@ def test_edge_cases_match_oracle(env, case):
         kw["inner_increment"] = 2
         okw["inner_increment"] = 2
     elif case == "independent":
-        # Sec. V's "independent" method: tiles solved alone, then blended
+        # Sec. IV's "independent" method: tiles solved alone, then blended
         kw.update(gamma=1e-9, n_outer=1, n_inner=40)
     plan = dv.Plan(hy, wy, psfs, **kw)
     xd, st = plan.solve(torch.from_numpy(y).cuda())

@@ -1,4 +1,4 @@
-"""Pins of the oracle's evaluation measures (reading R19, Sec. V): SNR in
+"""Pins of the oracle's evaluation measures (reading R19, Sec. IV-C): SNR in
 closed form, SSIM against its definition evaluated window by window, its
 closed form on constant images, identity and symmetry."""
 
