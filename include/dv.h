@@ -82,7 +82,7 @@ typedef enum dv_weight_kind {
   /* One PSF per block, the paper's own layout (Sec. III-A, III-C): the PSF
    * grid is the tile grid (grid_r = n_tr, grid_c = n_tc) and tile (tr, tc)
    * blurs with PSF (tr, tc) alone, weight 1 on the whole tile (the local
-   * operators H_i = C_i H_i of Sec. III-A).  Without explicit tile bounds,
+   * operators H_i = C_i H_i of Sec. II-B).  Without explicit tile bounds,
    * x-tile i spans the grid points i - 1 .. i + 1 of the bilinear grid
    * (c_a = a (n - 1)/(G - 1)): [ceil(c_{i-1}), ceil(c_{i+1})) with c_{-1} = 0 and
    * c_G = n; the y-block is the x-tile less K - 1 at its end.  Neighbours then
