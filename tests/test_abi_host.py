@@ -86,6 +86,9 @@ def test_layout_with_noise_weights(dv):
     (dict(path=4), "operator path"),
     (dict(precision=3), "precision"),
     (dict(n_tc=1025), "tile grid"),
+    (dict(local_solver=2), "local_solver"),
+    (dict(vm_memory=33), "vm_memory"),
+    (dict(weight_kind=3), "weight_kind"),
 ])
 def test_invalid_problems_rejected(dv, change, needle):
     psfs = np.full((1, 1, 3, 3), 1 / 9.0)
@@ -162,3 +165,24 @@ def test_per_tile_weights_need_the_tile_grid(dv):
     p, keep = dv.make_problem(128, 128, psfs, n_tiles=(2, 3), weights="per_tile")
     with pytest.raises(dv.DVError, match="tile grid"):
         dv.dv_layout_query(p)
+
+
+def test_per_tile_weights_take_no_arrays(dv):
+    psfs = np.full((2, 2, 5, 5), 1 / 25.0, dtype=np.float32)
+    wr = np.ones((2, 24), np.float32)
+    p, keep = dv.make_problem(20, 20, psfs, n_tiles=(2, 2), weights=(wr, wr))
+    p.weight_kind = dv.DV_WEIGHTS_PER_TILE
+    with pytest.raises(dv.DVError, match="no weight arrays"):
+        dv.dv_layout_query(p)
+
+
+@pytest.mark.parametrize("rows,cols,L", [(10, 40, 1.0), (40, 10, 1.0), (40, 40, 0.0),
+                                         (40, 40, float("inf"))])
+def test_image_quality_arguments_checked_before_any_work(dv, rows, cols, L):
+    """dv_image_quality refuses windows smaller than 11 x 11 and a bad dynamic
+    range before touching device memory (the pointers here are never read)."""
+    fake = C.c_void_p(16)
+    rc = dv._lib.dv_image_quality(fake, fake, rows, cols, L, fake, fake, None)
+    assert rc == dv.DV_ERR_INVALID_ARG
+    assert dv._lib.dv_image_quality(None, fake, 40, 40, 1.0, fake, fake, None) == dv.DV_ERR_INVALID_ARG
+    assert dv._lib.dv_image_quality_workspace(40, 70) == 3 * 3 * 3
