@@ -114,7 +114,10 @@ typedef enum dv_local_solver {
    * projected-gradient step when memory is empty or the direction is not a
    * descent direction.  One inner iteration = one VMLM-B iteration.  Runs
    * eagerly, driven from the host with per-tile scalars (use_graphs does not
-   * apply). */
+   * apply).  Its objectives and gradients use the plan's inner operator path:
+   * with BF16 / TF32 operands the Armijo comparisons carry that operator's
+   * error, so near convergence trials may fail and empty the memory; the FP32
+   * paths give the exact method. */
   DV_SOLVER_VMLMB = 1
 } dv_local_solver;
 
