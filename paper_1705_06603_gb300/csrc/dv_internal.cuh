@@ -351,9 +351,12 @@ struct dv_plan {
   float* d_vht = nullptr;                // H_i^T r
   float* d_vs = nullptr;                 // [m] pairs s
   float* d_vy = nullptr;                 // [m] pairs y
-  double* d_vpart = nullptr;             // per (tile, row chunk) partials
+  double* d_vpart = nullptr;             // [4] segments of per (tile, row chunk) partials
   double* d_vhub = nullptr;              // Huber partials per (tile, row block)
-  float* d_vcoef = nullptr;              // per-tile coefficients
+  float* d_vcoef = nullptr;              // ring of per-tile coefficient slots
+  float* h_vcoef = nullptr;              // pinned staging of the ring
+  double* h_vpart = nullptr;             // pinned landing of downloaded partials
+  int64_t h_vpart_cap = 0;               // doubles in h_vpart
 };
 
 namespace dv {

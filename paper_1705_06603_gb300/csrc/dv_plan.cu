@@ -939,6 +939,8 @@ dv_status release(dv_plan* P) {
                    P->d_vpart, P->d_vhub, P->d_vcoef};
   for (void* b : vbufs)
     if (b) cudaFree(b);
+  if (P->h_vcoef) cudaFreeHost(P->h_vcoef);
+  if (P->h_vpart) cudaFreeHost(P->h_vpart);
   void* bufs[] = {P->d_psf_flip, P->d_psf, P->d_wrow, P->d_wcol, P->d_omr, P->d_omc,
                   P->d_tiles, P->d_gtile, P->tab[0].H, P->tab[0].Ht, P->tab[0].Hg,
                   P->tab[0].Htg, P->tab[1].H, P->tab[1].Ht, P->tab[1].Hg, P->tab[1].Htg,

@@ -18,6 +18,7 @@
 // chunk) that the host adds in a fixed order and turns into the next step's
 // per-tile coefficients.  The kernels here are plain streaming kernels over
 // the tile stacks.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -180,63 +181,101 @@ int vm_chunks(const dv_plan* P) { return (P->max_nxr + VROWS - 1) / VROWS; }
 
 dim3 vm_grid(const dv_plan* P) { return dim3((unsigned)vm_chunks(P), (unsigned)P->T); }
 
+constexpr int VRING = 64;          // coefficient slots staged ahead of the kernels
+
 // Host side of one local solve: per-tile sums of device partials (fixed
-// order) and per-tile coefficients for the next kernel.
+// order) and per-tile coefficients for the next kernel.  Coefficients go
+// through a ring of pinned slots and matching device slots with stream-ordered
+// copies (a slot is rewritten only after a synchronisation that follows its
+// copy); device partials are downloaded into distinct segments of a pinned
+// landing buffer and summed after one synchronisation per batch.
 struct VmState {
   dv_plan* P;
   cudaStream_t s;
   int T, nch;
-  std::vector<double> host;
-  std::vector<float> coef;
+  int slot = 0, since_sync = 0;
+  int64_t used = 0;                    // doubles of the landing buffer queued
 
-  dv_status fetch(const double* dptr, int per, std::vector<double>& out) {
-    host.resize((size_t)T * per);
-    DV_TRY_CUDA(cudaMemcpyAsync(host.data(), dptr, host.size() * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
+  dv_status wait() {
     DV_TRY_CUDA(cudaStreamSynchronize(s));
-    out.assign(T, 0.0);
-    for (int t = 0; t < T; ++t)
-      for (int k = 0; k < per; ++k) out[t] += host[(size_t)t * per + k];
+    since_sync = 0;
     return DV_OK;
   }
 
-  // Per-tile sums of one vm_dot launch; synchronises the stream.
-  dv_status dot(const float* a, const float* b, const float* c, int mode, std::vector<double>& out) {
+  // Queues the download of T * per partials; returns their landing offset.
+  dv_status enqueue(const double* dptr, int64_t count, int64_t& off) {
+    if (used + count > P->h_vpart_cap) return fail(DV_ERR_UNSUPPORTED, "VMLM-B partials exceed the landing buffer");
+    off = used;
+    DV_TRY_CUDA(cudaMemcpyAsync(P->h_vpart + used, dptr, count * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    used += count;
+    return DV_OK;
+  }
+  // Per-tile sums of a landed download (after wait()), k-th partial in order.
+  void sum(int64_t off, int per, std::vector<double>& out) const {
+    const double* h = P->h_vpart + off;
+    out.assign(T, 0.0);
+    for (int t = 0; t < T; ++t)
+      for (int k = 0; k < per; ++k) out[t] += h[(size_t)t * per + k];
+  }
+  dv_status land() {
+    DV_TRY(wait());
+    used = 0;
+    return DV_OK;
+  }
+
+  // One vm_dot launch with its partials queued for download.
+  dv_status dot_async(const float* a, const float* b, const float* c, int mode, int64_t& off) {
     vm_dot_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, a, b, c, P->d_omr, P->d_omc,
                                             (float)P->prob.gamma, mode, P->d_vpart);
     DV_TRY_CUDA(cudaGetLastError());
     P->launches += 1;
-    return fetch(P->d_vpart, nch, out);
+    return enqueue(P->d_vpart, (int64_t)T * nch, off);
+  }
+  // Per-tile sums of one vm_dot launch; synchronises the stream.
+  dv_status dot(const float* a, const float* b, const float* c, int mode, std::vector<double>& out) {
+    int64_t off;
+    DV_TRY(dot_async(a, b, c, mode, off));
+    DV_TRY(land());
+    sum(off, nch, out);
+    return DV_OK;
   }
 
-  dv_status set_coef(const std::vector<double>& c) {
-    coef.resize(T);
-    for (int t = 0; t < T; ++t) coef[t] = (float)c[t];
-    DV_TRY_CUDA(cudaMemcpyAsync(P->d_vcoef, coef.data(), T * sizeof(float), cudaMemcpyHostToDevice, s));
-    // the host vector is reused: the copy must complete before it changes
-    DV_TRY_CUDA(cudaStreamSynchronize(s));
+  // Stages per-tile coefficients; returns the device slot the next kernel reads.
+  dv_status set_coef(const std::vector<double>& c, const float*& dev) {
+    if (since_sync == VRING) DV_TRY(wait());
+    float* h = P->h_vcoef + (size_t)slot * T;
+    float* d = P->d_vcoef + (size_t)slot * T;
+    for (int t = 0; t < T; ++t) h[t] = (float)c[t];
+    DV_TRY_CUDA(cudaMemcpyAsync(d, h, T * sizeof(float), cudaMemcpyHostToDevice, s));
+    slot = (slot + 1) % VRING;
+    since_sync += 1;
+    dev = d;
     return DV_OK;
   }
 
   dv_status axpy(float* y, const float* x, const std::vector<double>& c, int mode) {
-    DV_TRY(set_coef(c));
-    vm_axpy_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, y, x, P->d_vcoef, mode);
+    const float* cd;
+    DV_TRY(set_coef(c, cd));
+    vm_axpy_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, y, x, cd, mode);
     DV_TRY_CUDA(cudaGetLastError());
     P->launches += 1;
     return DV_OK;
   }
 
   dv_status free_set(const float* w, const float* g, float* q, const std::vector<double>* c) {
-    if (c) DV_TRY(set_coef(*c));
-    vm_free_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, w, g, q, P->d_vcoef, c ? 1 : 0);
+    const float* cd = P->d_vcoef;
+    if (c) DV_TRY(set_coef(*c, cd));
+    vm_free_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, w, g, q, cd, c ? 1 : 0);
     DV_TRY_CUDA(cudaGetLastError());
     P->launches += 1;
     return DV_OK;
   }
 
   dv_status trial(const float* w, const float* d, const std::vector<double>& a, float* wt) {
-    DV_TRY(set_coef(a));
-    vm_trial_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, w, d, P->d_vcoef, wt);
+    const float* cd;
+    DV_TRY(set_coef(a, cd));
+    vm_trial_kernel<<<vm_grid(P), VT, 0, s>>>(P->d_tiles, w, d, cd, wt);
     DV_TRY_CUDA(cudaGetLastError());
     P->launches += 1;
     return DV_OK;
@@ -244,22 +283,38 @@ struct VmState {
 
   // Phi_i at wq for every tile: data term from the H launch's per-item
   // partials, prior from the Huber partials, proximity term from vm_dot.
-  dv_status objective(const float* wq, std::vector<double>& phi) {
+  // objective_async queues the launches and downloads; objective_sum reads
+  // them after land().
+  struct ObjParts {
+    int64_t data, prior, prox;
+  };
+  dv_status objective_async(const float* wq, ObjParts& o) {
     const OpTables& tb = P->tab[tab_index_of(P->path)];
     DV_TRY_CUDA(launch_op_H(P, P->path, op_args_H(P, P->path, OP_OBJ, wq, nullptr, false), s));
+    P->launches += 1;
+    DV_TRY(enqueue(P->d_part, tb.nH, o.data));
     DV_TRY_CUDA(launch_huber_value(P->d_tiles, T, P->max_nxr, P->max_nxc, wq, P->prob.delta,
                                    P->d_vhub, s));
-    P->launches += 2;
-    std::vector<double> itemp(tb.nH), prior, prox;
-    DV_TRY_CUDA(cudaMemcpyAsync(itemp.data(), P->d_part, tb.nH * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
-    DV_TRY(fetch(P->d_vhub, huber_blocks(T, P->max_nxr, P->max_nxc) / T, prior));
-    DV_TRY(dot(nullptr, wq, P->d_u, 2, prox));
-    std::vector<double> data(T, 0.0);
+    P->launches += 1;
+    DV_TRY(enqueue(P->d_vhub, huber_blocks(T, P->max_nxr, P->max_nxc), o.prior));
+    return dot_async(nullptr, wq, P->d_u, 2, o.prox);
+  }
+  void objective_sum(const ObjParts& o, std::vector<double>& phi) const {
+    const OpTables& tb = P->tab[tab_index_of(P->path)];
+    std::vector<double> data(T, 0.0), prior, prox;
+    const double* itemp = P->h_vpart + o.data;
     for (int i = 0; i < tb.nH; ++i) data[tb.tileH[i]] += itemp[i];
+    sum(o.prior, huber_blocks(T, P->max_nxr, P->max_nxc) / T, prior);
+    sum(o.prox, nch, prox);
     phi.assign(T, 0.0);
     for (int t = 0; t < T; ++t)
       phi[t] = 0.5 * data[t] + P->prob.lambda * prior[t] + 0.5 * prox[t];
+  }
+  dv_status objective(const float* wq, std::vector<double>& phi) {
+    ObjParts o;
+    DV_TRY(objective_async(wq, o));
+    DV_TRY(land());
+    objective_sum(o, phi);
     return DV_OK;
   }
 
@@ -280,25 +335,46 @@ struct VmState {
 
 }  // namespace
 
-// Device state of the VMLM-B solver (allocated on the first call).
+// Device and pinned-host state of the VMLM-B solver (allocated on the first call).
 dv_status vmlmb_alloc(dv_plan* P) {
-  if (P->d_vg) return DV_OK;
+  if (P->h_vpart) return DV_OK;          // allocated last: everything is in place
   const int m = P->vm_m;
   const size_t n = (size_t)P->xstack;
-  float** bufs[] = {&P->d_vg, &P->d_vgt, &P->d_vd, &P->d_vq, &P->d_vht};
-  for (float** b : bufs) {
-    DV_TRY_CUDA(cudaMalloc(b, n * sizeof(float)));
-    P->device_bytes += (int64_t)(n * sizeof(float));
-  }
-  DV_TRY_CUDA(cudaMalloc(&P->d_vs, (size_t)m * n * sizeof(float)));
-  DV_TRY_CUDA(cudaMalloc(&P->d_vy, (size_t)m * n * sizeof(float)));
-  P->device_bytes += (int64_t)(2 * m * n * sizeof(float));
   const size_t np = (size_t)P->T * vm_chunks(P);
   const size_t nh = (size_t)huber_blocks(P->T, P->max_nxr, P->max_nxc);
-  DV_TRY_CUDA(cudaMalloc(&P->d_vpart, np * sizeof(double)));
-  DV_TRY_CUDA(cudaMalloc(&P->d_vhub, nh * sizeof(double)));
-  DV_TRY_CUDA(cudaMalloc(&P->d_vcoef, (size_t)P->T * sizeof(float)));
-  P->device_bytes += (int64_t)((np + nh) * sizeof(double) + P->T * sizeof(float));
+  // a buffer left by an earlier call that failed part-way is kept
+  auto dev = [&](void** b, size_t bytes) -> dv_status {
+    if (*b) return DV_OK;
+    DV_TRY_CUDA(cudaMalloc(b, bytes));
+    P->device_bytes += (int64_t)bytes;
+    return DV_OK;
+  };
+  float** bufs[] = {&P->d_vg, &P->d_vgt, &P->d_vd, &P->d_vq, &P->d_vht};
+  for (float** b : bufs) DV_TRY(dev((void**)b, n * sizeof(float)));
+  DV_TRY(dev((void**)&P->d_vs, (size_t)m * n * sizeof(float)));
+  DV_TRY(dev((void**)&P->d_vy, (size_t)m * n * sizeof(float)));
+  DV_TRY(dev((void**)&P->d_vpart, np * sizeof(double)));
+  DV_TRY(dev((void**)&P->d_vhub, nh * sizeof(double)));
+  DV_TRY(dev((void**)&P->d_vcoef, (size_t)VRING * P->T * sizeof(float)));
+  // landing: the largest batch is one objective (H items, Huber blocks, one
+  // vm_dot) plus one vm_dot
+  int64_t nitems = 0;
+  for (const OpTables& tb : P->tab) nitems = std::max<int64_t>(nitems, tb.nH);
+  const int64_t cap = nitems + (int64_t)nh + 2 * (int64_t)np;
+  if (!P->h_vcoef &&
+      cudaHostAlloc((void**)&P->h_vcoef, (size_t)VRING * P->T * sizeof(float),
+                    cudaHostAllocDefault) != cudaSuccess) {
+    P->h_vcoef = nullptr;
+    cudaGetLastError();
+    return fail(DV_ERR_OOM, "pinned coefficient ring of the VMLM-B solver");
+  }
+  if (cudaHostAlloc((void**)&P->h_vpart, (size_t)cap * sizeof(double), cudaHostAllocDefault) !=
+      cudaSuccess) {
+    P->h_vpart = nullptr;
+    cudaGetLastError();
+    return fail(DV_ERR_OOM, "pinned landing buffer of the VMLM-B solver");
+  }
+  P->h_vpart_cap = cap;
   return DV_OK;
 }
 
@@ -313,7 +389,7 @@ dv_status vmlmb_alloc(dv_plan* P) {
 dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
   if (n_iter <= 0) return DV_OK;
   DV_TRY(vmlmb_alloc(P));
-  VmState V{P, s, P->T, vm_chunks(P), {}, {}};
+  VmState V{P, s, P->T, vm_chunks(P)};
   const int T = V.T, m = P->vm_m;
   const size_t n = (size_t)P->xstack;
   int par = P->cur;
@@ -395,8 +471,13 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
       }
       if (!any) break;
       DV_TRY(V.trial(w, P->d_vd, at, wt));
-      DV_TRY(V.objective(wt, phit));
-      DV_TRY(V.dot(P->d_vg, wt, w, 1, lin));
+      VmState::ObjParts o;
+      int64_t olin;
+      DV_TRY(V.objective_async(wt, o));
+      DV_TRY(V.dot_async(P->d_vg, wt, w, 1, olin));
+      DV_TRY(V.land());
+      V.objective_sum(o, phit);
+      V.sum(olin, V.nch, lin);
       for (int t = 0; t < T; ++t) {
         if (done[t]) continue;
         if (phit[t] <= phi[t] + 1e-4 * lin[t]) {
@@ -426,8 +507,14 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
     const std::vector<double> minus(T, -1.0);
     DV_TRY(V.axpy(sv, w, minus, 0));
     DV_TRY(V.axpy(yv, P->d_vg, minus, 0));
-    DV_TRY(V.dot(sv, yv, nullptr, 0, sy));
-    DV_TRY(V.dot(yv, yv, nullptr, 0, yy));
+    {
+      int64_t osy, oyy;
+      DV_TRY(V.dot_async(sv, yv, nullptr, 0, osy));
+      DV_TRY(V.dot_async(yv, yv, nullptr, 0, oyy));
+      DV_TRY(V.land());
+      V.sum(osy, V.nch, sy);
+      V.sum(oyy, V.nch, yy);
+    }
     std::swap(P->d_vg, P->d_vgt);
     for (int t = 0; t < T; ++t) {
       if (sy[t] > 0.0 && yy[t] > 0.0) {
