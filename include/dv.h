@@ -56,7 +56,7 @@ typedef enum dv_status {
   DV_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
   DV_ERR_OOM = 3,          /* device or pinned-host allocation failed         */
   DV_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up              */
-  DV_ERR_UNSUPPORTED = 5   /* valid request this build does not implement     */
+  DV_ERR_UNSUPPORTED = 5   /* valid request the library does not implement    */
 } dv_status;
 
 /* Lowest operand precision allowed for the blur operator H and its adjoint

@@ -751,7 +751,7 @@ extern "C" dv_status dv_cnn_create(int32_t width, int32_t depth, uint64_t seed, 
   if (!out) return fail(DV_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (width != WID || depth != NLAYER)
-    return fail(DV_ERR_UNSUPPORTED, "this build implements width %d and depth %d only", WID, NLAYER);
+    return fail(DV_ERR_UNSUPPORTED, "the library implements width %d and depth %d only", WID, NLAYER);
   dv_cnn* c = new (std::nothrow) dv_cnn();
   if (!c) return fail(DV_ERR_OOM, "host allocation failed");
   int64_t off = 0;
