@@ -1,24 +1,33 @@
 """Benchmark of the consensus deblurring hot path (Algorithm 1 on the GPU).
 
-Workload: the 2048x2048 star field (8x8 grid of 31x31 Moffat PSFs, 4x4 tiles
-overlapping by 64 px).  The plain form (FP32 block-FFT operator, one launch per
-kernel, blurred-image start, 100 consensus iterations x 10 projected-gradient
-steps) sets the target objective F*.  One step = one dv_consensus_solve of the
-chosen form (autotuned operator with BF16 operands allowed, CUDA graph per
-local solve, learned warm start, 3 projected-gradient steps per outer
-iteration, gamma 0.2, rho 1.8) until F <= F*(1 + 1e-4): start, local solves,
-consensus and dual updates, objective checks, assembly of x_hat.  Inputs are
-resident in HBM when the timed region starts; L2 is flushed (256 MB write)
-before every timed step.  The Douglas-Rachford fixed point does not depend on
-gamma, rho or the inner step count, so the chosen form reaches the same
-minimiser as the plain form.
+Default workload (wide8192): an 8192 x 8192 observation of a synthetic star
+field (Poisson-placed stars with power-law fluxes, elliptical blobs, constant
+background) blurred by a 16 x 16 grid of 63 x 63 Moffat PSFs, with Poisson
+(peak 1e4) plus Gaussian (sigma 2e-3) noise and per-pixel inverse-variance
+weights W; uneven 9 x 9 tiles (7 interior y-blocks of 1024, boundary blocks of
+768) overlapping by 64 px.  The plain form (FP32 block-FFT operator, one launch
+per kernel, blurred-image start, 100 consensus iterations x 10
+projected-gradient steps) sets the target objective F*.  One step = one
+dv_consensus_solve of the chosen form (autotuned operator with BF16 operands
+allowed, CUDA graph per local solve, learned warm start, 3 projected-gradient
+steps per outer iteration, gamma 0.2, rho 1.8) until F <= F*(1 + 1e-4): start,
+local solves, consensus and dual updates, objective checks, assembly of x_hat.
+Inputs are resident in HBM when the timed region starts; L2 is flushed (256 MB
+write) before every timed step.  The Douglas-Rachford fixed point does not
+depend on gamma, rho or the inner step count, so the chosen form reaches the
+same minimiser as the plain form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload wide8192|giga32768|stars2048]
+
+giga32768 (a 32768 x 32768 observation, 32 x 32 Moffat + Airy PSFs, 36 x 36
+tiles, 200 x 10 plain iterations) runs the same protocol; its plain-form solve
+alone takes minutes, so it is run with small --steps / --warmup.
 
 Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
 independent image (replicas: the method's only exchange is inside one image),
 timings are max-reduced and rank 0 prints.  --impl reference times the FP64
-oracle on the host cores on a bounded sample of the same workload.
+oracle on all host cores on a bounded sample of the same workload.
 """
 
 from __future__ import annotations
@@ -38,7 +47,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "stars2048"
+DEFAULT_WORKLOAD = "wide8192"
 METRIC = "Mpixel/s to converged objective (within 1e-4 of the plain form's F*), chosen form"
 UNIT = "Mpixel/s"
 SM_COUNT, FP32_LANES = 152, 128
@@ -50,18 +59,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["wide8192", "giga32768", "stars2048"], default=None,
+                    help="headline workload (default wide8192; --mode paper / compare default "
+                         "to stars2048)")
     ap.add_argument("--mode", choices=["chosen", "paper", "compare"], default="chosen",
                     help="chosen: the headline metric; paper: the paper-literal solve (one PSF "
                          "per block, 25 outer iterations, 10 + 10k inner steps); compare: SNR / "
                          "SSIM against the ground truth of the proposed, centralized, "
                          "independent and paper-literal methods (Sec. IV)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--precision", choices=["fp32", "tf32", "bf16"], default="bf16",
                     help="lowest operand precision the chosen form may use for H / H^T "
                          "(the autotuner picks the fastest allowed path)")
-    ap.add_argument("--ws-pairs", type=int, default=24,
-                    help="warm-start training pairs made by the plain method")
+    ap.add_argument("--ws-pairs", type=int, default=0,
+                    help="warm-start training pairs made by the plain method (0: the "
+                         "workload's default)")
     ap.add_argument("--ws-steps", type=int, default=40000, help="warm-start Adam steps")
     ap.add_argument("--ws-schedule", choices=["const", "cosine"], default="cosine",
                     help="warm-start learning-rate schedule")
@@ -80,7 +92,10 @@ def parse():
     ap.add_argument("--profile-path", choices=["fft", "direct", "bf16", "tf32"], default="fft",
                     help="operator of --profile-case: FP32 block FFT or direct, or the "
                          "tensor-core path with BF16 / TF32 operands")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.workload is None:
+        a.workload = DEFAULT_WORKLOAD if a.mode == "chosen" else "stars2048"
+    return a
 
 
 def max_over_ranks(values, world, device="cuda"):
@@ -114,6 +129,29 @@ def measured_peaks():
         with open(p) as f:
             return json.load(f)
     return {}
+
+
+def peak_value(peaks, key, fallback):
+    """(value, 'of measured' | 'of fallback') of one roofline denominator."""
+    v = peaks.get(key)
+    return (float(v), "measured") if v else (float(fallback), "fallback")
+
+
+def describe(w):
+    """Workload description: what it is, with its sizes (no file names)."""
+    noise = (f"Poisson (peak {w.poisson_peak:g}) + Gaussian (sigma {w.noise_sigma:g}) noise, "
+             f"per-pixel inverse-variance weights W" if w.poisson_peak > 0
+             else f"Gaussian noise sigma {w.noise_sigma:g}")
+    tiles = (f"uneven {w.n_tiles[0]}x{w.n_tiles[1]} tiles (y-blocks "
+             f"{sorted(set(b - a for a, b in w.yrows))} px)" if w.yrows is not None
+             else f"{w.n_tiles[0]}x{w.n_tiles[1]} tiles")
+    kind = w.extra.get("psf", ("moffat", 0.0))
+    psf = (f"{w.grid[0]}x{w.grid[1]} Moffat {w.K}x{w.K} PSFs"
+           + (f" with {kind[1]:.0%} Airy ring" if kind[0] == "moffat" and kind[1] > 0 else "")
+           if kind[0] == "moffat" else f"{w.grid[0]}x{w.grid[1]} Gaussian {w.K}x{w.K} PSFs")
+    return (f"{w.name}: {w.hy}x{w.wy} star field (Poisson stars, power-law fluxes, elliptical "
+            f"blobs), {psf}, {tiles} overlapping by {w.overlap} px, {noise}; plain form "
+            f"{w.n_outer} outer x {w.n_inner} inner iterations")
 
 
 # --------------------------------------------------------------------------- clocks
@@ -179,15 +217,34 @@ class ClockSampler:
 
 
 def make_inputs(torch, dv, w, psfs, rank):
-    from paper_1705_06603_gb300.synth import gaussian_noise, star_field
+    """Observed image y (device) and noise weights W (host float32, or None for
+    W = 1) of a workload: y = H x_true + noise, H applied by the library."""
+    from paper_1705_06603_gb300.synth import gaussian_noise, poisson_gaussian, star_field
     x_true = star_field(w.nx, w.scene_seed + 1000 * rank)
     plan0 = dv.Plan(w.hy, w.wy, psfs, n_outer=0, n_inner=0, path=dv.DV_PATH_DIRECT)
     y = plan0.apply_H(torch.from_numpy(x_true).cuda())
-    y += torch.from_numpy(gaussian_noise((w.hy, w.wy), w.noise_sigma,
-                                         w.noise_seed + 1000 * rank, np.float32)).cuda()
+    del x_true
+    W = None
+    if w.poisson_peak > 0:
+        yb, Wd = poisson_gaussian(y.cpu().numpy(), w.poisson_peak, w.noise_sigma,
+                                  w.noise_seed + 1000 * rank)
+        y.copy_(torch.from_numpy(yb.astype(np.float32)))
+        W = Wd.astype(np.float32)
+        del yb, Wd
+    else:
+        y += torch.from_numpy(gaussian_noise((w.hy, w.wy), w.noise_sigma,
+                                             w.noise_seed + 1000 * rank, np.float32)).cuda()
     torch.cuda.synchronize()
     plan0.close()
-    return y
+    return y, W
+
+
+def tile_kw(w):
+    """Tile layout arguments of dv.Plan for a workload."""
+    kw = dict(n_tiles=w.n_tiles, overlap=w.overlap)
+    if w.yrows is not None:
+        kw["tile_bounds"] = (w.yrows, w.ycols)
+    return kw
 
 
 def traffic_for(kernel: str):
@@ -209,79 +266,133 @@ def traffic_for(kernel: str):
 
 # --------------------------------------------------------------------------- oracle arm
 
+ORACLE_CROP = 192          # y-pixels per side of one worker's crop
 
-def oracle_sample(w, psfs64, seed=0):
-    """Inputs of the bounded CPU sample: interior tile (1, 1) of the workload,
-    its observation made with the oracle's own operator."""
+
+def _oracle_crop_step(job):
+    """Process-pool worker: one Local-Solver step (H, H^T, Huber prior,
+    projected update) of the FP64 oracle on a crop of an interior tile of the
+    workload: a crop-sized star field seen through the workload's PSF grid at
+    the crop's place in the field, the workload's noise model.  Returns (crop
+    y-pixels, seconds of the timed step)."""
+    name, idx = job
     from oracle import dv_oracle as O
-    from paper_1705_06603_gb300.synth import gaussian_noise, star_field
-    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap)
-    tr, tc = 1, 1
+    from paper_1705_06603_gb300.synth import (WORKLOADS, gaussian_noise, poisson_gaussian,
+                                              psf_grid_for, star_field)
+    w = WORKLOADS[name]
+    psfs = psf_grid_for(w)
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap, w.yrows, w.ycols)
+    nr, nc = w.n_tiles
+    tr = 1 + idx % max(1, nr - 2) if nr > 2 else 0
+    tc = 1 + (idx // max(1, nr - 2)) % max(1, nc - 2) if nc > 2 else 0
     rs, cs = lay.xslice(tr, tc)
-    x_true = star_field(w.nx, w.scene_seed + seed, dtype=np.float64)
-    wr = O.bilinear_weights(lay.nx[0], w.grid[0])[:, rs]
-    wc = O.bilinear_weights(lay.nx[1], w.grid[1])[:, cs]
-    yi = O.apply_H(x_true[rs, cs], psfs64, wr, wc)
-    yi = yi + gaussian_noise(yi.shape, w.noise_sigma, w.noise_seed)
+    cy = min(ORACLE_CROP, rs.stop - rs.start - w.K + 1, cs.stop - cs.start - w.K + 1)
+    cx = cy + w.K - 1
+    r0 = rs.start + (rs.stop - rs.start - cx) // 2
+    c0 = cs.start + (cs.stop - cs.start - cx) // 2
+    wr = O.bilinear_weights(lay.nx[0], w.grid[0])[:, r0:r0 + cx]
+    wc = O.bilinear_weights(lay.nx[1], w.grid[1])[:, c0:c0 + cx]
+    x = star_field((cx, cx), w.scene_seed + 7919 * (idx + 1), dtype=np.float64)
+    yi = O.apply_H(x, psfs, wr, wc)
+    Wi = None
+    if w.poisson_peak > 0:
+        yi, Wi = poisson_gaussian(yi, w.poisson_peak, w.noise_sigma, w.noise_seed + idx)
+    else:
+        yi = yi + gaussian_noise(yi.shape, w.noise_sigma, w.noise_seed + idx)
     w0 = O.start_image(yi, w.K)
-    tau = O.tile_step(lay, tr, tc, psfs64, None, w.lam, w.gamma)
-    alpha = w.gamma * lay.omega(tr, tc)
-    return lay, (w0, yi, wr, wc, alpha, tau)
-
-
-def oracle_step_seconds(O, w, psfs64, sample):
-    w0, yi, wr, wc, alpha, tau = sample
+    om = lay.omega(tr, tc)[r0 - rs.start:r0 - rs.start + cx, c0 - cs.start:c0 - cs.start + cx]
+    alpha = w.gamma * om
+    Wmax = 1.0 if Wi is None else float(Wi.max())
+    tau = 1.0 / (Wmax * O.lipschitz_bound_H(psfs) + 8.0 * w.lam + w.gamma * float(om.max()))
     t = time.perf_counter()
-    O.local_solve(w0, w0, yi, None, psfs64, wr, wc, alpha, w.lam, w.delta, tau, 1)
-    return time.perf_counter() - t
+    O.local_solve(w0, w0, yi, Wi, psfs, wr, wc, alpha, w.lam, w.delta, tau, 1)
+    return cy * cy, time.perf_counter() - t
 
 
-def oracle_rate(w, lay, t_step, t_cons):
-    """Mpixel/s of the oracle's full solve extrapolated from one tile step."""
-    T = len(lay.tiles)
-    t_solve = w.n_outer * (w.n_inner * T * t_step + t_cons)
-    return w.hy * w.wy / t_solve / 1e6, t_solve
+class OraclePool:
+    """The FP64 oracle on every host core: a spawn-context process pool (safe
+    after CUDA initialisation), one crop per core and sample."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        try:
+            self.cores = len(os.sched_getaffinity(0))
+        except AttributeError:
+            self.cores = os.cpu_count() or 1
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.sample_no = 0
+
+    def sample(self, name):
+        """One Local-Solver step on `cores` crops in parallel: (y-pixels per
+        second of local steps over all cores, wall seconds of the slowest)."""
+        jobs = [(name, self.sample_no * self.cores + i) for i in range(self.cores)]
+        self.sample_no += 1
+        res = self.pool.map(_oracle_crop_step, jobs)
+        px = sum(r[0] for r in res)
+        t = max(r[1] for r in res)
+        return px / t, t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
-def oracle_consensus_seconds(O, lay):
-    g = np.random.default_rng(0)
-    xs = [g.uniform(0, 1, (r.stop - r.start, c.stop - c.start))
-          for r, c in (lay.xslice(*t) for t in lay.tiles)]
-    al = [0.4 * lay.omega(*t) for t in lay.tiles]
-    t = time.perf_counter()
-    z = O.consensus_average(lay, [2 * x - x for x in xs], al)
-    _ = [x + (z[lay.xslice(*tt)] - x) for x, tt in zip(xs, lay.tiles)]
-    return time.perf_counter() - t
+def oracle_solve_seconds(w, lay_tiles, rate_px):
+    """Seconds of the oracle's plain-form solve extrapolated from its local-step
+    rate: n_outer x n_inner Local-Solver steps over every tile's y-block (the
+    consensus steps, 1/600 - 1/800 of the local solves in the paper's own
+    measurements, Sec. IV-C, are left out)."""
+    y_px = sum((r1 - r0) * (c1 - c0) for (r0, r1), (c0, c1) in lay_tiles)
+    return w.n_outer * w.n_inner * y_px / rate_px
 
 
-SAMPLE_DESC = ("one Local-Solver step (H, H^T, Huber prior, projected update) of the FP64 "
-               "oracle on interior tile (1,1) (590x590 x-pixels) plus one consensus step over "
-               "the 2078x2078 x grid, extrapolated to 100 outer x 10 inner steps on 16 tiles")
+def oracle_desc(w, cores):
+    return (f"one Local-Solver step (H, H^T, Huber prior, projected update) of the FP64 oracle "
+            f"on {cores} crops of {ORACLE_CROP}x{ORACLE_CROP} y-pixels ({ORACLE_CROP + w.K - 1}^2 "
+            f"x-pixels, interior tiles, the workload's PSF grid and noise model), one per host "
+            f"core in parallel; the rate in y-pixels per second extrapolated to the plain form's "
+            f"{w.n_outer} x {w.n_inner} steps over all {w.n_tiles[0] * w.n_tiles[1]} tiles")
+
+
+def layout_tiles(w):
+    from oracle import dv_oracle as O
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap, w.yrows, w.ycols)
+    return [(r, c) for r in lay.yrows for c in lay.ycols]
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from oracle import dv_oracle as O
-    from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
-    w = WORKLOADS[WORKLOAD]
-    psfs64 = psf_grid_for(w)
-    lay, sample = oracle_sample(w, psfs64)
-    t_cons = oracle_consensus_seconds(O, lay)
+    from paper_1705_06603_gb300.synth import WORKLOADS
+    w = WORKLOADS[args.workload]
+    tiles = layout_tiles(w)
+    pool = OraclePool()
     for _ in range(args.warmup):
-        oracle_step_seconds(O, w, psfs64, sample)
-    ts = [oracle_step_seconds(O, w, psfs64, sample) for _ in range(args.steps)]
-    t_step = sum(ts) / len(ts)
-    value, t_solve = oracle_rate(w, lay, t_step, t_cons)
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC}
+        pool.sample(w.name)
+    rates, walls = [], []
+    for _ in range(args.steps):
+        r, t = pool.sample(w.name)
+        rates.append(r)
+        walls.append(t)
+    pool.close()
+    rate = sum(rates) / len(rates)
+    t_solve = oracle_solve_seconds(w, tiles, rate)
+    value = w.hy * w.wy / t_solve / 1e6
+    cpu = {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+           "sample": oracle_desc(w, pool.cores)}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_solve * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(walls) / len(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "stars2048: 2048x2048 star field, 8x8 "
-                                        "Moffat 31x31 PSFs, 4x4 tiles / 64 px, 100 x 10 "
-                                        "iterations", "sample": "bounded (see cpu_baseline)"},
+        "data": "synthetic",
+        "config": {"workload": describe(w),
+                   "sample": "bounded: each step is one sample (see cpu_baseline); "
+                             "ms_per_step is its wall time",
+                   "extrapolated_solve_s": t_solve},
         "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -289,25 +400,35 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- GPU arm
 
+WS_DEFAULTS = {"stars2048": dict(pairs=24, size=256, vary=False),
+               "wide8192": dict(pairs=64, size=512, vary=True),
+               "giga32768": dict(pairs=64, size=512, vary=True)}
 
-def train_warmstart(dv, w, psfs, seed=0, n_pairs=24, size=256, steps=2000, schedule="const"):
+
+def train_warmstart(dv, w, psfs, seed=0, n_pairs=24, size=256, steps=2000, schedule="const",
+                    vary=False):
     """Trains the warm-start network on pairs the plain method produces from
-    other seeded scenes with the workload's PSF grid and noise level."""
+    other seeded scenes with the workload's noise model and iteration count;
+    vary: each pair draws its own Moffat PSF grid (2 x 2 over the pair, random
+    width and shape ranges), else every pair uses the workload's PSF grid."""
     from paper_1705_06603_gb300 import warmstart as WS
     t0 = time.perf_counter()
     pairs = []
     for s in range(n_pairs):
-        f, t, *_ = WS.make_pair(50_000 + s, size=size, K=w.K, grid=w.grid, n_tiles=(2, 2),
-                                overlap=w.overlap, n_outer=w.n_outer, n_inner=w.n_inner,
-                                lam=w.lam, delta=w.delta, gamma=w.gamma, psfs=psfs,
-                                sigma=w.noise_sigma)
+        f, t, *_ = WS.make_pair(50_000 + s, size=size, K=w.K, grid=(2, 2) if vary else w.grid,
+                                n_tiles=(2, 2), overlap=w.overlap, n_outer=w.n_outer,
+                                n_inner=w.n_inner, lam=w.lam, delta=w.delta, gamma=w.gamma,
+                                psfs=None if vary else psfs, sigma=w.noise_sigma,
+                                poisson_peak=w.poisson_peak)
         pairs.append((f, t))
+    t_pairs = time.perf_counter() - t0
     net = dv.Cnn(seed=seed)
     losses = WS.train(net, pairs, steps=steps, batch=16, crop=64, lr=1e-3, seed=seed,
                       schedule=schedule)
-    return net, {"pairs": n_pairs, "pair_size": size, "steps": steps, "schedule": schedule,
+    return net, {"pairs": n_pairs, "pair_size": size, "psf_grids": "random per pair" if vary
+                 else "the workload's", "steps": steps, "schedule": schedule,
                  "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:])),
-                 "seconds": time.perf_counter() - t0}
+                 "pair_seconds": t_pairs, "seconds": time.perf_counter() - t0}
 
 
 def run_ours(args):
@@ -322,12 +443,14 @@ def run_ours(args):
     from paper_1705_06603_gb300 import dv
     from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
 
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     psfs = psf_grid_for(w).astype(np.float32)
-    y = make_inputs(torch, dv, w, psfs, rank)
+    t_in = time.perf_counter()
+    y, W = make_inputs(torch, dv, w, psfs, rank)
+    t_in = time.perf_counter() - t_in
     stream = torch.cuda.current_stream()
-    common = dict(n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam, delta=w.delta, gamma=w.gamma,
-                  rho=w.rho, n_inner=w.n_inner, noise_sigma=w.noise_sigma)
+    common = dict(lam=w.lam, delta=w.delta, gamma=w.gamma, rho=w.rho, n_inner=w.n_inner,
+                  noise_sigma=w.noise_sigma, noise_w=W, **tile_kw(w))
     x_out = torch.empty(w.nx, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, device="cuda")   # 256 MB > 129 MB L2
 
@@ -347,19 +470,25 @@ def run_ours(args):
         return e0.elapsed_time(e1), r
 
     # plain form: FP32 block-FFT operator at its fixed size, one launch per
-    # kernel, blurred-image start, the workload's fixed iteration count
+    # kernel, blurred-image start, the workload's fixed iteration count; one
+    # solve gives F* and its own duration (events on the stream, stats excluded)
+    t_plan = time.perf_counter()
     plain = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=w.n_outer, path=dv.DV_PATH_FFT,
                     use_graphs=0, **common)
+    t_plan_plain = time.perf_counter() - t_plan
     st_plain = dv.dv_stats()
-    dv.dv_consensus_solve(plain.handle, y, None, x_out, st_plain, stream)   # warm-up, F*
-    f_star = st_plain.objective
-    ms_plain, _ = timed(lambda: dv.dv_consensus_solve(plain.handle, y, None, x_out, None, stream))
+    flush.fill_(1.0)
+    dv.dv_consensus_solve(plain.handle, y, None, x_out, st_plain, stream)
+    f_star, ms_plain = st_plain.objective, st_plain.ms_total
     plain.close()
 
     # chosen form: autotuned operator, CUDA graphs, learned warm start, stops at
-    # F <= F*(1 + 1e-4) (objective checked every 2 outer iterations)
-    net, train_info = train_warmstart(dv, w, psfs, seed=rank, n_pairs=args.ws_pairs,
-                                      steps=args.ws_steps, schedule=args.ws_schedule)
+    # F <= F*(1 + 1e-4) (objective checked every check_every outer iterations)
+    wsd = WS_DEFAULTS[w.name]
+    net, train_info = train_warmstart(dv, w, psfs, seed=rank,
+                                      n_pairs=args.ws_pairs or wsd["pairs"], size=wsd["size"],
+                                      steps=args.ws_steps, schedule=args.ws_schedule,
+                                      vary=wsd["vary"])
     target = f_star * (1.0 + 1e-4)
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
     chosen = dict(common)
@@ -369,9 +498,11 @@ def run_ours(args):
         chosen["rho"] = args.rho
     if args.gamma > 0:
         chosen["gamma"] = args.gamma
+    t_plan = time.perf_counter()
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=4 * w.n_outer, use_warmstart=1,
                    check_every=args.check_every, target_objective=target, precision=prec,
                    **chosen)
+    t_plan_chosen = time.perf_counter() - t_plan
     dv.dv_plan_set_warmstart(plan.handle, net)
     st = dv.dv_stats()
     for i in range(args.warmup):
@@ -404,20 +535,24 @@ def run_ours(args):
     value = aggregate_rate(w.hy * w.wy, world, ms_step * 1e-3)
     plain_value = aggregate_rate(w.hy * w.wy, world, ms_plain * 1e-3)
 
-    # end to end: host buffers through dv_consensus_solve_host (H2D + solve + D2H)
+    # end to end: host buffers through dv_consensus_solve_host (H2D + solve +
+    # D2H), the same step count and L2 flush as the device-resident steps
     yh = torch.empty((w.hy, w.wy), dtype=torch.float32, pin_memory=True)
     yh.copy_(y)
     xh = torch.empty(plan.nx, dtype=torch.float32, pin_memory=True)
     yn, xn = yh.numpy(), xh.numpy()
     dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream)
     barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream)
-    t_e2e = (time.perf_counter() - t0) / args.e2e_steps
-    t_e2e = max_over_ranks([t_e2e], world)[0]
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        ms, _ = timed(lambda: dv.dv_consensus_solve_host(plan.handle, yn, None, xn, None, stream))
+        e2e_ms += ms
+    t_e2e = max_over_ranks([e2e_ms / args.steps * 1e-3], world)[0]
     e2e = {"value": aggregate_rate(w.hy * w.wy, world, t_e2e), "unit": UNIT,
-           "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1]}
+           "h2d_bytes_per_step": 4 * w.hy * w.wy, "d2h_bytes_per_step": 4 * plan.nx[0] * plan.nx[1],
+           "ms_per_step": t_e2e * 1e3,
+           "timing": f"{args.steps} steps, L2 flushed before each, CUDA events on the stream "
+                     f"around each dv_consensus_solve_host call (pinned host buffers)"}
 
     # operator rates (m / t(H apply), m / t(H^T apply)): one whole-image
     # launch of each on the plan's path, outside the timed region
@@ -425,31 +560,89 @@ def run_ours(args):
     rs_in = torch.rand((w.hy, w.wy), device="cuda")
     op_ms = {}
     for nm, fn, arg in (("H", plan.apply_H, xs_in), ("Ht", plan.apply_Ht, rs_in)):
-        fn(arg)
+        out_buf = fn(arg)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(10):
-            fn(arg)
+        for _ in range(5):
+            fn(arg, out_buf)
         e1.record(stream)
         e1.synchronize()
-        op_ms[nm] = e0.elapsed_time(e1) / 10
+        op_ms[nm] = e0.elapsed_time(e1) / 5
+        del out_buf
     operator = {"H_ms": op_ms["H"], "Ht_ms": op_ms["Ht"],
                 "H_mpix_s": w.hy * w.wy / (op_ms["H"] * 1e-3) / 1e6,
                 "Ht_mpix_s": w.hy * w.wy / (op_ms["Ht"] * 1e-3) / 1e6,
                 "note": "dv_apply_H / dv_apply_Ht: one launch over the whole image on the "
-                        "plan's operator path, 10 back-to-back calls (output allocation included), "
-                        "inputs resident"}
+                        "plan's operator path, 5 back-to-back calls, inputs resident"}
+    del xs_in, rs_in
 
-    # roofline of the dominant kernel, live event timing
+    roof, roof_cons, kernels = roofline(dv, w, plan, args, ktime, total_ms)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = OraclePool()
+        rate, _ = pool.sample(w.name)
+        pool.close()
+        t_solve = oracle_solve_seconds(w, layout_tiles(w), rate)
+        cpu = {"value": w.hy * w.wy / t_solve / 1e6, "unit": UNIT, "cores": pool.cores,
+               "kind": "oracle", "sample": oracle_desc(w, pool.cores)}
+
+    info = dv.dv_plan_get_info(plan.handle)
+    pname = {dv.DV_PATH_DIRECT: "direct", dv.DV_PATH_FFT: "block-FFT",
+             dv.DV_PATH_TENSOR: "tensor-core"}[info.path]
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bf16" if args.precision == "bf16" else "tf32")
+            if info.path == dv.DV_PATH_TENSOR else "f32", "data": "synthetic",
+            "config": {"workload": describe(w),
+                       "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
+                                      "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
+                                      "per local solve (%d tile groups on concurrent streams), "
+                                      "learned warm start (%d pairs of %d^2, %d Adam "
+                                      "steps), %d projected-gradient steps per outer iteration, "
+                                      "gamma %.3g, rho %.3g, "
+                                      "stop at F <= F*(1 + 1e-4) checked every %d outer "
+                                      "iterations; objective with the FP32 operator"
+                                      % (pname, args.precision, info.tune_ms_direct,
+                                         info.tune_ms_fft, info.tune_ms_tensor, info.tile_groups,
+                                         train_info["pairs"], train_info["pair_size"],
+                                         args.ws_steps, args.inner or w.n_inner,
+                                         chosen["gamma"], chosen["rho"], args.check_every),
+                       "plain_form": f"FP32 block-FFT at fixed S = 128, one launch per kernel, "
+                                     f"blurred-image start, {w.n_outer} x {w.n_inner} iterations",
+                       "plain_value": plain_value, "plain_ms": ms_plain, "f_star": f_star,
+                       "chosen_outer_iterations": outer, "chosen_objective": objs,
+                       "reached_f_star": reached, "warmstart_training": train_info,
+                       "setup_seconds": {"inputs": t_in, "plain_plan": t_plan_plain,
+                                         "chosen_plan": t_plan_chosen},
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "roofline_streaming": roof_cons, "kernels": kernels,
+            "operator": operator,
+            "cpu_baseline": cpu,
+            "device_bytes": info.device_bytes,
+        }
+        print(json.dumps(out), flush=True)
+    plan.close()
+    net.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline(dv, w, plan, args, ktime, total_ms):
+    """Roofline objects of the dominant unit (the local solve with concurrent
+    tile groups, else the slower operator kernel) and of the HBM-bound
+    consensus kernel, from the live CUDA-event timings of the timed region."""
     info = dv.dv_plan_get_info(plan.handle)
     rows, cols, _ = dv.dv_layout_query(plan.problem)
     lay_tiles = [(r, c) for r in rows for c in cols]
     y_px = sum((r1 - r0) * (c1 - c0) for (r0, r1), (c0, c1) in lay_tiles)
     x_px = sum((r1 - r0 + w.K - 1) * (c1 - c0 + w.K - 1) for (r0, r1), (c0, c1) in lay_tiles)
     path = info.path
-    pname = {dv.DV_PATH_DIRECT: "direct", dv.DV_PATH_FFT: "block-FFT",
-             dv.DV_PATH_TENSOR: "tensor-core"}[path]
-    tc_prec = 0 if args.precision == "bf16" else 1
     kH, kHt = {dv.DV_PATH_FFT: ("fft_H_kernel", "fft_Ht_kernel"),
                dv.DV_PATH_DIRECT: (f"direct_H_kernel<{w.K}>", f"direct_Ht_kernel<{w.K}>"),
                dv.DV_PATH_TENSOR: ((f"tcT_H_kernel<{w.K}>", f"tcT_Ht_kernel<{w.K}>")
@@ -457,8 +650,6 @@ def run_ours(args):
                                    (f"tc_H_kernel<1,{w.K}>", f"tc_Ht_kernel<1,{w.K}>"))}[path]
     names = {0: f"{kH} (H_i with residual)", 1: f"{kHt} (H_i^T + fused prox step)",
              2: "consensus_kernel"}
-    # with concurrent tile groups the local solve (n_inner x {H, H^T} over all
-    # tiles, kind 3) is the timed unit; otherwise the slower operator kernel
     grouped = info.tile_groups > 1
     n_in = args.inner or w.n_inner
     dom = max((0, 1), key=lambda k: ktime[k][0])
@@ -473,11 +664,6 @@ def run_ours(args):
         # active PSFs (first-order interpolation); the tensor pipe also runs
         # the zero band of the Toeplitz operand and the ragged block tails
         flops = 8.0 * w.K * w.K * px
-        # executed MMA work: per (block, PSF) pair and tap row, k-steps of
-        # 128 x N x KM; BF16 column-band blocks: N = the block's rows (up to
-        # 256), at most ceil((127 + K) / 16) k-steps, those where the PSF's
-        # column weight vanishes skipped (the plan reports the sum);
-        # TF32 row-band blocks: 128 x 64, ceil((63 + K) / 8) k-steps
         if args.precision == "bf16":
             def mma_work(k):
                 mean_rows = (y_px if k == 0 else x_px) / max(info.blocks[k], 1) / 128.0
@@ -496,12 +682,11 @@ def run_ours(args):
             executed = info.block_psfs[dom] * w.K * ks * km * 2.0 * 128 * 64
             work_note = (f"{info.block_psfs[dom]} block-PSF pairs x K x {ks * km} Toeplitz "
                          f"columns x 2 x 128 x 64")
-        sus = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        sus, src = peak_value(peaks, "bf16_tflops_sustained", 1700.0)
         peak = sus if args.precision == "bf16" else sus * 1.1 / 2.25
         bound, unit = "tensor", "TFLOP/s"
-        peak_src = ("measured sustained cuBLAS BF16 (MEASURED_PEAKS.json)"
-                    if args.precision == "bf16" else
-                    "measured sustained cuBLAS BF16 x nominal TF32/BF16 ratio 1.1/2.25")
+        peak_src = (f"{src} sustained cuBLAS BF16" if args.precision == "bf16" else
+                    f"{src} sustained cuBLAS BF16 x nominal TF32/BF16 ratio 1.1/2.25")
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
                f"{px} pixels; executed MMA work {executed / 1e9:.1f} GFLOP per launch "
                f"({work_note})")
@@ -511,17 +696,18 @@ def run_ours(args):
                    f"{executed / 1e9:.1f} GFLOP per local solve ({work_note})")
     elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
-        # per 128 x 128 complex 2-D transform (N = 16384) and 8 flop per spectral
-        # product; H runs one forward per PSF pair and one inverse per block,
-        # H^T one forward per block and one inverse per pair
-        n = 128 * 128
+        # per S x S complex 2-D transform and 8 flop per spectral product; H runs
+        # one forward per PSF pair and one inverse per block, H^T one forward per
+        # block and one inverse per pair
+        S = info.fft_size if hasattr(info, "fft_size") and info.fft_size else 128
+        n = S * S
         f2d = 5.0 * n * np.log2(n)
         flops = (info.blocks[dom] + info.psf_pairs[dom]) * f2d + info.psf_pairs[dom] * 8.0 * n
         peak = SM_COUNT * FP32_LANES * 2 * sm_max * 1e6 / 1e12
         bound, unit = "alu", "TFLOP/s"
         peak_src = (f"FP32 FMA: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 flop x {sm_max:.0f} MHz "
                     f"(unit counts and max SM clock)")
-        alg = (f"5 N log2 N flop per 128x128 complex 2-D transform + 8 N per spectral product; "
+        alg = (f"5 N log2 N flop per {S}x{S} complex 2-D transform + 8 N per spectral product; "
                f"{info.blocks[dom]} blocks, {info.psf_pairs[dom]} PSF pairs per launch")
     else:
         flops = 8.0 * w.K * w.K * px
@@ -541,79 +727,27 @@ def run_ours(args):
                  f"step}} on {info.tile_groups} concurrent tile groups, timed as one graph)")
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "kernel": kname,
-            "peak_source": peak_src, "algorithmic": alg}
+            "ms_per_unit": ms_launch, "peak_source": peak_src, "algorithmic": alg}
     # the HBM-bound consensus + dual update: read x_i, u_i and write u_i per
     # tile pixel, read and write zbar_prev per global pixel (residuals tracked)
     ms_cons = ktime[2][0] / max(ktime[2][1], 1)
     cons_bytes = 12.0 * x_px + 8.0 * plan.nx[0] * plan.nx[1]
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    cons_gbs = cons_bytes / (ms_cons * 1e-3) / 1e9
+    hbm, hsrc = peak_value(peaks, "hbm_gbs", 6800.0)
+    cons_gbs = cons_bytes / (ms_cons * 1e-3) / 1e9 if ms_cons > 0 else 0.0
     roof_cons = {"bound": "hbm", "achieved": cons_gbs, "peak": hbm, "unit": "GB/s",
                  "frac": cons_gbs / hbm, "traffic": traffic_for("consensus_kernel"),
-                 "kernel": "consensus_kernel",
+                 "kernel": "consensus_kernel", "ms_per_launch": ms_cons,
                  "algorithmic": f"12 B per tile pixel ({x_px}) + 8 B per global x pixel "
                                 f"({plan.nx[0] * plan.nx[1]}) = {cons_bytes / 1e6:.1f} MB per launch",
-                 "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+                 "peak_source": f"{hsrc} copy bandwidth (hbm_gbs)"}
     names[3] = f"local solve ({kH} + {kHt} on {info.tile_groups} concurrent tile groups)"
     kernels = {names[k]: {"launches": ktime[k][1], "ms_per_launch": ktime[k][0] / max(ktime[k][1], 1),
                           "share": ktime[k][0] / max(total_ms, 1e-9)}
                for k in (0, 1, 2, 3) if ktime[k][1] > 0}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import dv_oracle as O
-        psfs64 = psfs.astype(np.float64)
-        lay, sample = oracle_sample(w, psfs64)
-        t_cons = oracle_consensus_seconds(O, lay)
-        t_step = min(oracle_step_seconds(O, w, psfs64, sample) for _ in range(2))
-        cval, _ = oracle_rate(w, lay, t_step, t_cons)
-        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": SAMPLE_DESC}
-
-    if rank == 0:
-        out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": ("bf16" if args.precision == "bf16" else "tf32")
-            if path == dv.DV_PATH_TENSOR else "f32", "data": "synthetic",
-            "config": {"workload": "stars2048: 2048x2048 star field (Poisson stars, power-law "
-                                   "fluxes, elliptical blobs), 8x8 Moffat 31x31 PSFs, 4x4 tiles "
-                                   "overlapping by 64 px, sigma 0.005; plain form 100 outer x 10 "
-                                   "inner iterations",
-                       "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
-                                      "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
-                                      "per local solve (%d tile groups on concurrent streams), "
-                                      "learned warm start (%d pairs, %d Adam "
-                                      "steps), %d projected-gradient steps per outer iteration, "
-                                      "gamma %.3g, rho %.3g, "
-                                      "stop at F <= F*(1 + 1e-4) checked every %d outer "
-                                      "iterations; objective with the FP32 operator"
-                                      % (pname, args.precision, info.tune_ms_direct,
-                                         info.tune_ms_fft, info.tune_ms_tensor, info.tile_groups,
-                                         args.ws_pairs,
-                                         args.ws_steps, args.inner or w.n_inner,
-                                         chosen["gamma"], chosen["rho"], args.check_every),
-                       "plain_form": "FP32 block-FFT at fixed S = 128, one launch per kernel, "
-                                     "blurred-image start, 100 x 10 iterations",
-                       "plain_value": plain_value, "plain_ms": ms_plain, "f_star": f_star,
-                       "chosen_outer_iterations": outer, "chosen_objective": objs,
-                       "reached_f_star": reached, "warmstart_training": train_info,
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches,
-            "roofline": roof, "roofline_streaming": roof_cons, "kernels": kernels,
-            "operator": operator,
-            "cpu_baseline": cpu,
-            "device_bytes": info.device_bytes,
-        }
-        print(json.dumps(out), flush=True)
-    plan.close()
-    net.close()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return roof, roof_cons, kernels
 
 
-def run_profile_case(which):
+def run_profile_case(args):
     """Launch sequence for ncu: inputs, a plan on the requested path (no autotuning), then
     scatter, H, H^T (+ step), consensus and assembly of one 1 x 1 solve,
     eagerly (no graphs)."""
@@ -623,15 +757,15 @@ def run_profile_case(which):
     dvbuild.build()
     from paper_1705_06603_gb300 import dv
     from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     psfs = psf_grid_for(w).astype(np.float32)
-    y = make_inputs(torch, dv, w, psfs, 0)
+    y, W = make_inputs(torch, dv, w, psfs, 0)
     kw = {"fft": dict(path=dv.DV_PATH_FFT), "direct": dict(path=dv.DV_PATH_DIRECT),
           "bf16": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_BF16),
-          "tf32": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_TF32)}[which]
-    plan = dv.Plan(w.hy, w.wy, psfs, n_tiles=w.n_tiles, overlap=w.overlap, lam=w.lam,
-                   delta=w.delta, gamma=w.gamma, rho=w.rho, n_outer=1, n_inner=1, use_graphs=0,
-                   noise_sigma=w.noise_sigma, **kw)
+          "tf32": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_TF32)}[args.profile_path]
+    plan = dv.Plan(w.hy, w.wy, psfs, lam=w.lam, delta=w.delta, gamma=w.gamma, rho=w.rho,
+                   n_outer=1, n_inner=1, use_graphs=0, noise_sigma=w.noise_sigma, noise_w=W,
+                   **tile_kw(w), **kw)
     plan.solve(y, stats=False)
     torch.cuda.synchronize()
     plan.close()
@@ -649,6 +783,17 @@ PAPER_SAMPLE = ("one Local-Solver step of the FP64 oracle on block (1,1) with it
 
 def paper_inner_total():
     return sum(PAPER_INNER + k * PAPER_INCR for k in range(PAPER_OUTER))
+
+
+def oracle_consensus_seconds(O, lay):
+    g = np.random.default_rng(0)
+    xs = [g.uniform(0, 1, (r.stop - r.start, c.stop - c.start))
+          for r, c in (lay.xslice(*t) for t in lay.tiles)]
+    al = [0.4 * lay.omega(*t) for t in lay.tiles]
+    t = time.perf_counter()
+    z = O.consensus_average(lay, [2 * x - x for x in xs], al)
+    _ = [x + (z[lay.xslice(*tt)] - x) for x, tt in zip(xs, lay.tiles)]
+    return time.perf_counter() - t
 
 
 def paper_oracle_rate(w, psfs64):
@@ -687,9 +832,9 @@ def run_paper(args):
     dvbuild.build()
     from paper_1705_06603_gb300 import dv
     from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     psfs = psf_grid_for(w).astype(np.float32)
-    y = make_inputs(torch, dv, w, psfs, rank)
+    y, _ = make_inputs(torch, dv, w, psfs, rank)
     stream = torch.cuda.current_stream()
     prec = {"fp32": dv.DV_PREC_FP32, "tf32": dv.DV_PREC_TF32, "bf16": dv.DV_PREC_BF16}[args.precision]
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_tiles=w.grid, weights="per_tile",
@@ -792,9 +937,9 @@ def run_paper(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": ("bf16" if args.precision == "bf16" else "tf32")
             if info.path == dv.DV_PATH_TENSOR else "f32", "data": "synthetic",
-            "config": {"workload": "stars2048: 2048x2048 star field, 8x8 Moffat 31x31 PSFs; "
-                                   "8x8 blocks from the PSF grid, overlapping by half a block, "
-                                   "one PSF per block",
+            "config": {"workload": f"{describe(w)}; solved as {w.grid[0]}x{w.grid[1]} blocks "
+                                   f"from the PSF grid, overlapping by half a block, one PSF "
+                                   f"per block",
                        "solve": f"{pname} operator (autotuned, operands >= {args.precision}), "
                                 f"CUDA graphs, blurred-image start, {PAPER_OUTER} outer x "
                                 f"({PAPER_INNER} + {PAPER_INCR}k) inner, gamma {w.gamma}, rho 1",
@@ -828,7 +973,7 @@ def run_compare(args):
     from paper_1705_06603_gb300 import dv
     from paper_1705_06603_gb300.synth import (WORKLOADS, gaussian_noise, psf_grid_for,
                                               star_field)
-    w = WORKLOADS[WORKLOAD]
+    w = WORKLOADS[args.workload]
     psfs = psf_grid_for(w).astype(np.float32)
     x_true = torch.from_numpy(star_field(w.nx, w.scene_seed + 1000 * rank)).cuda()
     plan0 = dv.Plan(w.hy, w.wy, psfs, n_outer=0, n_inner=0, path=dv.DV_PATH_DIRECT)
@@ -916,9 +1061,8 @@ def run_compare(args):
             "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": res["proposed"]["ms"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "stars2048: 2048x2048 star field (ground truth known), 8x8 "
-                                   "Moffat 31x31 PSFs, sigma 0.005; lambda, delta as the "
-                                   "workload for every method",
+            "config": {"workload": f"{describe(w)} (ground truth known); lambda, delta as "
+                                   f"the workload for every method",
                        "quality": "SNR = 10 log10(|x_true|^2 / |x - x_true|^2) over the x grid; "
                                   "mean SSIM (11x11 Gaussian window, sigma 1.5, L = 1)",
                        "methods": res},
@@ -929,7 +1073,7 @@ def run_compare(args):
 def main():
     args = parse()
     if args.profile_case:
-        run_profile_case(args.profile_path)
+        run_profile_case(args)
         return
     if args.mode == "paper":
         run_paper(args)

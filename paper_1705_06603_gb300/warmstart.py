@@ -13,7 +13,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import dv
-from .synth import gaussian_noise, moffat_psf_grid, rng, star_field
+from .synth import gaussian_noise, moffat_psf_grid, poisson_gaussian, rng, star_field
 
 
 def random_case(seed, size, K, grid):
@@ -31,17 +31,27 @@ def random_case(seed, size, K, grid):
 
 
 def make_pair(seed, size=96, K=15, grid=(3, 3), n_tiles=(2, 2), overlap=16, n_outer=40,
-              n_inner=10, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, psfs=None, sigma=None):
+              n_inner=10, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, psfs=None, sigma=None,
+              poisson_peak=0.0):
     """(features [nx, nx, 5], target [nx, nx], y, psfs, sigma) of one seeded case
-    (CUDA tensors); psfs / sigma, when given, replace the random draws."""
+    (CUDA tensors); psfs / sigma, when given, replace the random draws.  With
+    poisson_peak > 0 the noise is Poisson(peak H x) / peak + N(0, sigma^2) and the
+    solve weighs the data term with the per-pixel inverse-variance weights."""
     import torch
     x, rpsfs, rsigma = random_case(seed, size, K, grid)
     psfs = rpsfs if psfs is None else np.ascontiguousarray(psfs, dtype=np.float32)
     sigma = rsigma if sigma is None else float(sigma)
-    plan = dv.Plan(size, size, psfs, n_tiles=n_tiles, overlap=overlap, lam=lam, delta=delta,
-                   gamma=gamma, n_outer=n_outer, n_inner=n_inner, noise_sigma=sigma)
+    kw = dict(n_tiles=n_tiles, overlap=overlap, lam=lam, delta=delta, gamma=gamma,
+              n_outer=n_outer, n_inner=n_inner, noise_sigma=sigma)
+    plan = dv.Plan(size, size, psfs, **kw)
     y = plan.apply_H(torch.from_numpy(x).cuda())
-    y += torch.from_numpy(gaussian_noise(y.shape, sigma, 20_000 + seed, np.float32)).cuda()
+    if poisson_peak > 0:
+        yb, W = poisson_gaussian(y.cpu().numpy(), poisson_peak, sigma, 20_000 + seed)
+        y.copy_(torch.from_numpy(yb.astype(np.float32)))
+        plan.close()
+        plan = dv.Plan(size, size, psfs, noise_w=W.astype(np.float32), **kw)
+    else:
+        y += torch.from_numpy(gaussian_noise(y.shape, sigma, 20_000 + seed, np.float32)).cuda()
     xhat, _ = plan.solve(y, stats=False)
     feat = torch.empty(plan.nx + (dv.CNN_IN_CH,), device="cuda")
     dv.dv_warmstart_features(plan.handle, y, feat)

@@ -53,3 +53,24 @@ def oracle_solve(w, psfs, y, n_outer, n_inner, **kw):
     xhat, info = O.solve(y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta,
                          w.gamma, w.rho, n_outer, n_inner, **kw)
     return lay, xhat, info
+
+
+def max_abs_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b))) if a.size else 0.0
+
+
+def assert_close(a, b, tol):
+    """The GPU result a against the oracle's b: relative L2 error <= tol, and
+    element by element |a - b| <= 10 tol max|b| (a wrong row, column or block
+    edge that a norm over the whole image would dilute fails the second)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (a.shape, b.shape)
+    e = rel_l2(a, b)
+    assert e <= tol, f"relative L2 error {e:.3e} > {tol:.1e}"
+    scale = float(np.max(np.abs(b))) if b.size else 0.0
+    m = max_abs_err(a, b)
+    assert m <= 10.0 * tol * scale, (f"max |error| {m:.3e} > 10 x {tol:.1e} x max|ref| "
+                                     f"({scale:.3e}) at {np.unravel_index(np.argmax(np.abs(a - b)), a.shape)}")

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import dv_oracle as O
-from tests.gpu_common import need_gpu
+from tests.gpu_common import assert_close, need_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +58,7 @@ def _device_image(torch, shape, pts):
     return x
 
 
-def _check(name, path, prec, n_samples=48):
+def _check(name, path, prec, n_samples=256, strip=256):
     torch, dv = need_gpu()
     from paper_1705_06603_gb300.synth import WORKLOADS, psf_grid_for
     w = WORKLOADS[name]
@@ -79,19 +79,26 @@ def _check(name, path, prec, n_samples=48):
     wr = O.bilinear_weights(nxr, w.grid[0])
     wc = O.bilinear_weights(nxc, w.grid[1])
     sg = np.random.default_rng(13)
-    # sampled y pixels (corners and block edges included)
-    pi = np.concatenate([[0, w.hy - 1, w.hy // 2], sg.integers(0, w.hy, n_samples)])
-    pj = np.concatenate([[0, w.wy - 1, w.wy // 3], sg.integers(0, w.wy, n_samples)])
+    # sampled y pixels (corners and block edges included) and a contiguous
+    # strip of one row across the first tile boundary (block and band edges)
+    b0 = w.yrows[1][0] if w.yrows is not None else w.wy // 2
+    sj = np.arange(max(0, b0 - strip // 2), min(w.wy, b0 + strip // 2))
+    pi = np.concatenate([[0, w.hy - 1, w.hy // 2], sg.integers(0, w.hy, n_samples),
+                         np.full(sj.size, w.hy // 2 + 1)])
+    pj = np.concatenate([[0, w.wy - 1, w.wy // 3], sg.integers(0, w.wy, n_samples), sj])
     got, ref = [], []
     for i, j in zip(pi, pj):
         win = xs[i:i + K, j:j + K]
         ref.append(O.apply_H_at(win, ps, wr[:, i:i + K], wc[:, j:j + K], [(0, 0)])[0])
         got.append(float(y[i, j]))
     got, ref = np.array(got), np.array(ref)
-    assert np.linalg.norm(got - ref) <= TOL[prec] * np.linalg.norm(ref)
-    # sampled x pixels of H^T
-    pR = np.concatenate([[0, nxr - 1, nxr // 2], sg.integers(0, nxr, n_samples)])
-    pC = np.concatenate([[0, nxc - 1, nxc // 3], sg.integers(0, nxc, n_samples)])
+    assert_close(got, ref, TOL[prec])
+    # sampled x pixels of H^T, and a strip of one x row across the first
+    # tile boundary
+    sC = np.arange(max(0, b0 - strip // 2), min(nxc, b0 + strip // 2 + K))
+    pR = np.concatenate([[0, nxr - 1, nxr // 2], sg.integers(0, nxr, n_samples),
+                         np.full(sC.size, nxr // 2 - 1)])
+    pC = np.concatenate([[0, nxc - 1, nxc // 3], sg.integers(0, nxc, n_samples), sC])
     got, ref = [], []
     for R, C in zip(pR, pC):
         win = rs[R - K + 1:R + 1, C - K + 1:C + 1]
@@ -102,7 +109,7 @@ def _check(name, path, prec, n_samples=48):
         ref.append(O.apply_Ht_at(win, ps, wrs, wcs, [(K - 1, K - 1)])[0])
         got.append(float(g[R, C]))
     got, ref = np.array(got), np.array(ref)
-    assert np.linalg.norm(got - ref) <= TOL[prec] * np.linalg.norm(ref)
+    assert_close(got, ref, TOL[prec])
     plan.close()
 
 

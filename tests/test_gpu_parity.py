@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 from oracle import dv_oracle as O
-from tests.gpu_common import (need_gpu, oracle_solve, random_psfs, rel_l2, workload_case)
+from tests.gpu_common import (assert_close, need_gpu, oracle_solve, random_psfs, rel_l2,
+                              workload_case)
 
 pytestmark = pytest.mark.gpu
 
@@ -59,8 +60,8 @@ DIRECT, FFT = 1, 2
 ])
 def test_operator_matches_oracle(env, hy, wy, K, G, path):
     yd, y_ref, gd, g_ref, x, r = _apply_both(env, hy, wy, K, G, seed=K * 7 + hy, path=path)
-    assert rel_l2(yd, y_ref) <= OP_TOL
-    assert rel_l2(gd, g_ref) <= OP_TOL
+    assert_close(yd, y_ref, OP_TOL)
+    assert_close(gd, g_ref, OP_TOL)
 
 
 @pytest.mark.parametrize("path", [DIRECT, FFT])
@@ -75,8 +76,8 @@ def test_operator_signed_psfs_and_separable_weights(env, path):
     yd, y_ref, gd, g_ref, *_ = _apply_both(env, hy, wy, K, G, 5, negative=True,
                                            weights=(wr.astype(np.float32), wc.astype(np.float32)),
                                            path=path)
-    assert rel_l2(yd, y_ref) <= OP_TOL
-    assert rel_l2(gd, g_ref) <= OP_TOL
+    assert_close(yd, y_ref, OP_TOL)
+    assert_close(gd, g_ref, OP_TOL)
 
 
 @pytest.mark.parametrize("path", [DIRECT, FFT])
@@ -104,7 +105,7 @@ def test_short_solve_matches_oracle(env, path):
     w, psfs, y, _ = workload_case("disks128")
     plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 2, path=path)
     lay, xr, info = oracle_solve(w, psfs, y, 3, 2)
-    assert rel_l2(xd, xr) <= 1e-5
+    assert_close(xd, xr, 1e-5)
     F, data, prior = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam,
                                  w.delta)
     assert abs(st["objective"] - F) <= 1e-5 * F
@@ -122,7 +123,7 @@ def test_full_small_workload_matches_oracle(env, path):
     w, psfs, y, _ = workload_case("disks128")
     plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, path=path)
     lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
-    assert rel_l2(xd, xr) <= 1e-3
+    assert_close(xd, xr, 1e-3)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
     assert abs(st["objective"] - F) <= 1e-4 * F
     assert xd.min() >= 0.0
@@ -212,7 +213,7 @@ def test_edge_cases_match_oracle(env, case):
     xr, info = O.solve(y.astype(np.float64), psfs.astype(np.float64), lay, kw["lam"], kw["delta"],
                        kw["gamma"], 1.0, kw["n_outer"], kw["n_inner"],
                        W=None if W is None else W.astype(np.float64), **okw)
-    assert rel_l2(xd, xr) <= 1e-5
+    assert_close(xd, xr, 1e-5)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, kw["lam"],
                     kw["delta"], None if W is None else W.astype(np.float64))[0]
     assert abs(st["objective"] - F) <= 1e-5 * F
@@ -262,7 +263,7 @@ def test_full_size_tile_step_matches_oracle(env, path, prec):
     xi = O.local_solve(x0[rs, cs], x0[rs, cs], y.astype(np.float64)[lay.yslice(tr, tc)], None,
                        psfs.astype(np.float64), wr, wc, w.gamma * lay.omega(tr, tc), w.lam,
                        w.delta, tau, 1)
-    assert rel_l2(x_gpu, xi) <= {0: 1e-5, 2: 3e-3, 1: 5e-4}[prec]
+    assert_close(x_gpu, xi, {0: 1e-5, 2: 3e-3, 1: 5e-4}[prec])
     plan.close()
 
 
@@ -327,8 +328,8 @@ def test_tensor_operator_matches_oracle(env, prec, hy, wy, K, G):
     gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
     wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
     ps = psfs.astype(np.float64)
-    assert rel_l2(yd, O.apply_H(x.astype(np.float64), ps, wr, wc)) <= TC_TOL[prec]
-    assert rel_l2(gd, O.apply_Ht(r.astype(np.float64), ps, wr, wc)) <= TC_TOL[prec]
+    assert_close(yd, O.apply_H(x.astype(np.float64), ps, wr, wc), TC_TOL[prec])
+    assert_close(gd, O.apply_Ht(r.astype(np.float64), ps, wr, wc), TC_TOL[prec])
     plan.close()
 
 
@@ -342,7 +343,7 @@ def test_tensor_solve_close_to_oracle(env, prec):
     assert plan.info.path == TENSOR and plan.info.fp32_path in (DIRECT, FFT)
     lay, xr, info = oracle_solve(w, psfs, y, 10, 10)
     tol = 1e-2 if prec == BF16 else 2e-3
-    assert rel_l2(xd, xr) <= tol
+    assert_close(xd, xr, tol)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
     assert abs(st["objective"] - F) <= tol * F
     plan.close()
@@ -369,7 +370,7 @@ def test_paper_mode_solve_matches_oracle(env, path, prec, tol):
     ps, y64 = psfs.astype(np.float64), y.astype(np.float64)
     xr, info = O.solve(y64, ps, lay, w.lam, w.delta, w.gamma, w.rho, 4, 3, inner_increment=2,
                        weights="per_tile")
-    assert rel_l2(xd.cpu().numpy(), xr) <= tol
+    assert_close(xd.cpu().numpy(), xr, tol)
     F = O.objective(xr, y64, ps, lay, w.lam, w.delta, weights="per_tile")[0]
     assert abs(st["objective"] - F) <= tol * F
     assert st["inner_done"] == 3 + 5 + 7 + 9
@@ -377,7 +378,7 @@ def test_paper_mode_solve_matches_oracle(env, path, prec, tol):
     x = g.uniform(0, 1, plan.nx).astype(np.float32)
     hx = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
     wr, wc = O.bilinear_weights(plan.nx[0], G[0]), O.bilinear_weights(plan.nx[1], G[1])
-    assert rel_l2(hx, O.apply_H(x.astype(np.float64), ps, wr, wc)) <= max(tol, 1e-5)
+    assert_close(hx, O.apply_H(x.astype(np.float64), ps, wr, wc), max(tol, 1e-5))
     plan.close()
 
 
@@ -413,7 +414,7 @@ def test_vmlmb_solve_matches_oracle(env, path):
     plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 4, path=path, local_solver=1, vm_memory=3)
     assert st["inner_done"] == 12
     lay, xr, info = oracle_solve(w, psfs, y, 3, 4, local_solver="vmlmb", vm_memory=3)
-    assert rel_l2(xd, xr) <= 1e-4
+    assert_close(xd, xr, 1e-4)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
     assert abs(st["objective"] - F) <= 1e-5 * F
     plan.close()

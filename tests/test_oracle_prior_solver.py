@@ -286,3 +286,40 @@ def test_single_tile_is_centralised_solver():
                          inner_increment=10)
     np.testing.assert_allclose(info.us[0], info.xs[0], atol=1e-14)
     np.testing.assert_allclose(xhat, ref, atol=1e-7)
+
+
+# --------------------------------------------------------------------------- residuals
+
+
+def test_dual_and_primal_residuals_golden(golden_dir):
+    """Two outer iterations of Algorithm 1 derived by hand (one tile, H = I,
+    no prior): iterates, duals and both residuals of the oracle's solve."""
+    d = json.load(open(os.path.join(golden_dir, "dual_residual_two_iterations.json")))
+    y = np.array(d["y"], dtype=float)
+    lay = O.make_layout(y.shape[0], y.shape[1], 1, 1, 1, 0)
+    psfs = np.ones((1, 1, 1, 1))
+    assert abs(O.tile_step(lay, 0, 0, psfs, None, d["lambda"], d["gamma"]) - d["tau"]) <= 1e-15
+    for k in (1, 2):
+        _, info = O.solve(y, psfs, lay, d["lambda"], 1.0 / 60.0, d["gamma"], d["rho"], k, 1,
+                          x0=np.array(d["x0"], dtype=float))
+        np.testing.assert_allclose(info.xs[0], d["x"][k - 1], atol=1e-15)
+        np.testing.assert_allclose(info.us[0], d["u"][k - 1], atol=1e-15)
+        np.testing.assert_allclose(info.primal, d["primal"][:k], atol=1e-15)
+        np.testing.assert_allclose(info.dual, d["dual"][:k], atol=1e-15)
+
+
+def test_dual_residual_alpha_metric_reading():
+    """Reading of the dual residual: the unweighted ||zbar^k - zbar^(k-1)||
+    the oracle reports times rho sqrt(gamma) is the product-space norm
+    rho ||zbar^k - zbar^(k-1)||_alpha summed over the tiles, because
+    sum_i alpha_i(l) = gamma sum_i omega_i(l) = gamma at every x pixel."""
+    from paper_1705_06603_gb300.synth import WORKLOADS
+    w = WORKLOADS["disks128"]
+    lay = O.make_layout(w.hy, w.wy, w.K, *w.n_tiles, w.overlap, w.yrows, w.ycols)
+    g = np.random.default_rng(11)
+    dz = g.standard_normal(lay.nx)
+    gamma, rho = 0.4, 1.7
+    prod = sum(np.sum(gamma * lay.omega(tr, tc) * dz[lay.xslice(tr, tc)] ** 2)
+               for tr, tc in lay.tiles)
+    assert abs(rho * np.sqrt(prod) - rho * np.sqrt(gamma) * np.linalg.norm(dz)) <= \
+        1e-12 * rho * np.sqrt(gamma) * np.linalg.norm(dz)
