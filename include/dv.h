@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define DV_ABI_VERSION 1
+#define DV_ABI_VERSION 2
 
 typedef enum dv_status {
   DV_OK = 0,
@@ -114,10 +114,13 @@ typedef enum dv_local_solver {
    * projected-gradient step when memory is empty or the direction is not a
    * descent direction.  One inner iteration = one VMLM-B iteration.  Runs
    * eagerly, driven from the host with per-tile scalars (use_graphs does not
-   * apply).  Its objectives and gradients use the plan's inner operator path:
-   * with BF16 / TF32 operands the Armijo comparisons carry that operator's
-   * error, so near convergence trials may fail and empty the memory; the FP32
-   * paths give the exact method. */
+   * apply).  Its objectives and gradients use the plan's inner operator path;
+   * they are FP64 sums of per-pixel terms formed in FP32 (or from BF16 / TF32
+   * operands), which resolve relative changes of about 1e-7 and no finer, so
+   * near convergence the Armijo comparisons can fail on rounding alone.  A tile
+   * therefore ends its local solve once the decrease a full step promises,
+   * -g'd, is at most vm_stop_rel |Phi_i| (dv_problem.vm_stop_rel; 0 runs every
+   * iteration).  dv_stats reports the Armijo trials. */
   DV_SOLVER_VMLMB = 1
 } dv_local_solver;
 
@@ -168,7 +171,11 @@ typedef struct dv_problem {
   double noise_sigma;
   int32_t local_solver;    /* dv_local_solver */
   int32_t vm_memory;       /* VMLM-B memory pairs, 1..32 (0: 5) */
-  int32_t reserved[3];
+  /* VMLM-B: a tile ends its local solve once -g'd <= vm_stop_rel |Phi_i(w)|
+   * (>= 0; dv_problem_init sets 1e-7, the resolution of the FP32-formed
+   * objective; 0 runs every iteration) */
+  double vm_stop_rel;
+  int32_t reserved[2];
 } dv_problem;
 
 typedef struct dv_stats {
@@ -181,6 +188,15 @@ typedef struct dv_stats {
   int32_t inner_done;      /* projected-gradient steps per tile performed */
   double ms_total;         /* wall time of the solve on the stream (events) */
   int64_t kernel_launches; /* libdv kernels launched by the call */
+  /* VMLM-B Local-Solver (0 for projected gradient): Armijo trials per
+   * iteration of the batched line search (the maximum over the tiles still
+   * iterating), averaged over the iterations of the call, and their maximum;
+   * trials per iteration of one tile averaged over (tile, iteration); and the
+   * number of (tile, local solve) pairs ended by the vm_stop_rel test */
+  double vm_trials_per_iter;
+  double vm_tile_trials;
+  int32_t vm_trials_max;
+  int32_t vm_stops;
 } dv_stats;
 
 typedef struct dv_plan dv_plan;
@@ -305,6 +321,25 @@ dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);
 dv_status dv_plan_set_timing(dv_plan* plan, int32_t enable);
 dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int64_t* launches);
 
+/* Bound, in seconds, of every pipeline wait (mbarrier) of the BF16
+ * tensor-core operator kernels this plan launches from now on; 0 restores the
+ * default of 2 s, at most 60.  A wait that runs out sets the plan's device
+ * error word and makes every role of its CTA stop, wait (bounded) for the
+ * copies and MMAs it issued, free its tensor memory and return, so the context
+ * stays usable; the next call that synchronises (a solve with stats or
+ * objective checks, a host-buffer solve) returns DV_ERR_TIMEOUT, after which
+ * only dv_destroy is valid.  Drops the plan's captured CUDA graphs (they are
+ * captured again with the new bound) and synchronises the device. */
+dv_status dv_plan_set_wait_limit(dv_plan* plan, double seconds);
+
+/* Test of that failure path, with no GPU fault, trap or hang: with
+ * withhold = 1 the BF16 tensor-core kernels of this plan issue none of their
+ * operand copies, so the first ring wait of every CTA's MMA lane runs out
+ * (after the wait limit) with no copy or MMA in flight and the solve reports
+ * DV_ERR_TIMEOUT; 0 turns it off.  Drops the captured graphs and synchronises
+ * the device, like dv_plan_set_wait_limit. */
+dv_status dv_plan_set_wait_test(dv_plan* plan, int32_t withhold);
+
 /* Allocation-free Huber prior value (the paper has no counterpart; this is a
  * service for callers that may not allocate device memory, such as plug-ins
  * running inside a host framework that owns all device memory, or real-time
@@ -318,10 +353,14 @@ dv_status dv_plan_kernel_time(dv_plan* plan, int32_t kind, double* total_ms, int
  * and 256 columns, so rows * ceil(cols / 256) must not exceed
  * DV_NOALLOC_MAX_BLOCKS and rows must not exceed 65535; larger images are
  * rejected with DV_ERR_INVALID_ARG.  The first call on each device looks up
- * the array's device address (no allocation); make that first call before any
- * stream capture.  All calls share the array, so calls whose work overlaps on
- * the GPU (different streams, no ordering) race and give wrong sums; calls
- * ordered on one stream are safe.  Enqueued on stream; returns without
+ * the array's device address (no allocation of its own); under CUDA's lazy
+ * module loading that first call also loads this part of the library onto the
+ * device, which places the array and the kernels in device memory, so make it
+ * before a host framework reserves the device memory it manages, and before
+ * any stream capture.  All calls share the array, so calls whose work overlaps
+ * on the GPU (different streams, no ordering) race and give wrong sums; calls
+ * ordered on one stream are safe.  Runs on the calling thread's current device
+ * (x_dev and value_dev must be on it).  Enqueued on stream; returns without
  * synchronising. */
 #define DV_NOALLOC_MAX_BLOCKS 65536
 dv_status dv_prior_value_noalloc(const float* x_dev, int32_t rows, int32_t cols, double delta,

@@ -76,6 +76,14 @@ Readings taken where the paper is silent, ambiguous or garbled:
      1e-4 g'(w(a) - w), a = 1, 1/2, ..., at most 20 trials; no acceptance: stay
      and empty the memory.  The pair (s, y) is kept if s'y > 0 (the oldest of
      m + 1 dropped), else the memory is emptied.
+ R21 VMLM-B stop at the objective's resolution (the paper runs a fixed
+     number of VMLM-B iterations per local solve, Sec. IV-B): with stop_rel >
+     0 a tile ends its local solve -- keeps its iterate for the remaining
+     iterations -- as soon as the first-order decrease promised by a full step
+     along its direction, -g'd, is at most stop_rel * |Phi_i(w)|.  Objectives
+     formed from FP32 residuals do not resolve smaller changes (about 1e-7
+     relative), so without the stop their Armijo tests fail on rounding alone.
+     stop_rel = 0 (the default here) runs every iteration.
  R18 One PSF per block (weights="per_tile", the paper's own layout, Sec.
      III-A and III-C): the PSF grid is the tile grid and tile (tr, tc) blurs
      with PSF (tr, tc) alone, weight 1 on the whole tile; its step uses L_H of
@@ -413,8 +421,12 @@ def local_solve(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau, n_in
     return w
 
 
-def local_solve_vmlmb(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau, n_iter, m=5):
-    """n_iter VMLM-B iterations of reading R20 on Phi_i from w."""
+def local_solve_vmlmb(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau, n_iter, m=5,
+                      stop_rel=0.0, stats=None):
+    """n_iter VMLM-B iterations of reading R20 on Phi_i from w, ending early
+    under reading R21 when stop_rel > 0.  stats (a dict, optional) receives
+    "trials" (Armijo trials of every iteration run) and "stopped_at" (the
+    iteration at which the stop of R21 ended the solve, or None)."""
     def phi(v):
         return prox_objective(v, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta)
 
@@ -426,8 +438,11 @@ def local_solve_vmlmb(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau
 
     pairs = []            # (s, y, 1 / s'y), oldest first
     h0 = 1.0
+    if stats is not None:
+        stats.setdefault("trials", [])
+        stats["stopped_at"] = None
     f, g = phi(w), grad(w)
-    for _ in range(n_iter):
+    for it in range(n_iter):
         free = (w > 0) | (g < 0)
         q = np.where(free, g, 0.0)
         a = []
@@ -444,14 +459,20 @@ def local_solve_vmlmb(w, u, y_i, W_i, psfs, wr_i, wc_i, alpha_i, lam, delta, tau
         if not float(np.sum(g * d)) < 0.0:
             pairs = []
             d = np.where(free, -tau * g, 0.0)
+        if stop_rel > 0.0 and -float(np.sum(g * d)) <= stop_rel * abs(f):
+            if stats is not None:
+                stats["stopped_at"] = it
+            break
         step, wt, ft = 1.0, None, None
-        for _ in range(20):
+        for trial in range(20):
             cand = np.maximum(0.0, w + step * d)
             fc = phi(cand)
             if fc <= f + 1e-4 * float(np.sum(g * (cand - w))):
                 wt, ft = cand, fc
                 break
             step *= 0.5
+        if stats is not None:
+            stats["trials"].append(trial + 1)
         if wt is None:
             pairs = []
             wt, ft = w.copy(), f
@@ -528,7 +549,7 @@ class SolveInfo:
 
 def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
           inner_increment=0, W=None, x0=None, weights=None, history=False,
-          local_solver="pg", vm_memory=5):
+          local_solver="pg", vm_memory=5, vm_stop_rel=0.0, vm_stats=None):
     """Algorithm 1 with the explicit D-R updates of Sec. III-B:
       x_i   <- Local-Solver(u_i; alpha_i, f_i)                    (all tiles)
       zbar  <- sum alpha_i (2 x_i - u_i) / sum alpha_i             (Lemma 1)
@@ -555,7 +576,8 @@ def solve(y, psfs, layout: Layout, lam, delta, gamma, rho, n_outer, n_inner,
             pi, wri, wci = ops[n]
             Wi = None if W is None else W[layout.yslice(tr, tc)]
             solver = local_solve if local_solver == "pg" else local_solve_vmlmb
-            extra = {} if local_solver == "pg" else {"m": vm_memory}
+            extra = ({} if local_solver == "pg" else
+                     {"m": vm_memory, "stop_rel": vm_stop_rel, "stats": vm_stats})
             xs[n] = solver(xs[n], us[n], y[layout.yslice(tr, tc)], Wi, pi, wri, wci,
                            alphas[n], lam, delta, taus[n], ni, **extra)
         zbar = consensus_average(layout, [2.0 * x - u for x, u in zip(xs, us)], alphas)

@@ -124,6 +124,9 @@ struct OpArgs {
   int32_t pad3;
   int* err;               // tensor-core path: nonzero after a bounded wait gave up
   const uint16_t* ksr;    // BF16 tensor-core path: [n_work][kTcMaxB] k-step ranges (lo | hi << 8)
+  uint64_t wait_ns;       // BF16 tensor-core path: bound of a pipeline wait (0: 2 s)
+  int32_t test_withhold;  // BF16 tensor-core path: issue no operand copy (dv_plan_set_test_fault)
+  int32_t pad4;
 };
 
 // One item of the consensus / assembly kernels: a rectangle of the global x
@@ -293,6 +296,8 @@ struct dv_plan {
   unsigned char* d_tcopH = nullptr;   // tensor-core B operands (flipped PSFs, for H)
   unsigned char* d_tcopHt = nullptr;  // tensor-core B operands (PSFs, for H^T)
   int* d_err = nullptr;               // device error word of the tensor-core kernels
+  uint64_t wait_ns = 0;               // bound of the BF16 tensor kernels' waits (0: 2 s)
+  int test_fault = 0;                 // dv_plan_set_test_fault kind
   double tune_ms[3] = {0.0, 0.0, 0.0};  // autotuner: one H + one H^T apply per path
   dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
   float* d_desc = nullptr;         // per-PSF descriptors [G][3]
@@ -344,6 +349,13 @@ struct dv_plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // VMLM-B Local-Solver (dv_problem.local_solver = DV_SOLVER_VMLMB), lazy
   int vm_m = 5;                          // memory pairs
+  // Armijo trial counts of the current call (reset by the solve entry points)
+  int64_t vm_iters = 0;                  // batched VMLM-B iterations run
+  int64_t vm_trials = 0;                 // sum over iterations of the trials run
+  int64_t vm_tile_iters = 0;             // (tile, iteration) pairs that searched
+  int64_t vm_tile_trials = 0;            // their trials
+  int vm_trials_max = 0;
+  int vm_stops = 0;                      // (tile, local solve) pairs ended by vm_stop_rel
   float* d_vg = nullptr;                 // gradient at the iterate
   float* d_vgt = nullptr;                // gradient at the new iterate
   float* d_vd = nullptr;                 // search direction

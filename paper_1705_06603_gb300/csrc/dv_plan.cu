@@ -246,6 +246,8 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     return fail(DV_ERR_INVALID_ARG, "unknown local_solver %d", p->local_solver);
   if (p->vm_memory < 0 || p->vm_memory > 32)
     return fail(DV_ERR_INVALID_ARG, "vm_memory must be in [0, 32] (0: 5)");
+  if (!(p->vm_stop_rel >= 0.0) || !std::isfinite(p->vm_stop_rel))
+    return fail(DV_ERR_INVALID_ARG, "vm_stop_rel must be finite and >= 0");
   if (!(p->noise_sigma >= 0.0)) return fail(DV_ERR_INVALID_ARG, "noise_sigma must be >= 0");
 
   const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
@@ -422,6 +424,8 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
   a.tcop = p->d_tcopH;
   a.prec = p->prob.precision;
   a.err = p->d_err;
+  a.wait_ns = p->wait_ns;
+  a.test_withhold = p->test_fault;
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
@@ -510,6 +514,7 @@ extern "C" void dv_problem_init(dv_problem* p) {
   p->precision = DV_PREC_FP32;
   p->path = DV_PATH_AUTO;
   p->use_graphs = 1;
+  p->vm_stop_rel = 1e-7;
 }
 
 extern "C" dv_status dv_layout_query(const dv_problem* prob, int32_t* tile_r0, int32_t* tile_r1,

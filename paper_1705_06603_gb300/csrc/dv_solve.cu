@@ -331,8 +331,19 @@ dv_status finish(dv_plan* P, float* x_out, dv_stats* st, const RunResult& rr, in
     DV_TRY_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
     st->ms_total = ms;
     st->kernel_launches = P->launches - l0;
+    st->vm_trials_per_iter = P->vm_iters > 0 ? (double)P->vm_trials / (double)P->vm_iters : 0.0;
+    st->vm_tile_trials =
+        P->vm_tile_iters > 0 ? (double)P->vm_tile_trials / (double)P->vm_tile_iters : 0.0;
+    st->vm_trials_max = P->vm_trials_max;
+    st->vm_stops = P->vm_stops;
   }
   return DV_OK;
+}
+
+// Clears the per-call Armijo counters of the VMLM-B Local-Solver.
+void reset_call_counters(dv_plan* P) {
+  P->vm_iters = P->vm_trials = P->vm_tile_iters = P->vm_tile_trials = 0;
+  P->vm_trials_max = P->vm_stops = 0;
 }
 
 dv_status check_plan(const dv_plan* P) {
@@ -344,6 +355,7 @@ dv_status check_plan(const dv_plan* P) {
 dv_status solve_internal(dv_plan* P, const float* x0, float* x_out, dv_stats* st, cudaStream_t s,
                          int64_t l0) {
   Range range("dv solve");
+  reset_call_counters(P);
   const GridArgs g = grid_args(P);
   const bool track_z = st || P->prob.check_every > 0;
   if (!x0 && P->prob.use_warmstart) {
@@ -420,7 +432,11 @@ extern "C" dv_status dv_consensus_solve_host(dv_plan* P, const float* y_host, co
     DV_TRY_CUDA(cudaMemcpyAsync(P->d_hx0, x0_host, nx * sizeof(float), cudaMemcpyHostToDevice, s));
   DV_TRY(solve_internal(P, x0_host ? P->d_hx0 : nullptr, P->d_xg, stats, s, l0));
   DV_TRY_CUDA(cudaMemcpyAsync(x_out_host, P->d_xg, nx * sizeof(float), cudaMemcpyDeviceToHost, s));
+  int* h_err = reinterpret_cast<int*>(P->h_scal + 6);
+  DV_TRY_CUDA(cudaMemcpyAsync(h_err, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   DV_TRY_CUDA(cudaStreamSynchronize(s));
+  if (*h_err != 0)
+    return fail(DV_ERR_TIMEOUT, "a tensor-core operator kernel gave up waiting on its pipeline");
   return DV_OK;
 }
 
@@ -436,6 +452,7 @@ extern "C" dv_status dv_consensus_continue(dv_plan* P, const float* y_dev, int32
   DV_TRY_CUDA(cudaMemcpyAsync(P->d_y, y_dev, (size_t)P->hy * P->wy * sizeof(float),
                               cudaMemcpyDeviceToDevice, s));
   RunResult rr;
+  reset_call_counters(P);
   if ((stats || P->prob.check_every > 0) && n_outer > 0) {
     // the dual residual needs the previous zbar: rebuild it from the current state
     DV_TRY_CUDA(launch_assemble(grid_args(P), P->d_w[P->cur], P->d_z, s));
@@ -469,6 +486,41 @@ extern "C" dv_status dv_state_import(dv_plan* P, const float* x_stack_dev, const
   DV_TRY_CUDA(cudaMemcpyAsync(P->d_u, u_stack_dev, b, cudaMemcpyDeviceToDevice, s));
   P->cur = 0;
   P->outer_done = outer_done;
+  return DV_OK;
+}
+
+namespace dv {
+namespace {
+// Destroys the captured local solves (they hold the kernel arguments of the
+// time of capture); they are captured again on their next use.
+dv_status drop_graphs(dv_plan* P) {
+  DV_TRY_CUDA(cudaDeviceSynchronize());
+  for (GraphEntry& g : P->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  P->graphs.clear();
+  return DV_OK;
+}
+}  // namespace
+}  // namespace dv
+
+extern "C" dv_status dv_plan_set_wait_limit(dv_plan* P, double seconds) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (!(seconds >= 0.0 && seconds <= 60.0))
+    return fail(DV_ERR_INVALID_ARG, "the wait limit must be in [0, 60] seconds");
+  DV_TRY(drop_graphs(P));
+  P->wait_ns = (uint64_t)(seconds * 1e9);
+  return DV_OK;
+}
+
+extern "C" dv_status dv_plan_set_wait_test(dv_plan* P, int32_t withhold) {
+  clear_error();
+  DV_TRY(check_plan(P));
+  if (withhold != 0 && withhold != 1) return fail(DV_ERR_INVALID_ARG, "withhold must be 0 or 1");
+  DV_TRY(drop_graphs(P));
+  P->test_fault = withhold;
   return DV_OK;
 }
 

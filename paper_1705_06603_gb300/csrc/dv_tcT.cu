@@ -25,7 +25,7 @@
 // 32 (w % 4) .. + 31 = its tensor-memory lanes, and rows 16 (w / 4) .. + 15 of
 // every 32-row chunk of the accumulator), warp 8 allocates tensor memory and
 // one of its lanes issues the MMAs, one lane of warp 9 refills the ring.
-// Every wait is bounded (see dv_tcgen05.cuh).
+// Every wait is bounded (see dv_tcgen05.cuh), by OpArgs.wait_ns when set.
 #include <algorithm>
 #include <climits>
 #include <cstring>
@@ -90,6 +90,7 @@ struct Bars {
   uint64_t sfull[2], sempty[2];  // S buffer staged / consumed (H: per PSF, H^T: buffer 0 once)
   uint64_t dfull[2], dempty[2];  // accumulator buffer complete / read (H: buffer 0 only)
   uint64_t fin;
+  uint64_t wait_ns;           // bound of every pipeline wait of this launch
   uint32_t tmem;
   int abort;
   int ksr[kMaxB];             // k-step range of PSF grid column b_lo + b: lo | hi << 8
@@ -99,7 +100,7 @@ static_assert(sizeof(Bars) <= kHdr, "barrier header");
 __device__ __forceinline__ void sync_stage() { named_sync<NT>(); }
 __device__ __forceinline__ bool all_stage(bool v) { return named_all<NT>(v); }
 
-__device__ __forceinline__ void init_bars(Bars* H) {
+__device__ __forceinline__ void init_bars(Bars* H, uint64_t wait_ns) {
   for (int s = 0; s < NST; ++s) {
     mbar_init(&H->rfull[s], 1);
     mbar_init(&H->rempty[s], 1);
@@ -114,6 +115,7 @@ __device__ __forceinline__ void init_bars(Bars* H) {
   }
   mbar_init(&H->fin, 1);
   H->abort = 0;
+  H->wait_ns = wait_ns ? wait_ns : kWaitNs;
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
@@ -122,12 +124,15 @@ __device__ __forceinline__ void init_bars(Bars* H) {
 template <int K>
 __device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned char* ring, int np) {
   using G = GeoT<K>;
+  // test of the bounded waits (dv_plan_set_test_fault): no copy is issued, so
+  // the MMA lane's first wait on the ring runs out with nothing in flight
+  if (A.test_withhold) return;
   const int nb = wi.b_hi - wi.b_lo + 1;
   const int total = np * K;
   int issued = 0;
   for (int it = 0; it < total; ++it) {
     const int s = it % NST;
-    if (it >= NST && !wait_bar(&H->rempty[s], (uint32_t)((it / NST - 1) & 1), &H->abort, A.err))
+    if (it >= NST && !wait_bar(&H->rempty[s], (uint32_t)((it / NST - 1) & 1), &H->abort, A.err, H->wait_ns))
       break;
     const int p = it / K, a = it - p * K;
     const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
@@ -186,10 +191,10 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
   bool fresh = true;   // the next MMA overwrites the accumulator
   for (int p = 0; p < np && ok; ++p) {
     if (ADJ) {
-      ok = p == 0 ? wait_bar(&H->sfull[0], 0, &H->abort, A.err)
-                  : wait_bar(&H->dempty[0], (uint32_t)((p - 1) & 1), &H->abort, A.err);
+      ok = p == 0 ? wait_bar(&H->sfull[0], 0, &H->abort, A.err, H->wait_ns)
+                  : wait_bar(&H->dempty[0], (uint32_t)((p - 1) & 1), &H->abort, A.err, H->wait_ns);
     } else {
-      ok = wait_bar(&H->sfull[p & 1], (uint32_t)((p >> 1) & 1), &H->abort, A.err);
+      ok = wait_bar(&H->sfull[p & 1], (uint32_t)((p >> 1) & 1), &H->abort, A.err, H->wait_ns);
     }
     if (!ok) break;
     tc_fence_after();
@@ -202,7 +207,7 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
                          (uint64_t)(2 * klo * (G::SPANEL >> 4));
     if (ADJ) fresh = true;
     for (int a = 0; a < K; ++a) {
-      if (!wait_bar(&H->rfull[s], ph, &H->abort, A.err)) {
+      if (!wait_bar(&H->rfull[s], ph, &H->abort, A.err, H->wait_ns)) {
         ok = false;
         break;
       }
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
   const TileDesc td = A.tiles[wi.tile];
   const int nrow = wi.pad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) init_bars(H);
+  if (tid == 0) init_bars(H, A.wait_ns);
   if (warp == NWE) {
     tmem_alloc(&H->tmem, G::TMEM_H);
     load_ranges(A, H, lane);
@@ -401,7 +406,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       sync_stage();
       // S buffer p & 1 was last read by PSF p - 2
       if (p >= 2) {
-        ok = all_stage(wait_bar(&H->sempty[p & 1], (uint32_t)(((p >> 1) - 1) & 1), &H->abort, A.err));
+        ok = all_stage(wait_bar(&H->sempty[p & 1], (uint32_t)(((p >> 1) - 1) & 1), &H->abort, A.err, H->wait_ns));
         if (!ok) break;
       }
       restage_h<K>(sS + (p & 1) * G::SBYTES, img, td.xpitch, al, wi.r0, wi.c0, td.nxr, td.nxc, sWr,
@@ -417,7 +422,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
     constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
     const bool obs = A.mode != OP_PLAIN;
     if (ok && np >= 2)   // the other buffer was last read by PSF np - 2
-      ok = all_stage(wait_bar(&H->sempty[np & 1], (uint32_t)(((np - 2) >> 1) & 1), &H->abort, A.err));
+      ok = all_stage(wait_bar(&H->sempty[np & 1], (uint32_t)(((np - 2) >> 1) & 1), &H->abort, A.err, H->wait_ns));
     float* sYb = reinterpret_cast<float*>(sS + (np & 1) * G::SBYTES);   // [2][32 * MC] observed image
     float* sWb = sYb + 2 * 32 * MC;                      // [2][32 * MC] noise weights
     auto prefetch = [&](int i0, int buf) {
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (ok && np > 0) prefetch(0, 0);
-    if (ok && np > 0) ok = all_stage(wait_bar(&H->dfull[0], 0, &H->abort, A.err));
+    if (ok && np > 0) ok = all_stage(wait_bar(&H->dfull[0], 0, &H->abort, A.err, H->wait_ns));
     if (ok && np == 0) prefetch(0, 0);
     tc_fence_after();
     sync_stage();
@@ -516,7 +521,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
   const TileDesc td = A.tiles[wi.tile];
   const int nrow = wi.pad;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) init_bars(H);
+  if (tid == 0) init_bars(H, A.wait_ns);
   if (warp == NWE) {
     tmem_alloc(&H->tmem, G::TMEM_HT);
     load_ranges(A, H, lane);
@@ -624,7 +629,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
         }
       if (step)
         for (int k = 0; k < qper && qc < nck; ++k) q_chunk(32 * qc++);
-      if (!all_stage(wait_bar(&H->dfull[0], (uint32_t)(p & 1), &H->abort, A.err))) {
+      if (!all_stage(wait_bar(&H->dfull[0], (uint32_t)(p & 1), &H->abort, A.err, H->wait_ns))) {
         ok = false;
         break;
       }

@@ -41,22 +41,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Pipeline wait: false after kWaitNs (the CTA-wide abort flag set and the
+// Pipeline wait: false after limit_ns (the CTA-wide abort flag set and the
 // timeout recorded in err), or at once when another role has already given up.
-static __device__ __noinline__ bool wait_bar_slow(uint64_t* b, uint32_t parity, int* abort, int* err) {
+static __device__ __noinline__ bool wait_bar_slow(uint64_t* b, uint32_t parity, int* abort, int* err,
+                                                  uint64_t limit_ns) {
   const uint64_t t0 = gtime();
   while (true) {
     if (mbar_try(b, parity)) return true;
     if (*(volatile int*)abort) return false;
-    if (gtime() - t0 > kWaitNs) {
+    if (gtime() - t0 > limit_ns) {
       *(volatile int*)abort = 1;
       if (err) atomicExch(err, 1);
       return false;
     }
   }
 }
-__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, int* abort, int* err) {
-  return mbar_try(b, parity) || wait_bar_slow(b, parity, abort, err);
+__device__ __forceinline__ bool wait_bar(uint64_t* b, uint32_t parity, int* abort, int* err,
+                                         uint64_t limit_ns = kWaitNs) {
+  return mbar_try(b, parity) || wait_bar_slow(b, parity, abort, err, limit_ns);
 }
 // Teardown wait for work this CTA issued: ignores the abort flag, own bound.
 static __device__ __noinline__ bool drain_bar(uint64_t* b, uint32_t parity, int* err) {

@@ -396,6 +396,9 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
   std::vector<double> phi, gd, lin, sy, yy;
   std::vector<double> rho((size_t)m * T, 0.0), gamma0(T, 1.0), tau(T);
   std::vector<int> npair(T, 0);
+  // frozen[t]: tile t ended this local solve under the vm_stop_rel test
+  std::vector<int> frozen(T, 0);
+  const double stop_rel = P->prob.vm_stop_rel;
   for (int t = 0; t < T; ++t) tau[t] = P->tau[t];
   auto clear = [&](int t) {
     npair[t] = 0;
@@ -403,6 +406,7 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
   };
   DV_TRY(V.objective(P->d_w[par], phi));
   DV_TRY(V.gradient(P->d_w[par], P->d_vg));
+  int it_run = 0;
   for (int it = 0; it < n_iter; ++it) {
     float* w = P->d_w[par];
     float* wt = P->d_w[par ^ 1];
@@ -459,9 +463,21 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
       DV_TRY(V.axpy(P->d_vd, P->d_vq, step, 0));
       DV_TRY(V.dot(P->d_vg, P->d_vd, nullptr, 0, gd));
     }
+    // a tile whose full step promises a decrease below the resolution of its
+    // objective ends its local solve: it keeps its iterate from here on
+    int active = 0;
+    for (int t = 0; t < T; ++t) {
+      if (!frozen[t] && stop_rel > 0.0 && -gd[t] <= stop_rel * std::fabs(phi[t])) {
+        frozen[t] = 1;
+        P->vm_stops += 1;
+      }
+      active += !frozen[t];
+    }
+    if (active == 0) break;
     // Armijo along the projection arc, alpha = 1, 1/2, ...
     std::vector<double> alpha(T, 1.0), acc(T, 0.0), phit, phinew(phi);
-    std::vector<int> done(T, 0);
+    std::vector<int> done(frozen), tries(T, 0);
+    int trials_run = 0;
     for (int trial = 0; trial < 20; ++trial) {
       std::vector<double> at(T);
       bool any = false;
@@ -470,6 +486,7 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
         any = any || !done[t];
       }
       if (!any) break;
+      trials_run = trial + 1;
       DV_TRY(V.trial(w, P->d_vd, at, wt));
       VmState::ObjParts o;
       int64_t olin;
@@ -480,6 +497,7 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
       V.sum(olin, V.nch, lin);
       for (int t = 0; t < T; ++t) {
         if (done[t]) continue;
+        tries[t] = trial + 1;
         if (phit[t] <= phi[t] + 1e-4 * lin[t]) {
           done[t] = 1;
           acc[t] = alpha[t];
@@ -497,6 +515,14 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
       }
     if (failed) DV_TRY(V.trial(w, P->d_vd, acc, wt));   // unaccepted tiles stay put
     phi = phinew;
+    P->vm_iters += 1;
+    P->vm_trials += trials_run;
+    P->vm_trials_max = std::max(P->vm_trials_max, trials_run);
+    for (int t = 0; t < T; ++t)
+      if (!frozen[t]) {
+        P->vm_tile_iters += 1;
+        P->vm_tile_trials += tries[t];
+      }
     // gradient at the new iterate and the pair (s, y) = (wt - w, gt - g)
     DV_TRY(V.gradient(wt, P->d_vgt));
     const int sl = it % m;
@@ -526,7 +552,13 @@ dv_status vmlmb_local_solve(dv_plan* P, int n_iter, cudaStream_t s) {
       }
     }
     par ^= 1;
+    it_run = it + 1;
   }
+  // every tile stopped early: the result is in d_w[par]; the caller expects it
+  // where n_iter iterations would leave it
+  if ((it_run & 1) != (n_iter & 1))
+    DV_TRY_CUDA(cudaMemcpyAsync(P->d_w[P->cur ^ (n_iter & 1)], P->d_w[par], n * sizeof(float),
+                                cudaMemcpyDeviceToDevice, s));
   return DV_OK;
 }
 

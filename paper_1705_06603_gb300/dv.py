@@ -53,14 +53,16 @@ class dv_problem(C.Structure):
                 ("check_every", C.c_int32), ("target_objective", C.c_double),
                 ("use_graphs", C.c_int32), ("noise_sigma", C.c_double),
                 ("local_solver", C.c_int32), ("vm_memory", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("vm_stop_rel", C.c_double), ("reserved", C.c_int32 * 2)]
 
 
 class dv_stats(C.Structure):
     _fields_ = [("objective", C.c_double), ("data_term", C.c_double),
                 ("prior_term", C.c_double), ("primal_res", C.c_double),
                 ("dual_res", C.c_double), ("outer_done", C.c_int32), ("inner_done", C.c_int32),
-                ("ms_total", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_total", C.c_double), ("kernel_launches", C.c_int64),
+                ("vm_trials_per_iter", C.c_double), ("vm_tile_trials", C.c_double),
+                ("vm_trials_max", C.c_int32), ("vm_stops", C.c_int32)]
 
 
 class dv_plan_info(C.Structure):
@@ -90,6 +92,8 @@ _sigs = {
     "dv_state_import": (C.c_int, [_vp, _vp, _vp, C.c_int32, _vp]),
     "dv_plan_get_info": (C.c_int, [_vp, C.POINTER(dv_plan_info)]),
     "dv_plan_set_timing": (C.c_int, [_vp, C.c_int32]),
+    "dv_plan_set_wait_limit": (C.c_int, [_vp, C.c_double]),
+    "dv_plan_set_wait_test": (C.c_int, [_vp, C.c_int32]),
     "dv_plan_kernel_time": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]),
     "dv_prior_value_noalloc": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_double, _vp, _vp]),
@@ -170,7 +174,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
                  noise_w=None, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, rho=1.0, n_outer=30,
                  n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
                  use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1,
-                 noise_sigma=0.0, local_solver=0, vm_memory=0):
+                 noise_sigma=0.0, local_solver=0, vm_memory=0, vm_stop_rel=None):
     """Builds a dv_problem.  weights: None (bilinear tents), (weights_r,
     weights_c) separable profiles, or "per_tile" (one PSF per tile, the PSF
     grid being the tile grid).  Returns (problem, keepalive) where keepalive
@@ -213,6 +217,8 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
     p.check_every, p.target_objective, p.use_graphs = check_every, target_objective, use_graphs
     p.noise_sigma = noise_sigma
     p.local_solver, p.vm_memory = local_solver, vm_memory
+    if vm_stop_rel is not None:
+        p.vm_stop_rel = vm_stop_rel
     return p, keep
 
 
@@ -281,6 +287,14 @@ def dv_plan_set_timing(plan, enable):
     _check(_lib.dv_plan_set_timing(plan, int(bool(enable))))
 
 
+def dv_plan_set_wait_limit(plan, seconds):
+    _check(_lib.dv_plan_set_wait_limit(plan, float(seconds)))
+
+
+def dv_plan_set_wait_test(plan, withhold):
+    _check(_lib.dv_plan_set_wait_test(plan, int(withhold)))
+
+
 def dv_plan_kernel_time(plan, kind):
     ms, n = C.c_double(), C.c_int64()
     _check(_lib.dv_plan_kernel_time(plan, int(kind), C.byref(ms), C.byref(n)))
@@ -316,16 +330,22 @@ def image_quality(x, ref, dynamic_range=1.0, stream=None):
 
 def dv_prior_value_noalloc(x, delta, value, stream=None):
     """Huber prior value of the 2-D image x written to value (a 1-element float64
-    CUDA tensor), with no device allocation (see include/dv.h)."""
+    CUDA tensor on x's device), with no device allocation (see include/dv.h).
+    The call is made with x's device current, on `stream` (default: that
+    device's current stream)."""
     import torch
     if not (isinstance(value, torch.Tensor) and value.is_cuda and value.dtype == torch.float64
             and value.numel() >= 1):
         raise TypeError("value must be a float64 CUDA tensor with at least one element")
+    _dptr(x, "x")
     if x.dim() != 2:
         raise ValueError("x must be a 2-D image")
-    _check(_lib.dv_prior_value_noalloc(_dptr(x, "x"), int(x.shape[0]), int(x.shape[1]),
-                                       float(delta), C.c_void_p(value.data_ptr()),
-                                       _stream_handle(stream)))
+    if value.device != x.device:
+        raise ValueError(f"value is on {value.device}, x on {x.device}: both must be on one GPU")
+    with torch.cuda.device(x.device):
+        st = _stream_handle(stream if stream is not None else torch.cuda.current_stream(x.device))
+        _check(_lib.dv_prior_value_noalloc(_dptr(x, "x"), int(x.shape[0]), int(x.shape[1]),
+                                           float(delta), C.c_void_p(value.data_ptr()), st))
 
 
 CNN_IN_CH = 5

@@ -413,11 +413,53 @@ def test_vmlmb_solve_matches_oracle(env, path):
     w, psfs, y, _ = workload_case("disks128")
     plan, xd, st = _gpu_solve(env, w, psfs, y, 3, 4, path=path, local_solver=1, vm_memory=3)
     assert st["inner_done"] == 12
-    lay, xr, info = oracle_solve(w, psfs, y, 3, 4, local_solver="vmlmb", vm_memory=3)
+    lay, xr, info = oracle_solve(w, psfs, y, 3, 4, local_solver="vmlmb", vm_memory=3,
+                                 vm_stop_rel=1e-7)
     assert_close(xd, xr, 1e-4)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
     assert abs(st["objective"] - F) <= 1e-5 * F
+    assert 1.0 <= st["vm_tile_trials"] <= st["vm_trials_per_iter"] <= st["vm_trials_max"] <= 20
     plan.close()
+
+
+def test_vmlmb_line_search_trials_stay_near_the_oracles(env):
+    """The paper's schedule with VMLM-B (25 % of it: 6 outer iterations of
+    10 + 10k iterations, one PSF per block) on the 128^2 workload: with the
+    stop at the objective's resolution (reading R21, vm_stop_rel = 1e-7 on both
+    sides) the batched line search needs about as many Armijo trials per
+    iteration as the FP64 oracle's (about one), where without it the tiles
+    near convergence spend up to 20 trials on rounding."""
+    torch, dv = env
+    w, psfs, y, _ = workload_case("disks128")
+    G = psfs.shape[:2]
+    kw = dict(n_tiles=G, weights="per_tile", lam=w.lam, delta=w.delta, gamma=w.gamma,
+              rho=w.rho, n_outer=6, n_inner=10, inner_increment=10, path=DIRECT,
+              local_solver=1, vm_memory=5)
+    res = {}
+    for stop in (1e-7, 0.0):
+        plan = dv.Plan(w.hy, w.wy, psfs, vm_stop_rel=stop, **kw)
+        xd, st = plan.solve(torch.from_numpy(y).cuda())
+        torch.cuda.synchronize()
+        res[stop] = (xd.cpu().numpy(), st)
+        plan.close()
+    lay = O.paper_layout(w.hy, w.wy, w.K, *G)
+    ps, y64 = psfs.astype(np.float64), y.astype(np.float64)
+    vst = {}
+    xr, _ = O.solve(y64, ps, lay, w.lam, w.delta, w.gamma, w.rho, 6, 10, inner_increment=10,
+                    weights="per_tile", local_solver="vmlmb", vm_memory=5, vm_stop_rel=1e-7,
+                    vm_stats=vst)
+    oracle_mean = float(np.mean(vst["trials"]))
+    xd, st = res[1e-7]
+    print(f"trials per iteration: GPU batched {st['vm_trials_per_iter']:.2f} (max "
+          f"{st['vm_trials_max']}), GPU per tile {st['vm_tile_trials']:.2f}, oracle per tile "
+          f"{oracle_mean:.2f}; without the stop: batched {res[0.0][1]['vm_trials_per_iter']:.2f}; "
+          f"stops {st['vm_stops']}")
+    assert oracle_mean <= 1.5
+    assert st["vm_tile_trials"] <= oracle_mean + 0.5
+    assert st["vm_trials_per_iter"] <= 2.5
+    F = O.objective(xr, y64, ps, lay, w.lam, w.delta, weights="per_tile")[0]
+    assert abs(st["objective"] - F) <= 1e-4 * F
+    assert abs(res[0.0][1]["objective"] - F) <= 1e-4 * F
 
 
 def test_grouped_tensor_solve_is_bit_identical_to_eager(env):
