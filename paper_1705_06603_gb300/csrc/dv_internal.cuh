@@ -226,13 +226,19 @@ cudaError_t launch_tcT_Ht(const OpArgs& a, cudaStream_t s);
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
-// One captured local solve (n_inner projected-gradient steps on all tiles),
-// replayed once per outer iteration.  With timing on, every kernel node is
-// bracketed by event-record nodes whose events are swapped before each launch.
+// One captured outer iteration of Algorithm 1: the local solve (n_inner
+// projected-gradient steps on all tiles), the consensus and dual update and,
+// when due, the kernels and read-back of the FP64 objective reduction;
+// replayed once per outer iteration.  With timing on, the timed units (every
+// operator kernel, or the whole local solve when its tile groups run
+// concurrently, and the consensus kernel) are bracketed by event-record nodes
+// whose events are swapped before each launch.
 struct GraphEntry {
   int n_inner = 0;
   int parity = 0;          // w buffer holding x_i when the local solve starts
   bool timed = false;
+  int cons = 0;            // 0: local solve only; 1: + consensus; bit 1: zbar tracked;
+                           // bit 2: residual partials; bit 3: objective reduction
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaGraphNode_t> ev_start, ev_end;  // per kernel node (timed only)

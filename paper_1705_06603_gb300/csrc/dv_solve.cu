@@ -125,7 +125,57 @@ dv_status capture_node(cudaStream_t cs, cudaGraphNode_t* node) {
   return DV_OK;
 }
 
-dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
+// Objective reduction of eval_objective, enqueued only: x_hat, its tile
+// restrictions, the FP32 operator's data-term partials, the prior partials,
+// the fixed-order FP64 sums and their read-back (with the device error word)
+// into pinned memory.
+dv_status enqueue_objective(dv_plan* P, bool residuals, cudaStream_t s) {
+  const GridArgs g = grid_args(P);
+  float* tmp = P->d_w[P->cur ^ 1];
+  DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
+  DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, P->d_xg, nullptr, P->hy, P->wy,
+                             P->rad, tmp, nullptr, s, nullptr));
+  DV_TRY_CUDA(launch_op_H(P, P->fpath, op_args_H(P, P->fpath, OP_OBJ, tmp, nullptr, false), s));
+  DV_TRY_CUDA(launch_huber_value(P->d_tiles, P->T, P->max_nxr, P->max_nxc, tmp, P->prob.delta,
+                                 part_hub(P), s));
+  const double* parts[4] = {part_data(P), part_hub(P), part_cons(P), part_cons(P) + ncons(P)};
+  const int counts[4] = {obj_parts(P), nhub(P), ncons(P), ncons(P)};
+  DV_TRY_CUDA(launch_reduce(parts, counts, residuals ? 4 : 2, P->d_scal, s));
+  DV_TRY_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  int* h_err = reinterpret_cast<int*>(P->h_scal + 6);
+  DV_TRY_CUDA(cudaMemcpyAsync(h_err, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return DV_OK;
+}
+constexpr int kObjLaunches = 5;
+
+// Waits for an enqueued objective reduction and checks the error word.
+dv_status read_objective(dv_plan* P, bool residuals, cudaStream_t s) {
+  DV_TRY_CUDA(cudaStreamSynchronize(s));
+  const int* h_err = reinterpret_cast<const int*>(P->h_scal + 6);
+  if (*h_err != 0)
+    return fail(DV_ERR_TIMEOUT, "a tensor-core operator kernel gave up waiting on its pipeline");
+  if (!residuals) P->h_scal[2] = P->h_scal[3] = NAN;
+  return DV_OK;
+}
+
+cudaError_t launch_cons(dv_plan* P, int cur, bool track_z, bool residuals, cudaStream_t s) {
+  return launch_consensus(grid_args(P), P->d_w[cur], P->d_u, (float)P->prob.gamma,
+                          (float)P->prob.rho, track_z ? P->d_z : nullptr,
+                          residuals ? part_cons(P) : nullptr, s, nullptr);
+}
+
+// Records an external event-record node on the capture stream (timed graphs).
+dv_status timing_node(dv_plan* P, cudaStream_t cs, int which, cudaGraphNode_t* node) {
+  const cudaError_t e = cudaEventRecordWithFlags(P->timer.placeholders[which], cs,
+                                                 cudaEventRecordExternal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+  return capture_node(cs, node);
+}
+
+// Captures one outer iteration: the local solve (tile groups on their own
+// streams, or one launch per operator), then, with g.cons, the consensus and
+// dual update on the resulting iterate and, with bit 3, the objective reduction.
+dv_status capture_outer(dv_plan* P, GraphEntry& g) {
   cudaStream_t cs = P->cap_stream;
   if (g.timed && P->timer.placeholders.empty()) {
     cudaEvent_t a, b;
@@ -136,32 +186,43 @@ dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
   DV_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   dv_status st = DV_OK;
   int par = g.parity;
-  // the tensor path runs its tile groups concurrently (timed as one local
-  // solve); otherwise one launch per operator, each with its own event nodes
   const bool grp = grouped(P);
-  if (grp) st = capture_groups(P, cs, par, g.n_inner);
-  for (int i = 0; i < g.n_inner && st == DV_OK && !grp; ++i) {
-    for (int k = 0; k < 2 && st == DV_OK; ++k) {
-      cudaGraphNode_t n0 = nullptr, n1 = nullptr;
-      if (g.timed) {
-        cudaError_t e = cudaEventRecordWithFlags(P->timer.placeholders[0], cs, cudaEventRecordExternal);
-        st = e == cudaSuccess ? capture_node(cs, &n0) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
-        if (st != DV_OK) break;
-      }
-      cudaError_t e = k == 0 ? launch_inner_H(P, par, cs) : launch_inner_Ht(P, par, cs);
-      if (e != cudaSuccess) {
-        st = cuda_fail(e, "kernel launch during capture", __FILE__, __LINE__);
-        break;
-      }
-      if (g.timed) {
-        e = cudaEventRecordWithFlags(P->timer.placeholders[1], cs, cudaEventRecordExternal);
-        st = e == cudaSuccess ? capture_node(cs, &n1) : cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
-        g.ev_start.push_back(n0);
-        g.ev_end.push_back(n1);
-        g.kinds.push_back(k == 0 ? KIND_H : KIND_HT);
-      }
+  auto bracket = [&](int kind, auto&& body) -> dv_status {
+    cudaGraphNode_t n0 = nullptr, n1 = nullptr;
+    if (g.timed) DV_TRY(timing_node(P, cs, 0, &n0));
+    DV_TRY(body());
+    if (g.timed) {
+      DV_TRY(timing_node(P, cs, 1, &n1));
+      g.ev_start.push_back(n0);
+      g.ev_end.push_back(n1);
+      g.kinds.push_back(kind);
     }
-    par ^= 1;
+    return DV_OK;
+  };
+  if (grp) {
+    // the tile groups run concurrently: the local solve is timed as a whole
+    st = bracket(KIND_LOCAL, [&]() { return capture_groups(P, cs, par, g.n_inner); });
+    par ^= (g.n_inner & 1);
+  } else {
+    for (int i = 0; i < g.n_inner && st == DV_OK; ++i) {
+      for (int k = 0; k < 2 && st == DV_OK; ++k)
+        st = bracket(k == 0 ? KIND_H : KIND_HT, [&]() -> dv_status {
+          const cudaError_t e = k == 0 ? launch_inner_H(P, par, cs) : launch_inner_Ht(P, par, cs);
+          return e == cudaSuccess ? DV_OK : cuda_fail(e, "kernel launch during capture", __FILE__, __LINE__);
+        });
+      par ^= 1;
+    }
+  }
+  if (st == DV_OK && (g.cons & 1))
+    st = bracket(KIND_CONS, [&]() -> dv_status {
+      const cudaError_t e = launch_cons(P, par, (g.cons & 2) != 0, (g.cons & 4) != 0, cs);
+      return e == cudaSuccess ? DV_OK : cuda_fail(e, "kernel launch during capture", __FILE__, __LINE__);
+    });
+  if (st == DV_OK && (g.cons & 8)) {
+    const int keep = P->cur;
+    P->cur = par;                       // the objective reads the iterate the graph leaves
+    st = enqueue_objective(P, (g.cons & 4) != 0, cs);
+    P->cur = keep;
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
@@ -175,9 +236,9 @@ dv_status capture_local_solve(dv_plan* P, GraphEntry& g) {
   return DV_OK;
 }
 
-dv_status get_graph(dv_plan* P, int n_inner, int par, GraphEntry** out) {
+dv_status get_graph(dv_plan* P, int n_inner, int par, int cons, GraphEntry** out) {
   for (GraphEntry& g : P->graphs)
-    if (g.n_inner == n_inner && g.parity == par && g.timed == P->timing) {
+    if (g.n_inner == n_inner && g.parity == par && g.timed == P->timing && g.cons == cons) {
       *out = &g;
       return DV_OK;
     }
@@ -185,14 +246,35 @@ dv_status get_graph(dv_plan* P, int n_inner, int par, GraphEntry** out) {
   g.n_inner = n_inner;
   g.parity = par;
   g.timed = P->timing;
-  DV_TRY(capture_local_solve(P, g));
+  g.cons = cons;
+  DV_TRY(capture_outer(P, g));
   P->graphs.push_back(g);
   *out = &P->graphs.back();
   return DV_OK;
 }
 
+// Launches a captured outer iteration (or local solve), swapping pool events
+// into its timing nodes.
+dv_status launch_graph(dv_plan* P, GraphEntry* g, cudaStream_t s) {
+  if (g->timed) {
+    for (size_t j = 0; j < g->kinds.size(); ++j) {
+      int e0, e1;
+      DV_TRY(pool_event(P, &e0));
+      DV_TRY(pool_event(P, &e1));
+      DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_start[j], P->timer.pool[e0]));
+      DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_end[j], P->timer.pool[e1]));
+      P->timer.pending.push_back(Pending{g->kinds[j], e0, e1});
+    }
+  }
+  DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
+  P->launches += 2 * g->n_inner * (grouped(P) ? P->ngrp : 1) + ((g->cons & 1) ? 1 : 0) +
+                 ((g->cons & 8) ? kObjLaunches : 0);
+  return DV_OK;
+}
+
 // The Local-Solver of Algorithm 1 on every tile: n_inner x {r = W (H_i w - y_i);
 // w <- max(0, w - tau (H_i^T r + lambda D^T psi(D w) + alpha (w - u)))}.
+// Eager (no graphs) or VMLM-B; the captured form runs in run_outer.
 dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
   Range range("dv local solve");
   if (n_inner <= 0) return DV_OK;
@@ -203,31 +285,8 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
   }
   if (P->prob.use_graphs) {
     GraphEntry* g = nullptr;
-    DV_TRY(get_graph(P, n_inner, P->cur, &g));
-    if (g->timed && grouped(P)) {
-      int e0, e1;
-      DV_TRY(pool_event(P, &e0));
-      DV_TRY(pool_event(P, &e1));
-      DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e0], s));
-      DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
-      DV_TRY_CUDA(cudaEventRecord(P->timer.pool[e1], s));
-      P->timer.pending.push_back(Pending{KIND_LOCAL, e0, e1});
-      P->launches += 2 * n_inner * P->ngrp;
-      P->cur ^= (n_inner & 1);
-      return DV_OK;
-    }
-    if (g->timed) {
-      for (size_t j = 0; j < g->kinds.size(); ++j) {
-        int e0, e1;
-        DV_TRY(pool_event(P, &e0));
-        DV_TRY(pool_event(P, &e1));
-        DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_start[j], P->timer.pool[e0]));
-        DV_TRY_CUDA(cudaGraphExecEventRecordNodeSetEvent(g->exec, g->ev_end[j], P->timer.pool[e1]));
-        P->timer.pending.push_back(Pending{g->kinds[j], e0, e1});
-      }
-    }
-    DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
-    P->launches += 2 * n_inner * (grouped(P) ? P->ngrp : 1);
+    DV_TRY(get_graph(P, n_inner, P->cur, 0, &g));
+    DV_TRY(launch_graph(P, g, s));
   } else {
     int par = P->cur;
     for (int i = 0; i < n_inner; ++i) {
@@ -242,11 +301,8 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
 
 dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t s) {
   Range range("dv consensus");
-  const GridArgs g = grid_args(P);
   return timed_launch(P, KIND_CONS, s, [&](cudaStream_t st) {
-    return launch_consensus(g, P->d_w[P->cur], P->d_u, (float)P->prob.gamma, (float)P->prob.rho,
-                            track_z ? P->d_z : nullptr, residuals ? part_cons(P) : nullptr, st,
-                            nullptr);
+    return launch_cons(P, P->cur, track_z, residuals, st);
   });
 }
 
@@ -256,26 +312,9 @@ dv_status consensus_step(dv_plan* P, bool track_z, bool residuals, cudaStream_t 
 // them) h_scal[2..3] = the squared primal / dual residuals.  Synchronises the stream.
 dv_status eval_objective(dv_plan* P, bool residuals, cudaStream_t s) {
   Range range("dv objective");
-  const GridArgs g = grid_args(P);
-  float* tmp = P->d_w[P->cur ^ 1];
-  DV_TRY_CUDA(launch_assemble(g, P->d_w[P->cur], P->d_xg, s));
-  DV_TRY_CUDA(launch_scatter(g, P->T, P->max_nxr, P->max_nxc, P->d_xg, nullptr, P->hy, P->wy,
-                             P->rad, tmp, nullptr, s, nullptr));
-  DV_TRY_CUDA(launch_op_H(P, P->fpath, op_args_H(P, P->fpath, OP_OBJ, tmp, nullptr, false), s));
-  DV_TRY_CUDA(launch_huber_value(P->d_tiles, P->T, P->max_nxr, P->max_nxc, tmp, P->prob.delta,
-                                 part_hub(P), s));
-  const double* parts[4] = {part_data(P), part_hub(P), part_cons(P), part_cons(P) + ncons(P)};
-  const int counts[4] = {obj_parts(P), nhub(P), ncons(P), ncons(P)};
-  DV_TRY_CUDA(launch_reduce(parts, counts, residuals ? 4 : 2, P->d_scal, s));
-  P->launches += 5;
-  DV_TRY_CUDA(cudaMemcpyAsync(P->h_scal, P->d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  int* h_err = reinterpret_cast<int*>(P->h_scal + 6);
-  DV_TRY_CUDA(cudaMemcpyAsync(h_err, P->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  DV_TRY_CUDA(cudaStreamSynchronize(s));
-  if (*h_err != 0)
-    return fail(DV_ERR_TIMEOUT, "a tensor-core operator kernel gave up waiting on its pipeline");
-  if (!residuals) P->h_scal[2] = P->h_scal[3] = NAN;
-  return DV_OK;
+  DV_TRY(enqueue_objective(P, residuals, s));
+  P->launches += kObjLaunches;
+  return read_objective(P, residuals, s);
 }
 
 struct RunResult {
@@ -284,23 +323,40 @@ struct RunResult {
   bool have_obj = false;
 };
 
-// n outer iterations of Algorithm 1 from the plan's current state.
+// n outer iterations of Algorithm 1 from the plan's current state.  With CUDA
+// graphs (projected gradient) one graph launch covers an outer iteration:
+// local solve, consensus and dual update and, when due, the objective
+// reduction, whose read-back is the only host synchronisation.
 dv_status run_outer(dv_plan* P, int n, bool want_stats, cudaStream_t s, RunResult& rr) {
   const dv_problem& pr = P->prob;
   const bool track_z = want_stats || pr.check_every > 0;
+  const bool captured = pr.use_graphs && pr.local_solver == DV_SOLVER_PG;
   for (int k = 0; k < n; ++k) {
     const int ni = pr.n_inner + P->outer_done * pr.inner_increment;
-    DV_TRY(local_solve(P, ni, s));
-    rr.inner_done += ni;
     const bool check = pr.check_every > 0 && (k + 1) % pr.check_every == 0;
     const bool last = k + 1 == n;
     const bool resid = track_z && (check || last);
-    DV_TRY(consensus_step(P, track_z, resid, s));
+    if (captured && ni > 0) {
+      Range range("dv outer iteration");
+      const int cons = 1 | (track_z ? 2 : 0) | (resid ? 4 : 0) | (check ? 8 : 0);
+      GraphEntry* g = nullptr;
+      DV_TRY(get_graph(P, ni, P->cur, cons, &g));
+      DV_TRY(launch_graph(P, g, s));
+      P->cur ^= (ni & 1);
+      if (check) {
+        Range robj("dv objective");
+        DV_TRY(read_objective(P, true, s));
+      }
+    } else {
+      DV_TRY(local_solve(P, ni, s));
+      DV_TRY(consensus_step(P, track_z, resid, s));
+      if (check) DV_TRY(eval_objective(P, true, s));
+    }
+    rr.inner_done += ni;
     P->outer_done += 1;
     rr.have_resid = resid;
     rr.have_obj = false;
     if (check) {
-      DV_TRY(eval_objective(P, true, s));
       rr.have_obj = true;
       const double F = 0.5 * P->h_scal[0] + pr.lambda * P->h_scal[1];
       if (pr.target_objective > 0.0 && F <= pr.target_objective) break;

@@ -104,7 +104,8 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
           const int64_t id = it.base[s] + (int64_t)r * it.pitch[s] + C;
           xs[g][s] = x[id];
           us[g][s] = u[id];
-          as[g][s] = gamma * G.omr[it.obr[s] + R] * G.omc[it.obc[s] + C];
+          // one covering tile: its weight cancels in the average
+          if constexpr (NS > 1) as[g][s] = gamma * G.omr[it.obr[s] + R] * G.omc[it.obc[s] + C];
         }
       }
     }
@@ -114,13 +115,18 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
       if (p0 + g * NBR + tx >= npix) continue;
       const int r = rs[g];
       const int R = it.r0 + r, C = it.c0 + cs[g];
-      float num = 0.f, den = 0.f;
+      float z;
+      if constexpr (NS == 1) {
+        z = 2.f * xs[g][0] - us[g][0];
+      } else {
+        float num = 0.f, den = 0.f;
 #pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        num += as[g][s] * (2.f * xs[g][s] - us[g][s]);
-        den += as[g][s];
+        for (int s = 0; s < NS; ++s) {
+          num += as[g][s] * (2.f * xs[g][s] - us[g][s]);
+          den += as[g][s];
+        }
+        z = num / den;
       }
-      const float z = num / den;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         u[it.base[s] + (int64_t)r * it.pitch[s] + C] = us[g][s] + rho * (z - xs[g][s]);
@@ -138,7 +144,7 @@ __device__ __forceinline__ void consensus_item(const GridArgs& G, const ConsItem
   }
 }
 
-__global__ void __launch_bounds__(NBR, 8) consensus_kernel(const GridArgs G, const float* __restrict__ x,
+__global__ void __launch_bounds__(NBR, 6) consensus_kernel(const GridArgs G, const float* __restrict__ x,
                                                         float* __restrict__ u, float gamma, float rho,
                                                         float* __restrict__ zg,
                                                         double* __restrict__ partials) {

@@ -43,7 +43,7 @@ constexpr int KM = 16, CH = 8;            // BF16: K per MMA, elements per 16-by
 constexpr int NWE = 8;                    // staging / epilogue warps
 constexpr int NT = 32 * NWE;
 constexpr int NTH = 32 * (NWE + 2);       // + the MMA warp and the bulk-copy warp
-constexpr int NST = 4;                    // ring stages (one tap row each)
+constexpr int kMaxNST = 8;                // ring stages (one tap row each), at most
 constexpr int TP = MC + 1;                // fp32 transposition tile pitch (floats)
 constexpr int HW = MC + 2;                // halo tile pitch (floats)
 constexpr int kHdr = 512;
@@ -52,32 +52,45 @@ constexpr int kSmemMax = 227 * 1024;
 
 template <int K>
 struct GeoT {
+  static constexpr int NST = 4;                           // ring stages (one tap row each)
   static constexpr int KS = (MC - 1 + K + KM - 1) / KM;   // MMAs per tap row
   static constexpr int COLS = KS * KM;                    // staged input columns
   static constexpr int NCH = COLS / CH;                   // 16-byte column panels of S
-  static constexpr int NR = K <= 31 ? 256 : 128;          // output rows per CTA (MMA N max)
+  // output rows per CTA: the MMA N dimension at its maximum, 256 (an MMA with
+  // N = 128 takes about as long as one with N = 256)
+  static constexpr int NR = 256;
   static constexpr int ROWS = NR + K - 1;                 // staged input rows
   static constexpr int SPANEL = ROWS * 16 + 16;
   static constexpr int SBYTES = NCH * SPANEL;
+  // H: S buffers.  Two let the next PSF's S be built while the current PSF's
+  // MMAs run; for K = 63 two buffers of 256 + 62 rows do not fit next to the
+  // ring, so one buffer is rebuilt after each PSF's MMAs
+  static constexpr int DBUF = K <= 31 ? 2 : 1;
   static constexpr int RA = MC + KM * (KS - 1);           // rows of the tall Toeplitz operand
   static constexpr int APANEL = RA * 16;
   static constexpr int ABYTES = 2 * APANEL;               // one ring stage
   static constexpr int WR = K + CH - 1;                   // nonzero rows per panel
   static constexpr int S0 = KM * (KS - 1) - K + 1;        // first nonzero row of panel 0
   static constexpr int WTX = 2 * WR * 16;                 // bytes streamed per tap row
-  static constexpr int UBYTES = 64 * 1024;                // H^T: fp32 staging / epilogue tiles
+  // H^T: fp32 staging / epilogue tiles
+  static constexpr int UBYTES = K <= 31 ? 64 * 1024 : 48 * 1024;
   static constexpr int WCOFF = (ROWS + 3) / 4 * 4;        // H: sWc after sWr, 16-byte aligned
-  static constexpr int SMEM_H = kHdr + 2 * SBYTES + NST * ABYTES + (WCOFF + COLS) * 4;
+  static constexpr int SMEM_H = kHdr + DBUF * SBYTES + NST * ABYTES + (WCOFF + COLS) * 4;
   // H^T: [... | row weights of two PSF grid rows [2][NR] | omega rows [NR] | omega columns [MC]]
   static constexpr int SMEM_HT = kHdr + SBYTES + UBYTES + NST * ABYTES + 2 * NR * 4 +
                                  (NR + MC) * 4;
+  // H epilogue with one S buffer: transposition tile, then the observed image
+  // and noise weights of two 32-row chunks
+  static constexpr int TOFF = (32 * TP * 4 + 15) / 16 * 16;
   static constexpr int TMEM_H = NR;
   static constexpr int TMEM_HT = 2 * NR;                  // accumulator D and sum G
   static_assert(S0 >= 0 && S0 + CH + WR <= RA, "Toeplitz windows inside the panels");
+  static_assert(NST <= kMaxNST, "ring barriers");
   static_assert(SMEM_H <= kSmemMax && SMEM_HT <= kSmemMax, "shared memory");
   static_assert(SBYTES >= 32 * TP * 4 && UBYTES >= 32 * TP * 4 + 34 * HW * 4, "epilogue tiles");
   static_assert(UBYTES >= (COLS + 4) * 4 && SBYTES >= (COLS + 4) * 4, "staging chunk");
-  static_assert(SBYTES >= 4 * 32 * MC * 4, "H epilogue prefetch buffers in a free S buffer");
+  static_assert(SBYTES >= 4 * 32 * MC * 4 + (DBUF == 1 ? TOFF : 0),
+                "H epilogue prefetch buffers in an S buffer");
   // 16-byte alignment of every region accessed with 16-byte vectors or bulk copies
   static_assert(SPANEL % 16 == 0 && SBYTES % 16 == 0 && APANEL % 16 == 0 &&
                     (COLS * 2) % 16 == 0 && (COLS * 4) % 16 == 0 && (WCOFF * 4) % 16 == 0 &&
@@ -86,7 +99,7 @@ struct GeoT {
 };
 
 struct Bars {
-  uint64_t rfull[NST], rempty[NST];
+  uint64_t rfull[kMaxNST], rempty[kMaxNST];
   uint64_t sfull[2], sempty[2];  // S buffer staged / consumed (H: per PSF, H^T: buffer 0 once)
   uint64_t dfull[2], dempty[2];  // accumulator buffer complete / read (H: buffer 0 only)
   uint64_t fin;
@@ -101,7 +114,7 @@ __device__ __forceinline__ void sync_stage() { named_sync<NT>(); }
 __device__ __forceinline__ bool all_stage(bool v) { return named_all<NT>(v); }
 
 __device__ __forceinline__ void init_bars(Bars* H, uint64_t wait_ns) {
-  for (int s = 0; s < NST; ++s) {
+  for (int s = 0; s < kMaxNST; ++s) {
     mbar_init(&H->rfull[s], 1);
     mbar_init(&H->rempty[s], 1);
   }
@@ -131,8 +144,9 @@ __device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned 
   const int total = np * K;
   int issued = 0;
   for (int it = 0; it < total; ++it) {
-    const int s = it % NST;
-    if (it >= NST && !wait_bar(&H->rempty[s], (uint32_t)((it / NST - 1) & 1), &H->abort, A.err, H->wait_ns))
+    const int s = it % G::NST;
+    if (it >= G::NST &&
+        !wait_bar(&H->rempty[s], (uint32_t)((it / G::NST - 1) & 1), &H->abort, A.err, H->wait_ns))
       break;
     const int p = it / K, a = it - p * K;
     const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
@@ -143,8 +157,8 @@ __device__ void producer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned 
     bulk_g2s(dst + G::APANEL + (G::S0 + CH) * 16, src + G::WR * 16, G::WR * 16, &H->rfull[s]);
     issued = it + 1;
   }
-  for (int it = (issued > NST ? issued - NST : 0); it < issued; ++it)
-    if (!drain_bar(&H->rfull[it % NST], (uint32_t)((it / NST) & 1), A.err)) break;
+  for (int it = (issued > G::NST ? issued - G::NST : 0); it < issued; ++it)
+    if (!drain_bar(&H->rfull[it % G::NST], (uint32_t)((it / G::NST) & 1), A.err)) break;
 }
 
 // K-step ranges of the block's PSF grid columns (computed on the host by
@@ -193,8 +207,10 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
     if (ADJ) {
       ok = p == 0 ? wait_bar(&H->sfull[0], 0, &H->abort, A.err, H->wait_ns)
                   : wait_bar(&H->dempty[0], (uint32_t)((p - 1) & 1), &H->abort, A.err, H->wait_ns);
-    } else {
+    } else if (G::DBUF == 2) {
       ok = wait_bar(&H->sfull[p & 1], (uint32_t)((p >> 1) & 1), &H->abort, A.err, H->wait_ns);
+    } else {
+      ok = wait_bar(&H->sfull[0], (uint32_t)(p & 1), &H->abort, A.err, H->wait_ns);
     }
     if (!ok) break;
     tc_fence_after();
@@ -203,7 +219,8 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
     const int kr = b < kMaxB ? H->ksr[b] : (G::KS - 1) << 8;
     const int klo = kr & 0xff, nks = (kr >> 8) - klo + 1;
     const uint64_t adk = ad0 - (uint64_t)(klo * KM);
-    const uint64_t bdk = sdesc(saddr(sS + (ADJ ? 0 : (p & 1) * G::SBYTES)), G::SPANEL) +
+    const int sb = (ADJ || G::DBUF == 1) ? 0 : (p & 1);
+    const uint64_t bdk = sdesc(saddr(sS + sb * G::SBYTES), G::SPANEL) +
                          (uint64_t)(2 * klo * (G::SPANEL >> 4));
     if (ADJ) fresh = true;
     for (int a = 0; a < K; ++a) {
@@ -217,13 +234,13 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
       issue_n<G::KS, 2 * (G::SPANEL >> 4)>(nks, dp, ad, bd, id, fresh ? 0u : 1u);
       fresh = false;
       tc_commit(&H->rempty[s]);
-      if (++s == NST) {
+      if (++s == G::NST) {
         s = 0;
         ph ^= 1u;
       }
     }
     if (!ok) break;
-    tc_commit(ADJ ? &H->dfull[0] : &H->sempty[p & 1]);
+    tc_commit(ADJ ? &H->dfull[0] : &H->sempty[sb]);
   }
   if (!ADJ && ok && np > 0) tc_commit(&H->dfull[0]);
   tc_commit(&H->fin);
@@ -234,7 +251,7 @@ __device__ void issuer(const OpArgs& A, const WorkItem& wi, Bars* H, unsigned ch
 template <int K>
 __device__ __forceinline__ void zero_ring(unsigned char* ring, int tid) {
   using G = GeoT<K>;
-  for (int e = tid; e < NST * 2 * G::RA; e += NT) {
+  for (int e = tid; e < G::NST * 2 * G::RA; e += NT) {
     const int st = e / (2 * G::RA), rem = e - st * 2 * G::RA, pn = rem / G::RA, n = rem - pn * G::RA;
     const int w0 = G::S0 + pn * CH;
     if (n < w0 || n >= w0 + G::WR)
@@ -307,7 +324,7 @@ __device__ __forceinline__ void restage_h(unsigned char* sb, const float* __rest
                                           const float* sWr, const float* sWc, int qlo, int nq,
                                           int tid) {
   using G = GeoT<K>;
-  constexpr int U = 4;
+  constexpr int U = 8;   // items (8 values each) in flight per thread
   const int total = G::ROWS * nq;
   for (int e0 = tid; e0 < total; e0 += U * NT) {
     float v[U][CH];
@@ -358,9 +375,9 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
   using G = GeoT<K>;
   extern __shared__ __align__(1024) unsigned char smem[];
   Bars* H = reinterpret_cast<Bars*>(smem);
-  unsigned char* sS = smem + kHdr;                                        // [2][SBYTES]
-  unsigned char* ring = sS + 2 * G::SBYTES;
-  float* sWr = reinterpret_cast<float*>(ring + (size_t)NST * G::ABYTES);   // [ROWS]
+  unsigned char* sS = smem + kHdr;                                        // [DBUF][SBYTES]
+  unsigned char* ring = sS + G::DBUF * G::SBYTES;
+  float* sWr = reinterpret_cast<float*>(ring + (size_t)G::NST * G::ABYTES);   // [ROWS]
   float* sWc = sWr + G::WCOFF;                                            // [COLS]
   __shared__ double red[NWE];
   const WorkItem wi = A.work[blockIdx.x];
@@ -404,15 +421,22 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
         sWc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
       }
       sync_stage();
-      // S buffer p & 1 was last read by PSF p - 2
-      if (p >= 2) {
-        ok = all_stage(wait_bar(&H->sempty[p & 1], (uint32_t)(((p >> 1) - 1) & 1), &H->abort, A.err, H->wait_ns));
+      // two buffers: S buffer p & 1 was last read by PSF p - 2; one buffer:
+      // by PSF p - 1
+      const int sb = G::DBUF == 2 ? (p & 1) : 0;
+      if (G::DBUF == 2 && p >= 2) {
+        ok = all_stage(wait_bar(&H->sempty[sb], (uint32_t)(((p >> 1) - 1) & 1), &H->abort, A.err,
+                                H->wait_ns));
+        if (!ok) break;
+      } else if (G::DBUF == 1 && p >= 1) {
+        ok = all_stage(wait_bar(&H->sempty[0], (uint32_t)((p - 1) & 1), &H->abort, A.err,
+                                H->wait_ns));
         if (!ok) break;
       }
-      restage_h<K>(sS + (p & 1) * G::SBYTES, img, td.xpitch, al, wi.r0, wi.c0, td.nxr, td.nxc, sWr,
+      restage_h<K>(sS + sb * G::SBYTES, img, td.xpitch, al, wi.r0, wi.c0, td.nxr, td.nxc, sWr,
                    sWc, qlo, nq, tid);
       fence_async_smem();
-      mbar_arrive(&H->sfull[p & 1]);
+      mbar_arrive(&H->sfull[sb]);
     }
     // epilogue: 32-row chunks of the accumulator, transposed through the S
     // buffer of the last PSF (free once every MMA has completed).  The
@@ -421,9 +445,14 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
     // overlaps the last PSF's MMAs.
     constexpr int PER = 32 * MC / NT;    // outputs per thread and chunk
     const bool obs = A.mode != OP_PLAIN;
-    if (ok && np >= 2)   // the other buffer was last read by PSF np - 2
-      ok = all_stage(wait_bar(&H->sempty[np & 1], (uint32_t)(((np - 2) >> 1) & 1), &H->abort, A.err, H->wait_ns));
-    float* sYb = reinterpret_cast<float*>(sS + (np & 1) * G::SBYTES);   // [2][32 * MC] observed image
+    if (G::DBUF == 2 && ok && np >= 2)   // the other buffer was last read by PSF np - 2
+      ok = all_stage(wait_bar(&H->sempty[np & 1], (uint32_t)(((np - 2) >> 1) & 1), &H->abort,
+                              A.err, H->wait_ns));
+    // two buffers: the prefetch goes to the buffer the last PSF did not read
+    // and the transposition to the other; one buffer: both share it, after
+    // every MMA has completed
+    float* sYb = reinterpret_cast<float*>(G::DBUF == 2 ? sS + (np & 1) * G::SBYTES
+                                                       : sS + G::TOFF);   // [2][32 * MC] observed image
     float* sWb = sYb + 2 * 32 * MC;                      // [2][32 * MC] noise weights
     auto prefetch = [&](int i0, int buf) {
       if (obs) {
@@ -439,12 +468,12 @@ __global__ void __launch_bounds__(NTH, 1) tcT_H_kernel(const OpArgs A) {
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    if (ok && np > 0) prefetch(0, 0);
+    if (G::DBUF == 2 && ok && np > 0) prefetch(0, 0);
     if (ok && np > 0) ok = all_stage(wait_bar(&H->dfull[0], 0, &H->abort, A.err, H->wait_ns));
-    if (ok && np == 0) prefetch(0, 0);
+    if (ok && (np == 0 || G::DBUF == 1)) prefetch(0, 0);
     tc_fence_after();
     sync_stage();
-    float* sT = reinterpret_cast<float*>(sS + ((np + 1) & 1) * G::SBYTES);
+    float* sT = reinterpret_cast<float*>(G::DBUF == 2 ? sS + ((np + 1) & 1) * G::SBYTES : sS);
     const int j = 32 * (warp & 3) + lane, hf = warp >> 2;
     const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
     double part = 0.0;
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(NTH, 1) tcT_Ht_kernel(const OpArgs A) {
   unsigned char* sS = smem + kHdr;
   float* sU = reinterpret_cast<float*>(sS + G::SBYTES);                 // staging / epilogue
   unsigned char* ring = reinterpret_cast<unsigned char*>(sU) + G::UBYTES;
-  float* sWr = reinterpret_cast<float*>(ring + (size_t)NST * G::ABYTES); // [2][NR]
+  float* sWr = reinterpret_cast<float*>(ring + (size_t)G::NST * G::ABYTES); // [2][NR]
   float* sOr = sWr + 2 * G::NR;                                          // gamma omega rows [NR]
   float* sOc = sOr + G::NR;                                              // omega columns [MC]
   const WorkItem wi = A.work[blockIdx.x];
@@ -760,7 +789,7 @@ uint16_t to_bf16(float f) {
 }  // namespace
 
 int tcT_block_cols() { return MC; }
-int tcT_max_rows(int K) { return K <= 31 ? 256 : 128; }
+int tcT_max_rows(int K) { return K > 0 ? 256 : 0; }
 
 // A k-step covers staged columns [16 ks, 16 ks + 16) and so reaches output
 // columns 16 ks - K + 1 .. 16 ks + 15 of the block.  H: S = w_p . x is zero
