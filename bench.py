@@ -82,7 +82,9 @@ def parse():
     ap.add_argument("--gamma", type=float, default=0.1,
                     help="proximal weight gamma of the chosen form (0: the workload's)")
     ap.add_argument("--check-every", type=int, default=4,
-                    help="outer iterations between objective checks of the chosen form")
+                    help="outer iterations before the chosen form's first objective check (the "
+                         "library schedules the later ones from the decrease rate, at most "
+                         "twice this apart)")
     ap.add_argument("--inner", type=int, default=3,
                     help="projected-gradient steps per outer iteration of the chosen form "
                          "(0: the workload's count)")
@@ -618,8 +620,10 @@ def run_ours(args):
                                       "learned warm start (%d pairs of %d^2, %d Adam "
                                       "steps), %d projected-gradient steps per outer iteration, "
                                       "gamma %.3g, rho %.3g, "
-                                      "stop at F <= F*(1 + 1e-4) checked every %d outer "
-                                      "iterations; objective with the FP32 operator"
+                                      "stop at F <= F*(1 + 1e-4), the objective (FP32 "
+                                      "operator, FP64 sums) first checked after %d outer "
+                                      "iterations, then where the decrease rate predicts the "
+                                      "target"
                                       % (pname, args.precision, info.tune_ms_direct,
                                          info.tune_ms_fft, info.tune_ms_tensor, info.tile_groups,
                                          train_info["pairs"], train_info["pair_size"],

@@ -162,8 +162,12 @@ typedef struct dv_problem {
   int32_t precision;       /* dv_precision */
   int32_t path;            /* dv_operator_path */
   int32_t use_warmstart;   /* 0: blurred-image start; 1: learned warm start */
-  /* if > 0, evaluate the objective every check_every outer iterations and
-   * stop as soon as it is <= target_objective (when target_objective > 0) */
+  /* if > 0, evaluate the objective after check_every outer iterations and
+   * stop as soon as it is <= target_objective (when target_objective > 0);
+   * without a target it is evaluated every check_every iterations, with one
+   * the next evaluation comes where the decrease per outer iteration since the
+   * previous evaluation would reach the target (0.9 of that estimate, between
+   * 1 and 2 check_every iterations) */
   int32_t check_every;
   double target_objective;
   int32_t use_graphs;      /* 1: replay each outer iteration as a CUDA graph */

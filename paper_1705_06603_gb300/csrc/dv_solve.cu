@@ -331,9 +331,13 @@ dv_status run_outer(dv_plan* P, int n, bool want_stats, cudaStream_t s, RunResul
   const dv_problem& pr = P->prob;
   const bool track_z = want_stats || pr.check_every > 0;
   const bool captured = pr.use_graphs && pr.local_solver == DV_SOLVER_PG;
+  const bool target = pr.check_every > 0 && pr.target_objective > 0.0;
+  int next_check = pr.check_every;   // outer iterations of this call before the next check
+  int k_prev = -1;
+  double F_prev = 0.0;
   for (int k = 0; k < n; ++k) {
     const int ni = pr.n_inner + P->outer_done * pr.inner_increment;
-    const bool check = pr.check_every > 0 && (k + 1) % pr.check_every == 0;
+    const bool check = pr.check_every > 0 && k + 1 == next_check;
     const bool last = k + 1 == n;
     const bool resid = track_z && (check || last);
     if (captured && ni > 0) {
@@ -359,7 +363,20 @@ dv_status run_outer(dv_plan* P, int n, bool want_stats, cudaStream_t s, RunResul
     if (check) {
       rr.have_obj = true;
       const double F = 0.5 * P->h_scal[0] + pr.lambda * P->h_scal[1];
-      if (pr.target_objective > 0.0 && F <= pr.target_objective) break;
+      if (target && F <= pr.target_objective) break;
+      // next check: with a target, where the decrease per outer iteration
+      // since the last check would reach it (0.9 of that, between 1 and
+      // 2 check_every iterations; the decrease slows, so this errs early);
+      // otherwise every check_every iterations
+      int gap = pr.check_every;
+      if (target && k_prev >= 0 && F_prev > F) {
+        const double rate = (F_prev - F) / (double)(k - k_prev);
+        const double need = (F - pr.target_objective) / rate;
+        gap = (int)std::min<double>(2.0 * pr.check_every, std::max(1.0, std::ceil(0.9 * need)));
+      }
+      k_prev = k;
+      F_prev = F;
+      next_check = k + 1 + gap;
     }
   }
   return DV_OK;
