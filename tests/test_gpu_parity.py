@@ -335,14 +335,18 @@ def test_tensor_operator_matches_oracle(env, prec, hy, wy, K, G):
 
 @pytest.mark.parametrize("prec", [BF16, TF32])
 def test_tensor_solve_close_to_oracle(env, prec):
-    """The 128x128 workload with the tensor-core operator in the inner
-    iterations: the objective is evaluated with the FP32 operator, the image
-    stays within 1e-2 (BF16) / 2e-3 (TF32) of the FP64 oracle."""
+    """The 128x128 workload at the plain iteration count (30 x 10) with the
+    tensor-core operator in the inner iterations: the objective is evaluated
+    with the FP32 operator; the image is held to 3e-3 (BF16) / 1e-3 (TF32) of
+    the FP64 oracle -- the iterates converge to the fixed point of the rounded
+    operator, whose distance from the exact one the operator's rounding sets
+    (3e-3 and 5e-4 per apply)."""
     w, psfs, y, _ = workload_case("disks128")
-    plan, xd, st = _gpu_solve(env, w, psfs, y, 10, 10, precision=prec, path=TENSOR)
+    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, precision=prec, path=TENSOR)
     assert plan.info.path == TENSOR and plan.info.fp32_path in (DIRECT, FFT)
-    lay, xr, info = oracle_solve(w, psfs, y, 10, 10)
-    tol = 1e-2 if prec == BF16 else 2e-3
+    lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
+    tol = 3e-3 if prec == BF16 else 1e-3
+    print(f"prec {prec}: x_hat rel L2 {rel_l2(xd, xr):.3e}")
     assert_close(xd, xr, tol)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
     assert abs(st["objective"] - F) <= tol * F
