@@ -337,15 +337,15 @@ def test_tensor_operator_matches_oracle(env, prec, hy, wy, K, G):
 def test_tensor_solve_close_to_oracle(env, prec):
     """The 128x128 workload at the plain iteration count (30 x 10) with the
     tensor-core operator in the inner iterations: the objective is evaluated
-    with the FP32 operator; the image is held to 3e-3 (BF16) / 1e-3 (TF32) of
-    the FP64 oracle -- the iterates converge to the fixed point of the rounded
-    operator, whose distance from the exact one the operator's rounding sets
-    (3e-3 and 5e-4 per apply)."""
+    with the FP32 operator; the image is held to the final-image bound 1e-3 of
+    the FP64 oracle (measured on a GB300: 4.1e-4 BF16, 8.2e-5 TF32) -- the
+    iterates converge to the fixed point of the rounded operator, whose
+    distance from the exact one the operator's rounding sets."""
     w, psfs, y, _ = workload_case("disks128")
     plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, precision=prec, path=TENSOR)
     assert plan.info.path == TENSOR and plan.info.fp32_path in (DIRECT, FFT)
     lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
-    tol = 3e-3 if prec == BF16 else 1e-3
+    tol = 1e-3
     print(f"prec {prec}: x_hat rel L2 {rel_l2(xd, xr):.3e}")
     assert_close(xd, xr, tol)
     F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
