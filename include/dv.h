@@ -179,7 +179,14 @@ typedef struct dv_problem {
    * (>= 0; dv_problem_init sets 1e-7, the resolution of the FP32-formed
    * objective; 0 runs every iteration) */
   double vm_stop_rel;
-  int32_t reserved[2];
+  /* tensor-core path, BF16 allowed, the operator H of the inner iterations:
+   * 0 = whichever of the two forms below the plan-time autotuner finds faster,
+   * 1 = banded Toeplitz MMAs (BF16 operands), 2 = block DFT on the tensor
+   * cores: 128 x 128 overlap-save blocks transformed by dense DFT GEMMs with
+   * FP16 operands and FP32 accumulation, the PSF spectra applied between the
+   * forward and inverse transforms (K <= 97).  H^T always uses form 1. */
+  int32_t tensor_h;
+  int32_t reserved;
 } dv_problem;
 
 typedef struct dv_stats {
@@ -308,7 +315,10 @@ typedef struct dv_plan_info {
    * concurrent streams (tensor path with CUDA graphs; 1 = one launch per
    * operator over every tile) */
   int32_t tile_groups;
-  int32_t reserved;
+  /* 1 when H runs as the block DFT on the tensor cores (dv_problem.tensor_h) */
+  int32_t tensor_h_dft;
+  /* autotuner: one block-DFT H + one banded H^T (0 if not timed) */
+  double tune_ms_tensor_dft;
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

@@ -126,7 +126,7 @@ struct OpArgs {
   const uint16_t* ksr;    // BF16 tensor-core path: [n_work][kTcMaxB] k-step ranges (lo | hi << 8)
   uint64_t wait_ns;       // BF16 tensor-core path: bound of a pipeline wait (0: 2 s)
   int32_t test_withhold;  // BF16 tensor-core path: issue no operand copy (dv_plan_set_test_fault)
-  int32_t pad4;
+  int32_t ctas;           // persistent kernels: CTAs of the launch (0: one per SM)
 };
 
 // One item of the consensus / assembly kernels: a rectangle of the global x
@@ -199,6 +199,13 @@ cudaError_t fft_prepare();            // twiddles + shared-memory limits (plan t
 void fft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
 cudaError_t launch_fft_H(const OpArgs& a, cudaStream_t s, int grid);
 cudaError_t launch_fft_Ht(const OpArgs& a, cudaStream_t s, int grid);
+
+// Block DFT of H on the tensor cores (FP16 operands; the FFT path's work tables)
+bool dft_supported(int K);
+cudaError_t dft_prepare();
+void dft_constants(std::vector<uint8_t>& out);
+void dft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
+cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid);
 
 // Tensor-core path (tcgen05, BF16 / TF32 operands; its own work tables)
 int tc_block_m();
@@ -295,6 +302,11 @@ struct dv_plan {
   bool tensor_ok = false;  // tensor-core tables and operands were built
   dv::OpTables tab[3];    // [0] direct 64x64, [1] FFT b x b, [2] tensor 128x64 blocks
   bool fft_ok = false;
+  bool dft_ok = false;             // H as the block DFT on the tensor cores is available
+  bool dft_H = false;              // ... and used by the tensor path
+  float2* d_dspec = nullptr;       // its PSF spectra [G][128][128], natural order, / 128
+  unsigned char* d_dconst = nullptr;  // its constant operand [Fr; Fi] (FP16 panels)
+  int* d_dcounter = nullptr;       // its work counters: [0] whole launches, [1 + g] group g
   float2* d_spec = nullptr;
   int* d_counter = nullptr;        // [0] H launches, [1] H^T launches (FFT path)
   float2* d_fft_scr = nullptr;     // FFT path: n_sm spectra of S x S
@@ -305,6 +317,7 @@ struct dv_plan {
   uint64_t wait_ns = 0;               // bound of the BF16 tensor kernels' waits (0: 2 s)
   int test_fault = 0;                 // dv_plan_set_test_fault kind
   double tune_ms[3] = {0.0, 0.0, 0.0};  // autotuner: one H + one H^T apply per path
+  double tune_ms_dft = 0.0;             // ... tensor path with H as the block DFT
   dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
   float* d_desc = nullptr;         // per-PSF descriptors [G][3]
   float* d_feat = nullptr;         // warm-start features [nx][5] (lazy)

@@ -248,6 +248,8 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     return fail(DV_ERR_INVALID_ARG, "vm_memory must be in [0, 32] (0: 5)");
   if (!(p->vm_stop_rel >= 0.0) || !std::isfinite(p->vm_stop_rel))
     return fail(DV_ERR_INVALID_ARG, "vm_stop_rel must be finite and >= 0");
+  if (p->tensor_h < 0 || p->tensor_h > 2)
+    return fail(DV_ERR_INVALID_ARG, "tensor_h must be 0, 1 or 2");
   if (!(p->noise_sigma >= 0.0)) return fail(DV_ERR_INVALID_ARG, "noise_sigma must be >= 0");
 
   const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
@@ -397,10 +399,13 @@ static int tab_index(int path) {
 
 int tab_index_of(int path) { return tab_index(path); }
 
+// H as the block DFT: the tensor path with dft_H set
+static bool dft_h(const dv_plan* p, int path) { return path == DV_PATH_TENSOR && p->dft_H; }
+
 dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, float* out,
                      bool global) {
   OpArgs a{};
-  const OpTables& tb = p->tab[tab_index(path)];
+  const OpTables& tb = p->tab[dft_h(p, path) ? 1 : tab_index(path)];
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Hg : tb.H;
   a.ksr = global ? tb.ksHg : tb.ksH;
@@ -429,6 +434,12 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
   a.lambda = (float)p->prob.lambda;
   a.delta = (float)p->prob.delta;
   a.gamma = (float)p->prob.gamma;
+  if (dft_h(p, path)) {
+    a.ksr = nullptr;
+    a.spec = p->d_dspec;
+    a.tcop = p->d_dconst;
+    a.counter = p->d_dcounter;
+  }
   return a;
 }
 
@@ -436,6 +447,7 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, flo
                       bool global, const float* w, const float* u) {
   OpArgs a = op_args_H(p, path, mode, in, out, global);
   const OpTables& tb = p->tab[tab_index(path)];
+  a.spec = p->d_spec;
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Htg : tb.Ht;
   a.ksr = global ? tb.ksHtg : tb.ksHt;
@@ -451,6 +463,7 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, flo
 }
 
 cudaError_t launch_op_H(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
+  if (dft_h(P, path)) return launch_dft_H(a, s, a.ctas > 0 ? a.ctas : P->n_sm);
   if (path == DV_PATH_TENSOR)
     return P->prob.precision == DV_PREC_BF16 ? launch_tcT_H(a, s) : launch_tc_H(a, s);
   return path == DV_PATH_FFT ? launch_fft_H(a, s, P->n_sm) : launch_direct_H(a, s);
@@ -465,11 +478,17 @@ cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream
 int obj_parts(const dv_plan* P) { return P->tab[tab_index(P->fpath)].nH; }
 
 dv::OpArgs group_args(const dv_plan* p, int path, dv::OpArgs a, bool adjoint, int g) {
-  const OpTables& tb = p->tab[tab_index(path)];
+  const bool dft = !adjoint && dft_h(p, path);
+  const OpTables& tb = p->tab[dft ? 1 : tab_index(path)];
   const int* b = adjoint ? tb.gHt : tb.gH;
   a.work += b[g];
   a.n_work = b[g + 1] - b[g];
   if (a.ksr) a.ksr += (size_t)b[g] * kTcMaxB;
+  if (dft) {
+    // persistent launches of the concurrent groups share the SMs
+    a.counter = p->d_dcounter + 1 + g;
+    a.ctas = std::max(1, p->n_sm / std::max(1, p->ngrp));
+  }
   return a;
 }
 
@@ -569,13 +588,31 @@ static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
     if (P->tune_ms[1] < P->tune_ms[0]) P->fpath = DV_PATH_FFT;
   }
   P->path = P->fpath;
+  // the tensor path's H: banded Toeplitz MMAs or the block DFT (tensor_h)
+  auto tensor_form = [&]() -> dv_status {
+    P->dft_H = false;
+    if (!P->dft_ok) return DV_OK;
+    if (P->prob.tensor_h == 2) {
+      P->dft_H = true;
+      return DV_OK;
+    }
+    if (P->tune_ms[2] == 0.0) DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms[2]));
+    P->dft_H = true;
+    DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms_dft));
+    P->dft_H = P->tune_ms_dft < P->tune_ms[2];
+    return DV_OK;
+  };
   if (requested == DV_PATH_TENSOR) {
     P->path = DV_PATH_TENSOR;
+    DV_TRY(tensor_form());
   } else if (P->tensor_ok) {
     DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms[2]));
+    DV_TRY(tensor_form());
     const double fp32_ms = P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0];
     if (fp32_ms == 0.0) DV_TRY(time_path(P, P->fpath, s, P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]));
-    if (P->tune_ms[2] < P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]) P->path = DV_PATH_TENSOR;
+    const double t_ms = P->dft_H ? P->tune_ms_dft : P->tune_ms[2];
+    if (t_ms < P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]) P->path = DV_PATH_TENSOR;
+    else P->dft_H = false;
   }
   return DV_OK;
 }
@@ -589,6 +626,12 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     return fail(DV_ERR_UNSUPPORTED, "the tensor-core operator supports K = 9, 15, 31, 63");
   if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
+  if (prob->tensor_h == 2 && (prob->precision != DV_PREC_BF16 || !dft_supported(prob->K) ||
+                              !tc_supported(prob->K) || prob->path == DV_PATH_DIRECT ||
+                              prob->path == DV_PATH_FFT))
+    return fail(DV_ERR_UNSUPPORTED,
+                "the block-DFT form of H needs the tensor-core path with BF16 allowed and "
+                "K in 9, 15, 31, 63");
 
   P->prob = *prob;
   P->vm_m = prob->vm_memory > 0 ? prob->vm_memory : 5;
@@ -612,6 +655,8 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   P->tensor_ok = prob->precision != DV_PREC_FP32 && tc_supported(prob->K) &&
                  (prob->path == DV_PATH_AUTO || prob->path == DV_PATH_TENSOR);
   P->fft_ok = prob->path != DV_PATH_DIRECT && fft_supported(prob->K);
+  P->dft_ok = P->tensor_ok && P->fft_ok && prob->precision == DV_PREC_BF16 &&
+              dft_supported(prob->K) && prob->tensor_h != 1;
   {
     int dev = 0;
     DV_TRY_CUDA(cudaGetDevice(&dev));
@@ -748,7 +793,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     auto group = [&](std::vector<WorkItem>& v, int* bounds) {
       std::fill(bounds, bounds + kMaxGroups + 1, (int)v.size());
       bounds[0] = 0;
-      if (k != 2 || P->ngrp <= 1) return;
+      if (!(k == 2 || (k == 1 && P->dft_ok)) || P->ngrp <= 1) return;
       std::stable_sort(v.begin(), v.end(), [&](const WorkItem& x, const WorkItem& y) {
         return tgroup[x.tile] < tgroup[y.tile];
       });
@@ -813,6 +858,16 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
   }
   DV_TRY(alloc(P, &P->d_err, 1));
   DV_TRY_CUDA(cudaMemsetAsync(P->d_err, 0, sizeof(int), s));
+  if (P->dft_ok) {
+    std::vector<uint8_t> cst;
+    dft_constants(cst);
+    DV_TRY(upload(P, &P->d_dconst, cst.data(), cst.size(), s));
+    std::vector<float2> dsp;
+    dft_spectra(prob->psfs, G, K, dsp);
+    DV_TRY(upload(P, &P->d_dspec, dsp.data(), dsp.size(), s));
+    DV_TRY(alloc(P, &P->d_dcounter, 1 + kMaxGroups));
+    DV_TRY_CUDA(dft_prepare());
+  }
   if (P->fft_ok) {
     DV_TRY(alloc(P, &P->d_counter, 2));
     DV_TRY(alloc(P, &P->d_fft_scr, (size_t)P->n_sm * fft_size() * fft_size()));
@@ -952,7 +1007,7 @@ dv_status release(dv_plan* P) {
                   P->d_spec, P->d_counter, P->d_fft_scr, P->d_desc, P->d_feat, P->d_wsd,
                   P->tab[2].H, P->tab[2].Ht, P->tab[2].Hg, P->tab[2].Htg,
                   P->tab[2].ksH, P->tab[2].ksHt, P->tab[2].ksHg, P->tab[2].ksHtg,
-                  P->d_tcopH, P->d_tcopHt, P->d_err,
+                  P->d_tcopH, P->d_tcopHt, P->d_err, P->d_dspec, P->d_dconst, P->d_dcounter,
                   P->d_rowcov, P->d_colcov, P->d_citems, P->d_w[0], P->d_w[1], P->d_u, P->d_r, P->d_y,
                   P->d_W, P->d_z, P->d_xg, P->d_part, P->d_scal, P->d_hx, P->d_hy, P->d_hx0};
   for (void* b : bufs)
@@ -1002,7 +1057,14 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->mma_ksteps[0] = P->tab[k].ksteps[0];
   info->mma_ksteps[1] = P->tab[k].ksteps[1];
   info->tile_groups = (P->ngrp > 1 && P->path == DV_PATH_TENSOR) ? P->ngrp : 1;
-  info->reserved = 0;
+  info->tensor_h_dft = P->path == DV_PATH_TENSOR && P->dft_H ? 1 : 0;
+  info->tune_ms_tensor_dft = P->tune_ms_dft;
+  if (info->tensor_h_dft) {
+    info->blocks[0] = P->tab[1].nH;
+    info->block_psfs[0] = P->tab[1].psfs[0];
+    info->psf_pairs[0] = P->tab[1].pairs[0];
+    info->mma_ksteps[0] = 0;
+  }
   info->block_side = k == 1 ? fft_block(P->K)
                             : (k == 2 ? (P->prob.precision == DV_PREC_BF16 ? tcT_max_rows(P->K)
                                                                           : tc_block_m())

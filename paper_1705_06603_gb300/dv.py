@@ -53,7 +53,8 @@ class dv_problem(C.Structure):
                 ("check_every", C.c_int32), ("target_objective", C.c_double),
                 ("use_graphs", C.c_int32), ("noise_sigma", C.c_double),
                 ("local_solver", C.c_int32), ("vm_memory", C.c_int32),
-                ("vm_stop_rel", C.c_double), ("reserved", C.c_int32 * 2)]
+                ("vm_stop_rel", C.c_double), ("tensor_h", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class dv_stats(C.Structure):
@@ -74,7 +75,8 @@ class dv_plan_info(C.Structure):
                 ("block_psfs", C.c_int64 * 2), ("psf_pairs", C.c_int64 * 2),
                 ("block_side", C.c_int32), ("fp32_path", C.c_int32),
                 ("tune_ms_tensor", C.c_double), ("mma_ksteps", C.c_int64 * 2),
-                ("tile_groups", C.c_int32), ("reserved", C.c_int32)]
+                ("tile_groups", C.c_int32), ("tensor_h_dft", C.c_int32),
+                ("tune_ms_tensor_dft", C.c_double)]
 
 
 _vp = C.c_void_p
@@ -174,7 +176,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
                  noise_w=None, lam=1e-3, delta=1.0 / 60.0, gamma=0.4, rho=1.0, n_outer=30,
                  n_inner=10, inner_increment=0, precision=DV_PREC_FP32, path=DV_PATH_AUTO,
                  use_warmstart=0, check_every=0, target_objective=0.0, use_graphs=1,
-                 noise_sigma=0.0, local_solver=0, vm_memory=0, vm_stop_rel=None):
+                 noise_sigma=0.0, local_solver=0, vm_memory=0, vm_stop_rel=None, tensor_h=0):
     """Builds a dv_problem.  weights: None (bilinear tents), (weights_r,
     weights_c) separable profiles, or "per_tile" (one PSF per tile, the PSF
     grid being the tile grid).  Returns (problem, keepalive) where keepalive
@@ -219,6 +221,7 @@ def make_problem(hy, wy, psfs, n_tiles=(1, 1), overlap=16, tile_bounds=None, wei
     p.local_solver, p.vm_memory = local_solver, vm_memory
     if vm_stop_rel is not None:
         p.vm_stop_rel = vm_stop_rel
+    p.tensor_h = tensor_h
     return p, keep
 
 

@@ -322,14 +322,55 @@ def test_tensor_operator_matches_oracle(env, prec, hy, wy, K, G):
     nxr, nxc = hy + K - 1, wy + K - 1
     x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
     r = g.standard_normal((hy, wy)).astype(np.float32)
-    plan = dv.Plan(hy, wy, psfs, precision=prec, path=TENSOR)
+    plan = dv.Plan(hy, wy, psfs, precision=prec, path=TENSOR, tensor_h=1 if prec == BF16 else 0)
     assert plan.info.path == TENSOR and plan.info.block_side in (128, 256)
+    assert plan.info.tensor_h_dft == 0
     yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
     gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
     wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
     ps = psfs.astype(np.float64)
     assert_close(yd, O.apply_H(x.astype(np.float64), ps, wr, wc), TC_TOL[prec])
     assert_close(gd, O.apply_Ht(r.astype(np.float64), ps, wr, wc), TC_TOL[prec])
+    plan.close()
+
+
+@pytest.mark.parametrize("hy,wy,K,G", [(130, 70, 9, (3, 3)), (200, 180, 31, (4, 3)),
+                                       (150, 97, 63, (2, 2)), (66, 64, 15, (1, 1)),
+                                       (300, 260, 15, (8, 8)), (250, 301, 31, (5, 6)),
+                                       (331, 203, 63, (4, 3))])
+def test_block_dft_H_matches_oracle(env, hy, wy, K, G):
+    """H as the block DFT on the tensor cores (FP16 operands, FP32 accumulation):
+    several 128 x 128 overlap-save blocks with ragged edges, blocks straddling
+    PSF cells (up to 3 x 3 PSFs per block on the 8 x 8 grid), every K of the
+    tensor path, at the BF16 operator tolerance; H^T stays the banded form."""
+    torch, dv = env
+    g = np.random.default_rng(K + 2000)
+    psfs = random_psfs(g, G, K)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
+    plan = dv.Plan(hy, wy, psfs, precision=BF16, path=TENSOR, tensor_h=2)
+    assert plan.info.path == TENSOR and plan.info.tensor_h_dft == 1
+    yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
+    y_ref = O.apply_H(x.astype(np.float64), psfs.astype(np.float64), wr, wc)
+    print(f"K {K} G {G}: rel L2 {rel_l2(yd, y_ref):.3e}")
+    assert_close(yd, y_ref, TC_TOL[BF16])
+    plan.close()
+
+
+def test_block_dft_solve_matches_oracle(env):
+    """The 128x128 workload at the plain iteration count with H as the block
+    DFT in the inner iterations (residual epilogue, tile groups in the
+    captured graphs): within the final-image bound 1e-3 of the oracle."""
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, precision=BF16,
+                              path=TENSOR, tensor_h=2)
+    assert plan.info.tensor_h_dft == 1
+    lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
+    print(f"block-DFT solve: x_hat rel L2 {rel_l2(xd, xr):.3e}")
+    assert_close(xd, xr, 1e-3)
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
+    assert abs(st["objective"] - F) <= 1e-3 * F
     plan.close()
 
 
