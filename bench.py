@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--inner", type=int, default=3,
                     help="projected-gradient steps per outer iteration of the chosen form "
                          "(0: the workload's count)")
+    ap.add_argument("--tensor-h", type=int, choices=[0, 1, 2], default=0,
+                    help="tensor-core H of the chosen form: 0 autotuned, 1 banded Toeplitz "
+                         "(BF16), 2 block DFT (FP16)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one eager solve of 1 outer x 1 inner iteration on the workload (a "
                          "short, fixed launch sequence for ncu captures); prints nothing")
@@ -503,7 +506,7 @@ def run_ours(args):
     t_plan = time.perf_counter()
     plan = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=4 * w.n_outer, use_warmstart=1,
                    check_every=args.check_every, target_objective=target, precision=prec,
-                   **chosen)
+                   tensor_h=args.tensor_h, **chosen)
     t_plan_chosen = time.perf_counter() - t_plan
     dv.dv_plan_set_warmstart(plan.handle, net)
     st = dv.dv_stats()
@@ -562,7 +565,7 @@ def run_ours(args):
     # blurred-image start (one warm-up solve, one timed), outside the timed region
     nows = dv.Plan(w.hy, w.wy, psfs, stream=stream, n_outer=4 * w.n_outer, use_warmstart=0,
                    check_every=args.check_every, target_objective=target, precision=prec,
-                   **chosen)
+                   tensor_h=args.tensor_h, **chosen)
     st_nows = dv.dv_stats()
     dv.dv_consensus_solve(nows.handle, y, None, x_out, st_nows, stream)
     ms_nows, _ = timed(lambda: dv.dv_consensus_solve(nows.handle, y, None, x_out, st_nows, stream))
@@ -784,7 +787,8 @@ def run_profile_case(args):
     psfs = psf_grid_for(w).astype(np.float32)
     y, W = make_inputs(torch, dv, w, psfs, 0)
     kw = {"fft": dict(path=dv.DV_PATH_FFT), "direct": dict(path=dv.DV_PATH_DIRECT),
-          "bf16": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_BF16),
+          "bf16": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_BF16,
+                       tensor_h=args.tensor_h),
           "tf32": dict(path=dv.DV_PATH_TENSOR, precision=dv.DV_PREC_TF32)}[args.profile_path]
     plan = dv.Plan(w.hy, w.wy, psfs, lam=w.lam, delta=w.delta, gamma=w.gamma, rho=w.rho,
                    n_outer=1, n_inner=1, use_graphs=0, noise_sigma=w.noise_sigma, noise_w=W,

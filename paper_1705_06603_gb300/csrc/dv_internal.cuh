@@ -204,7 +204,7 @@ cudaError_t launch_fft_Ht(const OpArgs& a, cudaStream_t s, int grid);
 bool dft_supported(int K);
 cudaError_t dft_prepare();
 void dft_constants(std::vector<uint8_t>& out);
-void dft_spectra(const float* psfs, int G, int K, std::vector<float2>& out);
+void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out);
 cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid);
 
 // Tensor-core path (tcgen05, BF16 / TF32 operands; its own work tables)
@@ -304,7 +304,7 @@ struct dv_plan {
   bool fft_ok = false;
   bool dft_ok = false;             // H as the block DFT on the tensor cores is available
   bool dft_H = false;              // ... and used by the tensor path
-  float2* d_dspec = nullptr;       // its PSF spectra [G][128][128], natural order, / 128
+  uint32_t* d_dspec = nullptr;     // its PSF spectra [G][128][128] (FP16 pairs), natural order, / 128
   unsigned char* d_dconst = nullptr;  // its constant operand [Fr; Fi] (FP16 panels)
   int* d_dcounter = nullptr;       // its work counters: [0] whole launches, [1 + g] group g
   float2* d_spec = nullptr;

@@ -436,7 +436,7 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
   a.gamma = (float)p->prob.gamma;
   if (dft_h(p, path)) {
     a.ksr = nullptr;
-    a.spec = p->d_dspec;
+    a.spec = reinterpret_cast<const float2*>(p->d_dspec);
     a.tcop = p->d_dconst;
     a.counter = p->d_dcounter;
   }
@@ -862,7 +862,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     std::vector<uint8_t> cst;
     dft_constants(cst);
     DV_TRY(upload(P, &P->d_dconst, cst.data(), cst.size(), s));
-    std::vector<float2> dsp;
+    std::vector<uint32_t> dsp;
     dft_spectra(prob->psfs, G, K, dsp);
     DV_TRY(upload(P, &P->d_dspec, dsp.data(), dsp.size(), s));
     DV_TRY(alloc(P, &P->d_dcounter, 1 + kMaxGroups));

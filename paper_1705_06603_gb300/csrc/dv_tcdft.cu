@@ -11,12 +11,13 @@
 // Sec. II-B: circular convolution of size 128, then the valid part).
 //
 // Each DFT stage is a GEMM on the tensor cores with the constant matrices
-// [Fr; Fi] (cos and -sin, FP16) in shared memory:
-//   stage 1  Y^T[c][kr]  = sum_r X[r][c] F[kr][r]          (M = c, N = re|im kr)
-//   stage 2  Z^T[kc][kr] = sum_c F[kc][c] Y[kr][c]          (M = kc, N = re|im kr)
+// [Fr; Fi] (cos and -sin, FP16) in shared memory, ordered so that every
+// tensor-memory lane (a thread) owns one row of the next stage's operand:
+//   stage 1  Y[kr][c]    = sum_r F[kr][r] X[r][c]            (M = kr, N = c; Fr and Fi)
+//   stage 2  Z^T[kc][kr] = sum_c F[kc][c] Y[kr][c]            (M = kc, N = re|im kr)
 //            as Fr [Yr | Yi] + Fi [-Yi | Yr] over one buffer [-Yi | Yr | Yi]
-//   inverse  T^T[c][kr]  = sum_kc conj F[c][kc] Z[kr][kc]   (Fr [Zr | Zi] + Fi [Zi | -Zr])
-//            x[r][c]     = Re sum_kr conj F[r][kr] T[kr][c]  (Fr Tr + Fi Ti)
+//   inverse  U[r][kc]    = sum_kr conj F[r][kr] Z[kr][kc]     (Fr [Zr | Zi] + Fi [Zi | -Zr])
+//            x[r][c]     = Re sum_kc U[r][kc] conj F[c][kc]   (Ur Fr + Ui Fi)
 // Operands are K-major, no swizzle: a matrix of R rows and K columns is stored
 // as K / 8 panels of R 16-byte rows (a panel stride padded by 16 bytes), so a
 // 16-wide k-step is two consecutive panels (LBO = panel stride, SBO = 128).
@@ -26,9 +27,9 @@
 // Scaling keeps the FP16 values in range: the spectra carry 1 / 128 and the
 // first inverse stage's result another 1 / 128 (the inverse DFT's 1 / 128^2).
 //
-// Warps 0-7 stage operands and run the epilogue, one lane of warp 8 allocates
-// tensor memory and issues the MMAs.  The grid is persistent (one CTA per SM,
-// items from an atomic counter, heaviest first).  Every wait is bounded.
+// Eight warps stage operands, take the products and run the epilogue; thread
+// 0 issues the MMAs.  The grid is persistent (one CTA per SM, items from an
+// atomic counter, heaviest first).  Every wait is bounded.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -43,9 +44,8 @@ namespace {
 using namespace tcg;
 
 constexpr int S = 128;                      // transform size
-constexpr int NWS = 8;                      // staging / epilogue warps
+constexpr int NWS = 8;                      // warps (two per tensor-memory lane quarter)
 constexpr int NTS = 32 * NWS;
-constexpr int NTH = NTS + 32;               // + the MMA warp
 constexpr int CROWS = 2 * S;                // [Fr; Fi]
 constexpr int CPAN = CROWS * 16 + 16;       // panel stride (bytes) of the constants
 constexpr int CBYTES = (S / 8) * CPAN;
@@ -59,29 +59,21 @@ constexpr int SMEM_D = kHdrD + CBYTES + XBYTES + YBYTES + 2 * S * 4;
 constexpr uint32_t TMEM_COLS = 512;         // D [0, 256), Z sum [256, 512)
 static_assert(SMEM_D <= 227 * 1024, "shared memory");
 static_assert(YBYTES >= 2 * XBYTES, "T operands fit in the Y buffer");
+static_assert(YBYTES >= S * (S + 1) * 4, "output tile fits in the Y buffer");
 static_assert(CPAN % 16 == 0 && XPAN % 16 == 0 && YPAN % 16 == 0, "alignment");
 
 struct BarsD {
-  uint64_t bx, by, bd, fin;
+  uint64_t bd, fin;
   uint32_t tmem;
   int abort;
-  int item;
+  int item[2];                // work items of the two slots (current, next)
 };
 static_assert(sizeof(BarsD) <= 256, "barrier header");
-
-__device__ __forceinline__ void sync_st() { named_sync<NTS>(); }
-__device__ __forceinline__ bool all_st(bool v) { return named_all<NTS>(v); }
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   const __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
-__device__ __forceinline__ void st_h(unsigned char* base, int off, float v) {
-  *reinterpret_cast<__half*>(base + off) = __float2half_rn(v);
-}
-
-// Byte offset of element (row, k) in a panel layout with panel stride pan.
-__device__ __forceinline__ int el(int row, int k, int pan) { return (k >> 3) * pan + 16 * row + 2 * (k & 7); }
 
 // One GEMM chain of 8 k-steps (K = 128): D (+)= A B^T, A rows from a0, B rows
 // from b0 (shared-memory addresses of row 0 of panel 0).
@@ -91,10 +83,15 @@ __device__ __forceinline__ void chain(uint32_t d, uint32_t a0, uint32_t apan, ui
 #pragma unroll
   for (int j = 0; j < 8; ++j)
     mma_bf16(d, ad + (uint64_t)(j * 2 * (apan >> 4)), bd + (uint64_t)(j * 2 * (bpan >> 4)), id,
-            (acc || j > 0) ? 1u : 0u);
+             (acc || j > 0) ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(NTH, 1) dft_H_kernel(const OpArgs A) {
+// All 8 warps stage operands, take the products and run the epilogue; thread
+// 0 also issues each stage's MMAs once every warp has written the operand
+// (a CTA barrier, then the MMAs run asynchronously and complete on bd).  8
+// warps, two per SM sub-partition, may hold up to 255 registers a thread: the
+// block's x window and a PSF's spectrum slice stay in registers.
+__global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
   BarsD* H = reinterpret_cast<BarsD*>(smem);
   unsigned char* sC = smem + kHdrD;
@@ -102,21 +99,29 @@ __global__ void __launch_bounds__(NTH, 1) dft_H_kernel(const OpArgs A) {
   unsigned char* sY = sX + XBYTES;
   float* sWr = reinterpret_cast<float*>(sY + YBYTES);
   float* sWc = sWr + S;
-  __shared__ WorkItem wi;
-  __shared__ TileDesc td;
+  __shared__ WorkItem wis[2];
+  __shared__ TileDesc tds[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K, b = S - K + 1;
+  const uint64_t limit = A.wait_ns ? A.wait_ns : kWaitNs;
+  // thread 0: the next work item into slot s
+  auto fetch = [&](int slot) {
+    const int it = atomicAdd(A.counter, 1);
+    H->item[slot] = it;
+    if (it < A.n_work) {
+      wis[slot] = A.work[it];
+      tds[slot] = A.tiles[wis[slot].tile];
+    }
+  };
   if (tid == 0) {
-    mbar_init(&H->bx, NTS);
-    mbar_init(&H->by, NTS);
     mbar_init(&H->bd, 1);
     mbar_init(&H->fin, 1);
     H->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == NWS) tmem_alloc(&H->tmem, TMEM_COLS);
+  if (warp == 0) tmem_alloc(&H->tmem, TMEM_COLS);
   // constants [Fr; Fi] (the plan's byte image of the panels)
-  for (int e = tid; e < CBYTES / 16; e += NTH)
+  for (int e = tid; e < CBYTES / 16; e += NTS)
     reinterpret_cast<uint4*>(sC)[e] = __ldg(reinterpret_cast<const uint4*>(A.tcop) + e);
   fence_async_smem();
   tc_fence_before();
@@ -125,246 +130,63 @@ __global__ void __launch_bounds__(NTH, 1) dft_H_kernel(const OpArgs A) {
   const uint32_t tbase = H->tmem;
   const uint32_t aC = saddr(sC), aX = saddr(sX), aY = saddr(sY);
   const uint32_t id256 = idesc(0, 128, 256), id128 = idesc(0, 128, 128);
-  // phase counters (uses of each barrier so far)
-  uint32_t nx = 0, ny = 0, nd = 0;
+  uint32_t nd = 0;                          // completions of bd waited for so far
   const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-  const int h = warp >> 2;          // column half of the staging warp
-  const int L = 32 * (warp & 3) + lane;   // its tensor-memory lane
+  const int h = warp >> 2;                  // column half of the warp
+  const int L = 32 * (warp & 3) + lane;     // its tensor-memory lane
   bool ok = true;
 
-  for (;;) {
-    // the previous item's tensor-memory reads are ordered before the next
-    // item's MMAs
+  // operands written by every thread -> visible to the MMAs, thread 0 issues
+  auto publish = [&]() {
+    fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
-      const int it = atomicAdd(A.counter, 1);
-      H->item = it;
-      if (it < A.n_work) {
-        wi = A.work[it];
-        td = A.tiles[wi.tile];
+    tc_fence_after();
+  };
+  auto wait_d = [&]() {
+    const bool w = wait_bar(&H->bd, nd++ & 1, &H->abort, A.err, limit);
+    __syncthreads();
+    ok = ok && w && !*(volatile int*)&H->abort;
+    tc_fence_after();
+    return ok;
+  };
+
+  // the 128 x 128 x window of a block, kept in registers (FP16) for all its
+  // PSFs: item u of this thread = column c, rows 8q .. 8q + 7 (e = tid + 256 u);
+  // loaded for the next block while the current block's inverse runs
+  uint32_t xv[8][4];
+  auto load_x = [&](const WorkItem& w2, const TileDesc& t2) {
+    const float* img2 = A.in + t2.xoff;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * NTS;
+      const int c = e & (S - 1), q = e >> 7, C = w2.c0 + c;
+      float v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int R = w2.r0 + 8 * q + t;
+        v[t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img2 + (int64_t)R * t2.xpitch + C) : 0.f;
       }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) xv[u][t] = pack_h2(v[2 * t], v[2 * t + 1]);
     }
+  };
+  auto psfs_of = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
+  if (tid == 0) fetch(0);
+  int cur = 0;
+  bool have_x = false;
+  for (;;) {
+    tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (H->item >= A.n_work || !ok || *(volatile int*)&H->abort) break;
+    if (H->item[cur] >= A.n_work || !ok || *(volatile int*)&H->abort) break;
+    const WorkItem& wi = wis[cur];
+    const TileDesc& td = tds[cur];
     const int nb = wi.b_hi - wi.b_lo + 1;
-    const int np = (wi.a_hi - wi.a_lo + 1) * nb;
-
-    if (warp == NWS) {
-      // ---------------------------------------------------------- MMA lane
-      if (lane == 0) {
-        for (int p = 0; p < np && ok; ++p) {
-          ok = wait_bar(&H->bx, nx++ & 1, &H->abort, A.err, A.wait_ns ? A.wait_ns : kWaitNs);
-          if (!ok) break;
-          tc_fence_after();
-          chain(tbase, aX, XPAN, aC, CPAN, id256, false);                  // Y^T
-          tc_commit(&H->bd);
-          ok = wait_bar(&H->by, ny++ & 1, &H->abort, A.err, A.wait_ns ? A.wait_ns : kWaitNs);
-          if (!ok) break;
-          tc_fence_after();
-          chain(tbase, aC, CPAN, aY + 16 * S, YPAN, id256, false);         // Fr [Yr | Yi]
-          chain(tbase, aC + 16 * S, CPAN, aY, YPAN, id256, true);          // Fi [-Yi | Yr]
-          tc_commit(&H->bd);
-        }
-        if (ok && np > 0) {
-          ok = wait_bar(&H->by, ny++ & 1, &H->abort, A.err, A.wait_ns ? A.wait_ns : kWaitNs);
-          if (ok) {
-            tc_fence_after();
-            chain(tbase, aC, CPAN, aY, YPAN, id256, false);                // Fr [Zr | Zi]
-            chain(tbase, aC + 16 * S, CPAN, aY + 16 * S, YPAN, id256, true);   // Fi [Zi | -Zr]
-            tc_commit(&H->bd);
-            ok = wait_bar(&H->by, ny++ & 1, &H->abort, A.err, A.wait_ns ? A.wait_ns : kWaitNs);
-          }
-          if (ok) {
-            tc_fence_after();
-            chain(tbase, aC, CPAN, aX, XPAN, id128, false);                // Fr Tr
-            chain(tbase, aC + 16 * S, CPAN, aY, XPAN, id128, true);        // Fi Ti
-            tc_commit(&H->bd);
-          }
-        }
-        if (!ok) *(volatile int*)&H->abort = 1;
-      }
-      __syncwarp();
-      continue;
-    }
-
-    // -------------------------------------------------- staging / epilogue
-    const float* img = A.in + td.xoff;
-    // X_p^T into sX: element (m = c, k = r) = w_p(r0 + r, c0 + c) x(r0 + r, c0 + c)
-    auto stage_x = [&](int p) {
-      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      for (int e = tid; e < S; e += NTS) {
-        const int R = wi.r0 + e, C = wi.c0 + e;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
-        sWc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
-      }
-      sync_st();
-      // item (c, q): column c, rows 8q .. 8q + 7; threads of a warp take
-      // consecutive columns (coalesced loads)
-      for (int e0 = tid; e0 < S * (S / 8); e0 += 2 * NTS) {
-        float v[2][8];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = e0 + u * NTS;
-          const int c = e & (S - 1), q = e >> 7;
-          const int C = wi.c0 + c;
-          const float wc = sWc[c];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int r = 8 * q + t, R = wi.r0 + r;
-            const float w = sWr[r] * wc;
-            v[u][t] = (w != 0.f && R < td.nxr && C < td.nxc)
-                          ? w * __ldg(img + (int64_t)R * td.xpitch + C) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int e = e0 + u * NTS;
-          const int c = e & (S - 1), q = e >> 7;
-          *reinterpret_cast<uint4*>(sX + q * XPAN + 16 * c) =
-              make_uint4(pack_h2(v[u][0], v[u][1]), pack_h2(v[u][2], v[u][3]),
-                         pack_h2(v[u][4], v[u][5]), pack_h2(v[u][6], v[u][7]));
-        }
-      }
-      fence_async_smem();
-    };
-    auto wait_d = [&]() {
-      const bool w = wait_bar(&H->bd, nd++ & 1, &H->abort, A.err, A.wait_ns ? A.wait_ns : kWaitNs);
-      ok = all_st(w);
-      tc_fence_after();
-      return ok;
-    };
-    auto arrive = [&](uint64_t* bar) {
-      tc_fence_before();
-      mbar_arrive(bar);
-    };
-
-    if (np > 0) {
-      stage_x(0);
-      arrive(&H->bx);
-    }
-    for (int p = 0; p < np && ok; ++p) {
-      // Y^T (lane c): columns 0..127 = Yr[kr], 128..255 = Yi[kr]; this warp
-      // takes half h -> rows of the buffer [-Yi | Yr | Yi]
-      if (!wait_d()) break;
-      for (int c0 = 0; c0 < S; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + c0), r);
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const float v = __uint_as_float(r[t]);
-          const int kr = c0 + t;
-          if (h == 0) {
-            st_h(sY, el(S + kr, L, YPAN), v);
-          } else {
-            st_h(sY, el(kr, L, YPAN), -v);
-            st_h(sY, el(2 * S + kr, L, YPAN), v);
-          }
-        }
-      }
-      fence_async_smem();
-      arrive(&H->by);
-      // the next PSF's X (its MMAs wait until the product below has read D)
-      if (p + 1 < np) stage_x(p + 1);
-      if (!wait_d()) break;
-      // Z^T (lane kc): columns kr (re) and S + kr (im); sum += Z . Hh_p over
-      // kr in this warp's half
-      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      const float2* hh = A.spec + (size_t)(ga * A.Gc + gb) * S * S;
-      for (int k0 = 64 * h; k0 < 64 * h + 64; k0 += 16) {
-        uint32_t zr[16], zi[16], ar[16], ai[16];
-        float2 hv[16];
-#pragma unroll
-        for (int t = 0; t < 16; ++t) hv[t] = __ldg(hh + (size_t)(k0 + t) * S + L);
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)k0, zr);
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S + k0), zi);
-        if (p > 0) {
-          tmem_ld16_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-          tmem_ld16_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const float a = __uint_as_float(zr[t]), bb = __uint_as_float(zi[t]);
-          const float re = a * hv[t].x - bb * hv[t].y, im = a * hv[t].y + bb * hv[t].x;
-          ar[t] = __float_as_uint(p > 0 ? __uint_as_float(ar[t]) + re : re);
-          ai[t] = __float_as_uint(p > 0 ? __uint_as_float(ai[t]) + im : im);
-        }
-        tmem_st16_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-        tmem_st16_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-      }
-      tmem_wait_st();
-      if (p + 1 < np) arrive(&H->bx);   // D read: the next PSF may overwrite it
-    }
+    const int np = psfs_of(wi);
     float* out = A.out;
-    if (np > 0 && ok) {
-      // inverse, stage 1 operand: the sum (lane kc) -> [Zr | Zi | -Zr]
-      for (int k0 = 64 * h; k0 < 64 * h + 64; k0 += 16) {
-        uint32_t ar[16], ai[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int kr = k0 + t;
-          const float zr = __uint_as_float(ar[t]), zi = __uint_as_float(ai[t]);
-          st_h(sY, el(kr, L, YPAN), zr);
-          st_h(sY, el(S + kr, L, YPAN), zi);
-          st_h(sY, el(2 * S + kr, L, YPAN), -zr);
-        }
-      }
-      fence_async_smem();
-      arrive(&H->by);
-      // T^T (lane c): columns kr (re), S + kr (im), scaled by 1 / 128, into the
-      // stage-2 operands Tr (sX) and Ti (sY), rows c, k = kr
-      if (wait_d()) {
-        for (int k0 = 0; k0 < S; k0 += 16) {
-          uint32_t r[16];
-          tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + k0), r);
-          tmem_wait_ld();
-          unsigned char* dst = h == 0 ? sX : sY;
-#pragma unroll
-          for (int t = 0; t < 16; t += 8) {
-            const float s = 1.f / S;
-            *reinterpret_cast<uint4*>(dst + ((k0 + t) >> 3) * XPAN + 16 * L) = make_uint4(
-                pack_h2(s * __uint_as_float(r[t]), s * __uint_as_float(r[t + 1])),
-                pack_h2(s * __uint_as_float(r[t + 2]), s * __uint_as_float(r[t + 3])),
-                pack_h2(s * __uint_as_float(r[t + 4]), s * __uint_as_float(r[t + 5])),
-                pack_h2(s * __uint_as_float(r[t + 6]), s * __uint_as_float(r[t + 7])));
-          }
-        }
-        fence_async_smem();
-        arrive(&H->by);
-      }
-      // x (lane r, columns c): rows and columns K - 1 .. 127 are the block's
-      // valid outputs
-      if (ok && wait_d()) {
-        const int r = L;
-        const int i = wi.r0 + r - (K - 1);
-        const bool rin = r >= K - 1 && i < td.nyr;
-        for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16_nowait(tbase + lanes + (uint32_t)c0, v);
-          tmem_wait_ld();
-          if (!rin) continue;
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int c = c0 + t, jj = wi.c0 + c - (K - 1);
-            if (c < K - 1 || jj >= td.nyc || jj - wi.c0 >= b) continue;
-            const float y = __uint_as_float(v[t]);
-            if (A.mode == OP_PLAIN) {
-              out[td.yoff + (int64_t)i * td.ypitch + jj] = y;
-            } else {
-              const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
-              const float wt = A.W ? A.W[gi] : 1.f;
-              out[td.yoff + (int64_t)i * td.ypitch + jj] = wt * (y - A.y[gi]);
-            }
-          }
-        }
-      }
-    } else if (np == 0 && ok) {
+
+    if (np == 0) {
       // no PSF reaches the block: H x is zero there
       for (int e = tid; e < b * b; e += NTS) {
         const int i = wi.r0 + e / b, jj = wi.c0 + e % b;
@@ -373,17 +195,218 @@ __global__ void __launch_bounds__(NTH, 1) dft_H_kernel(const OpArgs A) {
         const float wt = (A.mode != OP_PLAIN && A.W) ? A.W[gi] : 1.f;
         out[td.yoff + (int64_t)i * td.ypitch + jj] = A.mode == OP_PLAIN ? 0.f : -wt * A.y[gi];
       }
+      __syncthreads();
+      if (tid == 0) fetch(cur ^ 1);
+      cur ^= 1;
+      have_x = false;
+      continue;
     }
-    if (!ok) *(volatile int*)&H->abort = 1;
+    if (!have_x) load_x(wi, td);
+
+    // X_p^T into sX: element (m = c, k = r) = w_p(r0 + r, c0 + c) x(r0 + r, c0 + c)
+    auto stage_x = [&](int p) {
+      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+      __syncthreads();   // the previous PSF's weights are no longer read
+      for (int e = tid; e < S; e += NTS) {
+        const int R = wi.r0 + e, C = wi.c0 + e;
+        sWr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
+        sWc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + u * NTS;
+        const int c = e & (S - 1), q = e >> 7;
+        const float wc = sWc[c];
+        uint32_t o[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const float2 fx = __half22float2(*reinterpret_cast<const __half2*>(&xv[u][t]));
+          o[t] = pack_h2(sWr[8 * q + 2 * t] * wc * fx.x, sWr[8 * q + 2 * t + 1] * wc * fx.y);
+        }
+        *reinterpret_cast<uint4*>(sX + q * XPAN + 16 * c) = make_uint4(o[0], o[1], o[2], o[3]);
+      }
+    };
+
+    stage_x(0);
+    publish();
+    if (tid == 0) {
+      chain(tbase, aC, CPAN, aX, XPAN, id128, false);                    // Yr = Fr X
+      chain(tbase + S, aC + 16 * S, CPAN, aX, XPAN, id128, false);       // Yi = Fi X
+      tc_commit(&H->bd);
+    }
+    for (int p = 0; p < np; ++p) {
+      // Y (lane kr): columns 0..127 = Yr[kr][c], 128..255 = Yi[kr][c]; half h
+      // of the warps takes Yr (row S + kr of the buffer [-Yi | Yr | Yi]) or Yi
+      // (rows kr and 2S + kr), 8 consecutive c per 16-byte store
+      if (!wait_d()) break;
+      for (int c0 = 0; c0 < S; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + c0), r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; t += 8) {
+          const float* f = reinterpret_cast<const float*>(r + t);
+          const int off = ((c0 + t) >> 3) * YPAN + 16 * L;
+          if (h == 0) {
+            *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
+                pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
+          } else {
+            *reinterpret_cast<uint4*>(sY + off) = make_uint4(
+                pack_h2(-f[0], -f[1]), pack_h2(-f[2], -f[3]), pack_h2(-f[4], -f[5]),
+                pack_h2(-f[6], -f[7]));
+            *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
+                pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
+          }
+        }
+      }
+      publish();
+      if (tid == 0) {
+        chain(tbase, aC, CPAN, aY + 16 * S, YPAN, id256, false);         // Fr [Yr | Yi]
+        chain(tbase, aC + 16 * S, CPAN, aY, YPAN, id256, true);          // Fi [-Yi | Yr]
+        tc_commit(&H->bd);
+      }
+      // the PSF's spectrum at this thread's column kc = L and rows kr of its
+      // half, fetched while the stage-2 MMAs run
+      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
+      const unsigned int* hh =
+          reinterpret_cast<const unsigned int*>(A.spec) + (size_t)(ga * A.Gc + gb) * S * S;
+      uint32_t hv[64];
+#pragma unroll
+      for (int t = 0; t < 64; ++t) hv[t] = __ldg(hh + (size_t)(64 * h + t) * S + L);
+      // the next PSF's X (S1 of PSF p has completed: sX is free)
+      if (p + 1 < np) stage_x(p + 1);
+      if (!wait_d()) break;
+      // Z^T (lane kc): columns kr (re) and S + kr (im); sum += Z . Hh_p over
+      // kr in this warp's half
+#pragma unroll
+      for (int k8 = 0; k8 < 8; ++k8) {
+        const int k0 = 64 * h + 8 * k8;
+        uint32_t zr[8], zi[8], ar[8], ai[8];
+        tmem_ld8_nowait(tbase + lanes + (uint32_t)k0, zr);
+        tmem_ld8_nowait(tbase + lanes + (uint32_t)(S + k0), zi);
+        if (p > 0) {
+          tmem_ld8_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
+          tmem_ld8_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
+        }
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hv[8 * k8 + t]));
+          const float a = __uint_as_float(zr[t]), bb = __uint_as_float(zi[t]);
+          const float re = a * hf.x - bb * hf.y, im = a * hf.y + bb * hf.x;
+          ar[t] = __float_as_uint(p > 0 ? __uint_as_float(ar[t]) + re : re);
+          ai[t] = __float_as_uint(p > 0 ? __uint_as_float(ai[t]) + im : im);
+        }
+        tmem_st8_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
+        tmem_st8_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
+      }
+      tmem_wait_st();
+      if (p + 1 < np) {
+        publish();   // D read, X_{p+1} written
+        if (tid == 0) {
+          chain(tbase, aC, CPAN, aX, XPAN, id128, false);
+          chain(tbase + S, aC + 16 * S, CPAN, aX, XPAN, id128, false);
+          tc_commit(&H->bd);
+        }
+      }
+    }
+    if (!ok) break;
+    if (tid == 0) fetch(cur ^ 1);   // published with the inverse's first operand
+    // inverse, stage 1 operand: the sum (lane kc, columns kr) -> rows kc,
+    // S + kc, 2S + kc of [Zr | Zi | -Zr], 8 consecutive kr per 16-byte store
+    for (int k0 = 64 * h; k0 < 64 * h + 64; k0 += 16) {
+      uint32_t ar[16], ai[16];
+      tmem_ld16_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
+      tmem_ld16_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
+      tmem_wait_ld();
+#pragma unroll
+      for (int t = 0; t < 16; t += 8) {
+        const float* zr = reinterpret_cast<const float*>(ar + t);
+        const float* zi = reinterpret_cast<const float*>(ai + t);
+        const int off = ((k0 + t) >> 3) * YPAN + 16 * L;
+        *reinterpret_cast<uint4*>(sY + off) = make_uint4(
+            pack_h2(zr[0], zr[1]), pack_h2(zr[2], zr[3]), pack_h2(zr[4], zr[5]), pack_h2(zr[6], zr[7]));
+        *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
+            pack_h2(zi[0], zi[1]), pack_h2(zi[2], zi[3]), pack_h2(zi[4], zi[5]), pack_h2(zi[6], zi[7]));
+        *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
+            pack_h2(-zr[0], -zr[1]), pack_h2(-zr[2], -zr[3]), pack_h2(-zr[4], -zr[5]),
+            pack_h2(-zr[6], -zr[7]));
+      }
+    }
+    publish();
+    if (tid == 0) {
+      chain(tbase, aC, CPAN, aY, YPAN, id256, false);                    // Fr [Zr | Zi]
+      chain(tbase, aC + 16 * S, CPAN, aY + 16 * S, YPAN, id256, true);   // Fi [Zi | -Zr]
+      tc_commit(&H->bd);
+    }
+    // the next block's x window, in flight while this block's inverse runs
+    have_x = H->item[cur ^ 1] < A.n_work && psfs_of(wis[cur ^ 1]) > 0;
+    if (have_x) load_x(wis[cur ^ 1], tds[cur ^ 1]);
+    // U (lane r): columns kc (re), S + kc (im), scaled by 1 / 128, into the
+    // last stage's operands Ur (sX) and Ui (sY), rows r, k = kc
+    if (!wait_d()) break;
+    for (int k0 = 0; k0 < S; k0 += 16) {
+      uint32_t r[16];
+      tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + k0), r);
+      tmem_wait_ld();
+      unsigned char* dst = h == 0 ? sX : sY;
+      const float sc = 1.f / S;
+#pragma unroll
+      for (int t = 0; t < 16; t += 8)
+        *reinterpret_cast<uint4*>(dst + ((k0 + t) >> 3) * XPAN + 16 * L) = make_uint4(
+            pack_h2(sc * __uint_as_float(r[t]), sc * __uint_as_float(r[t + 1])),
+            pack_h2(sc * __uint_as_float(r[t + 2]), sc * __uint_as_float(r[t + 3])),
+            pack_h2(sc * __uint_as_float(r[t + 4]), sc * __uint_as_float(r[t + 5])),
+            pack_h2(sc * __uint_as_float(r[t + 6]), sc * __uint_as_float(r[t + 7])));
+    }
+    publish();
+    if (tid == 0) {
+      chain(tbase, aX, XPAN, aC, CPAN, id128, false);                    // Ur Fr
+      chain(tbase, aY, XPAN, aC + 16 * S, CPAN, id128, true);            // Ui Fi
+      tc_commit(&H->bd);
+    }
+    // x (lane r, columns c) -> an FP32 tile in the Y buffer (free once the
+    // last MMAs have completed), then the valid rows and columns K - 1 .. 127
+    // are written row by row (coalesced observed image, weights and output)
+    if (!wait_d()) break;
+    {
+      float* tile = reinterpret_cast<float*>(sY);
+      constexpr int TPT = S + 1;
+      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16_nowait(tbase + lanes + (uint32_t)c0, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) tile[L * TPT + c0 + t] = __uint_as_float(v[t]);
+      }
+      __syncthreads();
+      const int nr = min(b, td.nyr - wi.r0), nc = min(b, td.nyc - wi.c0);
+      for (int e = tid; e < nr * b; e += NTS) {
+        const int il = e / b, jl = e - il * b;
+        if (jl >= nc) continue;
+        const int i = wi.r0 + il, jj = wi.c0 + jl;
+        const float y = tile[(il + K - 1) * TPT + jl + K - 1];
+        if (A.mode == OP_PLAIN) {
+          out[td.yoff + (int64_t)i * td.ypitch + jj] = y;
+        } else {
+          const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
+          const float wt = A.W ? A.W[gi] : 1.f;
+          out[td.yoff + (int64_t)i * td.ypitch + jj] = wt * (y - A.y[gi]);
+        }
+      }
+    }
+    cur ^= 1;
   }
+  if (!ok) *(volatile int*)&H->abort = 1;
   // teardown: every MMA this CTA issued has completed before tensor memory is freed
-  if (warp == NWS && lane == 0) {
+  if (tid == 0) {
     tc_commit(&H->fin);
     drain_bar(&H->fin, 0, A.err);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == NWS) {
+  if (warp == 0) {
     tc_fence_after();
     tmem_free(tbase, TMEM_COLS);
   }
@@ -413,15 +436,16 @@ void dft_constants(std::vector<uint8_t>& out) {
 }
 
 // Spectra of the zero-padded PSFs, natural order [kr][kc], scaled by 1 / 128:
-// Hh(kr, kc) = sum_{m, n < K} h(m, n) exp(-2 pi i (kr m + kc n) / 128) / 128, FP64.
-void dft_spectra(const float* psfs, int G, int K, std::vector<float2>& out) {
+// Hh(kr, kc) = sum_{m, n < K} h(m, n) exp(-2 pi i (kr m + kc n) / 128) / 128,
+// summed in FP64 on the host and stored as FP16 (re, im) pairs.
+void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out) {
   std::vector<double> cr(S), ci(S);
   for (int j = 0; j < S; ++j) {
     const double a = -2.0 * 3.14159265358979323846 * j / S;
     cr[j] = std::cos(a);
     ci[j] = std::sin(a);
   }
-  out.assign((size_t)G * S * S, make_float2(0.f, 0.f));
+  out.assign((size_t)G * S * S, 0u);
   std::vector<double> tr((size_t)K * S), ti((size_t)K * S);
   for (int g = 0; g < G; ++g) {
     const float* hp = psfs + (size_t)g * K * K;
@@ -445,7 +469,8 @@ void dft_spectra(const float* psfs, int G, int K, std::vector<float2>& out) {
           sr += ar * cr[j] - ai * ci[j];
           si += ar * ci[j] + ai * cr[j];
         }
-        out[((size_t)g * S + kr) * S + kc] = make_float2((float)(sr / S), (float)(si / S));
+        const __half2 hv = __floats2half2_rn((float)(sr / S), (float)(si / S));
+        std::memcpy(&out[((size_t)g * S + kr) * S + kc], &hv, 4);
       }
   }
 }
@@ -454,7 +479,7 @@ cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid) {
   if (a.n_work <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  dft_H_kernel<<<std::min(grid, a.n_work), NTH, SMEM_D, s>>>(a);
+  dft_H_kernel<<<std::min(grid, a.n_work), NTS, SMEM_D, s>>>(a);
   return cudaGetLastError();
 }
 
