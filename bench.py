@@ -620,7 +620,8 @@ def run_ours(args):
             if info.path == dv.DV_PATH_TENSOR else "f32", "data": "synthetic",
             "config": {"workload": describe(w),
                        "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
-                                      "direct %.3f ms, FFT %.3f ms, tensor %.3f ms), CUDA graph "
+                                      "direct %.3f ms, FFT %.3f ms, tensor %.3f ms, tensor with "
+                                      "block-DFT H %.3f ms; block-DFT H in use: %s), CUDA graph "
                                       "per local solve (%d tile groups on concurrent streams), "
                                       "learned warm start (%d pairs of %d^2, %d Adam "
                                       "steps), %d projected-gradient steps per outer iteration, "
@@ -630,7 +631,9 @@ def run_ours(args):
                                       "iterations, then where the decrease rate predicts the "
                                       "target"
                                       % (pname, args.precision, info.tune_ms_direct,
-                                         info.tune_ms_fft, info.tune_ms_tensor, info.tile_groups,
+                                         info.tune_ms_fft, info.tune_ms_tensor,
+                                         info.tune_ms_tensor_dft,
+                                         "yes" if info.tensor_h_dft else "no", info.tile_groups,
                                          train_info["pairs"], train_info["pair_size"],
                                          args.ws_steps, args.inner or w.n_inner,
                                          chosen["gamma"], chosen["rho"], args.check_every),
