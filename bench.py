@@ -675,6 +675,9 @@ def roofline(dv, w, plan, args, ktime, total_ms):
                dv.DV_PATH_TENSOR: ((f"tcT_H_kernel<{w.K}>", f"tcT_Ht_kernel<{w.K}>")
                                    if args.precision == "bf16" else
                                    (f"tc_H_kernel<1,{w.K}>", f"tc_Ht_kernel<1,{w.K}>"))}[path]
+    dft_h = path == dv.DV_PATH_TENSOR and bool(info.tensor_h_dft)
+    if dft_h:
+        kH = "dft_H_kernel"
     names = {0: f"{kH} (H_i with residual)", 1: f"{kHt} (H_i^T + fused prox step)",
              2: "consensus_kernel"}
     grouped = info.tile_groups > 1
@@ -686,6 +689,12 @@ def roofline(dv, w, plan, args, ktime, total_ms):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     px = y_px if dom == 0 else x_px
+    # block-DFT H: per 128 x 128 block and active PSF the two forward DFT GEMM
+    # stages (2 x 2 x 128^3 and 2 x 2 x 128 x 256 x 128 flop), per block the two
+    # inverse stages (the same two sizes): the dense transform is this form's
+    # algorithm, so its GEMMs count as its work
+    dft_stage = 2.0 * 128 * 128 * 128
+    dft_h_flops = ((info.block_psfs[0] + info.blocks[0]) * 6 * dft_stage) if dft_h else 0.0
     if path == dv.DV_PATH_TENSOR:
         # algorithmic: 2 K^2 flop per output pixel per active PSF, at most 4
         # active PSFs (first-order interpolation); the tensor pipe also runs
@@ -703,6 +712,13 @@ def roofline(dv, w, plan, args, ktime, total_ms):
                 executed = n_in * (mma_work(0) + mma_work(1))
                 work_note = (f"{n_in} x ({info.mma_ksteps[0]} + {info.mma_ksteps[1]}) (block, PSF) "
                              f"k-steps per tap row x K x 16 x 2 x 128 x block rows")
+                if dft_h:
+                    flops = n_in * (dft_h_flops + 8.0 * w.K * w.K * x_px)
+                    executed = n_in * (dft_h_flops + mma_work(1))
+                    work_note = (f"H as the block DFT: ({info.block_psfs[0]} (block, PSF) pairs + "
+                                 f"{info.blocks[0]} blocks) x 6 x 2 x 128^3 flop of DFT GEMMs; "
+                                 f"H^T banded: {info.mma_ksteps[1]} (block, PSF) k-steps per tap "
+                                 f"row x K x 16 x 2 x 128 x block rows")
         else:
             km, band = 8, 63 + w.K
             ks = (band + km - 1) // km
@@ -721,6 +737,13 @@ def roofline(dv, w, plan, args, ktime, total_ms):
             alg = (f"8 K^2 flop per y-pixel (H) and per x-pixel (H^T), 4 active PSFs, "
                    f"{n_in} x ({y_px} + {x_px}) pixels per local solve; executed MMA work "
                    f"{executed / 1e9:.1f} GFLOP per local solve ({work_note})")
+            if dft_h:
+                alg = (f"H: the block-DFT GEMMs as scheduled ({dft_h_flops / 1e9:.1f} GFLOP per "
+                       f"apply; 8 K^2 flop per y-pixel would be "
+                       f"{8.0 * w.K * w.K * y_px / 1e9:.1f}); H^T: 8 K^2 flop per x-pixel, 4 "
+                       f"active PSFs, {x_px} pixels; {n_in} x (H + H^T) per local solve; "
+                       f"executed MMA work {executed / 1e9:.1f} GFLOP per local solve "
+                       f"({work_note})")
     elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
         # per S x S complex 2-D transform and 8 flop per spectral product; H runs
