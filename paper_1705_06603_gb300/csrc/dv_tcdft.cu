@@ -55,7 +55,7 @@ constexpr int YROWS = 3 * S;                // [-Yi | Yr | Yi] or [Zr | Zi | -Zr
 constexpr int YPAN = YROWS * 16 + 16;
 constexpr int YBYTES = (S / 8) * YPAN;
 constexpr int kHdrD = 1024;
-constexpr int SMEM_D = kHdrD + CBYTES + XBYTES + YBYTES + 2 * S * 4;
+constexpr int SMEM_D = kHdrD + CBYTES + XBYTES + YBYTES + 2 * S * (int)sizeof(WTab) + 4 * S * 4;
 constexpr uint32_t TMEM_COLS = 512;         // D [0, 256), Z sum [256, 512)
 static_assert(SMEM_D <= 227 * 1024, "shared memory");
 static_assert(YBYTES >= 2 * XBYTES, "T operands fit in the Y buffer");
@@ -97,8 +97,9 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
   unsigned char* sC = smem + kHdrD;
   unsigned char* sX = sC + CBYTES;
   unsigned char* sY = sX + XBYTES;
-  float* sWr = reinterpret_cast<float*>(sY + YBYTES);
-  float* sWc = sWr + S;
+  WTab* sTr = reinterpret_cast<WTab*>(sY + YBYTES);   // interpolation weights of the
+  WTab* sTc = sTr + S;                                  // window's rows and columns
+  float* sWv = reinterpret_cast<float*>(sTc + S);       // [2][wr | wc] of a PSF
   __shared__ WorkItem wis[2];
   __shared__ TileDesc tds[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -155,23 +156,66 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
   // PSFs: item u of this thread = column c, rows 8q .. 8q + 7 (e = tid + 256 u);
   // loaded for the next block while the current block's inverse runs
   uint32_t xv[8][4];
-  auto load_x = [&](const WorkItem& w2, const TileDesc& t2) {
+  // every load of the window is issued before the first is used; threads
+  // 0 .. 2S - 1 also fetch the weight table of one window row or column
+  // (stored once the current block's last X_p has been staged)
+  auto load_x = [&](const WorkItem& w2, const TileDesc& t2, WTab& tab) {
     const float* img2 = A.in + t2.xoff;
+    const int C = w2.c0 + (tid & (S - 1));
+    float v[8][8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = tid + u * NTS;
-      const int c = e & (S - 1), q = e >> 7, C = w2.c0 + c;
-      float v[8];
+      const int q = (tid + u * NTS) >> 7;
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         const int R = w2.r0 + 8 * q + t;
-        v[t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img2 + (int64_t)R * t2.xpitch + C) : 0.f;
+        v[u][t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img2 + (int64_t)R * t2.xpitch + C) : 0.f;
       }
+    }
+    tab = WTab{-2, 0.f, 0.f, 0};
+    if (tid < S) {
+      const int R = w2.r0 + tid;
+      if (R < t2.nxr) tab = A.wrow[t2.wr0 + R];
+    } else {
+      const int Cc = w2.c0 + tid - S;
+      if (Cc < t2.nxc) tab = A.wcol[t2.wc0 + Cc];
+    }
 #pragma unroll
-      for (int t = 0; t < 4; ++t) xv[u][t] = pack_h2(v[2 * t], v[2 * t + 1]);
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) xv[u][t] = pack_h2(v[u][2 * t], v[u][2 * t + 1]);
+  };
+  static_assert(NTS == 2 * S, "one weight table entry per thread");
+  auto store_tab = [&](const WTab& tab) { (tid < S ? sTr : sTc - S)[tid] = tab; };
+  auto psfs_of = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
+  // the x window of the item in slot s and the observed image and weights of
+  // its output block, prefetched into L2 a block ahead (one 128-byte line
+  // per request, at an element inside the image)
+  auto prefetch_next = [&](int slot) {
+    if (H->item[slot] >= A.n_work) return;
+    const WorkItem& w2 = wis[slot];
+    const TileDesc& t2 = tds[slot];
+    if (psfs_of(w2) == 0) return;
+    const int rr = tid & (S - 1);
+    const int R = w2.r0 + rr, c_end = min(w2.c0 + S, t2.nxc);
+    if (R < t2.nxr) {
+      const float* row = A.in + t2.xoff + (int64_t)R * t2.xpitch;
+      for (int C = w2.c0 + 32 * (tid >> 7); C < c_end; C += 64) prefetch_l2(row + C);
+      if ((tid >> 7) == 0) prefetch_l2(row + c_end - 1);
+    }
+    if (A.mode != OP_PLAIN) {
+      const int bb = S - A.K + 1;
+      const int i = w2.r0 + rr, j_end = min(w2.c0 + bb, t2.nyc);
+      if (rr < bb && i < t2.nyr && w2.c0 < j_end) {
+        const int64_t g0 = (int64_t)(t2.xr0 + i) * A.wy + t2.xc0;
+        const float* src = (tid >> 7) == 0 ? A.y : A.W;
+        if (src) {
+          for (int j = w2.c0; j < j_end; j += 32) prefetch_l2(src + g0 + j);
+          prefetch_l2(src + g0 + j_end - 1);
+        }
+      }
     }
   };
-  auto psfs_of = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
   if (tid == 0) fetch(0);
   int cur = 0;
   bool have_x = false;
@@ -180,6 +224,9 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
     __syncthreads();
     tc_fence_after();
     if (H->item[cur] >= A.n_work || !ok || *(volatile int*)&H->abort) break;
+    // the next item (slot cur ^ 1 is free: the previous block has finished),
+    // published by the next barrier
+    if (tid == 0) fetch(cur ^ 1);
     const WorkItem& wi = wis[cur];
     const TileDesc& td = tds[cur];
     const int nb = wi.b_hi - wi.b_lo + 1;
@@ -201,28 +248,35 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
       have_x = false;
       continue;
     }
-    if (!have_x) load_x(wi, td);
+    if (!have_x) {
+      WTab tab;
+      load_x(wi, td, tab);
+      store_tab(tab);
+      __syncthreads();
+    }
 
     // X_p^T into sX: element (m = c, k = r) = w_p(r0 + r, c0 + c) x(r0 + r, c0 + c)
+    // (rows and columns outside the tile have the table {-2, 0, 0}); the
+    // PSF's row and column weights go to buffer p & 1 of sWv, which stage
+    // p - 2 last read, before the barriers of pair p - 2's stages
     auto stage_x = [&](int p) {
       const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      __syncthreads();   // the previous PSF's weights are no longer read
-      for (int e = tid; e < S; e += NTS) {
-        const int R = wi.r0 + e, C = wi.c0 + e;
-        sWr[e] = R < td.nxr ? wsel(A.wrow[td.wr0 + R], ga) : 0.f;
-        sWc[e] = C < td.nxc ? wsel(A.wcol[td.wc0 + C], gb) : 0.f;
-      }
+      float* wv = sWv + (p & 1) * 2 * S;
+      wv[tid] = tid < S ? wsel(sTr[tid], ga) : wsel(sTc[tid - S], gb);
       __syncthreads();
+      const int c = tid & (S - 1);
+      const float wc = wv[S + c];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int e = tid + u * NTS;
-        const int c = e & (S - 1), q = e >> 7;
-        const float wc = sWc[c];
+        const int q = (tid + u * NTS) >> 7;
+        const float4 w0 = *reinterpret_cast<const float4*>(wv + 8 * q);
+        const float4 w1 = *reinterpret_cast<const float4*>(wv + 8 * q + 4);
+        const float wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
         uint32_t o[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           const float2 fx = __half22float2(*reinterpret_cast<const __half2*>(&xv[u][t]));
-          o[t] = pack_h2(sWr[8 * q + 2 * t] * wc * fx.x, sWr[8 * q + 2 * t + 1] * wc * fx.y);
+          o[t] = pack_h2(wr[2 * t] * wc * fx.x, wr[2 * t + 1] * wc * fx.y);
         }
         *reinterpret_cast<uint4*>(sX + q * XPAN + 16 * c) = make_uint4(o[0], o[1], o[2], o[3]);
       }
@@ -235,29 +289,30 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
       chain(tbase + S, aC + 16 * S, CPAN, aX, XPAN, id128, false);       // Yi = Fi X
       tc_commit(&H->bd);
     }
+    prefetch_next(cur ^ 1);
     for (int p = 0; p < np; ++p) {
-      // Y (lane kr): columns 0..127 = Yr[kr][c], 128..255 = Yi[kr][c]; half h
-      // of the warps takes Yr (row S + kr of the buffer [-Yi | Yr | Yi]) or Yi
-      // (rows kr and 2S + kr), 8 consecutive c per 16-byte store
+      // Y (lane kr): columns 0..127 = Yr[kr][c], 128..255 = Yi[kr][c] into
+      // rows S + kr (Yr), kr (-Yi) and 2S + kr (Yi) of the buffer [-Yi | Yr | Yi];
+      // half h of the warps takes c in [64h, 64h + 64), 8 consecutive c per
+      // 16-byte store
       if (!wait_d()) break;
-      for (int c0 = 0; c0 < S; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + c0), r);
+      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
+        uint32_t yr[16], yi[16];
+        tmem_ld16_nowait(tbase + lanes + (uint32_t)c0, yr);
+        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S + c0), yi);
         tmem_wait_ld();
 #pragma unroll
         for (int t = 0; t < 16; t += 8) {
-          const float* f = reinterpret_cast<const float*>(r + t);
+          const float* f = reinterpret_cast<const float*>(yr + t);
+          const float* g = reinterpret_cast<const float*>(yi + t);
           const int off = ((c0 + t) >> 3) * YPAN + 16 * L;
-          if (h == 0) {
-            *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
-                pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
-          } else {
-            *reinterpret_cast<uint4*>(sY + off) = make_uint4(
-                pack_h2(-f[0], -f[1]), pack_h2(-f[2], -f[3]), pack_h2(-f[4], -f[5]),
-                pack_h2(-f[6], -f[7]));
-            *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
-                pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
-          }
+          *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
+              pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
+          *reinterpret_cast<uint4*>(sY + off) = make_uint4(
+              pack_h2(-g[0], -g[1]), pack_h2(-g[2], -g[3]), pack_h2(-g[4], -g[5]),
+              pack_h2(-g[6], -g[7]));
+          *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
+              pack_h2(g[0], g[1]), pack_h2(g[2], g[3]), pack_h2(g[4], g[5]), pack_h2(g[6], g[7]));
         }
       }
       publish();
@@ -312,7 +367,6 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
       }
     }
     if (!ok) break;
-    if (tid == 0) fetch(cur ^ 1);   // published with the inverse's first operand
     // inverse, stage 1 operand: the sum (lane kc, columns kr) -> rows kc,
     // S + kc, 2S + kc of [Zr | Zi | -Zr], 8 consecutive kr per 16-byte store
     for (int k0 = 64 * h; k0 < 64 * h + 64; k0 += 16) {
@@ -342,7 +396,11 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
     }
     // the next block's x window, in flight while this block's inverse runs
     have_x = H->item[cur ^ 1] < A.n_work && psfs_of(wis[cur ^ 1]) > 0;
-    if (have_x) load_x(wis[cur ^ 1], tds[cur ^ 1]);
+    if (have_x) {
+      WTab tab;
+      load_x(wis[cur ^ 1], tds[cur ^ 1], tab);
+      store_tab(tab);   // this block's tables were last read by its last X_p
+    }
     // U (lane r): columns kc (re), S + kc (im), scaled by 1 / 128, into the
     // last stage's operands Ur (sX) and Ui (sY), rows r, k = kc
     if (!wait_d()) break;
@@ -382,17 +440,29 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
       }
       __syncthreads();
       const int nr = min(b, td.nyr - wi.r0), nc = min(b, td.nyc - wi.c0);
-      for (int e = tid; e < nr * b; e += NTS) {
-        const int il = e / b, jl = e - il * b;
-        if (jl >= nc) continue;
-        const int i = wi.r0 + il, jj = wi.c0 + jl;
-        const float y = tile[(il + K - 1) * TPT + jl + K - 1];
-        if (A.mode == OP_PLAIN) {
-          out[td.yoff + (int64_t)i * td.ypitch + jj] = y;
-        } else {
-          const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
-          const float wt = A.W ? A.W[gi] : 1.f;
-          out[td.yoff + (int64_t)i * td.ypitch + jj] = wt * (y - A.y[gi]);
+      // batches of EPB elements a thread: the observed image and weights of
+      // a batch are loaded before any of its outputs is written
+      constexpr int EPB = 18;
+      for (int e0 = tid; e0 < nr * b; e0 += EPB * NTS) {
+        float yo[EPB], wo[EPB];
+#pragma unroll
+        for (int u = 0; u < EPB; ++u) {
+          const int e = e0 + u * NTS, il = e / b, jl = e - il * b;
+          yo[u] = 0.f;
+          wo[u] = 1.f;
+          if (A.mode != OP_PLAIN && e < nr * b && jl < nc) {
+            const int64_t gi = (int64_t)(td.xr0 + wi.r0 + il) * A.wy + (td.xc0 + wi.c0 + jl);
+            yo[u] = __ldg(A.y + gi);
+            if (A.W) wo[u] = __ldg(A.W + gi);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < EPB; ++u) {
+          const int e = e0 + u * NTS, il = e / b, jl = e - il * b;
+          if (e >= nr * b || jl >= nc) continue;
+          const float y = tile[(il + K - 1) * TPT + jl + K - 1];
+          out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
+              A.mode == OP_PLAIN ? y : wo[u] * (y - yo[u]);
         }
       }
     }

@@ -272,5 +272,10 @@ __device__ __forceinline__ void huber_p(const float* sW, int SPW, int li, int lj
   pc = k * dc;
 }
 
+// hint: bring the 128-byte line holding *p (a global address) into L2
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 }  // namespace tcg
 }  // namespace dv
