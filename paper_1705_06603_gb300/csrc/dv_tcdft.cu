@@ -1,35 +1,46 @@
 // Block-DFT form of the shift-variant operator H of Sec. II-B on the tensor
 // cores (tcgen05, FP16 operands, FP32 accumulation in tensor memory).
 //
-// Overlap-save on 128 x 128 blocks, as the FP32 block-FFT path: a CTA owns a
-// b x b block of H's output (b = 129 - K) and reads the 128 x 128 x window
-// below it.  For every PSF p active on the block, X_p = w_p . x (zero outside
-// the tile) is transformed by two dense DFT stages, Z_p = F X_p F with
-// F[k][n] = exp(-2 pi i k n / 128), multiplied by the PSF's spectrum, and the
-// products are summed; one inverse transform of the sum, cropped to rows and
-// columns K - 1 .. 127, is the block of H x (the non-circulant local blur of
-// Sec. II-B: circular convolution of size 128, then the valid part).
+// Overlap-save on 128 x 128 blocks: a work item is a b x b block of H's output
+// (b = 129 - K) and the 128 x 128 window of x below it.  For every PSF
+// p = (a, b) active on the block (Eq. (2): first-order interpolation, weights
+// w_p(r, c) = wr_a(r) wc_b(c)), X_p = w_p . x is transformed, multiplied by
+// the PSF's spectrum, and the products are summed; one inverse transform of the
+// sum, cropped to rows and columns K - 1 .. 127, is the block of H x (the
+// valid part of a circular convolution of size 128 is the non-circulant
+// local blur).
 //
-// Each DFT stage is a GEMM on the tensor cores with the constant matrices
-// [Fr; Fi] (cos and -sin, FP16) in shared memory, ordered so that every
-// tensor-memory lane (a thread) owns one row of the next stage's operand:
-//   stage 1  Y[kr][c]    = sum_r F[kr][r] X[r][c]            (M = kr, N = c; Fr and Fi)
-//   stage 2  Z^T[kc][kr] = sum_c F[kc][c] Y[kr][c]            (M = kc, N = re|im kr)
-//            as Fr [Yr | Yi] + Fi [-Yi | Yr] over one buffer [-Yi | Yr | Yi]
-//   inverse  U[r][kc]    = sum_kr conj F[r][kr] Z[kr][kc]     (Fr [Zr | Zi] + Fi [Zi | -Zr])
-//            x[r][c]     = Re sum_kc U[r][kc] conj F[c][kc]   (Ur Fr + Ui Fi)
+// The input is real, so only half of every spectrum is formed (k = 0 .. 64
+// along the first transformed axis; the other half is its conjugate mirror).
+// With F[k][n] = exp(-2 pi i k n / 128) = Fr + i Fi, each stage is a GEMM on
+// the tensor cores, ordered so that every tensor-memory lane (a thread) owns a
+// row of the next stage's operand:
+//   F1 (per row weight a)  Y'[j][c] = sum_r A1[j][r] wr_a(r) x[r][c]
+//        A1 rows 2k = Fr(k), 2k + 1 = Fi(k) (k < 64), row 1 = Fr(64): the
+//        packed real and imaginary parts of Y(k) = F x along r (Y(0), Y(64)
+//        are real, Y(128 - k) = conj Y(k))
+//   F2 (per PSF)  P = Fr (wc_b Y')^T, Q = Fi (wc_b Y')^T     (M = kc, N = j)
+//        Z(k)[kc] = P[2k] - Q[2k+1] + i (Q[2k] + P[2k+1])   (k = 0, 64 apart)
+//   product  S(k)[kc] += Z(k)[kc] Hh_p(k, kc)               (FP32, tensor memory)
+//   I1  U[r][kc] = sum_k alpha_k exp(+2 pi i r k / 128) S(k)[kc]   (alpha = 1 at
+//        k = 0, 64, else 2: the mirror half folded in), as one N = 256 GEMM
+//        [Ur | Ui] = Fr [aSr | aSi] + Fi [aSi | -aSr] over k = 0 .. 79
+//   I2  x[r][c] = Re sum_kc exp(+2 pi i c kc / 128) U[r][kc] / 128 = Ur Fr + Ui Fi
 // Operands are K-major, no swizzle: a matrix of R rows and K columns is stored
-// as K / 8 panels of R 16-byte rows (a panel stride padded by 16 bytes), so a
+// as K / 8 panels of R 16-byte rows (panel stride padded by 16 bytes), so a
 // 16-wide k-step is two consecutive panels (LBO = panel stride, SBO = 128).
-// Between stages the staging warps read the accumulators (each warp owns 32
-// tensor-memory lanes and half of the columns), round to FP16 and write the
-// next operand; the spectral products accumulate in FP32 in tensor memory.
 // Scaling keeps the FP16 values in range: the spectra carry 1 / 128 and the
-// first inverse stage's result another 1 / 128 (the inverse DFT's 1 / 128^2).
+// staged U another 1 / 128 (the inverse DFT's 1 / 128^2).
 //
-// Eight warps stage operands, take the products and run the epilogue; thread
-// 0 issues the MMAs.  The grid is persistent (one CTA per SM, items from an
-// atomic counter, heaviest first).  Every wait is bounded.
+// Roles: 8 staging warps (two per tensor-memory lane quarter, one per half of
+// a stage's columns) stage operands, take the products and write the output;
+// warp 8 issues the MMAs; warp 9 claims work items, loads the x window (FP32
+// -> FP16, transposed) and the interpolation tables, and prefetches the next
+// item's data into L2.  A stage's operand is written in 16-wide K chunks, each
+// with its own mbarrier, and the MMA warp issues a chunk's k-steps as soon as
+// it is complete, so the MMAs trail the staging.  The grid is persistent (one
+// CTA per SM, items from an atomic counter, heaviest first).  Every wait is
+// bounded; the staging warps take every branch after a wait together.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -44,410 +55,283 @@ namespace {
 using namespace tcg;
 
 constexpr int S = 128;                      // transform size
-constexpr int NWS = 8;                      // warps (two per tensor-memory lane quarter)
-constexpr int NTS = 32 * NWS;
-constexpr int CROWS = 2 * S;                // [Fr; Fi]
-constexpr int CPAN = CROWS * 16 + 16;       // panel stride (bytes) of the constants
+constexpr int NWK = 8;                      // staging warps
+constexpr int NTW = 32 * NWK;
+constexpr int WMMA = NWK, WLOAD = NWK + 1;  // MMA warp, loader warp
+constexpr int NT = 32 * (NWK + 2);
+constexpr int CPAN = 2 * S * 16 + 16;       // [Fr; Fi] (256 rows) panel stride
 constexpr int CBYTES = (S / 8) * CPAN;
-constexpr int XPAN = S * 16 + 16;           // 128-row operand
+constexpr int XPAN = S * 16 + 16;           // 128-row operand panel stride
 constexpr int XBYTES = (S / 8) * XPAN;
-constexpr int YROWS = 3 * S;                // [-Yi | Yr | Yi] or [Zr | Zi | -Zr]
-constexpr int YPAN = YROWS * 16 + 16;
-constexpr int YBYTES = (S / 8) * YPAN;
+constexpr int IPAN = 3 * S * 16 + 16;       // I1 operand [aSr; aSi; -aSr] (384 rows)
+constexpr int IPANELS = 10;                 // k = 0 .. 79 (zero beyond 64)
 constexpr int kHdrD = 1024;
-constexpr int SMEM_D = kHdrD + CBYTES + XBYTES + YBYTES + 2 * S * (int)sizeof(WTab) + 4 * S * 4;
-constexpr uint32_t TMEM_COLS = 512;         // D [0, 256), Z sum [256, 512)
+constexpr int OFF_C = kHdrD;                // [Fr; Fi]
+constexpr int OFF_A1 = OFF_C + CBYTES;      // A1
+constexpr int OFF_WIN = OFF_A1 + XBYTES;    // the window, x^T (rows c, K = r)
+constexpr int OFF_X = OFF_WIN + XBYTES;     // (wr_a x)^T;  I1 operand, Ur, output tile
+constexpr int OFF_Y = OFF_X + XBYTES;       // wc_b Y';     (I1 operand), Ui, (output tile)
+constexpr int OFF_TAB = OFF_Y + XBYTES;     // [2 slots][rows | cols] interpolation tables
+constexpr int OFF_WV = OFF_TAB + 2 * 2 * S * (int)sizeof(WTab);   // [2][wr] [2][wc]
+constexpr int SMEM_D = OFF_WV + 4 * S * 4;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t TM_F1 = 0, TM_P = 128, TM_Q = 256, TM_SUM = 384;   // D columns
+constexpr uint32_t TM_I1 = 128, TM_I2 = 384;
 static_assert(SMEM_D <= 227 * 1024, "shared memory");
-static_assert(YBYTES >= 2 * XBYTES, "T operands fit in the Y buffer");
-static_assert(YBYTES >= S * (S + 1) * 4, "output tile fits in the Y buffer");
-static_assert(CPAN % 16 == 0 && XPAN % 16 == 0 && YPAN % 16 == 0, "alignment");
+static_assert(IPANELS * IPAN <= 2 * XBYTES, "I1 operand fits in the X and Y buffers");
+static_assert(S * (S + 1) * 4 <= 2 * XBYTES, "output tile fits in the X and Y buffers");
+static_assert(OFF_Y == OFF_X + XBYTES, "X and Y buffers are contiguous");
+static_assert(CPAN % 16 == 0 && XPAN % 16 == 0 && IPAN % 16 == 0 && OFF_WV % 16 == 0, "alignment");
 
 struct BarsD {
-  uint64_t bd, fin;
+  uint64_t win_full, win_empty;           // loader <-> staging warps
+  uint64_t f1_done, f2_done, i1_done, i2_done, fin;   // MMA completions
+  uint64_t p_done;                        // product read P, Q (staging -> MMA)
+  uint64_t xch[8], ych[8], sch[5], uch[8];  // operand chunks (staging -> MMA)
   uint32_t tmem;
   int abort;
-  int item[2];                // work items of the two slots (current, next)
+  int mbox[2];                            // na, nb of the next block for the MMA warp (na < 0: stop)
+  int item[2];                            // work item of a slot (-1: stop)
 };
-static_assert(sizeof(BarsD) <= 256, "barrier header");
+static_assert(sizeof(BarsD) <= kHdrD, "barrier header");
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
   const __half2 h = __floats2half2_rn(a, b);
   return *reinterpret_cast<const uint32_t*>(&h);
 }
-
-// One GEMM chain of 8 k-steps (K = 128): D (+)= A B^T, A rows from a0, B rows
-// from b0 (shared-memory addresses of row 0 of panel 0).
-__device__ __forceinline__ void chain(uint32_t d, uint32_t a0, uint32_t apan, uint32_t b0,
-                                      uint32_t bpan, uint32_t id, bool acc) {
-  const uint64_t ad = sdesc(a0, apan), bd = sdesc(b0, bpan);
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    mma_bf16(d, ad + (uint64_t)(j * 2 * (apan >> 4)), bd + (uint64_t)(j * 2 * (bpan >> 4)), id,
-             (acc || j > 0) ? 1u : 0u);
+__device__ __forceinline__ float2 unpack_h2(uint32_t v) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+// k-step i (16 wide) of a chain: D (+)= A B^T, A rows from a0, B rows from b0
+__device__ __forceinline__ void kstep(uint32_t d, uint32_t a0, uint32_t apan, uint32_t b0,
+                                      uint32_t bpan, uint32_t id, int i, bool acc) {
+  mma_bf16(d, sdesc(a0 + 2 * i * apan, apan), sdesc(b0 + 2 * i * bpan, bpan), id, acc ? 1u : 0u);
 }
 
-// All 8 warps stage operands, take the products and run the epilogue; thread
-// 0 also issues each stage's MMAs once every warp has written the operand
-// (a CTA barrier, then the MMAs run asynchronously and complete on bd).  8
-// warps, two per SM sub-partition, may hold up to 255 registers a thread: the
-// block's x window and a PSF's spectrum slice stay in registers.
-__global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
+__global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
   BarsD* H = reinterpret_cast<BarsD*>(smem);
-  unsigned char* sC = smem + kHdrD;
-  unsigned char* sX = sC + CBYTES;
-  unsigned char* sY = sX + XBYTES;
-  WTab* sTr = reinterpret_cast<WTab*>(sY + YBYTES);   // interpolation weights of the
-  WTab* sTc = sTr + S;                                  // window's rows and columns
-  float* sWv = reinterpret_cast<float*>(sTc + S);       // [2][wr | wc] of a PSF
+  unsigned char* sC = smem + OFF_C;
+  unsigned char* sWin = smem + OFF_WIN;
+  unsigned char* sX = smem + OFF_X;
+  unsigned char* sY = smem + OFF_Y;
+  WTab* sTab = reinterpret_cast<WTab*>(smem + OFF_TAB);
+  float* sWr = reinterpret_cast<float*>(smem + OFF_WV);   // [2][S]
+  float* sWc = sWr + 2 * S;                               // [2][S]
   __shared__ WorkItem wis[2];
   __shared__ TileDesc tds[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int K = A.K, b = S - K + 1;
   const uint64_t limit = A.wait_ns ? A.wait_ns : kWaitNs;
-  // thread 0: the next work item into slot s
-  auto fetch = [&](int slot) {
-    const int it = atomicAdd(A.counter, 1);
-    H->item[slot] = it;
-    if (it < A.n_work) {
-      wis[slot] = A.work[it];
-      tds[slot] = A.tiles[wis[slot].tile];
-    }
-  };
   if (tid == 0) {
-    mbar_init(&H->bd, 1);
+    mbar_init(&H->win_full, 1);
+    mbar_init(&H->win_empty, NWK);
+    mbar_init(&H->f1_done, 1);
+    mbar_init(&H->f2_done, 1);
+    mbar_init(&H->i1_done, 1);
+    mbar_init(&H->i2_done, 1);
     mbar_init(&H->fin, 1);
+    mbar_init(&H->p_done, NWK);
+    for (int i = 0; i < 8; ++i) {
+      mbar_init(&H->xch[i], NWK);
+      mbar_init(&H->ych[i], NWK);
+      mbar_init(&H->uch[i], NWK);
+    }
+    for (int i = 0; i < 5; ++i) mbar_init(&H->sch[i], NWK);
     H->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(&H->tmem, TMEM_COLS);
-  // constants [Fr; Fi] (the plan's byte image of the panels)
-  for (int e = tid; e < CBYTES / 16; e += NTS)
+  if (warp == WMMA) tmem_alloc(&H->tmem, TMEM_COLS);
+  // constants [Fr; Fi] and A1 (the plan's byte image of the panels)
+  for (int e = tid; e < (CBYTES + XBYTES) / 16; e += NT)
     reinterpret_cast<uint4*>(sC)[e] = __ldg(reinterpret_cast<const uint4*>(A.tcop) + e);
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = H->tmem;
-  const uint32_t aC = saddr(sC), aX = saddr(sX), aY = saddr(sY);
-  const uint32_t id256 = idesc(0, 128, 256), id128 = idesc(0, 128, 128);
-  uint32_t nd = 0;                          // completions of bd waited for so far
-  const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
-  const int h = warp >> 2;                  // column half of the warp
-  const int L = 32 * (warp & 3) + lane;     // its tensor-memory lane
   bool ok = true;
 
-  // operands written by every thread -> visible to the MMAs, thread 0 issues
-  auto publish = [&]() {
-    fence_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-  };
-  auto wait_d = [&]() {
-    const bool w = wait_bar(&H->bd, nd++ & 1, &H->abort, A.err, limit);
-    __syncthreads();
-    ok = ok && w && !*(volatile int*)&H->abort;
-    tc_fence_after();
-    return ok;
-  };
-
-  // the 128 x 128 x window of a block, kept in registers (FP16) for all its
-  // PSFs: item u of this thread = column c, rows 8q .. 8q + 7 (e = tid + 256 u);
-  // loaded for the next block while the current block's inverse runs
-  uint32_t xv[8][4];
-  // every load of the window is issued before the first is used; threads
-  // 0 .. 2S - 1 also fetch the weight table of one window row or column
-  // (stored once the current block's last X_p has been staged)
-  auto load_x = [&](const WorkItem& w2, const TileDesc& t2, WTab& tab) {
-    const float* img2 = A.in + t2.xoff;
-    const int C = w2.c0 + (tid & (S - 1));
-    float v[8][8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int q = (tid + u * NTS) >> 7;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int R = w2.r0 + 8 * q + t;
-        v[u][t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img2 + (int64_t)R * t2.xpitch + C) : 0.f;
+  if (warp == WLOAD) {
+    // ---------------------------------------------------------------- loader
+    auto psfs = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
+    int it = 0;
+    if (lane == 0) it = atomicAdd(A.counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    for (uint32_t n = 0; !A.test_withhold; ++n) {
+      const int slot = n & 1;
+      if (n > 0 && !wait_bar(&H->win_empty, (n - 1) & 1, &H->abort, A.err, limit)) {
+        ok = false;
+        break;
       }
-    }
-    tab = WTab{-2, 0.f, 0.f, 0};
-    if (tid < S) {
-      const int R = w2.r0 + tid;
-      if (R < t2.nxr) tab = A.wrow[t2.wr0 + R];
-    } else {
-      const int Cc = w2.c0 + tid - S;
-      if (Cc < t2.nxc) tab = A.wcol[t2.wc0 + Cc];
-    }
+      if (it >= A.n_work) {
+        if (lane == 0) H->item[slot] = -1;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&H->win_full);
+        break;
+      }
+      const WorkItem w2 = A.work[it];
+      const TileDesc t2 = A.tiles[w2.tile];
+      int it2 = 0;
+      if (lane == 0) {
+        it2 = atomicAdd(A.counter, 1);
+        wis[slot] = w2;
+        tds[slot] = t2;
+        H->item[slot] = it;
+      }
+      if (psfs(w2) > 0) {
+        // interpolation tables of the window's rows and columns ({-2, 0, 0}
+        // outside the tile: no grid index has a weight there)
+        WTab* tab = sTab + slot * 2 * S;
+        for (int e = lane; e < 2 * S; e += 32) {
+          WTab v{-2, 0.f, 0.f, 0};
+          if (e < S) {
+            if (w2.r0 + e < t2.nxr) v = A.wrow[t2.wr0 + w2.r0 + e];
+          } else if (w2.c0 + e - S < t2.nxc) {
+            v = A.wcol[t2.wc0 + w2.c0 + e - S];
+          }
+          tab[e] = v;
+        }
+        // the window as x^T in FP16: row c, 8 consecutive r per 16 bytes; 64
+        // loads in flight a lane
+        const float* img = A.in + t2.xoff;
+        for (int m = 0; m < 4; ++m) {
+          const int c = 32 * m + lane, C = w2.c0 + c;
+          for (int q0 = 0; q0 < S / 8; q0 += 8) {
+            float v[8][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+            for (int qq = 0; qq < 8; ++qq)
 #pragma unroll
-      for (int t = 0; t < 4; ++t) xv[u][t] = pack_h2(v[u][2 * t], v[u][2 * t + 1]);
-  };
-  static_assert(NTS == 2 * S, "one weight table entry per thread");
-  auto store_tab = [&](const WTab& tab) { (tid < S ? sTr : sTc - S)[tid] = tab; };
-  auto psfs_of = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
-  // the x window of the item in slot s and the observed image and weights of
-  // its output block, prefetched into L2 a block ahead (one 128-byte line
-  // per request, at an element inside the image)
-  auto prefetch_next = [&](int slot) {
-    if (H->item[slot] >= A.n_work) return;
-    const WorkItem& w2 = wis[slot];
-    const TileDesc& t2 = tds[slot];
-    if (psfs_of(w2) == 0) return;
-    const int rr = tid & (S - 1);
-    const int R = w2.r0 + rr, c_end = min(w2.c0 + S, t2.nxc);
-    if (R < t2.nxr) {
-      const float* row = A.in + t2.xoff + (int64_t)R * t2.xpitch;
-      for (int C = w2.c0 + 32 * (tid >> 7); C < c_end; C += 64) prefetch_l2(row + C);
-      if ((tid >> 7) == 0) prefetch_l2(row + c_end - 1);
-    }
-    if (A.mode != OP_PLAIN) {
-      const int bb = S - A.K + 1;
-      const int i = w2.r0 + rr, j_end = min(w2.c0 + bb, t2.nyc);
-      if (rr < bb && i < t2.nyr && w2.c0 < j_end) {
-        const int64_t g0 = (int64_t)(t2.xr0 + i) * A.wy + t2.xc0;
-        const float* src = (tid >> 7) == 0 ? A.y : A.W;
-        if (src) {
-          for (int j = w2.c0; j < j_end; j += 32) prefetch_l2(src + g0 + j);
-          prefetch_l2(src + g0 + j_end - 1);
+              for (int t = 0; t < 8; ++t) {
+                const int R = w2.r0 + 8 * (q0 + qq) + t;
+                v[qq][t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img + (int64_t)R * t2.xpitch + C) : 0.f;
+              }
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq)
+              *reinterpret_cast<uint4*>(sWin + (q0 + qq) * XPAN + 16 * c) =
+                  make_uint4(pack_h2(v[qq][0], v[qq][1]), pack_h2(v[qq][2], v[qq][3]),
+                             pack_h2(v[qq][4], v[qq][5]), pack_h2(v[qq][6], v[qq][7]));
+          }
         }
       }
-    }
-  };
-  if (tid == 0) fetch(0);
-  int cur = 0;
-  bool have_x = false;
-  for (;;) {
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (H->item[cur] >= A.n_work || !ok || *(volatile int*)&H->abort) break;
-    // the next item (slot cur ^ 1 is free: the previous block has finished),
-    // published by the next barrier
-    if (tid == 0) fetch(cur ^ 1);
-    const WorkItem& wi = wis[cur];
-    const TileDesc& td = tds[cur];
-    const int nb = wi.b_hi - wi.b_lo + 1;
-    const int np = psfs_of(wi);
-    float* out = A.out;
-
-    if (np == 0) {
-      // no PSF reaches the block: H x is zero there
-      for (int e = tid; e < b * b; e += NTS) {
-        const int i = wi.r0 + e / b, jj = wi.c0 + e % b;
-        if (i >= td.nyr || jj >= td.nyc) continue;
-        const int64_t gi = (int64_t)(td.xr0 + i) * A.wy + (td.xc0 + jj);
-        const float wt = (A.mode != OP_PLAIN && A.W) ? A.W[gi] : 1.f;
-        out[td.yoff + (int64_t)i * td.ypitch + jj] = A.mode == OP_PLAIN ? 0.f : -wt * A.y[gi];
-      }
-      __syncthreads();
-      if (tid == 0) fetch(cur ^ 1);
-      cur ^= 1;
-      have_x = false;
-      continue;
-    }
-    if (!have_x) {
-      WTab tab;
-      load_x(wi, td, tab);
-      store_tab(tab);
-      __syncthreads();
-    }
-
-    // X_p^T into sX: element (m = c, k = r) = w_p(r0 + r, c0 + c) x(r0 + r, c0 + c)
-    // (rows and columns outside the tile have the table {-2, 0, 0}); the
-    // PSF's row and column weights go to buffer p & 1 of sWv, which stage
-    // p - 2 last read, before the barriers of pair p - 2's stages
-    auto stage_x = [&](int p) {
-      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      float* wv = sWv + (p & 1) * 2 * S;
-      wv[tid] = tid < S ? wsel(sTr[tid], ga) : wsel(sTc[tid - S], gb);
-      __syncthreads();
-      const int c = tid & (S - 1);
-      const float wc = wv[S + c];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = (tid + u * NTS) >> 7;
-        const float4 w0 = *reinterpret_cast<const float4*>(wv + 8 * q);
-        const float4 w1 = *reinterpret_cast<const float4*>(wv + 8 * q + 4);
-        const float wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-        uint32_t o[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float2 fx = __half22float2(*reinterpret_cast<const __half2*>(&xv[u][t]));
-          o[t] = pack_h2(wr[2 * t] * wc * fx.x, wr[2 * t + 1] * wc * fx.y);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&H->win_full);
+      // the next item's window and residual rows into L2 while this block runs
+      it2 = __shfl_sync(0xffffffffu, it2, 0);
+      if (it2 < A.n_work) {
+        const WorkItem w3 = A.work[it2];
+        const TileDesc t3 = A.tiles[w3.tile];
+        if (psfs(w3) > 0) {
+          const int c_end = min(w3.c0 + S, t3.nxc);
+          for (int rr = lane; rr < S; rr += 32) {
+            const int R = w3.r0 + rr;
+            if (R >= t3.nxr || w3.c0 >= c_end) continue;
+            const float* row = A.in + t3.xoff + (int64_t)R * t3.xpitch;
+            for (int C = w3.c0; C < c_end; C += 32) prefetch_l2(row + C);
+            prefetch_l2(row + c_end - 1);
+          }
+          if (A.mode != OP_PLAIN) {
+            const int j_end = min(w3.c0 + b, t3.nyc);
+            for (int rr = lane; rr < b; rr += 32) {
+              const int i = w3.r0 + rr;
+              if (i >= t3.nyr || w3.c0 >= j_end) continue;
+              const int64_t g0 = (int64_t)(t3.xr0 + i) * A.wy + t3.xc0;
+              for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.y + g0 + j);
+              prefetch_l2(A.y + g0 + j_end - 1);
+              if (A.W) {
+                for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.W + g0 + j);
+                prefetch_l2(A.W + g0 + j_end - 1);
+              }
+            }
+          }
         }
-        *reinterpret_cast<uint4*>(sX + q * XPAN + 16 * c) = make_uint4(o[0], o[1], o[2], o[3]);
       }
+      it = it2;
+    }
+  } else if (warp == WMMA) {
+    // ------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t aC = saddr(sC), aA1 = saddr(smem + OFF_A1), aX = saddr(sX), aY = saddr(sY);
+      const uint32_t id256 = idesc(0, 128, 256), id128 = idesc(0, 128, 128);
+      uint32_t ph_x = 0, ph_y = 0, ph_p = 0, ph_b = 0;
+      auto wt = [&](uint64_t* bar, uint32_t ph) {
+        if (!wait_bar(bar, ph & 1, &H->abort, A.err, limit)) return false;
+        tc_fence_after();
+        return true;
+      };
+      while (ok) {
+        if (!(ok = wt(&H->xch[0], ph_x))) break;
+        const int na = H->mbox[0], nb = H->mbox[1];
+        if (na < 0) break;
+        for (int ai = 0; ai < na && ok; ++ai) {
+          // F1: Y' = A1 (wr_a x)
+          for (int i = 0; i < 8 && ok; ++i) {
+            if ((ai > 0 || i > 0) && !(ok = wt(&H->xch[i], ph_x))) break;
+            kstep(tbase + TM_F1, aA1, XPAN, aX, XPAN, id128, i, i > 0);
+          }
+          ++ph_x;
+          if (!ok) break;
+          tc_commit(&H->f1_done);
+          for (int bi = 0; bi < nb && ok; ++bi) {
+            // F2 once the previous product has read P and Q
+            if ((ai > 0 || bi > 0) && !(ok = wt(&H->p_done, ph_p++))) break;
+            for (int i = 0; i < 8 && ok; ++i) {
+              if (!(ok = wt(&H->ych[i], ph_y))) break;
+              kstep(tbase + TM_P, aC, CPAN, aY, XPAN, id128, i, i > 0);
+              kstep(tbase + TM_Q, aC + 16 * S, CPAN, aY, XPAN, id128, i, i > 0);
+            }
+            ++ph_y;
+            if (ok) tc_commit(&H->f2_done);
+          }
+        }
+        if (!ok || !(ok = wt(&H->p_done, ph_p++))) break;
+        // I1: [Ur | Ui] = Fr [aSr | aSi] + Fi [aSi | -aSr]
+        for (int i = 0; i < 5 && ok; ++i) {
+          if (!(ok = wt(&H->sch[i], ph_b))) break;
+          kstep(tbase + TM_I1, aC, CPAN, aX, IPAN, id256, i, i > 0);
+          kstep(tbase + TM_I1, aC + 16 * S, CPAN, aX + 16 * S, IPAN, id256, i, true);
+        }
+        if (!ok) break;
+        tc_commit(&H->i1_done);
+        // I2: x = Ur Fr + Ui Fi
+        for (int i = 0; i < 8 && ok; ++i) {
+          if (!(ok = wt(&H->uch[i], ph_b))) break;
+          kstep(tbase + TM_I2, aX, XPAN, aC, CPAN, id128, i, i > 0);
+          kstep(tbase + TM_I2, aY, XPAN, aC + 16 * S, CPAN, id128, i, true);
+        }
+        if (!ok) break;
+        tc_commit(&H->i2_done);
+        ++ph_b;
+      }
+    }
+  } else {
+    // --------------------------------------------------------- staging warps
+    const int q4 = warp & 3, h = warp >> 2;
+    const int L = 32 * q4 + lane;            // tensor-memory lane of this thread
+    const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+    const unsigned int* spec = reinterpret_cast<const unsigned int*>(A.spec);
+    uint32_t nblk = 0, ph_f1 = 0, ph_f2 = 0, ph_i = 0, nwr = 0, nwc = 0;
+    auto arrive = [&](uint64_t* bar) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar);
     };
-
-    stage_x(0);
-    publish();
-    if (tid == 0) {
-      chain(tbase, aC, CPAN, aX, XPAN, id128, false);                    // Yr = Fr X
-      chain(tbase + S, aC + 16 * S, CPAN, aX, XPAN, id128, false);       // Yi = Fi X
-      tc_commit(&H->bd);
-    }
-    prefetch_next(cur ^ 1);
-    for (int p = 0; p < np; ++p) {
-      // Y (lane kr): columns 0..127 = Yr[kr][c], 128..255 = Yi[kr][c] into
-      // rows S + kr (Yr), kr (-Yi) and 2S + kr (Yi) of the buffer [-Yi | Yr | Yi];
-      // half h of the warps takes c in [64h, 64h + 64), 8 consecutive c per
-      // 16-byte store
-      if (!wait_d()) break;
-      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
-        uint32_t yr[16], yi[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)c0, yr);
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)(S + c0), yi);
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 16; t += 8) {
-          const float* f = reinterpret_cast<const float*>(yr + t);
-          const float* g = reinterpret_cast<const float*>(yi + t);
-          const int off = ((c0 + t) >> 3) * YPAN + 16 * L;
-          *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
-              pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]), pack_h2(f[6], f[7]));
-          *reinterpret_cast<uint4*>(sY + off) = make_uint4(
-              pack_h2(-g[0], -g[1]), pack_h2(-g[2], -g[3]), pack_h2(-g[4], -g[5]),
-              pack_h2(-g[6], -g[7]));
-          *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
-              pack_h2(g[0], g[1]), pack_h2(g[2], g[3]), pack_h2(g[4], g[5]), pack_h2(g[6], g[7]));
-        }
-      }
-      publish();
-      if (tid == 0) {
-        chain(tbase, aC, CPAN, aY + 16 * S, YPAN, id256, false);         // Fr [Yr | Yi]
-        chain(tbase, aC + 16 * S, CPAN, aY, YPAN, id256, true);          // Fi [-Yi | Yr]
-        tc_commit(&H->bd);
-      }
-      // the PSF's spectrum at this thread's column kc = L and rows kr of its
-      // half, fetched while the stage-2 MMAs run
-      const int ga = wi.a_lo + p / nb, gb = wi.b_lo + p % nb;
-      const unsigned int* hh =
-          reinterpret_cast<const unsigned int*>(A.spec) + (size_t)(ga * A.Gc + gb) * S * S;
-      uint32_t hv[64];
-#pragma unroll
-      for (int t = 0; t < 64; ++t) hv[t] = __ldg(hh + (size_t)(64 * h + t) * S + L);
-      // the next PSF's X (S1 of PSF p has completed: sX is free)
-      if (p + 1 < np) stage_x(p + 1);
-      if (!wait_d()) break;
-      // Z^T (lane kc): columns kr (re) and S + kr (im); sum += Z . Hh_p over
-      // kr in this warp's half
-#pragma unroll
-      for (int k8 = 0; k8 < 8; ++k8) {
-        const int k0 = 64 * h + 8 * k8;
-        uint32_t zr[8], zi[8], ar[8], ai[8];
-        tmem_ld8_nowait(tbase + lanes + (uint32_t)k0, zr);
-        tmem_ld8_nowait(tbase + lanes + (uint32_t)(S + k0), zi);
-        if (p > 0) {
-          tmem_ld8_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-          tmem_ld8_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-        }
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const float2 hf = __half22float2(*reinterpret_cast<const __half2*>(&hv[8 * k8 + t]));
-          const float a = __uint_as_float(zr[t]), bb = __uint_as_float(zi[t]);
-          const float re = a * hf.x - bb * hf.y, im = a * hf.y + bb * hf.x;
-          ar[t] = __float_as_uint(p > 0 ? __uint_as_float(ar[t]) + re : re);
-          ai[t] = __float_as_uint(p > 0 ? __uint_as_float(ai[t]) + im : im);
-        }
-        tmem_st8_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-        tmem_st8_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-      }
-      tmem_wait_st();
-      if (p + 1 < np) {
-        publish();   // D read, X_{p+1} written
-        if (tid == 0) {
-          chain(tbase, aC, CPAN, aX, XPAN, id128, false);
-          chain(tbase + S, aC + 16 * S, CPAN, aX, XPAN, id128, false);
-          tc_commit(&H->bd);
-        }
-      }
-    }
-    if (!ok) break;
-    // inverse, stage 1 operand: the sum (lane kc, columns kr) -> rows kc,
-    // S + kc, 2S + kc of [Zr | Zi | -Zr], 8 consecutive kr per 16-byte store
-    for (int k0 = 64 * h; k0 < 64 * h + 64; k0 += 16) {
-      uint32_t ar[16], ai[16];
-      tmem_ld16_nowait(tbase + lanes + (uint32_t)(2 * S + k0), ar);
-      tmem_ld16_nowait(tbase + lanes + (uint32_t)(3 * S + k0), ai);
-      tmem_wait_ld();
-#pragma unroll
-      for (int t = 0; t < 16; t += 8) {
-        const float* zr = reinterpret_cast<const float*>(ar + t);
-        const float* zi = reinterpret_cast<const float*>(ai + t);
-        const int off = ((k0 + t) >> 3) * YPAN + 16 * L;
-        *reinterpret_cast<uint4*>(sY + off) = make_uint4(
-            pack_h2(zr[0], zr[1]), pack_h2(zr[2], zr[3]), pack_h2(zr[4], zr[5]), pack_h2(zr[6], zr[7]));
-        *reinterpret_cast<uint4*>(sY + off + 16 * S) = make_uint4(
-            pack_h2(zi[0], zi[1]), pack_h2(zi[2], zi[3]), pack_h2(zi[4], zi[5]), pack_h2(zi[6], zi[7]));
-        *reinterpret_cast<uint4*>(sY + off + 32 * S) = make_uint4(
-            pack_h2(-zr[0], -zr[1]), pack_h2(-zr[2], -zr[3]), pack_h2(-zr[4], -zr[5]),
-            pack_h2(-zr[6], -zr[7]));
-      }
-    }
-    publish();
-    if (tid == 0) {
-      chain(tbase, aC, CPAN, aY, YPAN, id256, false);                    // Fr [Zr | Zi]
-      chain(tbase, aC + 16 * S, CPAN, aY + 16 * S, YPAN, id256, true);   // Fi [Zi | -Zr]
-      tc_commit(&H->bd);
-    }
-    // the next block's x window, in flight while this block's inverse runs
-    have_x = H->item[cur ^ 1] < A.n_work && psfs_of(wis[cur ^ 1]) > 0;
-    if (have_x) {
-      WTab tab;
-      load_x(wis[cur ^ 1], tds[cur ^ 1], tab);
-      store_tab(tab);   // this block's tables were last read by its last X_p
-    }
-    // U (lane r): columns kc (re), S + kc (im), scaled by 1 / 128, into the
-    // last stage's operands Ur (sX) and Ui (sY), rows r, k = kc
-    if (!wait_d()) break;
-    for (int k0 = 0; k0 < S; k0 += 16) {
-      uint32_t r[16];
-      tmem_ld16_nowait(tbase + lanes + (uint32_t)(S * h + k0), r);
-      tmem_wait_ld();
-      unsigned char* dst = h == 0 ? sX : sY;
-      const float sc = 1.f / S;
-#pragma unroll
-      for (int t = 0; t < 16; t += 8)
-        *reinterpret_cast<uint4*>(dst + ((k0 + t) >> 3) * XPAN + 16 * L) = make_uint4(
-            pack_h2(sc * __uint_as_float(r[t]), sc * __uint_as_float(r[t + 1])),
-            pack_h2(sc * __uint_as_float(r[t + 2]), sc * __uint_as_float(r[t + 3])),
-            pack_h2(sc * __uint_as_float(r[t + 4]), sc * __uint_as_float(r[t + 5])),
-            pack_h2(sc * __uint_as_float(r[t + 6]), sc * __uint_as_float(r[t + 7])));
-    }
-    publish();
-    if (tid == 0) {
-      chain(tbase, aX, XPAN, aC, CPAN, id128, false);                    // Ur Fr
-      chain(tbase, aY, XPAN, aC + 16 * S, CPAN, id128, true);            // Ui Fi
-      tc_commit(&H->bd);
-    }
-    // x (lane r, columns c) -> an FP32 tile in the Y buffer (free once the
-    // last MMAs have completed), then the valid rows and columns K - 1 .. 127
-    // are written row by row (coalesced observed image, weights and output)
-    if (!wait_d()) break;
-    {
-      float* tile = reinterpret_cast<float*>(sY);
-      constexpr int TPT = S + 1;
-      for (int c0 = 64 * h; c0 < 64 * h + 64; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16_nowait(tbase + lanes + (uint32_t)c0, v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int t = 0; t < 16; ++t) tile[L * TPT + c0 + t] = __uint_as_float(v[t]);
-      }
-      __syncthreads();
+    auto wait_all = [&](uint64_t* bar, uint32_t ph) {
+      const bool w = wait_bar(bar, ph & 1, &H->abort, A.err, limit);
+      ok = named_all<NTW>(w && !*(volatile int*)&H->abort);
+      tc_fence_after();
+      return ok;
+    };
+    // the output block from an FP32 tile (pitch b + 1) or zero (tile null):
+    // H x, or W (H x - y) with the observed image and weights of a batch of
+    // EPB elements a thread loaded before any of its outputs is written
+    auto write_out = [&](const WorkItem& wi, const TileDesc& td, const float* tile) {
       const int nr = min(b, td.nyr - wi.r0), nc = min(b, td.nyc - wi.c0);
-      // batches of EPB elements a thread: the observed image and weights of
-      // a batch are loaded before any of its outputs is written
-      constexpr int EPB = 18;
-      for (int e0 = tid; e0 < nr * b; e0 += EPB * NTS) {
+      constexpr int EPB = 17;
+      for (int e0 = tid; e0 < nr * b; e0 += EPB * NTW) {
         float yo[EPB], wo[EPB];
 #pragma unroll
         for (int u = 0; u < EPB; ++u) {
-          const int e = e0 + u * NTS, il = e / b, jl = e - il * b;
+          const int e = e0 + u * NTW, il = e / b, jl = e - il * b;
           yo[u] = 0.f;
           wo[u] = 1.f;
           if (A.mode != OP_PLAIN && e < nr * b && jl < nc) {
@@ -458,25 +342,252 @@ __global__ void __launch_bounds__(NTS, 1) dft_H_kernel(const OpArgs A) {
         }
 #pragma unroll
         for (int u = 0; u < EPB; ++u) {
-          const int e = e0 + u * NTS, il = e / b, jl = e - il * b;
+          const int e = e0 + u * NTW, il = e / b, jl = e - il * b;
           if (e >= nr * b || jl >= nc) continue;
-          const float y = tile[(il + K - 1) * TPT + jl + K - 1];
-          out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
-              A.mode == OP_PLAIN ? y : wo[u] * (y - yo[u]);
+          const float v = tile ? tile[il * (b + 1) + jl] : 0.f;
+          A.out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
+              A.mode == OP_PLAIN ? v : wo[u] * (v - yo[u]);
         }
       }
+    };
+
+    while (ok) {
+      if (!wait_all(&H->win_full, nblk)) break;
+      const int slot = nblk & 1;
+      ++nblk;
+      if (H->item[slot] < 0) {
+        // stop: tell the MMA warp
+        if (tid == 0) H->mbox[0] = -1;
+        arrive(&H->xch[0]);
+        break;
+      }
+      // (the loader rewrites this slot for the block after next, once this
+      // block has finished)
+      const WorkItem& wi = wis[slot];
+      const TileDesc& td = tds[slot];
+      const int na = wi.a_hi - wi.a_lo + 1, nb = wi.b_hi - wi.b_lo + 1;
+      const WTab* tr = sTab + slot * 2 * S;
+      const WTab* tc = tr + S;
+      if (na * nb <= 0) {
+        // no PSF reaches the block: H x is zero there
+        arrive(&H->win_empty);
+        write_out(wi, td, nullptr);
+        continue;
+      }
+      if (tid == 0) {
+        H->mbox[0] = na;
+        H->mbox[1] = nb;
+      }
+      // (wr_a x)^T into sX in 8 chunks of 16 r (panels 2i + half), a chunk
+      // complete -> xch[i]
+      auto stage_x = [&](int ga, bool last_use) {
+        float* wr = sWr + (nwr++ & 1) * S;
+        if (tid < S) wr[tid] = wsel(tr[tid], ga);
+        named_sync<NTW>();
+        const int c = tid & (S - 1), half = tid >> 7;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int pan = 2 * i + half;
+          const uint4 xv = *reinterpret_cast<const uint4*>(sWin + pan * XPAN + 16 * c);
+          const float4 w0 = *reinterpret_cast<const float4*>(wr + 8 * pan);
+          const float4 w1 = *reinterpret_cast<const float4*>(wr + 8 * pan + 4);
+          const float2 x0 = unpack_h2(xv.x), x1 = unpack_h2(xv.y), x2 = unpack_h2(xv.z),
+                       x3 = unpack_h2(xv.w);
+          *reinterpret_cast<uint4*>(sX + pan * XPAN + 16 * c) =
+              make_uint4(pack_h2(w0.x * x0.x, w0.y * x0.y), pack_h2(w0.z * x1.x, w0.w * x1.y),
+                         pack_h2(w1.x * x2.x, w1.y * x2.y), pack_h2(w1.z * x3.x, w1.w * x3.y));
+          fence_async_smem();
+          arrive(&H->xch[i]);
+        }
+        if (last_use) arrive(&H->win_empty);
+      };
+      stage_x(wi.a_lo, na == 1);
+      float s64r = 0.f, s64i = 0.f;          // S(64) at this lane's kc (h == 0)
+      for (int ai = 0; ai < na && ok; ++ai) {
+        if (!wait_all(&H->f1_done, ph_f1++)) break;
+        for (int bi = 0; bi < nb && ok; ++bi) {
+          const bool first = ai == 0 && bi == 0;
+          const int gb = wi.b_lo + bi;
+          // wc_b Y' into sY: lane j, columns c = 16 i + 8 h + (0 .. 7) -> panel 2 i + h
+          {
+            float* wc = sWc + (nwc++ & 1) * S;
+            if (tid >= S) wc[tid - S] = wsel(tc[tid - S], gb);
+            named_sync<NTW>();
+            uint32_t v[8][8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) tmem_ld8_nowait(tbase + lanes + TM_F1 + 16 * i + 8 * h, v[i]);
+            tmem_wait_ld();
+            tc_fence_before();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int c0 = 16 * i + 8 * h;
+              const float4 w0 = *reinterpret_cast<const float4*>(wc + c0);
+              const float4 w1 = *reinterpret_cast<const float4*>(wc + c0 + 4);
+              const float* f = reinterpret_cast<const float*>(v[i]);
+              *reinterpret_cast<uint4*>(sY + (2 * i + h) * XPAN + 16 * L) =
+                  make_uint4(pack_h2(w0.x * f[0], w0.y * f[1]), pack_h2(w0.z * f[2], w0.w * f[3]),
+                             pack_h2(w1.x * f[4], w1.y * f[5]), pack_h2(w1.z * f[6], w1.w * f[7]));
+              fence_async_smem();
+              arrive(&H->ych[i]);
+            }
+          }
+          // the next row weight's X once F1 has been read for the last time
+          if (bi == nb - 1 && ai + 1 < na) stage_x(wi.a_lo + ai + 1, ai + 2 == na);
+          // this thread's spectrum values Hh_p(k, kc = L), k = 16 i + 8 h + t
+          // (and k = 64 for h == 0), fetched while F2 runs
+          const int ga = wi.a_lo + ai;
+          const unsigned int* hs = spec + (size_t)(ga * A.Gc + gb) * S * S + L;
+          uint32_t hv[33];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int t = 0; t < 8; ++t) hv[8 * i + t] = __ldg(hs + (size_t)(16 * i + 8 * h + t) * S);
+          hv[32] = h == 0 ? __ldg(hs + (size_t)64 * S) : 0u;
+          if (!wait_all(&H->f2_done, ph_f2++)) break;
+          // product: Z(k)[kc] from P, Q at columns 2k, 2k + 1, times Hh_p,
+          // summed in tensor memory (columns 2k, 2k + 1 of the sum)
+          float p1 = 0.f, q1 = 0.f;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const uint32_t col = 32 * i + 16 * h;
+            uint32_t pv[16], qv[16], sv[16];
+            tmem_ld16_nowait(tbase + lanes + TM_P + col, pv);
+            tmem_ld16_nowait(tbase + lanes + TM_Q + col, qv);
+            if (!first) tmem_ld16_nowait(tbase + lanes + TM_SUM + col, sv);
+            tmem_wait_ld();
+            if (i == 0) {
+              p1 = __uint_as_float(pv[1]);
+              q1 = __uint_as_float(qv[1]);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const float pr = __uint_as_float(pv[2 * t]), pi = __uint_as_float(pv[2 * t + 1]);
+              const float qr = __uint_as_float(qv[2 * t]), qi = __uint_as_float(qv[2 * t + 1]);
+              // k = 0 (i, t, h = 0): Y(0) is real, column 1 holds Y(64)
+              const bool k0 = i == 0 && t == 0 && h == 0;
+              const float zr = k0 ? pr : pr - qi, zi = k0 ? qr : qr + pi;
+              const float2 hf = unpack_h2(hv[8 * i + t]);
+              float sr = first ? 0.f : __uint_as_float(sv[2 * t]);
+              float si = first ? 0.f : __uint_as_float(sv[2 * t + 1]);
+              sr = fmaf(zr, hf.x, fmaf(-zi, hf.y, sr));
+              si = fmaf(zr, hf.y, fmaf(zi, hf.x, si));
+              sv[2 * t] = __float_as_uint(sr);
+              sv[2 * t + 1] = __float_as_uint(si);
+            }
+            tmem_st16_nowait(tbase + lanes + TM_SUM + col, sv);
+          }
+          if (h == 0) {
+            // k = 64: Z = P[1] + i Q[1] (Y(64) is real)
+            const float2 hf = unpack_h2(hv[32]);
+            s64r = fmaf(p1, hf.x, fmaf(-q1, hf.y, first ? 0.f : s64r));
+            s64i = fmaf(p1, hf.y, fmaf(q1, hf.x, first ? 0.f : s64i));
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          arrive(&H->p_done);
+        }
+      }
+      if (!ok) break;
+      // I1 operand rows kc ([aSr; aSi; -aSr] at rows kc, S + kc, 2S + kc) in
+      // 5 chunks of 16 k (panel 2 i + h, k = 16 i + 8 h + t), -> sch[i]
+      {
+        uint32_t sv[4][16];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tmem_ld16_nowait(tbase + lanes + TM_SUM + 32 * i + 16 * h, sv[i]);
+        tmem_wait_ld();
+        tc_fence_before();
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+          float sr[8], si[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            if (i < 4) {
+              const float al = (i == 0 && t == 0 && h == 0) ? 1.f : 2.f;
+              sr[t] = al * __uint_as_float(sv[i][2 * t]);
+              si[t] = al * __uint_as_float(sv[i][2 * t + 1]);
+            } else {
+              sr[t] = (t == 0 && h == 0) ? s64r : 0.f;
+              si[t] = (t == 0 && h == 0) ? s64i : 0.f;
+            }
+          }
+          unsigned char* dst = sX + (2 * i + h) * IPAN + 16 * L;
+          *reinterpret_cast<uint4*>(dst) =
+              make_uint4(pack_h2(sr[0], sr[1]), pack_h2(sr[2], sr[3]), pack_h2(sr[4], sr[5]),
+                         pack_h2(sr[6], sr[7]));
+          *reinterpret_cast<uint4*>(dst + 16 * S) =
+              make_uint4(pack_h2(si[0], si[1]), pack_h2(si[2], si[3]), pack_h2(si[4], si[5]),
+                         pack_h2(si[6], si[7]));
+          *reinterpret_cast<uint4*>(dst + 32 * S) =
+              make_uint4(pack_h2(-sr[0], -sr[1]), pack_h2(-sr[2], -sr[3]), pack_h2(-sr[4], -sr[5]),
+                         pack_h2(-sr[6], -sr[7]));
+          fence_async_smem();
+          arrive(&H->sch[i]);
+        }
+      }
+      // U / 128 (lane r, columns kc = 16 i + 8 h + t) into the I2 operands Ur
+      // (sX) and Ui (sY), panel 2 i + h, -> uch[i]
+      if (!wait_all(&H->i1_done, ph_i)) break;
+      for (int i0 = 0; i0 < 8; i0 += 4) {
+        uint32_t ur[4][8], ui[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          tmem_ld8_nowait(tbase + lanes + TM_I1 + 16 * (i0 + i) + 8 * h, ur[i]);
+          tmem_ld8_nowait(tbase + lanes + TM_I1 + S + 16 * (i0 + i) + 8 * h, ui[i]);
+        }
+        tmem_wait_ld();
+        tc_fence_before();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float sc = 1.f / S;
+          const float* fr = reinterpret_cast<const float*>(ur[i]);
+          const float* fi = reinterpret_cast<const float*>(ui[i]);
+          const int off = (2 * (i0 + i) + h) * XPAN + 16 * L;
+          *reinterpret_cast<uint4*>(sX + off) =
+              make_uint4(pack_h2(sc * fr[0], sc * fr[1]), pack_h2(sc * fr[2], sc * fr[3]),
+                         pack_h2(sc * fr[4], sc * fr[5]), pack_h2(sc * fr[6], sc * fr[7]));
+          *reinterpret_cast<uint4*>(sY + off) =
+              make_uint4(pack_h2(sc * fi[0], sc * fi[1]), pack_h2(sc * fi[2], sc * fi[3]),
+                         pack_h2(sc * fi[4], sc * fi[5]), pack_h2(sc * fi[6], sc * fi[7]));
+          fence_async_smem();
+          arrive(&H->uch[i0 + i]);
+        }
+      }
+      // x (lane r, columns c) -> the valid rows and columns K - 1 .. 127 of an
+      // FP32 tile in the X and Y buffers, then the output block row by row
+      if (!wait_all(&H->i2_done, ph_i++)) break;
+      {
+        float* tile = reinterpret_cast<float*>(sX);
+        const int r = L - (K - 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          uint32_t v[16];
+          tmem_ld16_nowait(tbase + lanes + TM_I2 + 64 * h + 16 * i, v);
+          tmem_wait_ld();
+          if (r >= 0) {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const int cc = 64 * h + 16 * i + t - (K - 1);
+              if (cc >= 0) tile[r * (b + 1) + cc] = __uint_as_float(v[t]);
+            }
+          }
+        }
+        tc_fence_before();
+        named_sync<NTW>();
+        write_out(wi, td, tile);
+        named_sync<NTW>();   // the tile is read before the next block's X is staged
+      }
     }
-    cur ^= 1;
   }
+
   if (!ok) *(volatile int*)&H->abort = 1;
   // teardown: every MMA this CTA issued has completed before tensor memory is freed
-  if (tid == 0) {
+  if (warp == WMMA && lane == 0) {
     tc_commit(&H->fin);
     drain_bar(&H->fin, 0, A.err);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == WMMA) {
     tc_fence_after();
     tmem_free(tbase, TMEM_COLS);
   }
@@ -490,18 +601,28 @@ cudaError_t dft_prepare() {
   return cudaFuncSetAttribute(dft_H_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D);
 }
 
-// Byte image of the constant operand [Fr; Fi]: 16 panels of 256 16-byte rows
-// (padded), row n < 128: cos(2 pi n k / 128), row 128 + n: -sin(2 pi n k / 128),
-// k the column; FP16, from FP64 on the host.
+// Byte image of the constant operands, FP16 from FP64 on the host: [Fr; Fi]
+// (16 panels of 256 16-byte rows, padded; row n < 128: cos(2 pi n k / 128),
+// row 128 + n: -sin(2 pi n k / 128), k the column), then A1 (16 panels of 128
+// rows; row 2m: cos(2 pi m k / 128), row 2m + 1: -sin(2 pi m k / 128) for
+// m = 1 .. 63, row 1: cos(pi k) = Fr(64)).
 void dft_constants(std::vector<uint8_t>& out) {
-  out.assign(CBYTES, 0);
-  for (int n = 0; n < CROWS; ++n)
+  out.assign(CBYTES + XBYTES, 0);
+  auto put = [&](size_t off, double v) {
+    const __half hv = __float2half_rn((float)v);
+    std::memcpy(out.data() + off, &hv, 2);
+  };
+  auto ang = [](int n, int k) { return 2.0 * 3.14159265358979323846 * (double)((n * k) % S) / S; };
+  for (int n = 0; n < 2 * S; ++n)
     for (int k = 0; k < S; ++k) {
       const int nn = n & (S - 1);
-      const double a = 2.0 * 3.14159265358979323846 * (double)((nn * k) % S) / S;
-      const float v = n < S ? (float)std::cos(a) : (float)-std::sin(a);
-      const __half hv = __float2half_rn(v);
-      std::memcpy(out.data() + (k >> 3) * CPAN + 16 * n + 2 * (k & 7), &hv, 2);
+      put((size_t)(k >> 3) * CPAN + 16 * n + 2 * (k & 7), n < S ? std::cos(ang(nn, k)) : -std::sin(ang(nn, k)));
+    }
+  for (int j = 0; j < S; ++j)
+    for (int k = 0; k < S; ++k) {
+      const int m = j >> 1;
+      const double v = j == 1 ? std::cos(ang(S / 2, k)) : (j & 1) ? -std::sin(ang(m, k)) : std::cos(ang(m, k));
+      put(CBYTES + (size_t)(k >> 3) * XPAN + 16 * j + 2 * (k & 7), v);
     }
 }
 
@@ -549,7 +670,7 @@ cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid) {
   if (a.n_work <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  dft_H_kernel<<<std::min(grid, a.n_work), NTS, SMEM_D, s>>>(a);
+  dft_H_kernel<<<std::min(grid, a.n_work), NT, SMEM_D, s>>>(a);
   return cudaGetLastError();
 }
 
