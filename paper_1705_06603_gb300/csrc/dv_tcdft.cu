@@ -57,8 +57,12 @@ using namespace tcg;
 constexpr int S = 128;                      // transform size
 constexpr int NWK = 8;                      // staging warps
 constexpr int NTW = 32 * NWK;
-constexpr int WMMA = NWK, WLOAD = NWK + 1;  // MMA warp, loader warp
-constexpr int NT = 32 * (NWK + 2);
+constexpr int NLW = 3;                      // loader warps
+constexpr int WMMA = NWK, WLOAD = NWK + 1;  // MMA warp, first loader warp
+constexpr int NT = 32 * (NWK + 1 + NLW);    // 12 warps, at most 3 per SM sub-partition
+// half spectra: per PSF [9 groups of 8 k][2][kc][4] FP16 pairs, k = 8 g + 4 u + t
+// (k = 0 .. 64 used), so that a warp's 16-byte loads of 4 k at its 32 kc are contiguous
+constexpr int SPSF = 9 * 2 * S * 4;
 constexpr int CPAN = 2 * S * 16 + 16;       // [Fr; Fi] (256 rows) panel stride
 constexpr int CBYTES = (S / 8) * CPAN;
 constexpr int XPAN = S * 16 + 16;           // 128-row operand panel stride
@@ -92,6 +96,7 @@ struct BarsD {
   int abort;
   int mbox[2];                            // na, nb of the next block for the MMA warp (na < 0: stop)
   int item[2];                            // work item of a slot (-1: stop)
+  int next_item;                          // the loaders' next claimed item
 };
 static_assert(sizeof(BarsD) <= kHdrD, "barrier header");
 
@@ -108,7 +113,19 @@ __device__ __forceinline__ void kstep(uint32_t d, uint32_t a0, uint32_t apan, ui
   mma_bf16(d, sdesc(a0 + 2 * i * apan, apan), sdesc(b0 + 2 * i * bpan, bpan), id, acc ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
+// barrier 2 over the loader warps, as an AND-vote
+__device__ __forceinline__ bool loader_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 2, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * NLW)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
   BarsD* H = reinterpret_cast<BarsD*>(smem);
   unsigned char* sC = smem + OFF_C;
@@ -124,7 +141,7 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
   const int K = A.K, b = S - K + 1;
   const uint64_t limit = A.wait_ns ? A.wait_ns : kWaitNs;
   if (tid == 0) {
-    mbar_init(&H->win_full, 1);
+    mbar_init(&H->win_full, NLW);
     mbar_init(&H->win_empty, NWK);
     mbar_init(&H->f1_done, 1);
     mbar_init(&H->f2_done, 1);
@@ -152,78 +169,125 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
   const uint32_t tbase = H->tmem;
   bool ok = true;
 
-  if (warp == WLOAD) {
-    // ---------------------------------------------------------------- loader
+  if (warp >= WLOAD) {
+    // --------------------------------------------------------------- loaders
+    // loader warp lw takes panels q = lw, lw + 3, .. of the window; warp 0
+    // claims the items, warps 1 and 2 fetch the row / column tables
+    const int lw = warp - WLOAD;
     auto psfs = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
     int it = 0;
-    if (lane == 0) it = atomicAdd(A.counter, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    if (lw == 0 && lane == 0) it = atomicAdd(A.counter, 1);
     for (uint32_t n = 0; !A.test_withhold; ++n) {
       const int slot = n & 1;
-      if (n > 0 && !wait_bar(&H->win_empty, (n - 1) & 1, &H->abort, A.err, limit)) {
-        ok = false;
-        break;
+      bool w = n == 0 || wait_bar(&H->win_empty, (n - 1) & 1, &H->abort, A.err, limit);
+      if (!(ok = loader_all(w && !*(volatile int*)&H->abort))) break;
+      if (lw == 0 && lane == 0) {
+        if (it < A.n_work) {
+          const WorkItem w2 = A.work[it];
+          wis[slot] = w2;
+          tds[slot] = A.tiles[w2.tile];
+          H->next_item = atomicAdd(A.counter, 1);
+        }
+        H->item[slot] = it < A.n_work ? it : -1;
       }
-      if (it >= A.n_work) {
-        if (lane == 0) H->item[slot] = -1;
+      loader_all(true);   // slot written
+      if (H->item[slot] < 0) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&H->win_full);
         break;
       }
-      const WorkItem w2 = A.work[it];
-      const TileDesc t2 = A.tiles[w2.tile];
-      int it2 = 0;
-      if (lane == 0) {
-        it2 = atomicAdd(A.counter, 1);
-        wis[slot] = w2;
-        tds[slot] = t2;
-        H->item[slot] = it;
-      }
+      const WorkItem& w2 = wis[slot];
+      const TileDesc& t2 = tds[slot];
       if (psfs(w2) > 0) {
-        // interpolation tables of the window's rows and columns ({-2, 0, 0}
-        // outside the tile: no grid index has a weight there)
-        WTab* tab = sTab + slot * 2 * S;
-        for (int e = lane; e < 2 * S; e += 32) {
-          WTab v{-2, 0.f, 0.f, 0};
-          if (e < S) {
-            if (w2.r0 + e < t2.nxr) v = A.wrow[t2.wr0 + w2.r0 + e];
-          } else if (w2.c0 + e - S < t2.nxc) {
-            v = A.wcol[t2.wc0 + w2.c0 + e - S];
+        if (lw > 0) {
+          // interpolation table of the window's rows (lw = 1) or columns ({-2, 0, 0}
+          // outside the tile: no grid index has a weight there)
+          WTab* tab = sTab + slot * 2 * S + (lw - 1) * S;
+          for (int e = lane; e < S; e += 32) {
+            WTab v{-2, 0.f, 0.f, 0};
+            if (lw == 1 && w2.r0 + e < t2.nxr) v = A.wrow[t2.wr0 + w2.r0 + e];
+            if (lw == 2 && w2.c0 + e < t2.nxc) v = A.wcol[t2.wc0 + w2.c0 + e];
+            tab[e] = v;
           }
-          tab[e] = v;
         }
-        // the window as x^T in FP16: row c, 8 consecutive r per 16 bytes; 64
-        // loads in flight a lane
+        // the window as x^T in FP16: row c, 8 consecutive r per 16 bytes;
+        // two panels (64 loads) in flight a lane, 8-byte loads where aligned
         const float* img = A.in + t2.xoff;
-        for (int m = 0; m < 4; ++m) {
-          const int c = 32 * m + lane, C = w2.c0 + c;
-          for (int q0 = 0; q0 < S / 8; q0 += 8) {
-            float v[8][8];
+        const bool al2 = ((reinterpret_cast<uintptr_t>(img + w2.c0) & 7) == 0) && (t2.xpitch % 2 == 0);
+        for (int q0 = lw; q0 < S / 8; q0 += 2 * NLW) {
+          const bool two = q0 + NLW < S / 8;
+          if (al2) {
+            float2 v[2][2][8];
 #pragma unroll
-            for (int qq = 0; qq < 8; ++qq)
+            for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-              for (int t = 0; t < 8; ++t) {
-                const int R = w2.r0 + 8 * (q0 + qq) + t;
-                v[qq][t] = (R < t2.nxr && C < t2.nxc) ? __ldg(img + (int64_t)R * t2.xpitch + C) : 0.f;
+              for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                  const int R = w2.r0 + 8 * (q0 + qq * NLW) + t, C = w2.c0 + 2 * lane + 64 * m;
+                  const float* src = img + (int64_t)R * t2.xpitch + C;
+                  float2 u = make_float2(0.f, 0.f);
+                  if ((qq == 0 || two) && R < t2.nxr) {
+                    if (C + 1 < t2.nxc) u = __ldg(reinterpret_cast<const float2*>(src));
+                    else if (C < t2.nxc) u.x = __ldg(src);
+                  }
+                  v[qq][m][t] = u;
+                }
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+              if (qq == 1 && !two) break;
+              const int q = q0 + qq * NLW;
+#pragma unroll
+              for (int m = 0; m < 2; ++m) {
+                const int c = 2 * lane + 64 * m;
+                const float2* f = v[qq][m];
+                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * c) =
+                    make_uint4(pack_h2(f[0].x, f[1].x), pack_h2(f[2].x, f[3].x),
+                               pack_h2(f[4].x, f[5].x), pack_h2(f[6].x, f[7].x));
+                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (c + 1)) =
+                    make_uint4(pack_h2(f[0].y, f[1].y), pack_h2(f[2].y, f[3].y),
+                               pack_h2(f[4].y, f[5].y), pack_h2(f[6].y, f[7].y));
               }
+            }
+          } else {
+            float v[2][4][8];
 #pragma unroll
-            for (int qq = 0; qq < 8; ++qq)
-              *reinterpret_cast<uint4*>(sWin + (q0 + qq) * XPAN + 16 * c) =
-                  make_uint4(pack_h2(v[qq][0], v[qq][1]), pack_h2(v[qq][2], v[qq][3]),
-                             pack_h2(v[qq][4], v[qq][5]), pack_h2(v[qq][6], v[qq][7]));
+            for (int qq = 0; qq < 2; ++qq)
+#pragma unroll
+              for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                  const int R = w2.r0 + 8 * (q0 + qq * NLW) + t, C = w2.c0 + lane + 32 * m;
+                  v[qq][m][t] = ((qq == 0 || two) && R < t2.nxr && C < t2.nxc)
+                                    ? __ldg(img + (int64_t)R * t2.xpitch + C)
+                                    : 0.f;
+                }
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+              if (qq == 1 && !two) break;
+              const int q = q0 + qq * NLW;
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const float* f = v[qq][m];
+                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (lane + 32 * m)) =
+                    make_uint4(pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]),
+                               pack_h2(f[6], f[7]));
+              }
+            }
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&H->win_full);
       // the next item's window and residual rows into L2 while this block runs
-      it2 = __shfl_sync(0xffffffffu, it2, 0);
+      const int it2 = H->next_item;
+      if (lw == 0) it = it2;
       if (it2 < A.n_work) {
         const WorkItem w3 = A.work[it2];
         const TileDesc t3 = A.tiles[w3.tile];
         if (psfs(w3) > 0) {
           const int c_end = min(w3.c0 + S, t3.nxc);
-          for (int rr = lane; rr < S; rr += 32) {
+          for (int rr = 32 * lw + lane; rr < S; rr += 32 * NLW) {
             const int R = w3.r0 + rr;
             if (R >= t3.nxr || w3.c0 >= c_end) continue;
             const float* row = A.in + t3.xoff + (int64_t)R * t3.xpitch;
@@ -232,7 +296,7 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
           }
           if (A.mode != OP_PLAIN) {
             const int j_end = min(w3.c0 + b, t3.nyc);
-            for (int rr = lane; rr < b; rr += 32) {
+            for (int rr = 32 * lw + lane; rr < b; rr += 32 * NLW) {
               const int i = w3.r0 + rr;
               if (i >= t3.nyr || w3.c0 >= j_end) continue;
               const int64_t g0 = (int64_t)(t3.xr0 + i) * A.wy + t3.xc0;
@@ -246,7 +310,6 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
           }
         }
       }
-      it = it2;
     }
   } else if (warp == WMMA) {
     // ------------------------------------------------------------------- MMA
@@ -322,32 +385,36 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
       return ok;
     };
     // the output block from an FP32 tile (pitch b + 1) or zero (tile null):
-    // H x, or W (H x - y) with the observed image and weights of a batch of
-    // EPB elements a thread loaded before any of its outputs is written
+    // H x, or W (H x - y); warp w writes rows w, w + 8, .., lanes columns,
+    // the observed image and weights of RB rows loaded before they are used
     auto write_out = [&](const WorkItem& wi, const TileDesc& td, const float* tile) {
       const int nr = min(b, td.nyr - wi.r0), nc = min(b, td.nyc - wi.c0);
-      constexpr int EPB = 17;
-      for (int e0 = tid; e0 < nr * b; e0 += EPB * NTW) {
-        float yo[EPB], wo[EPB];
+      constexpr int RB = 4, CB = S / 32;
+      for (int il0 = warp; il0 < nr; il0 += RB * NWK) {
+        float yo[RB][CB], wo[RB][CB];
 #pragma unroll
-        for (int u = 0; u < EPB; ++u) {
-          const int e = e0 + u * NTW, il = e / b, jl = e - il * b;
-          yo[u] = 0.f;
-          wo[u] = 1.f;
-          if (A.mode != OP_PLAIN && e < nr * b && jl < nc) {
-            const int64_t gi = (int64_t)(td.xr0 + wi.r0 + il) * A.wy + (td.xc0 + wi.c0 + jl);
-            yo[u] = __ldg(A.y + gi);
-            if (A.W) wo[u] = __ldg(A.W + gi);
+        for (int u = 0; u < RB; ++u)
+#pragma unroll
+          for (int v = 0; v < CB; ++v) {
+            const int il = il0 + u * NWK, jl = lane + 32 * v;
+            yo[u][v] = 0.f;
+            wo[u][v] = 1.f;
+            if (A.mode != OP_PLAIN && il < nr && jl < nc) {
+              const int64_t gi = (int64_t)(td.xr0 + wi.r0 + il) * A.wy + (td.xc0 + wi.c0 + jl);
+              yo[u][v] = __ldg(A.y + gi);
+              if (A.W) wo[u][v] = __ldg(A.W + gi);
+            }
           }
-        }
 #pragma unroll
-        for (int u = 0; u < EPB; ++u) {
-          const int e = e0 + u * NTW, il = e / b, jl = e - il * b;
-          if (e >= nr * b || jl >= nc) continue;
-          const float v = tile ? tile[il * (b + 1) + jl] : 0.f;
-          A.out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
-              A.mode == OP_PLAIN ? v : wo[u] * (v - yo[u]);
-        }
+        for (int u = 0; u < RB; ++u)
+#pragma unroll
+          for (int v = 0; v < CB; ++v) {
+            const int il = il0 + u * NWK, jl = lane + 32 * v;
+            if (il >= nr || jl >= nc) continue;
+            const float x = tile ? tile[il * (b + 1) + jl] : 0.f;
+            A.out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
+                A.mode == OP_PLAIN ? x : wo[u][v] * (x - yo[u][v]);
+          }
       }
     };
 
@@ -396,9 +463,10 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
           *reinterpret_cast<uint4*>(sX + pan * XPAN + 16 * c) =
               make_uint4(pack_h2(w0.x * x0.x, w0.y * x0.y), pack_h2(w0.z * x1.x, w0.w * x1.y),
                          pack_h2(w1.x * x2.x, w1.y * x2.y), pack_h2(w1.z * x3.x, w1.w * x3.y));
-          fence_async_smem();
-          arrive(&H->xch[i]);
         }
+        fence_async_smem();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) arrive(&H->xch[i]);
         if (last_use) arrive(&H->win_empty);
       };
       stage_x(wi.a_lo, na == 1);
@@ -427,22 +495,27 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
               *reinterpret_cast<uint4*>(sY + (2 * i + h) * XPAN + 16 * L) =
                   make_uint4(pack_h2(w0.x * f[0], w0.y * f[1]), pack_h2(w0.z * f[2], w0.w * f[3]),
                              pack_h2(w1.x * f[4], w1.y * f[5]), pack_h2(w1.z * f[6], w1.w * f[7]));
-              fence_async_smem();
-              arrive(&H->ych[i]);
             }
+            fence_async_smem();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) arrive(&H->ych[i]);
           }
           // the next row weight's X once F1 has been read for the last time
           if (bi == nb - 1 && ai + 1 < na) stage_x(wi.a_lo + ai + 1, ai + 2 == na);
           // this thread's spectrum values Hh_p(k, kc = L), k = 16 i + 8 h + t
           // (and k = 64 for h == 0), fetched while F2 runs
           const int ga = wi.a_lo + ai;
-          const unsigned int* hs = spec + (size_t)(ga * A.Gc + gb) * S * S + L;
+          const unsigned int* hs = spec + (size_t)(ga * A.Gc + gb) * SPSF + 4 * L;
           uint32_t hv[33];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int t = 0; t < 8; ++t) hv[8 * i + t] = __ldg(hs + (size_t)(16 * i + 8 * h + t) * S);
-          hv[32] = h == 0 ? __ldg(hs + (size_t)64 * S) : 0u;
+          for (int i = 0; i < 4; ++i) {
+            const int g = 2 * i + h;
+            const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(hs + (2 * g) * S * 4));
+            const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(hs + (2 * g + 1) * S * 4));
+            hv[8 * i + 0] = u0.x; hv[8 * i + 1] = u0.y; hv[8 * i + 2] = u0.z; hv[8 * i + 3] = u0.w;
+            hv[8 * i + 4] = u1.x; hv[8 * i + 5] = u1.y; hv[8 * i + 6] = u1.z; hv[8 * i + 7] = u1.w;
+          }
+          hv[32] = h == 0 ? __ldg(hs + 16 * S * 4) : 0u;
           if (!wait_all(&H->f2_done, ph_f2++)) break;
           // product: Z(k)[kc] from P, Q at columns 2k, 2k + 1, times Hh_p,
           // summed in tensor memory (columns 2k, 2k + 1 of the sum)
@@ -520,9 +593,10 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
           *reinterpret_cast<uint4*>(dst + 32 * S) =
               make_uint4(pack_h2(-sr[0], -sr[1]), pack_h2(-sr[2], -sr[3]), pack_h2(-sr[4], -sr[5]),
                          pack_h2(-sr[6], -sr[7]));
-          fence_async_smem();
-          arrive(&H->sch[i]);
         }
+        fence_async_smem();
+#pragma unroll
+        for (int i = 0; i < 5; ++i) arrive(&H->sch[i]);
       }
       // U / 128 (lane r, columns kc = 16 i + 8 h + t) into the I2 operands Ur
       // (sX) and Ui (sY), panel 2 i + h, -> uch[i]
@@ -548,9 +622,10 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
           *reinterpret_cast<uint4*>(sY + off) =
               make_uint4(pack_h2(sc * fi[0], sc * fi[1]), pack_h2(sc * fi[2], sc * fi[3]),
                          pack_h2(sc * fi[4], sc * fi[5]), pack_h2(sc * fi[6], sc * fi[7]));
-          fence_async_smem();
-          arrive(&H->uch[i0 + i]);
         }
+        fence_async_smem();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) arrive(&H->uch[i0 + i]);
       }
       // x (lane r, columns c) -> the valid rows and columns K - 1 .. 127 of an
       // FP32 tile in the X and Y buffers, then the output block row by row
@@ -558,18 +633,18 @@ __global__ void __launch_bounds__(384, 1) dft_H_kernel(const OpArgs A) {
       {
         float* tile = reinterpret_cast<float*>(sX);
         const int r = L - (K - 1);
+        uint32_t v[4][16];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          uint32_t v[16];
-          tmem_ld16_nowait(tbase + lanes + TM_I2 + 64 * h + 16 * i, v);
-          tmem_wait_ld();
-          if (r >= 0) {
+        for (int i = 0; i < 4; ++i) tmem_ld16_nowait(tbase + lanes + TM_I2 + 64 * h + 16 * i, v[i]);
+        tmem_wait_ld();
+        if (r >= 0) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const int cc = 64 * h + 16 * i + t - (K - 1);
-              if (cc >= 0) tile[r * (b + 1) + cc] = __uint_as_float(v[t]);
+              if (cc >= 0) tile[r * (b + 1) + cc] = __uint_as_float(v[i][t]);
             }
-          }
         }
         tc_fence_before();
         named_sync<NTW>();
@@ -626,7 +701,8 @@ void dft_constants(std::vector<uint8_t>& out) {
     }
 }
 
-// Spectra of the zero-padded PSFs, natural order [kr][kc], scaled by 1 / 128:
+// Half spectra of the zero-padded PSFs, kr = 0 .. 64 in the layout of SPSF,
+// scaled by 1 / 128:
 // Hh(kr, kc) = sum_{m, n < K} h(m, n) exp(-2 pi i (kr m + kc n) / 128) / 128,
 // summed in FP64 on the host and stored as FP16 (re, im) pairs.
 void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out) {
@@ -636,7 +712,7 @@ void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out) {
     cr[j] = std::cos(a);
     ci[j] = std::sin(a);
   }
-  out.assign((size_t)G * S * S, 0u);
+  out.assign((size_t)G * SPSF, 0u);
   std::vector<double> tr((size_t)K * S), ti((size_t)K * S);
   for (int g = 0; g < G; ++g) {
     const float* hp = psfs + (size_t)g * K * K;
@@ -651,7 +727,7 @@ void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out) {
         tr[(size_t)m * S + kc] = sr;
         ti[(size_t)m * S + kc] = si;
       }
-    for (int kr = 0; kr < S; ++kr)
+    for (int kr = 0; kr <= S / 2; ++kr)
       for (int kc = 0; kc < S; ++kc) {
         double sr = 0.0, si = 0.0;
         for (int m = 0; m < K; ++m) {
@@ -661,7 +737,8 @@ void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out) {
           si += ar * ci[j] + ai * cr[j];
         }
         const __half2 hv = __floats2half2_rn((float)(sr / S), (float)(si / S));
-        std::memcpy(&out[((size_t)g * S + kr) * S + kc], &hv, 4);
+        const size_t e = (size_t)g * SPSF + ((size_t)(2 * (kr >> 3) + ((kr >> 2) & 1)) * S + kc) * 4 + (kr & 3);
+        std::memcpy(&out[e], &hv, 4);
       }
   }
 }
