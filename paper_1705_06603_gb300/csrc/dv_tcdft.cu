@@ -389,22 +389,29 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
     // the observed image and weights of RB rows loaded before they are used
     auto write_out = [&](const WorkItem& wi, const TileDesc& td, const float* tile) {
       const int nr = min(b, td.nyr - wi.r0), nc = min(b, td.nyc - wi.c0);
+      float* const out = A.out + td.yoff + (int64_t)wi.r0 * td.ypitch + wi.c0;
+      const int64_t ypitch = td.ypitch;
+      const bool resid = A.mode != OP_PLAIN;
+      const float* const yb = A.y + (int64_t)(td.xr0 + wi.r0) * A.wy + td.xc0 + wi.c0;
+      const float* const wb = A.W ? A.W + (yb - A.y) : nullptr;
+      const int64_t wy = A.wy;
       constexpr int RB = 4, CB = S / 32;
       for (int il0 = warp; il0 < nr; il0 += RB * NWK) {
         float yo[RB][CB], wo[RB][CB];
+        if (resid) {
 #pragma unroll
-        for (int u = 0; u < RB; ++u)
+          for (int u = 0; u < RB; ++u)
 #pragma unroll
-          for (int v = 0; v < CB; ++v) {
-            const int il = il0 + u * NWK, jl = lane + 32 * v;
-            yo[u][v] = 0.f;
-            wo[u][v] = 1.f;
-            if (A.mode != OP_PLAIN && il < nr && jl < nc) {
-              const int64_t gi = (int64_t)(td.xr0 + wi.r0 + il) * A.wy + (td.xc0 + wi.c0 + jl);
-              yo[u][v] = __ldg(A.y + gi);
-              if (A.W) wo[u][v] = __ldg(A.W + gi);
+            for (int v = 0; v < CB; ++v) {
+              const int il = il0 + u * NWK, jl = lane + 32 * v;
+              yo[u][v] = 0.f;
+              wo[u][v] = 1.f;
+              if (il < nr && jl < nc) {
+                yo[u][v] = __ldg(yb + il * wy + jl);
+                if (wb) wo[u][v] = __ldg(wb + il * wy + jl);
+              }
             }
-          }
+        }
 #pragma unroll
         for (int u = 0; u < RB; ++u)
 #pragma unroll
@@ -412,8 +419,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
             const int il = il0 + u * NWK, jl = lane + 32 * v;
             if (il >= nr || jl >= nc) continue;
             const float x = tile ? tile[il * (b + 1) + jl] : 0.f;
-            A.out[td.yoff + (int64_t)(wi.r0 + il) * td.ypitch + wi.c0 + jl] =
-                A.mode == OP_PLAIN ? x : wo[u][v] * (x - yo[u][v]);
+            out[il * ypitch + jl] = resid ? wo[u][v] * (x - yo[u][v]) : x;
           }
       }
     };
@@ -454,6 +460,11 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         const int c = tid & (S - 1), half = tid >> 7;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+          if (i == 4) {   // first half complete: its k-steps can start
+            fence_async_smem();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) arrive(&H->xch[j]);
+          }
           const int pan = 2 * i + half;
           const uint4 xv = *reinterpret_cast<const uint4*>(sWin + pan * XPAN + 16 * c);
           const float4 w0 = *reinterpret_cast<const float4*>(wr + 8 * pan);
@@ -466,7 +477,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         }
         fence_async_smem();
 #pragma unroll
-        for (int i = 0; i < 8; ++i) arrive(&H->xch[i]);
+        for (int i = 4; i < 8; ++i) arrive(&H->xch[i]);
         if (last_use) arrive(&H->win_empty);
       };
       stage_x(wi.a_lo, na == 1);
@@ -488,6 +499,11 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
             tc_fence_before();
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
+              if (i == 4) {
+                fence_async_smem();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) arrive(&H->ych[j]);
+              }
               const int c0 = 16 * i + 8 * h;
               const float4 w0 = *reinterpret_cast<const float4*>(wc + c0);
               const float4 w1 = *reinterpret_cast<const float4*>(wc + c0 + 4);
@@ -498,7 +514,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
             }
             fence_async_smem();
 #pragma unroll
-            for (int i = 0; i < 8; ++i) arrive(&H->ych[i]);
+            for (int i = 4; i < 8; ++i) arrive(&H->ych[i]);
           }
           // the next row weight's X once F1 has been read for the last time
           if (bi == nb - 1 && ai + 1 < na) stage_x(wi.a_lo + ai + 1, ai + 2 == na);
