@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define DV_ABI_VERSION 2
+#define DV_ABI_VERSION 3
 
 typedef enum dv_status {
   DV_OK = 0,
@@ -179,12 +179,15 @@ typedef struct dv_problem {
    * (>= 0; dv_problem_init sets 1e-7, the resolution of the FP32-formed
    * objective; 0 runs every iteration) */
   double vm_stop_rel;
-  /* tensor-core path, BF16 allowed, the operator H of the inner iterations:
-   * 0 = whichever of the two forms below the plan-time autotuner finds faster,
-   * 1 = banded Toeplitz MMAs (BF16 operands), 2 = block DFT on the tensor
-   * cores: 128 x 128 overlap-save blocks transformed by dense DFT GEMMs with
-   * FP16 operands and FP32 accumulation, the PSF spectra applied between the
-   * forward and inverse transforms (K <= 97).  H^T always uses form 1. */
+  /* tensor-core path, BF16 allowed, the form of the operators H and H^T of
+   * the inner iterations: 0 = whichever of the forms below the plan-time
+   * autotuner finds fastest, 1 = banded Toeplitz MMAs (BF16 operands) for
+   * both, 2 = H as the block DFT and H^T banded, 3 = both as block DFTs.
+   * Block DFT: 128 x 128 overlap-save blocks of real data (each block scaled
+   * by a power of two into FP16 range) transformed by dense half-spectrum
+   * DFT GEMMs with FP16 operands and FP32 accumulation, the PSF spectra
+   * (conjugated for H^T) applied between the forward and inverse transforms
+   * (K in 9, 15, 31, 63). */
   int32_t tensor_h;
   int32_t reserved;
 } dv_problem;
@@ -319,6 +322,11 @@ typedef struct dv_plan_info {
   int32_t tensor_h_dft;
   /* autotuner: one block-DFT H + one banded H^T (0 if not timed) */
   double tune_ms_tensor_dft;
+  /* 1 when H^T runs as the block DFT too (dv_problem.tensor_h) */
+  int32_t tensor_ht_dft;
+  int32_t reserved_info;
+  /* autotuner: one block-DFT H + one block-DFT H^T (0 if not timed) */
+  double tune_ms_tensor_dft2;
 } dv_plan_info;
 
 dv_status dv_plan_get_info(const dv_plan* plan, dv_plan_info* info);

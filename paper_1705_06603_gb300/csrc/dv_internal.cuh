@@ -206,6 +206,8 @@ cudaError_t dft_prepare();
 void dft_constants(std::vector<uint8_t>& out);
 void dft_spectra(const float* psfs, int G, int K, std::vector<uint32_t>& out);
 cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid);
+cudaError_t launch_dft_Ht(const OpArgs& a, cudaStream_t s, int grid);
+int dft_Ht_kernels(int mode);   // kernels one block-DFT H^T launch runs
 
 // Tensor-core path (tcgen05, BF16 / TF32 operands; its own work tables)
 int tc_block_m();
@@ -304,6 +306,7 @@ struct dv_plan {
   bool fft_ok = false;
   bool dft_ok = false;             // H as the block DFT on the tensor cores is available
   bool dft_H = false;              // ... and used by the tensor path
+  bool dft_Ht = false;             // H^T as the block DFT on the tensor path
   uint32_t* d_dspec = nullptr;     // its PSF spectra [G][128][128] (FP16 pairs), natural order, / 128
   unsigned char* d_dconst = nullptr;  // its constant operand [Fr; Fi] (FP16 panels)
   int* d_dcounter = nullptr;       // its work counters: [0] whole launches, [1 + g] group g
@@ -318,6 +321,7 @@ struct dv_plan {
   int test_fault = 0;                 // dv_plan_set_test_fault kind
   double tune_ms[3] = {0.0, 0.0, 0.0};  // autotuner: one H + one H^T apply per path
   double tune_ms_dft = 0.0;             // ... tensor path with H as the block DFT
+  double tune_ms_dft2 = 0.0;            // ... tensor path with H and H^T as block DFTs
   dv_cnn* cnn = nullptr;           // warm-start network (borrowed)
   float* d_desc = nullptr;         // per-PSF descriptors [G][3]
   float* d_feat = nullptr;         // warm-start features [nx][5] (lazy)

@@ -248,8 +248,8 @@ dv_status validate_and_layout(const dv_problem* p, Layout& L) {
     return fail(DV_ERR_INVALID_ARG, "vm_memory must be in [0, 32] (0: 5)");
   if (!(p->vm_stop_rel >= 0.0) || !std::isfinite(p->vm_stop_rel))
     return fail(DV_ERR_INVALID_ARG, "vm_stop_rel must be finite and >= 0");
-  if (p->tensor_h < 0 || p->tensor_h > 2)
-    return fail(DV_ERR_INVALID_ARG, "tensor_h must be 0, 1 or 2");
+  if (p->tensor_h < 0 || p->tensor_h > 3)
+    return fail(DV_ERR_INVALID_ARG, "tensor_h must be 0, 1, 2 or 3");
   if (!(p->noise_sigma >= 0.0)) return fail(DV_ERR_INVALID_ARG, "noise_sigma must be >= 0");
 
   const int K = p->K, nxr = p->hy + K - 1, nxc = p->wy + K - 1;
@@ -399,8 +399,9 @@ static int tab_index(int path) {
 
 int tab_index_of(int path) { return tab_index(path); }
 
-// H as the block DFT: the tensor path with dft_H set
+// H / H^T as the block DFT: the tensor path with dft_H / dft_Ht set
 static bool dft_h(const dv_plan* p, int path) { return path == DV_PATH_TENSOR && p->dft_H; }
+static bool dft_ht(const dv_plan* p, int path) { return path == DV_PATH_TENSOR && p->dft_Ht; }
 
 dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, float* out,
                      bool global) {
@@ -446,7 +447,7 @@ dv::OpArgs op_args_H(const dv_plan* p, int path, int mode, const float* in, floa
 dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, float* out,
                       bool global, const float* w, const float* u) {
   OpArgs a = op_args_H(p, path, mode, in, out, global);
-  const OpTables& tb = p->tab[tab_index(path)];
+  const OpTables& tb = p->tab[dft_ht(p, path) ? 1 : tab_index(path)];
   a.spec = p->d_spec;
   a.tiles = global ? p->d_gtile : p->d_tiles;
   a.work = global ? tb.Htg : tb.Ht;
@@ -459,6 +460,14 @@ dv::OpArgs op_args_Ht(const dv_plan* p, int path, int mode, const float* in, flo
   a.u = u;
   a.omr = p->d_omr;
   a.omc = p->d_omc;
+  if (dft_ht(p, path)) {
+    // block DFT: the block FFT's H^T work items; the counters of the H
+    // launches (a group's H and H^T run in order on its stream)
+    a.ksr = nullptr;
+    a.spec = reinterpret_cast<const float2*>(p->d_dspec);
+    a.tcop = p->d_dconst;
+    a.counter = p->d_dcounter;
+  }
   return a;
 }
 
@@ -470,6 +479,7 @@ cudaError_t launch_op_H(const dv_plan* P, int path, const OpArgs& a, cudaStream_
 }
 
 cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream_t s) {
+  if (dft_ht(P, path)) return launch_dft_Ht(a, s, a.ctas > 0 ? a.ctas : P->n_sm);
   if (path == DV_PATH_TENSOR)
     return P->prob.precision == DV_PREC_BF16 ? launch_tcT_Ht(a, s) : launch_tc_Ht(a, s);
   return path == DV_PATH_FFT ? launch_fft_Ht(a, s, P->n_sm) : launch_direct_Ht(a, s);
@@ -478,7 +488,7 @@ cudaError_t launch_op_Ht(const dv_plan* P, int path, const OpArgs& a, cudaStream
 int obj_parts(const dv_plan* P) { return P->tab[tab_index(P->fpath)].nH; }
 
 dv::OpArgs group_args(const dv_plan* p, int path, dv::OpArgs a, bool adjoint, int g) {
-  const bool dft = !adjoint && dft_h(p, path);
+  const bool dft = adjoint ? dft_ht(p, path) : dft_h(p, path);
   const OpTables& tb = p->tab[dft ? 1 : tab_index(path)];
   const int* b = adjoint ? tb.gHt : tb.gH;
   a.work += b[g];
@@ -588,18 +598,24 @@ static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
     if (P->tune_ms[1] < P->tune_ms[0]) P->fpath = DV_PATH_FFT;
   }
   P->path = P->fpath;
-  // the tensor path's H: banded Toeplitz MMAs or the block DFT (tensor_h)
+  // the tensor path's forms: banded Toeplitz MMAs for H and H^T, the block
+  // DFT for H, or the block DFT for both (tensor_h)
   auto tensor_form = [&]() -> dv_status {
-    P->dft_H = false;
+    P->dft_H = P->dft_Ht = false;
     if (!P->dft_ok) return DV_OK;
-    if (P->prob.tensor_h == 2) {
+    if (P->prob.tensor_h >= 2) {
       P->dft_H = true;
+      P->dft_Ht = P->prob.tensor_h == 3;
       return DV_OK;
     }
     if (P->tune_ms[2] == 0.0) DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms[2]));
     P->dft_H = true;
     DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms_dft));
-    P->dft_H = P->tune_ms_dft < P->tune_ms[2];
+    P->dft_Ht = true;
+    DV_TRY(time_path(P, DV_PATH_TENSOR, s, P->tune_ms_dft2));
+    const double best = std::min(P->tune_ms[2], std::min(P->tune_ms_dft, P->tune_ms_dft2));
+    P->dft_Ht = best == P->tune_ms_dft2;
+    P->dft_H = P->dft_Ht || best == P->tune_ms_dft;
     return DV_OK;
   };
   if (requested == DV_PATH_TENSOR) {
@@ -610,9 +626,9 @@ static dv_status choose_path(dv_plan* P, int requested, cudaStream_t s) {
     DV_TRY(tensor_form());
     const double fp32_ms = P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0];
     if (fp32_ms == 0.0) DV_TRY(time_path(P, P->fpath, s, P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]));
-    const double t_ms = P->dft_H ? P->tune_ms_dft : P->tune_ms[2];
+    const double t_ms = P->dft_Ht ? P->tune_ms_dft2 : (P->dft_H ? P->tune_ms_dft : P->tune_ms[2]);
     if (t_ms < P->tune_ms[P->fpath == DV_PATH_FFT ? 1 : 0]) P->path = DV_PATH_TENSOR;
-    else P->dft_H = false;
+    else P->dft_H = P->dft_Ht = false;
   }
   return DV_OK;
 }
@@ -626,12 +642,12 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
     return fail(DV_ERR_UNSUPPORTED, "the tensor-core operator supports K = 9, 15, 31, 63");
   if (prob->path == DV_PATH_FFT && !fft_supported(prob->K))
     return fail(DV_ERR_UNSUPPORTED, "the FFT operator path needs K <= %d", fft_size() - 31);
-  if (prob->tensor_h == 2 && (prob->precision != DV_PREC_BF16 || !dft_supported(prob->K) ||
+  if (prob->tensor_h >= 2 && (prob->precision != DV_PREC_BF16 || !dft_supported(prob->K) ||
                               !tc_supported(prob->K) || prob->path == DV_PATH_DIRECT ||
                               prob->path == DV_PATH_FFT))
     return fail(DV_ERR_UNSUPPORTED,
-                "the block-DFT form of H needs the tensor-core path with BF16 allowed and "
-                "K in 9, 15, 31, 63");
+                "the block-DFT forms of H and H^T need the tensor-core path with BF16 allowed "
+                "and K in 9, 15, 31, 63");
 
   P->prob = *prob;
   P->vm_m = prob->vm_memory > 0 ? prob->vm_memory : 5;
@@ -1058,12 +1074,20 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->mma_ksteps[1] = P->tab[k].ksteps[1];
   info->tile_groups = (P->ngrp > 1 && P->path == DV_PATH_TENSOR) ? P->ngrp : 1;
   info->tensor_h_dft = P->path == DV_PATH_TENSOR && P->dft_H ? 1 : 0;
+  info->tensor_ht_dft = P->path == DV_PATH_TENSOR && P->dft_Ht ? 1 : 0;
   info->tune_ms_tensor_dft = P->tune_ms_dft;
+  info->tune_ms_tensor_dft2 = P->tune_ms_dft2;
   if (info->tensor_h_dft) {
     info->blocks[0] = P->tab[1].nH;
     info->block_psfs[0] = P->tab[1].psfs[0];
     info->psf_pairs[0] = P->tab[1].pairs[0];
     info->mma_ksteps[0] = 0;
+  }
+  if (info->tensor_ht_dft) {
+    info->blocks[1] = P->tab[1].nHt;
+    info->block_psfs[1] = P->tab[1].psfs[1];
+    info->psf_pairs[1] = P->tab[1].pairs[1];
+    info->mma_ksteps[1] = 0;
   }
   info->block_side = k == 1 ? fft_block(P->K)
                             : (k == 2 ? (P->prob.precision == DV_PREC_BF16 ? tcT_max_rows(P->K)

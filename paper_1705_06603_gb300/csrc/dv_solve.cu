@@ -68,6 +68,11 @@ dv_status timed_launch(dv_plan* P, int kind, cudaStream_t s, F fn) {
   return DV_OK;
 }
 
+// kernels one inner-iteration H^T launch runs (the block DFT adds its step kernel)
+static int ht_kernels(const dv_plan* P) {
+  return P->path == DV_PATH_TENSOR && P->dft_Ht ? dft_Ht_kernels(OP_STEP) : 1;
+}
+
 cudaError_t launch_inner_H(dv_plan* P, int par, cudaStream_t s) {
   return launch_op_H(P, P->path, op_args_H(P, P->path, OP_RESID, P->d_w[par], P->d_r, false), s);
 }
@@ -267,7 +272,7 @@ dv_status launch_graph(dv_plan* P, GraphEntry* g, cudaStream_t s) {
     }
   }
   DV_TRY_CUDA(cudaGraphLaunch(g->exec, s));
-  P->launches += 2 * g->n_inner * (grouped(P) ? P->ngrp : 1) + ((g->cons & 1) ? 1 : 0) +
+  P->launches += (1 + ht_kernels(P)) * g->n_inner * (grouped(P) ? P->ngrp : 1) + ((g->cons & 1) ? 1 : 0) +
                  ((g->cons & 8) ? kObjLaunches : 0);
   return DV_OK;
 }
@@ -292,6 +297,7 @@ dv_status local_solve(dv_plan* P, int n_inner, cudaStream_t s) {
     for (int i = 0; i < n_inner; ++i) {
       DV_TRY(timed_launch(P, KIND_H, s, [&](cudaStream_t st) { return launch_inner_H(P, par, st); }));
       DV_TRY(timed_launch(P, KIND_HT, s, [&](cudaStream_t st) { return launch_inner_Ht(P, par, st); }));
+      P->launches += ht_kernels(P) - 1;
       par ^= 1;
     }
   }

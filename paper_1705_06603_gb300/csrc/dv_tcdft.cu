@@ -81,9 +81,11 @@ constexpr int SMEM_D = OFF_WV + 4 * S * 4;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t TM_F1 = 0, TM_P = 128, TM_Q = 256, TM_SUM = 384;   // D columns
 constexpr uint32_t TM_I1 = 128, TM_I2 = 384;
+constexpr uint32_t TMT_I2 = 0, TMT_G = 384;   // H^T: I2 (summed over row weights), H^T r
 static_assert(SMEM_D <= 227 * 1024, "shared memory");
 static_assert(IPANELS * IPAN <= 2 * XBYTES, "I1 operand fits in the X and Y buffers");
 static_assert(S * (S + 1) * 4 <= 2 * XBYTES, "output tile fits in the X and Y buffers");
+static_assert(64 * 129 * 4 <= 2 * XBYTES, "H^T output band fits in the X and Y buffers");
 static_assert(OFF_Y == OFF_X + XBYTES, "X and Y buffers are contiguous");
 static_assert(CPAN % 16 == 0 && XPAN % 16 == 0 && IPAN % 16 == 0 && OFF_WV % 16 == 0, "alignment");
 
@@ -97,6 +99,9 @@ struct BarsD {
   int mbox[2];                            // na, nb of the next block for the MMA warp (na < 0: stop)
   int item[2];                            // work item of a slot (-1: stop)
   int next_item;                          // the loaders' next claimed item
+  uint32_t lmax[NLW];                     // the loader warps' largest |window value| (bits)
+  float wscale[2];                        // 2^e: the output factor of a slot's window
+  float sscale[2];                        // 2^-e or 1: the staging factor (1 if stored scaled)
 };
 static_assert(sizeof(BarsD) <= kHdrD, "barrier header");
 
@@ -125,7 +130,8 @@ __device__ __forceinline__ bool loader_all(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
+template <bool ADJ>
+__global__ void __launch_bounds__(NT, 1) dft_kernel(const OpArgs A) {
   extern __shared__ __align__(1024) unsigned char smem[];
   BarsD* H = reinterpret_cast<BarsD*>(smem);
   unsigned char* sC = smem + OFF_C;
@@ -172,9 +178,15 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
   if (warp >= WLOAD) {
     // --------------------------------------------------------------- loaders
     // loader warp lw takes panels q = lw, lw + 3, .. of the window; warp 0
-    // claims the items, warps 1 and 2 fetch the row / column tables
+    // claims the items, warps 1 and 2 fetch the row / column tables.  The
+    // window is H's x below the output block, or H^T's r from K - 1 rows and
+    // columns above and left of it (zero outside the tile), in FP16 as loaded
+    // while its largest magnitude m = f 2^e (f in [0.5, 1)) is found; the
+    // staging warps multiply by 2^-e (exact) and the output by 2^e.  Outside
+    // [2^-10, 2^15) a second pass stores the window times 2^-e instead.
     const int lw = warp - WLOAD;
     auto psfs = [](const WorkItem& w2) { return (w2.a_hi - w2.a_lo + 1) * (w2.b_hi - w2.b_lo + 1); };
+    const int off = ADJ ? K - 1 : 0;
     int it = 0;
     if (lw == 0 && lane == 0) it = atomicAdd(A.counter, 1);
     for (uint32_t n = 0; !A.test_withhold; ++n) {
@@ -200,8 +212,9 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
       const TileDesc& t2 = tds[slot];
       if (psfs(w2) > 0) {
         if (lw > 0) {
-          // interpolation table of the window's rows (lw = 1) or columns ({-2, 0, 0}
-          // outside the tile: no grid index has a weight there)
+          // interpolation table of the rows (lw = 1) or columns of the window
+          // of H / the output block of H^T ({-2, 0, 0} outside the tile: no
+          // grid index has a weight there)
           WTab* tab = sTab + slot * 2 * S + (lw - 1) * S;
           for (int e = lane; e < S; e += 32) {
             WTab v{-2, 0.f, 0.f, 0};
@@ -210,103 +223,165 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
             tab[e] = v;
           }
         }
-        // the window as x^T in FP16: row c, 8 consecutive r per 16 bytes;
-        // two panels (64 loads) in flight a lane, 8-byte loads where aligned
-        const float* img = A.in + t2.xoff;
-        const bool al2 = ((reinterpret_cast<uintptr_t>(img + w2.c0) & 7) == 0) && (t2.xpitch % 2 == 0);
-        for (int q0 = lw; q0 < S / 8; q0 += 2 * NLW) {
-          const bool two = q0 + NLW < S / 8;
-          if (al2) {
-            float2 v[2][2][8];
+        // the window as (scaled) v^T in FP16: row c, 8 consecutive r per 16
+        // bytes; two panels (64 loads) in flight a lane, 8-byte loads where
+        // aligned
+        const float* img = A.in + (ADJ ? t2.yoff : t2.xoff);
+        const int64_t pitch = ADJ ? t2.ypitch : t2.xpitch;
+        const int nrow = ADJ ? t2.nyr : t2.nxr, ncol = ADJ ? t2.nyc : t2.nxc;
+        const int wr0 = w2.r0 - off, wc0 = w2.c0 - off;
+        const bool al2 = ((reinterpret_cast<uintptr_t>(img + wc0) & 7) == 0) && (pitch % 2 == 0);
+        float sc = 1.f;
+        uint32_t mx = 0;   // bits of the largest magnitude (monotonic for |v|)
+        int e = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int q0 = lw; q0 < S / 8; q0 += 2 * NLW) {
+            const bool two = q0 + NLW < S / 8;
+            if (al2) {
+              float2 v[2][2][8];
 #pragma unroll
-            for (int qq = 0; qq < 2; ++qq)
+              for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-              for (int m = 0; m < 2; ++m)
+                for (int m = 0; m < 2; ++m)
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                  const int R = w2.r0 + 8 * (q0 + qq * NLW) + t, C = w2.c0 + 2 * lane + 64 * m;
-                  const float* src = img + (int64_t)R * t2.xpitch + C;
-                  float2 u = make_float2(0.f, 0.f);
-                  if ((qq == 0 || two) && R < t2.nxr) {
-                    if (C + 1 < t2.nxc) u = __ldg(reinterpret_cast<const float2*>(src));
-                    else if (C < t2.nxc) u.x = __ldg(src);
+                  for (int t = 0; t < 8; ++t) {
+                    const int R = wr0 + 8 * (q0 + qq * NLW) + t, C = wc0 + 2 * lane + 64 * m;
+                    const float* src = img + (int64_t)R * pitch + C;
+                    float2 u = make_float2(0.f, 0.f);
+                    if ((qq == 0 || two) && R >= 0 && R < nrow && C >= 0) {
+                      if (C + 1 < ncol) u = __ldg(reinterpret_cast<const float2*>(src));
+                      else if (C < ncol) u.x = __ldg(src);
+                    }
+                    v[qq][m][t] = u;
                   }
-                  v[qq][m][t] = u;
-                }
+              if (pass == 0) {
 #pragma unroll
-            for (int qq = 0; qq < 2; ++qq) {
-              if (qq == 1 && !two) break;
-              const int q = q0 + qq * NLW;
+                for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-              for (int m = 0; m < 2; ++m) {
-                const int c = 2 * lane + 64 * m;
-                const float2* f = v[qq][m];
-                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * c) =
-                    make_uint4(pack_h2(f[0].x, f[1].x), pack_h2(f[2].x, f[3].x),
-                               pack_h2(f[4].x, f[5].x), pack_h2(f[6].x, f[7].x));
-                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (c + 1)) =
-                    make_uint4(pack_h2(f[0].y, f[1].y), pack_h2(f[2].y, f[3].y),
-                               pack_h2(f[4].y, f[5].y), pack_h2(f[6].y, f[7].y));
+                  for (int m = 0; m < 2; ++m)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                      mx = max(mx, max(__float_as_uint(fabsf(v[qq][m][t].x)),
+                                       __float_as_uint(fabsf(v[qq][m][t].y))));
               }
-            }
-          } else {
-            float v[2][4][8];
 #pragma unroll
-            for (int qq = 0; qq < 2; ++qq)
+              for (int qq = 0; qq < 2; ++qq) {
+                if (qq == 1 && !two) break;
+                const int q = q0 + qq * NLW;
 #pragma unroll
-              for (int m = 0; m < 4; ++m)
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                  const int R = w2.r0 + 8 * (q0 + qq * NLW) + t, C = w2.c0 + lane + 32 * m;
-                  v[qq][m][t] = ((qq == 0 || two) && R < t2.nxr && C < t2.nxc)
-                                    ? __ldg(img + (int64_t)R * t2.xpitch + C)
-                                    : 0.f;
+                for (int m = 0; m < 2; ++m) {
+                  const int c = 2 * lane + 64 * m;
+                  const float2* f = v[qq][m];
+                  *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * c) =
+                      make_uint4(pack_h2(sc * f[0].x, sc * f[1].x), pack_h2(sc * f[2].x, sc * f[3].x),
+                                 pack_h2(sc * f[4].x, sc * f[5].x), pack_h2(sc * f[6].x, sc * f[7].x));
+                  *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (c + 1)) =
+                      make_uint4(pack_h2(sc * f[0].y, sc * f[1].y), pack_h2(sc * f[2].y, sc * f[3].y),
+                                 pack_h2(sc * f[4].y, sc * f[5].y), pack_h2(sc * f[6].y, sc * f[7].y));
                 }
+              }
+            } else {
+              float v[2][4][8];
 #pragma unroll
-            for (int qq = 0; qq < 2; ++qq) {
-              if (qq == 1 && !two) break;
-              const int q = q0 + qq * NLW;
+              for (int qq = 0; qq < 2; ++qq)
 #pragma unroll
-              for (int m = 0; m < 4; ++m) {
-                const float* f = v[qq][m];
-                *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (lane + 32 * m)) =
-                    make_uint4(pack_h2(f[0], f[1]), pack_h2(f[2], f[3]), pack_h2(f[4], f[5]),
-                               pack_h2(f[6], f[7]));
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                  for (int t = 0; t < 8; ++t) {
+                    const int R = wr0 + 8 * (q0 + qq * NLW) + t, C = wc0 + lane + 32 * m;
+                    v[qq][m][t] = ((qq == 0 || two) && R >= 0 && R < nrow && C >= 0 && C < ncol)
+                                      ? __ldg(img + (int64_t)R * pitch + C)
+                                      : 0.f;
+                  }
+              if (pass == 0) {
+#pragma unroll
+                for (int qq = 0; qq < 2; ++qq)
+#pragma unroll
+                  for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) mx = max(mx, __float_as_uint(fabsf(v[qq][m][t])));
+              }
+#pragma unroll
+              for (int qq = 0; qq < 2; ++qq) {
+                if (qq == 1 && !two) break;
+                const int q = q0 + qq * NLW;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                  const float* f = v[qq][m];
+                  *reinterpret_cast<uint4*>(sWin + q * XPAN + 16 * (lane + 32 * m)) =
+                      make_uint4(pack_h2(sc * f[0], sc * f[1]), pack_h2(sc * f[2], sc * f[3]),
+                                 pack_h2(sc * f[4], sc * f[5]), pack_h2(sc * f[6], sc * f[7]));
+                }
               }
             }
           }
+          if (pass == 0) {
+            // the window's largest magnitude over the three loader warps
+            mx = __reduce_max_sync(0xffffffffu, mx);
+            if (lane == 0) H->lmax[lw] = mx;
+            loader_all(true);
+            mx = max(H->lmax[0], max(H->lmax[1], H->lmax[2]));
+            if (mx > 0 && mx < 0x7f800000u) frexpf(__uint_as_float(mx), &e);
+            const bool again = e < -9 || e > 15;
+            if (lw == 0 && lane == 0) {
+              H->wscale[slot] = ldexpf(1.f, e);
+              H->sscale[slot] = again ? 1.f : ldexpf(1.f, -e);
+            }
+            if (!again) break;
+            sc = ldexpf(1.f, -e);
+          }
         }
       }
+      fence_async_smem();   // the window is an MMA operand (H^T) / staged from (H)
       __syncwarp();
       if (lane == 0) mbar_arrive(&H->win_full);
-      // the next item's window and residual rows into L2 while this block runs
+      // the next item's window and output-block rows into L2 while this block runs
       const int it2 = H->next_item;
       if (lw == 0) it = it2;
       if (it2 < A.n_work) {
         const WorkItem w3 = A.work[it2];
         const TileDesc t3 = A.tiles[w3.tile];
+        const float* img = A.in + (ADJ ? t3.yoff : t3.xoff);
+        const int64_t pitch = ADJ ? t3.ypitch : t3.xpitch;
+        const int nrow = ADJ ? t3.nyr : t3.nxr, ncol = ADJ ? t3.nyc : t3.nxc;
+        const int wr0 = w3.r0 - off, wc0 = max(w3.c0 - off, 0);
         if (psfs(w3) > 0) {
-          const int c_end = min(w3.c0 + S, t3.nxc);
+          const int c_end = min(w3.c0 - off + S, ncol);
           for (int rr = 32 * lw + lane; rr < S; rr += 32 * NLW) {
-            const int R = w3.r0 + rr;
-            if (R >= t3.nxr || w3.c0 >= c_end) continue;
-            const float* row = A.in + t3.xoff + (int64_t)R * t3.xpitch;
-            for (int C = w3.c0; C < c_end; C += 32) prefetch_l2(row + C);
+            const int R = wr0 + rr;
+            if (R < 0 || R >= nrow || wc0 >= c_end) continue;
+            const float* row = img + (int64_t)R * pitch;
+            for (int C = wc0; C < c_end; C += 32) prefetch_l2(row + C);
             prefetch_l2(row + c_end - 1);
           }
-          if (A.mode != OP_PLAIN) {
-            const int j_end = min(w3.c0 + b, t3.nyc);
-            for (int rr = 32 * lw + lane; rr < b; rr += 32 * NLW) {
-              const int i = w3.r0 + rr;
-              if (i >= t3.nyr || w3.c0 >= j_end) continue;
-              const int64_t g0 = (int64_t)(t3.xr0 + i) * A.wy + t3.xc0;
-              for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.y + g0 + j);
-              prefetch_l2(A.y + g0 + j_end - 1);
-              if (A.W) {
-                for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.W + g0 + j);
-                prefetch_l2(A.W + g0 + j_end - 1);
-              }
+        }
+        if (!ADJ && A.mode != OP_PLAIN) {
+          const int j_end = min(w3.c0 + b, t3.nyc);
+          for (int rr = 32 * lw + lane; rr < b; rr += 32 * NLW) {
+            const int i = w3.r0 + rr;
+            if (i >= t3.nyr || w3.c0 >= j_end) continue;
+            const int64_t g0 = (int64_t)(t3.xr0 + i) * A.wy + t3.xc0;
+            for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.y + g0 + j);
+            prefetch_l2(A.y + g0 + j_end - 1);
+            if (A.W) {
+              for (int j = w3.c0; j < j_end; j += 32) prefetch_l2(A.W + g0 + j);
+              prefetch_l2(A.W + g0 + j_end - 1);
             }
+          }
+        }
+        if (ADJ && A.mode != OP_PLAIN) {
+          // the iterate's rows r0 - 1 .. r0 + b and the dual's rows r0 .. r0 + b - 1
+          const int c0 = max(w3.c0 - 1, 0), j_end = min(w3.c0 + b + 1, t3.nxc);
+          for (int rr = 32 * lw + lane; rr < b + 2; rr += 32 * NLW) {
+            const int R = w3.r0 - 1 + rr;
+            if (R < 0 || R >= t3.nxr || c0 >= j_end) continue;
+            const int64_t g0 = t3.xoff + (int64_t)R * t3.xpitch;
+            for (int j = c0; j < j_end; j += 32) {
+              prefetch_l2(A.w + g0 + j);
+              prefetch_l2(A.u + g0 + j);
+            }
+            prefetch_l2(A.w + g0 + j_end - 1);
+            prefetch_l2(A.u + g0 + j_end - 1);
           }
         }
       }
@@ -322,6 +397,50 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         tc_fence_after();
         return true;
       };
+      if constexpr (ADJ) {
+        const uint32_t aWin = saddr(sWin);
+        uint32_t ph_s = 0, ph_u = 0;
+        while (ok) {
+          if (!(ok = wt(&H->xch[0], ph_x))) break;
+          const int na = H->mbox[0], nb = H->mbox[1];
+          if (na < 0) break;
+          // F1 on the window as loaded, F2 into P, Q
+          for (int i = 0; i < 8 && ok; ++i) {
+            if (i > 0 && !(ok = wt(&H->xch[i], ph_x))) break;
+            kstep(tbase + TM_F1, aA1, XPAN, aWin, XPAN, id128, i, i > 0);
+          }
+          ++ph_x;
+          if (!ok) break;
+          tc_commit(&H->f1_done);
+          for (int i = 0; i < 8 && ok; ++i) {
+            if (!(ok = wt(&H->ych[i], ph_y))) break;
+            kstep(tbase + TM_P, aC, CPAN, aY, XPAN, id128, i, i > 0);
+            kstep(tbase + TM_Q, aC + 16 * S, CPAN, aY, XPAN, id128, i, i > 0);
+          }
+          ++ph_y;
+          if (!ok) break;
+          tc_commit(&H->f2_done);
+          // per PSF (column weight outer): I1, then I2 summed over the row weights
+          for (int bi = 0; bi < nb && ok; ++bi)
+            for (int ai = 0; ai < na && ok; ++ai) {
+              for (int i = 0; i < 5 && ok; ++i) {
+                if (!(ok = wt(&H->sch[i], ph_s))) break;
+                kstep(tbase + TM_I1, aC, CPAN, aX, IPAN, id256, i, i > 0);
+                kstep(tbase + TM_I1, aC + 16 * S, CPAN, aX + 16 * S, IPAN, id256, i, true);
+              }
+              ++ph_s;
+              if (!ok) break;
+              tc_commit(&H->i1_done);
+              for (int i = 0; i < 8 && ok; ++i) {
+                if (!(ok = wt(&H->uch[i], ph_u))) break;
+                kstep(tbase + TMT_I2, aX, XPAN, aC, CPAN, id128, i, ai > 0 || i > 0);
+                kstep(tbase + TMT_I2, aY, XPAN, aC + 16 * S, CPAN, id128, i, true);
+              }
+              ++ph_u;
+              if (ok) tc_commit(&H->i2_done);
+            }
+        }
+      } else {
       while (ok) {
         if (!(ok = wt(&H->xch[0], ph_x))) break;
         const int na = H->mbox[0], nb = H->mbox[1];
@@ -365,6 +484,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         if (!ok) break;
         tc_commit(&H->i2_done);
         ++ph_b;
+      }
       }
     }
   } else {
@@ -424,6 +544,237 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
       }
     };
 
+    if constexpr (ADJ) {
+      uint32_t ph_i1 = 0, ph_i2 = 0;
+      while (ok) {
+        if (!wait_all(&H->win_full, nblk)) break;
+        const int slot = nblk & 1;
+        ++nblk;
+        if (H->item[slot] < 0) {
+          // stop: tell the MMA warp
+          if (tid == 0) H->mbox[0] = -1;
+          arrive(&H->xch[0]);
+          break;
+        }
+        const WorkItem& wi = wis[slot];
+        const TileDesc& td = tds[slot];
+        const int na = wi.a_hi - wi.a_lo + 1, nb = wi.b_hi - wi.b_lo + 1;
+        const WTab* tr = sTab + slot * 2 * S;
+        const WTab* tc = tr + S;
+        const bool any = na * nb > 0;
+        if (any) {
+          if (tid == 0) {
+            H->mbox[0] = na;
+            H->mbox[1] = nb;
+          }
+          // the window, as the loaders staged it, is F1's operand; F1's
+          // result is scaled by the staging factor when Y' is staged
+          const float sst = H->sscale[slot];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) arrive(&H->xch[i]);
+          if (!wait_all(&H->f1_done, ph_f1++)) break;
+          arrive(&H->win_empty);
+          // Y' into sY (rows j, K = c), released in two halves
+#pragma unroll
+          for (int i0 = 0; i0 < 8; i0 += 4) {
+            uint32_t v[4][8];
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) tmem_ld8_nowait(tbase + lanes + TM_F1 + 16 * (i0 + ii) + 8 * h, v[ii]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+              const float* f = reinterpret_cast<const float*>(v[ii]);
+              *reinterpret_cast<uint4*>(sY + (2 * (i0 + ii) + h) * XPAN + 16 * L) =
+                  make_uint4(pack_h2(sst * f[0], sst * f[1]), pack_h2(sst * f[2], sst * f[3]),
+                             pack_h2(sst * f[4], sst * f[5]), pack_h2(sst * f[6], sst * f[7]));
+            }
+            fence_async_smem();
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) arrive(&H->ych[i0 + ii]);
+          }
+          tc_fence_before();
+          if (!wait_all(&H->f2_done, ph_f2++)) break;
+          // Z(k)[kc = L] / 128 from P and Q, kept as FP16 pairs: k = 16 i + 8 h + t
+          // at index 8 i + t, and k = 64 (h == 0)
+          uint32_t zh[32], z64 = 0;
+#pragma unroll
+          for (int i0 = 0; i0 < 4; i0 += 2) {
+            uint32_t pv[2][16], qv[2][16];
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii) {
+              tmem_ld16_nowait(tbase + lanes + TM_P + 32 * (i0 + ii) + 16 * h, pv[ii]);
+              tmem_ld16_nowait(tbase + lanes + TM_Q + 32 * (i0 + ii) + 16 * h, qv[ii]);
+            }
+            tmem_wait_ld();
+            const float is = 1.f / S;
+            if (i0 == 0) z64 = pack_h2(is * __uint_as_float(pv[0][1]), is * __uint_as_float(qv[0][1]));
+#pragma unroll
+            for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                const float pr = __uint_as_float(pv[ii][2 * t]), pi = __uint_as_float(pv[ii][2 * t + 1]);
+                const float qr = __uint_as_float(qv[ii][2 * t]), qi = __uint_as_float(qv[ii][2 * t + 1]);
+                const bool k0 = i0 + ii == 0 && t == 0 && h == 0;   // Y(0) real; column 1 holds Y(64)
+                zh[8 * (i0 + ii) + t] = pack_h2(is * (k0 ? pr : pr - qi), is * (k0 ? qr : qr + pi));
+              }
+          }
+          tc_fence_before();   // P and Q have been read: I1 may overwrite them
+          for (int bi = 0; bi < nb && ok; ++bi) {
+            const int gb = wi.b_lo + bi;
+            float* wc = sWc + (nwc++ & 1) * S;
+            if (tid >= S) wc[tid - S] = wsel(tc[tid - S], gb);
+            for (int ai = 0; ai < na && ok; ++ai) {
+              const int ga = wi.a_lo + ai;
+              float* wr = sWr + (nwr++ & 1) * S;
+              if (tid < S) wr[tid] = wsel(tr[tid], ga);
+              named_sync<NTW>();
+              const unsigned int* hs = spec + (size_t)(ga * A.Gc + gb) * SPSF + 4 * L;
+              uint32_t hv[33];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const int g = 2 * i + h;
+                const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(hs + (2 * g) * S * 4));
+                const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(hs + (2 * g + 1) * S * 4));
+                hv[8 * i + 0] = u0.x; hv[8 * i + 1] = u0.y; hv[8 * i + 2] = u0.z; hv[8 * i + 3] = u0.w;
+                hv[8 * i + 4] = u1.x; hv[8 * i + 5] = u1.y; hv[8 * i + 6] = u1.z; hv[8 * i + 7] = u1.w;
+              }
+              hv[32] = h == 0 ? __ldg(hs + 16 * S * 4) : 0u;
+              // T = alpha Z conj(Hh) (correlation) into the I1 operand rows kc:
+              // [aTr; aTi; -aTr], 5 chunks of 16 k (panel 2 i + h), two releases
+#pragma unroll
+              for (int i = 0; i < 5; ++i) {
+                if (i == 2) {
+                  fence_async_smem();
+                  arrive(&H->sch[0]);
+                  arrive(&H->sch[1]);
+                }
+                float ar[8], ai_[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                  float2 z, hf;
+                  float al;
+                  if (i < 4) {
+                    z = unpack_h2(zh[8 * i + t]);
+                    hf = unpack_h2(hv[8 * i + t]);
+                    al = (i == 0 && t == 0 && h == 0) ? 1.f : 2.f;
+                  } else {
+                    const bool k64 = t == 0 && h == 0;
+                    z = k64 ? unpack_h2(z64) : make_float2(0.f, 0.f);
+                    hf = k64 ? unpack_h2(hv[32]) : make_float2(0.f, 0.f);
+                    al = 1.f;
+                  }
+                  ar[t] = al * fmaf(z.x, hf.x, z.y * hf.y);
+                  ai_[t] = al * fmaf(z.y, hf.x, -z.x * hf.y);
+                }
+                unsigned char* dst = sX + (2 * i + h) * IPAN + 16 * L;
+                *reinterpret_cast<uint4*>(dst) =
+                    make_uint4(pack_h2(ar[0], ar[1]), pack_h2(ar[2], ar[3]), pack_h2(ar[4], ar[5]),
+                               pack_h2(ar[6], ar[7]));
+                *reinterpret_cast<uint4*>(dst + 16 * S) =
+                    make_uint4(pack_h2(ai_[0], ai_[1]), pack_h2(ai_[2], ai_[3]), pack_h2(ai_[4], ai_[5]),
+                               pack_h2(ai_[6], ai_[7]));
+                *reinterpret_cast<uint4*>(dst + 32 * S) =
+                    make_uint4(pack_h2(-ar[0], -ar[1]), pack_h2(-ar[2], -ar[3]), pack_h2(-ar[4], -ar[5]),
+                               pack_h2(-ar[6], -ar[7]));
+              }
+              fence_async_smem();
+#pragma unroll
+              for (int i = 2; i < 5; ++i) arrive(&H->sch[i]);
+              if (!wait_all(&H->i1_done, ph_i1++)) break;
+              // U (lane r) times wr_a(r) into the I2 operands Ur (sX) and Ui (sY)
+              const float wrr = wr[L];
+#pragma unroll
+              for (int i0 = 0; i0 < 8; i0 += 4) {
+                uint32_t ur[4][8], ui[4][8];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  tmem_ld8_nowait(tbase + lanes + TM_I1 + 16 * (i0 + i) + 8 * h, ur[i]);
+                  tmem_ld8_nowait(tbase + lanes + TM_I1 + S + 16 * (i0 + i) + 8 * h, ui[i]);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const float* fr = reinterpret_cast<const float*>(ur[i]);
+                  const float* fi = reinterpret_cast<const float*>(ui[i]);
+                  const int o = (2 * (i0 + i) + h) * XPAN + 16 * L;
+                  *reinterpret_cast<uint4*>(sX + o) =
+                      make_uint4(pack_h2(wrr * fr[0], wrr * fr[1]), pack_h2(wrr * fr[2], wrr * fr[3]),
+                                 pack_h2(wrr * fr[4], wrr * fr[5]), pack_h2(wrr * fr[6], wrr * fr[7]));
+                  *reinterpret_cast<uint4*>(sY + o) =
+                      make_uint4(pack_h2(wrr * fi[0], wrr * fi[1]), pack_h2(wrr * fi[2], wrr * fi[3]),
+                                 pack_h2(wrr * fi[4], wrr * fi[5]), pack_h2(wrr * fi[6], wrr * fi[7]));
+                }
+                fence_async_smem();
+#pragma unroll
+                for (int i = 0; i < 4; ++i) arrive(&H->uch[i0 + i]);
+              }
+              tc_fence_before();
+              if (!wait_all(&H->i2_done, ph_i2++)) break;
+              if (ai == na - 1) {
+                // H^T r (+)= wc_b . sum_a (I2), columns c = 64 h + 16 i + t
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  uint32_t d[16], g[16];
+                  tmem_ld16_nowait(tbase + lanes + TMT_I2 + 64 * h + 16 * i, d);
+                  if (bi > 0) tmem_ld16_nowait(tbase + lanes + TMT_G + 64 * h + 16 * i, g);
+                  tmem_wait_ld();
+#pragma unroll
+                  for (int t = 0; t < 16; ++t) {
+                    const float v = wc[64 * h + 16 * i + t] * __uint_as_float(d[t]);
+                    d[t] = __float_as_uint(bi > 0 ? __uint_as_float(g[t]) + v : v);
+                  }
+                  tmem_st16_nowait(tbase + lanes + TMT_G + 64 * h + 16 * i, d);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+              }
+            }
+          }
+          if (!ok) break;
+        } else {
+          arrive(&H->win_empty);
+        }
+        // H^T r (times the window's scale; zero without PSFs) from tensor
+        // memory into an FP32 band of 64 output rows, then into the output
+        // (warp w rows w, w + 8, .., lanes columns); the projected-gradient
+        // step runs afterwards (dft_step_kernel)
+        const float scale = any ? H->wscale[slot] : 0.f;
+        constexpr int BH = 64, CB = S / 32;
+        const int TP = b + 1;
+        float* band = reinterpret_cast<float*>(sX);
+        const int nr = min(b, td.nxr - wi.r0), nc = min(b, td.nxc - wi.c0);
+        float* const out = A.out + td.xoff + (int64_t)wi.r0 * td.xpitch + wi.c0;
+        const int64_t xpitch = td.xpitch;
+        for (int i0 = 0; i0 < nr; i0 += BH) {
+          if (any && (32 * q4 == i0 || 32 * q4 == i0 + 32)) {
+            uint32_t v[4][16];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tmem_ld16_nowait(tbase + lanes + TMT_G + 64 * h + 16 * i, v[i]);
+            tmem_wait_ld();
+            const int rb = L - i0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int t = 0; t < 16; ++t) {
+                const int c = 64 * h + 16 * i + t;
+                if (c < b) band[rb * TP + c] = scale * __uint_as_float(v[i][t]);
+              }
+          } else if (!any) {
+            for (int e = tid; e < BH * TP; e += NTW) band[e] = 0.f;
+          }
+          tc_fence_before();
+          named_sync<NTW>();
+          const int iend = min(i0 + BH, nr);
+          for (int il = i0 + warp; il < iend; il += NWK)
+#pragma unroll
+            for (int v = 0; v < CB; ++v) {
+              const int jl = lane + 32 * v;
+              if (jl < nc) out[il * xpitch + jl] = band[(il - i0) * TP + jl];
+            }
+          named_sync<NTW>();   // the band is read before the next one is written
+        }
+      }
+    } else {
     while (ok) {
       if (!wait_all(&H->win_full, nblk)) break;
       const int slot = nblk & 1;
@@ -451,11 +802,12 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         H->mbox[0] = na;
         H->mbox[1] = nb;
       }
+      const float sst = H->sscale[slot];   // the window's staging factor
       // (wr_a x)^T into sX in 8 chunks of 16 r (panels 2i + half), a chunk
       // complete -> xch[i]
       auto stage_x = [&](int ga, bool last_use) {
         float* wr = sWr + (nwr++ & 1) * S;
-        if (tid < S) wr[tid] = wsel(tr[tid], ga);
+        if (tid < S) wr[tid] = wsel(tr[tid], ga) * sst;
         named_sync<NTW>();
         const int c = tid & (S - 1), half = tid >> 7;
 #pragma unroll
@@ -649,6 +1001,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
       {
         float* tile = reinterpret_cast<float*>(sX);
         const int r = L - (K - 1);
+        const float scale = H->wscale[slot];
         uint32_t v[4][16];
 #pragma unroll
         for (int i = 0; i < 4; ++i) tmem_ld16_nowait(tbase + lanes + TM_I2 + 64 * h + 16 * i, v[i]);
@@ -659,7 +1012,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
               const int cc = 64 * h + 16 * i + t - (K - 1);
-              if (cc >= 0) tile[r * (b + 1) + cc] = __uint_as_float(v[i][t]);
+              if (cc >= 0) tile[r * (b + 1) + cc] = scale * __uint_as_float(v[i][t]);
             }
         }
         tc_fence_before();
@@ -667,6 +1020,7 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
         write_out(wi, td, tile);
         named_sync<NTW>();   // the tile is read before the next block's X is staged
       }
+    }
     }
   }
 
@@ -684,12 +1038,58 @@ __global__ void __launch_bounds__(NT, 1) dft_H_kernel(const OpArgs A) {
   }
 }
 
+// The Local-Solver's projected-gradient step (the fused step of the other
+// H^T kernels) after the block-DFT H^T has written g = H^T r into the output:
+// w_next = max(0, w - tau (g + lambda D^T psi(D w) + alpha (w - u))), g read
+// in place.  One CTA per H^T output block (b x b x-pixels, the same work
+// items), the iterate's halo in shared memory; bound by HBM traffic.
+__global__ void __launch_bounds__(256) dft_step_kernel(const OpArgs A) {
+  extern __shared__ float sWs[];   // (b + 2)^2: iterate rows r0 - 1 .. r0 + b
+  const WorkItem wi = A.work[blockIdx.x];
+  const TileDesc td = A.tiles[wi.tile];
+  const int b = S - A.K + 1, HW = b + 2;
+  const int nr = min(b, td.nxr - wi.r0), nc = min(b, td.nxc - wi.c0);
+  if (nr <= 0 || nc <= 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int hr = warp; hr < nr + 2; hr += 8)
+    for (int hc = lane; hc < nc + 2; hc += 32) {
+      const int R = wi.r0 - 1 + hr, C = wi.c0 - 1 + hc;
+      sWs[hr * HW + hc] = (R >= 0 && R < td.nxr && C >= 0 && C < td.nxc)
+                              ? __ldg(A.w + td.xoff + (int64_t)R * td.xpitch + C)
+                              : 0.f;
+    }
+  __syncthreads();
+  for (int il = warp; il < nr; il += 8) {
+    const int R = wi.r0 + il;
+    const float orr = A.gamma * A.omr[td.omr_off + R];
+    for (int jl = lane; jl < nc; jl += 32) {
+      const int C = wi.c0 + jl;
+      const int64_t idx = td.xoff + (int64_t)R * td.xpitch + C;
+      const int li = il + 1, lj = jl + 1;
+      float pr, pc, pru, pcu, prl, pcl;
+      huber_p(sWs, HW, li, lj, R, C, td.nxr, td.nxc, A.delta, pr, pc);
+      huber_p(sWs, HW, li - 1, lj, R - 1, C, td.nxr, td.nxc, A.delta, pru, pcu);
+      huber_p(sWs, HW, li, lj - 1, R, C - 1, td.nxr, td.nxc, A.delta, prl, pcl);
+      const float hub = pru - pr + pcl - pc;
+      const float wv = sWs[li * HW + lj];
+      const float alpha = orr * A.omc[td.omc_off + C];
+      const float grad = A.out[idx] + A.lambda * hub + alpha * (wv - A.u[idx]);
+      A.out[idx] = fmaxf(0.f, wv - td.tau * grad);
+    }
+  }
+}
+
 }  // namespace
 
 bool dft_supported(int K) { return K >= 1 && S - K + 1 >= 32; }
 
 cudaError_t dft_prepare() {
-  return cudaFuncSetAttribute(dft_H_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D);
+  cudaError_t e = cudaFuncSetAttribute(dft_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(dft_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_D);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(dft_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (S + 2) * (S + 2) * (int)sizeof(float));
 }
 
 // Byte image of the constant operands, FP16 from FP64 on the host: [Fr; Fi]
@@ -763,8 +1163,25 @@ cudaError_t launch_dft_H(const OpArgs& a, cudaStream_t s, int grid) {
   if (a.n_work <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  dft_H_kernel<<<std::min(grid, a.n_work), NT, SMEM_D, s>>>(a);
+  dft_kernel<false><<<std::min(grid, a.n_work), NT, SMEM_D, s>>>(a);
   return cudaGetLastError();
 }
+
+// H^T r into the output, then (OP_STEP) the projected-gradient step in place
+cudaError_t launch_dft_Ht(const OpArgs& a, cudaStream_t s, int grid) {
+  if (a.n_work <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  OpArgs p = a;
+  p.mode = OP_PLAIN;
+  dft_kernel<true><<<std::min(grid, a.n_work), NT, SMEM_D, s>>>(p);
+  if (a.mode == OP_PLAIN) return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int b = S - a.K + 1;
+  dft_step_kernel<<<a.n_work, 256, (size_t)(b + 2) * (b + 2) * sizeof(float), s>>>(a);
+  return cudaGetLastError();
+}
+
+int dft_Ht_kernels(int mode) { return mode == OP_PLAIN ? 1 : 2; }
 
 }  // namespace dv

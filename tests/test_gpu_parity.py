@@ -358,6 +358,75 @@ def test_block_dft_H_matches_oracle(env, hy, wy, K, G):
     plan.close()
 
 
+@pytest.mark.parametrize("hy,wy,K,G", [(130, 70, 9, (3, 3)), (200, 180, 31, (4, 3)),
+                                       (150, 97, 63, (2, 2)), (66, 64, 15, (1, 1)),
+                                       (300, 260, 15, (8, 8)), (250, 301, 31, (5, 6)),
+                                       (331, 203, 63, (4, 3))])
+def test_block_dft_Ht_matches_oracle(env, hy, wy, K, G):
+    """H^T as the block DFT (tensor_h = 3): the correlation with each PSF on
+    128 x 128 blocks of the residual reaching K - 1 above and left of the output
+    block (zero outside the image), ragged edges, up to 3 x 3 PSFs per block,
+    at the BF16 operator tolerance; H is the block DFT too."""
+    torch, dv = env
+    g = np.random.default_rng(K + 3000)
+    psfs = random_psfs(g, G, K)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    r = g.standard_normal((hy, wy)).astype(np.float32)
+    x = g.uniform(0, 1, (nxr, nxc)).astype(np.float32)
+    plan = dv.Plan(hy, wy, psfs, precision=BF16, path=TENSOR, tensor_h=3)
+    assert plan.info.path == TENSOR and plan.info.tensor_h_dft == 1 and plan.info.tensor_ht_dft == 1
+    gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
+    yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
+    ps = psfs.astype(np.float64)
+    g_ref = O.apply_Ht(r.astype(np.float64), ps, wr, wc)
+    print(f"K {K} G {G}: H^T rel L2 {rel_l2(gd, g_ref):.3e}")
+    assert_close(gd, g_ref, TC_TOL[BF16])
+    assert_close(yd, O.apply_H(x.astype(np.float64), ps, wr, wc), TC_TOL[BF16])
+    plan.close()
+
+
+@pytest.mark.parametrize("mag", [1e-4, 3e3, 1e6])
+def test_block_dft_scales_each_block(env, mag):
+    """Inputs far from unit magnitude: each 128 x 128 block is scaled by a
+    power of two into FP16 range before the transforms, so H x and H^T r keep
+    the BF16 operator tolerance where unscaled FP16 operands would overflow
+    (1e6) or lose their low bits (1e-4)."""
+    torch, dv = env
+    hy, wy, K, G = 200, 180, 31, (4, 3)
+    g = np.random.default_rng(77)
+    psfs = random_psfs(g, G, K)
+    nxr, nxc = hy + K - 1, wy + K - 1
+    x = (mag * g.uniform(0, 1, (nxr, nxc))).astype(np.float32)
+    r = (mag * g.standard_normal((hy, wy))).astype(np.float32)
+    plan = dv.Plan(hy, wy, psfs, precision=BF16, path=TENSOR, tensor_h=3)
+    yd = plan.apply_H(torch.from_numpy(x).cuda()).cpu().numpy()
+    gd = plan.apply_Ht(torch.from_numpy(r).cuda()).cpu().numpy()
+    wr, wc = O.bilinear_weights(nxr, G[0]), O.bilinear_weights(nxc, G[1])
+    ps = psfs.astype(np.float64)
+    assert np.isfinite(yd).all() and np.isfinite(gd).all()
+    assert_close(yd, O.apply_H(x.astype(np.float64), ps, wr, wc), TC_TOL[BF16])
+    assert_close(gd, O.apply_Ht(r.astype(np.float64), ps, wr, wc), TC_TOL[BF16])
+    plan.close()
+
+
+def test_block_dft_both_solve_matches_oracle(env):
+    """The 128x128 workload at the plain iteration count with H and H^T as
+    block DFTs in the inner iterations (residual epilogue of H, projected
+    gradient step fused into H^T, tile groups in the captured graphs): within
+    the final-image bound 1e-3 of the oracle."""
+    w, psfs, y, _ = workload_case("disks128")
+    plan, xd, st = _gpu_solve(env, w, psfs, y, w.n_outer, w.n_inner, precision=BF16,
+                              path=TENSOR, tensor_h=3)
+    assert plan.info.tensor_h_dft == 1 and plan.info.tensor_ht_dft == 1
+    lay, xr, info = oracle_solve(w, psfs, y, w.n_outer, w.n_inner)
+    print(f"block-DFT H and H^T solve: x_hat rel L2 {rel_l2(xd, xr):.3e}")
+    assert_close(xd, xr, 1e-3)
+    F = O.objective(xr, y.astype(np.float64), psfs.astype(np.float64), lay, w.lam, w.delta)[0]
+    assert abs(st["objective"] - F) <= 1e-3 * F
+    plan.close()
+
+
 def test_block_dft_solve_matches_oracle(env):
     """The 128x128 workload at the plain iteration count with H as the block
     DFT in the inner iterations (residual epilogue, tile groups in the
