@@ -88,7 +88,7 @@ def parse():
     ap.add_argument("--inner", type=int, default=3,
                     help="projected-gradient steps per outer iteration of the chosen form "
                          "(0: the workload's count)")
-    ap.add_argument("--tensor-h", type=int, choices=[0, 1, 2], default=0,
+    ap.add_argument("--tensor-h", type=int, choices=[0, 1, 2, 3], default=0,
                     help="tensor-core H of the chosen form: 0 autotuned, 1 banded Toeplitz "
                          "(BF16), 2 block DFT (FP16)")
     ap.add_argument("--profile-case", action="store_true",
@@ -621,7 +621,8 @@ def run_ours(args):
             "config": {"workload": describe(w),
                        "chosen_form": "%s operator (operands >= %s; autotuned per H + H^T: "
                                       "direct %.3f ms, FFT %.3f ms, tensor %.3f ms, tensor with "
-                                      "block-DFT H %.3f ms; block-DFT H in use: %s), CUDA graph "
+                                      "block-DFT H %.3f ms, block-DFT H and H^T %.3f ms; "
+                                      "block-DFT H / H^T in use: %s / %s), CUDA graph "
                                       "per local solve (%d tile groups on concurrent streams), "
                                       "learned warm start (%d pairs of %d^2, %d Adam "
                                       "steps), %d projected-gradient steps per outer iteration, "
@@ -632,8 +633,9 @@ def run_ours(args):
                                       "target"
                                       % (pname, args.precision, info.tune_ms_direct,
                                          info.tune_ms_fft, info.tune_ms_tensor,
-                                         info.tune_ms_tensor_dft,
-                                         "yes" if info.tensor_h_dft else "no", info.tile_groups,
+                                         info.tune_ms_tensor_dft, info.tune_ms_tensor_dft2,
+                                         "yes" if info.tensor_h_dft else "no",
+                                         "yes" if info.tensor_ht_dft else "no", info.tile_groups,
                                          train_info["pairs"], train_info["pair_size"],
                                          args.ws_steps, args.inner or w.n_inner,
                                          chosen["gamma"], chosen["rho"], args.check_every),
@@ -676,9 +678,13 @@ def roofline(dv, w, plan, args, ktime, total_ms):
                                    if args.precision == "bf16" else
                                    (f"tc_H_kernel<1,{w.K}>", f"tc_Ht_kernel<1,{w.K}>"))}[path]
     dft_h = path == dv.DV_PATH_TENSOR and bool(info.tensor_h_dft)
+    dft_ht = path == dv.DV_PATH_TENSOR and bool(info.tensor_ht_dft)
     if dft_h:
-        kH = "dft_H_kernel"
-    names = {0: f"{kH} (H_i with residual)", 1: f"{kHt} (H_i^T + fused prox step)",
+        kH = "dft_kernel<false>"
+    if dft_ht:
+        kHt = "dft_kernel<true> + dft_step_kernel"
+    names = {0: f"{kH} (H_i with residual)",
+             1: f"{kHt} (H_i^T + {'prox step' if dft_ht else 'fused prox step'})",
              2: "consensus_kernel"}
     grouped = info.tile_groups > 1
     n_in = args.inner or w.n_inner
@@ -689,12 +695,15 @@ def roofline(dv, w, plan, args, ktime, total_ms):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     px = y_px if dom == 0 else x_px
-    # block-DFT H: per 128 x 128 block and active PSF the two forward DFT GEMM
-    # stages (2 x 2 x 128^3 and 2 x 2 x 128 x 256 x 128 flop), per block the two
-    # inverse stages (the same two sizes): the dense transform is this form's
-    # algorithm, so its GEMMs count as its work
-    dft_stage = 2.0 * 128 * 128 * 128
-    dft_h_flops = ((info.block_psfs[0] + info.blocks[0]) * 6 * dft_stage) if dft_h else 0.0
+    # block DFT (half spectra): U = 2 x 128^3 flop per 128 x 128 x 128 GEMM.
+    # H: one row transform per (block, PSF grid row) (1 U), per (block, PSF)
+    # the column transform (2 U), per block the inverse (2.5 U + 2 U).  H^T:
+    # per block the forward transform (3 U), per (block, PSF) the inverse
+    # (4.5 U).  The dense transforms are these forms' algorithm, so their GEMMs
+    # as scheduled count as their work.
+    U = 2.0 * 128 ** 3
+    dft_h_flops = (info.dft_h_rows + 2.0 * info.block_psfs[0] + 4.5 * info.blocks[0]) * U if dft_h else 0.0
+    dft_ht_flops = (3.0 * info.blocks[1] + 4.5 * info.block_psfs[1]) * U if dft_ht else 0.0
     if path == dv.DV_PATH_TENSOR:
         # algorithmic: 2 K^2 flop per output pixel per active PSF, at most 4
         # active PSFs (first-order interpolation); the tensor pipe also runs
@@ -712,13 +721,22 @@ def roofline(dv, w, plan, args, ktime, total_ms):
                 executed = n_in * (mma_work(0) + mma_work(1))
                 work_note = (f"{n_in} x ({info.mma_ksteps[0]} + {info.mma_ksteps[1]}) (block, PSF) "
                              f"k-steps per tap row x K x 16 x 2 x 128 x block rows")
-                if dft_h:
-                    flops = n_in * (dft_h_flops + 8.0 * w.K * w.K * x_px)
-                    executed = n_in * (dft_h_flops + mma_work(1))
-                    work_note = (f"H as the block DFT: ({info.block_psfs[0]} (block, PSF) pairs + "
-                                 f"{info.blocks[0]} blocks) x 6 x 2 x 128^3 flop of DFT GEMMs; "
-                                 f"H^T banded: {info.mma_ksteps[1]} (block, PSF) k-steps per tap "
-                                 f"row x K x 16 x 2 x 128 x block rows")
+                if dft_h or dft_ht:
+                    fH = dft_h_flops if dft_h else 8.0 * w.K * w.K * y_px
+                    fHt = dft_ht_flops if dft_ht else 8.0 * w.K * w.K * x_px
+                    flops = n_in * (fH + fHt)
+                    executed = n_in * ((dft_h_flops if dft_h else mma_work(0)) +
+                                       (dft_ht_flops if dft_ht else mma_work(1)))
+                    nH = (f"H as the block DFT: ({info.dft_h_rows} row transforms + 2 x "
+                          f"{info.block_psfs[0]} (block, PSF) pairs + 4.5 x {info.blocks[0]} "
+                          f"blocks) x 2 x 128^3 flop" if dft_h else
+                          f"H banded: {info.mma_ksteps[0]} (block, PSF) k-steps per tap row")
+                    nHt = (f"H^T as the block DFT: (3 x {info.blocks[1]} blocks + 4.5 x "
+                           f"{info.block_psfs[1]} (block, PSF) pairs) x 2 x 128^3 flop"
+                           if dft_ht else
+                           f"H^T banded: {info.mma_ksteps[1]} (block, PSF) k-steps per tap row "
+                           f"x K x 16 x 2 x 128 x block rows")
+                    work_note = f"{nH}; {nHt}"
         else:
             km, band = 8, 63 + w.K
             ks = (band + km - 1) // km
@@ -737,13 +755,15 @@ def roofline(dv, w, plan, args, ktime, total_ms):
             alg = (f"8 K^2 flop per y-pixel (H) and per x-pixel (H^T), 4 active PSFs, "
                    f"{n_in} x ({y_px} + {x_px}) pixels per local solve; executed MMA work "
                    f"{executed / 1e9:.1f} GFLOP per local solve ({work_note})")
-            if dft_h:
-                alg = (f"H: the block-DFT GEMMs as scheduled ({dft_h_flops / 1e9:.1f} GFLOP per "
-                       f"apply; 8 K^2 flop per y-pixel would be "
-                       f"{8.0 * w.K * w.K * y_px / 1e9:.1f}); H^T: 8 K^2 flop per x-pixel, 4 "
-                       f"active PSFs, {x_px} pixels; {n_in} x (H + H^T) per local solve; "
-                       f"executed MMA work {executed / 1e9:.1f} GFLOP per local solve "
-                       f"({work_note})")
+            if dft_h or dft_ht:
+                aH = (f"H: the block-DFT GEMMs as scheduled ({dft_h_flops / 1e9:.1f} GFLOP per "
+                      f"apply; 8 K^2 flop per y-pixel would be {8.0 * w.K * w.K * y_px / 1e9:.1f})"
+                      if dft_h else f"H: 8 K^2 flop per y-pixel, {y_px} pixels")
+                aHt = (f"H^T: the block-DFT GEMMs as scheduled ({dft_ht_flops / 1e9:.1f} GFLOP per "
+                       f"apply; 8 K^2 flop per x-pixel would be {8.0 * w.K * w.K * x_px / 1e9:.1f})"
+                       if dft_ht else f"H^T: 8 K^2 flop per x-pixel, 4 active PSFs, {x_px} pixels")
+                alg = (f"{aH}; {aHt}; {n_in} x (H + H^T) per local solve; executed MMA work "
+                       f"{executed / 1e9:.1f} GFLOP per local solve ({work_note})")
     elif path == dv.DV_PATH_FFT:
         # flops of the block-FFT operator as scheduled by the plan: 5 N log2 N
         # per S x S complex 2-D transform and 8 flop per spectral product; H runs
@@ -768,13 +788,25 @@ def roofline(dv, w, plan, args, ktime, total_ms):
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
                f"{px} pixels")
     achieved = flops / (ms_launch * 1e-3) / 1e12
-    kern = [kH, kHt][dom].split("<")[0]
-    traffic, kname = traffic_for(kern), names[dom]
+
+    def kernel_traffic(name):
+        # DRAM bytes of one launch of each kernel of `name` (the block-DFT
+        # kernels by their full template names, the others by family), summed
+        total = 0
+        for k in name.split(" + "):
+            t = traffic_for(k if k.startswith("dft") else k.split("<")[0])
+            if t is None:
+                return None
+            total += t
+        return total
+
+    traffic, kname = kernel_traffic([kH, kHt][dom]), names[dom]
     if grouped:
-        tH, tHt = traffic_for(kH.split("<")[0]), traffic_for(kHt.split("<")[0])
+        tH, tHt = kernel_traffic(kH), kernel_traffic(kHt)
         traffic = n_in * (tH + tHt) if tH is not None and tHt is not None else None
-        kname = (f"{kH} + {kHt} (local solve: {n_in} x {{H_i with residual, H_i^T + fused prox "
-                 f"step}} on {info.tile_groups} concurrent tile groups, timed as one graph)")
+        kname = (f"{kH} + {kHt} (local solve: {n_in} x {{H_i with residual, H_i^T + "
+                 f"{'prox step' if dft_ht else 'fused prox step'}}} on {info.tile_groups} "
+                 f"concurrent tile groups, timed as one graph)")
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic, "kernel": kname,
             "ms_per_unit": ms_launch, "peak_source": peak_src, "algorithmic": alg}

@@ -324,7 +324,9 @@ typedef struct dv_plan_info {
   double tune_ms_tensor_dft;
   /* 1 when H^T runs as the block DFT too (dv_problem.tensor_h) */
   int32_t tensor_ht_dft;
-  int32_t reserved_info;
+  /* block-DFT H: forward transforms along rows per tile-mode launch, one per
+   * (block, active PSF grid row) (0 without the block-DFT work tables) */
+  int32_t dft_h_rows;
   /* autotuner: one block-DFT H + one block-DFT H^T (0 if not timed) */
   double tune_ms_tensor_dft2;
 } dv_plan_info;

@@ -276,6 +276,7 @@ namespace dv {
 struct OpTables {
   int64_t psfs[2] = {0, 0};    // sum over H / H^T items of active PSFs
   int64_t pairs[2] = {0, 0};   // sum of ceil(active PSFs / 2)
+  int64_t rows[2] = {0, 0};    // sum over H / H^T items of active PSF grid rows
   WorkItem* H = nullptr;
   WorkItem* Ht = nullptr;
   WorkItem* Hg = nullptr;

@@ -823,6 +823,7 @@ static dv_status build_plan(const dv_problem* prob, cudaStream_t s, dv_plan* P) 
         const int64_t np = (int64_t)(it.a_hi - it.a_lo + 1) * (it.b_hi - it.b_lo + 1);
         tb.psfs[k2] += np;
         tb.pairs[k2] += (np + 1) / 2;
+        if (np > 0) tb.rows[k2] += it.a_hi - it.a_lo + 1;
       }
     };
     // BF16 tensor path: per-item k-step ranges of the PSF grid columns
@@ -1075,6 +1076,7 @@ extern "C" dv_status dv_plan_get_info(const dv_plan* P, dv_plan_info* info) {
   info->tile_groups = (P->ngrp > 1 && P->path == DV_PATH_TENSOR) ? P->ngrp : 1;
   info->tensor_h_dft = P->path == DV_PATH_TENSOR && P->dft_H ? 1 : 0;
   info->tensor_ht_dft = P->path == DV_PATH_TENSOR && P->dft_Ht ? 1 : 0;
+  info->dft_h_rows = (int32_t)std::min<int64_t>(P->tab[1].rows[0], INT32_MAX);
   info->tune_ms_tensor_dft = P->tune_ms_dft;
   info->tune_ms_tensor_dft2 = P->tune_ms_dft2;
   if (info->tensor_h_dft) {

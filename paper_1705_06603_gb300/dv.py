@@ -77,7 +77,7 @@ class dv_plan_info(C.Structure):
                 ("tune_ms_tensor", C.c_double), ("mma_ksteps", C.c_int64 * 2),
                 ("tile_groups", C.c_int32), ("tensor_h_dft", C.c_int32),
                 ("tune_ms_tensor_dft", C.c_double), ("tensor_ht_dft", C.c_int32),
-                ("reserved_info", C.c_int32), ("tune_ms_tensor_dft2", C.c_double)]
+                ("dft_h_rows", C.c_int32), ("tune_ms_tensor_dft2", C.c_double)]
 
 
 _vp = C.c_void_p
