@@ -1,27 +1,36 @@
-// Block-DFT form of the shift-variant operator H of Sec. II-B on the tensor
-// cores (tcgen05, FP16 operands, FP32 accumulation in tensor memory).
+// Block-DFT forms of the shift-variant operator H of Sec. II-B and of its
+// adjoint on the tensor cores (tcgen05, FP16 operands, FP32 accumulation in
+// tensor memory), and the Local-Solver step that follows the adjoint.
 //
-// Overlap-save on 128 x 128 blocks: a work item is a b x b block of H's output
-// (b = 129 - K) and the 128 x 128 window of x below it.  For every PSF
+// Overlap-save on 128 x 128 blocks.  H: a work item is a b x b block of the
+// output (b = 129 - K) and the 128 x 128 window of x below it.  For every PSF
 // p = (a, b) active on the block (Eq. (2): first-order interpolation, weights
 // w_p(r, c) = wr_a(r) wc_b(c)), X_p = w_p . x is transformed, multiplied by
 // the PSF's spectrum, and the products are summed; one inverse transform of the
 // sum, cropped to rows and columns K - 1 .. 127, is the block of H x (the
 // valid part of a circular convolution of size 128 is the non-circulant
-// local blur).
+// local blur).  H^T: a work item is a b x b block of x and the 128 x 128
+// window of r from K - 1 rows and columns above and left of it (zero outside
+// the tile); the window is transformed once, multiplied by each PSF's
+// conjugate spectrum (correlation), transformed back, and the PSF's weights
+// applied to the valid rows and columns 0 .. b - 1.
 //
 // The input is real, so only half of every spectrum is formed (k = 0 .. 64
 // along the first transformed axis; the other half is its conjugate mirror).
 // With F[k][n] = exp(-2 pi i k n / 128) = Fr + i Fi, each stage is a GEMM on
 // the tensor cores, ordered so that every tensor-memory lane (a thread) owns a
 // row of the next stage's operand:
-//   F1 (per row weight a)  Y'[j][c] = sum_r A1[j][r] wr_a(r) x[r][c]
-//        A1 rows 2k = Fr(k), 2k + 1 = Fi(k) (k < 64), row 1 = Fr(64): the
-//        packed real and imaginary parts of Y(k) = F x along r (Y(0), Y(64)
-//        are real, Y(128 - k) = conj Y(k))
-//   F2 (per PSF)  P = Fr (wc_b Y')^T, Q = Fi (wc_b Y')^T     (M = kc, N = j)
+//   F1  Y'[j][c] = sum_r A1[j][r] v[r][c]   (H: v = wr_a x, once per PSF grid
+//        row a; H^T: v = r, once per block).  A1 rows 2k = Fr(k), 2k + 1 =
+//        Fi(k) (k < 64), row 1 = Fr(64): the packed real and imaginary parts
+//        of Y(k) = F v along r (Y(0), Y(64) are real, Y(128 - k) = conj Y(k))
+//   F2  P = Fr (wc_b Y')^T, Q = Fi (wc_b Y')^T   (M = kc, N = j; H^T: wc = 1)
 //        Z(k)[kc] = P[2k] - Q[2k+1] + i (Q[2k] + P[2k+1])   (k = 0, 64 apart)
-//   product  S(k)[kc] += Z(k)[kc] Hh_p(k, kc)               (FP32, tensor memory)
+//   H: product  S(k)[kc] += Z(k)[kc] Hh_p(k, kc) over the PSFs (FP32, tensor
+//        memory), then one inverse per block; H^T: per PSF T = Z conj(Hh_p)
+//        and one inverse, the row weights wr_a applied to U (rows r) and
+//        summed over a inside I2, the column weight wc_b to I2's result as it
+//        is added to H^T r (tensor memory)
 //   I1  U[r][kc] = sum_k alpha_k exp(+2 pi i r k / 128) S(k)[kc]   (alpha = 1 at
 //        k = 0, 64, else 2: the mirror half folded in), as one N = 256 GEMM
 //        [Ur | Ui] = Fr [aSr | aSi] + Fi [aSi | -aSr] over k = 0 .. 79
@@ -29,18 +38,21 @@
 // Operands are K-major, no swizzle: a matrix of R rows and K columns is stored
 // as K / 8 panels of R 16-byte rows (panel stride padded by 16 bytes), so a
 // 16-wide k-step is two consecutive panels (LBO = panel stride, SBO = 128).
-// Scaling keeps the FP16 values in range: the spectra carry 1 / 128 and the
-// staged U another 1 / 128 (the inverse DFT's 1 / 128^2).
+// Scaling keeps the FP16 values in range: each window is staged times 2^-e
+// (its largest magnitude f 2^e, f in [0.5, 1); the output times 2^e, both
+// exact), the spectra carry 1 / 128 and the staged U (H^T: Z) another 1 / 128
+// (the inverse DFT's 1 / 128^2).
 //
 // Roles: 8 staging warps (two per tensor-memory lane quarter, one per half of
 // a stage's columns) stage operands, take the products and write the output;
-// warp 8 issues the MMAs; warp 9 claims work items, loads the x window (FP32
-// -> FP16, transposed) and the interpolation tables, and prefetches the next
-// item's data into L2.  A stage's operand is written in 16-wide K chunks, each
-// with its own mbarrier, and the MMA warp issues a chunk's k-steps as soon as
-// it is complete, so the MMAs trail the staging.  The grid is persistent (one
-// CTA per SM, items from an atomic counter, heaviest first).  Every wait is
-// bounded; the staging warps take every branch after a wait together.
+// warp 8 issues the MMAs; warps 9 .. 11 claim work items, load the window
+// (FP32 -> FP16, transposed) and the interpolation tables, and prefetch the
+// next item's rows into L2.  A stage's operand is released to the MMA warp in
+// two halves (one async-proxy fence each, one mbarrier per 16-wide K chunk),
+// so the MMAs of the first half run while the second is staged.  The grid is
+// persistent (one CTA per SM, items from an atomic counter, heaviest first).
+// Every wait is bounded; the staging warps take every branch after a wait
+// together, and so do the loader warps.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
