@@ -716,6 +716,13 @@ def roofline(dv, w, plan, args, ktime, total_ms):
             executed = mma_work(dom)
             work_note = (f"{info.mma_ksteps[dom]} (block, PSF) k-steps per tap row x K x 16 x "
                          f"2 x 128 x block rows")
+            if (dft_h and dom == 0) or (dft_ht and dom == 1):
+                # one block-DFT launch: its GEMMs as scheduled are its work
+                flops = executed = dft_h_flops if dom == 0 else dft_ht_flops
+                work_note = ("block-DFT GEMMs as scheduled, U = 2 x 128^3: " +
+                             (f"{info.dft_h_rows} U + 2 x {info.block_psfs[0]} U + 4.5 x "
+                              f"{info.blocks[0]} U" if dom == 0 else
+                              f"3 x {info.blocks[1]} U + 4.5 x {info.block_psfs[1]} U"))
             if grouped:
                 flops = n_in * 8.0 * w.K * w.K * (y_px + x_px)
                 executed = n_in * (mma_work(0) + mma_work(1))
@@ -751,6 +758,10 @@ def roofline(dv, w, plan, args, ktime, total_ms):
         alg = (f"8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel per launch (4 active PSFs), "
                f"{px} pixels; executed MMA work {executed / 1e9:.1f} GFLOP per launch "
                f"({work_note})")
+        if not grouped and ((dft_h and dom == 0) or (dft_ht and dom == 1)):
+            alg = (f"the block-DFT GEMMs as scheduled, {executed / 1e9:.1f} GFLOP per launch "
+                   f"({work_note}); 8 K^2 flop per {'y' if dom == 0 else 'x'}-pixel would be "
+                   f"{8.0 * w.K * w.K * px / 1e9:.1f}")
         if grouped:
             alg = (f"8 K^2 flop per y-pixel (H) and per x-pixel (H^T), 4 active PSFs, "
                    f"{n_in} x ({y_px} + {x_px}) pixels per local solve; executed MMA work "
